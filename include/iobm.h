@@ -1,0 +1,217 @@
+/*
+ * iobm.h -- C ABI of the GB300 IOBM transport solver.
+ *
+ * The library solves, for every incident electrode channel and energy, the
+ * complex-symmetric real-space finite-difference equations of the improved
+ * overbridging boundary-matching (IOBM) method,
+ *
+ *     [E - H_T - H~] Psi = b                                   (Eq. 7)
+ *
+ * on a transition region of N_x x N_y x (N_z+2) grid points (Eqs. 1-4),
+ * laterally periodic, between two identical semi-infinite jellium electrodes
+ * whose self-energy is diagonal in the lateral Fourier basis (Eqs. 8, 18-2,
+ * 19) and is applied through lateral 2D FFTs.  The solver is a
+ * preconditioned conjugate-orthogonal CG (the "CG method for a
+ * non-Hermitian matrix" of Sec. II, valid since the matrix equals its
+ * transpose) with the truncated-Laplacian-Green preconditioner of Eq. 10.
+ * The solved waves are projected onto the electrode channels (Eq. 6) to
+ * give transmission, reflection and the Landauer conductance (Sec. III).
+ *
+ * Units: Hartree atomic units (energies in Ha, lengths in bohr); the
+ * electrode potential is the zero of energy; the lateral Bloch vector is 0.
+ * Conductance is returned in units of G_0 = 2 e^2 / h.
+ *
+ * Layouts: grid functions are [z][y][x] with x fastest (z = plane index
+ * 0 .. N_z+1).  Complex vectors are interleaved (re, im) pairs of double
+ * (IOBM_FP64) or float (IOBM_FP32).  A batch of vectors is [rhs][z][y][x].
+ *
+ * Ownership: the caller owns every input buffer; the library copies what it
+ * keeps during iobm_create.  The handle owns its persistent device tables
+ * (allocated with cudaMalloc in iobm_create, freed in iobm_destroy).  Solve
+ * workspace is caller-provided device memory (iobm_workspace_size /
+ * iobm_set_workspace); when none is set the handle allocates and owns it.
+ * Every device operation is ordered on the CUDA stream given at create.
+ *
+ * Errors: every int-returning call returns IOBM_OK (0) or one of the
+ * IOBM_E_* codes; iobm_last_error(handle) then holds a one-line message.
+ * A right-hand side that does not converge does not fail the call: its
+ * status is reported per RHS in iobm_report.
+ */
+#ifndef IOBM_H
+#define IOBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define IOBM_OK               0
+#define IOBM_E_ARG            1  /* invalid argument (sizes, pointers, options)          */
+#define IOBM_E_THRESHOLD      2  /* E within 1e-9 Ha of a channel threshold (v -> 0)      */
+#define IOBM_E_PROJ_BOUNDARY  3  /* a projector touches the N_f outermost planes          */
+#define IOBM_E_NOCONV         4  /* per-RHS: iteration limit reached                      */
+#define IOBM_E_BREAKDOWN      5  /* per-RHS: COCG breakdown (r^T z or p^T A p vanished)   */
+#define IOBM_E_TIMEOUT        6  /* a bounded device wait gave up                         */
+#define IOBM_E_CUDA           7  /* CUDA runtime error                                    */
+#define IOBM_E_STATE          8  /* call out of order (e.g. transmission before solve)    */
+#define IOBM_E_UNSUPPORTED    9  /* size outside what this build supports (see message)   */
+
+/* precision of the solver */
+#define IOBM_FP64   0  /* plain FP64: vectors, stencil, Krylov recurrences in FP64     */
+#define IOBM_MIXED  1  /* complex FP32 Krylov inner iterations, FP64 residual
+                          replacement (iterative refinement) and FP64 projection   */
+
+/* element type of vectors passed to iobm_apply / iobm_apply_precond */
+#define IOBM_ELEM_C64   0  /* complex double, interleaved */
+#define IOBM_ELEM_C32   1  /* complex float, interleaved  */
+
+typedef struct iobm_handle iobm_handle;
+
+/* Transition-region grid (Sec. II).  nz counts the planes z_0 .. z_{N_z+1}
+ * (nz = N_z + 2).  nf is the FD half-width N_f of Eq. 1 (1 .. 4); the
+ * self-energy then acts on the nf outermost planes at each end.  x and y
+ * are periodic with period nx*hx and ny*hy.  nx and ny may only contain
+ * prime factors <= 13 (lateral FFT radices). */
+typedef struct {
+    int nx, ny, nz;
+    double hx, hy, hz;
+    int nf;
+} iobm_grid;
+
+/* Kleinman-Bylander projectors in CSR form (norm-conserving pseudopotential
+ * of Sec. III): projector p has support idx[row_ptr[p] .. row_ptr[p+1]) with
+ * values val[...] (linear grid index (z*ny + y)*nx + x, each index once per
+ * projector) and coupling E_p = coupling[p] in Ha.  The nonlocal operator is
+ * sum_p E_p |p><p| with <p|psi> = hx*hy*hz * sum_r p(r) psi(r).  nproj may
+ * be 0 (all pointers may then be NULL). */
+typedef struct {
+    int nproj;
+    const int64_t* row_ptr;
+    const int32_t* idx;
+    const double* val;
+    const double* coupling;
+} iobm_projectors;
+
+/* Solver options.  alpha: preconditioner parameter of Eq. 10 (C_0 = 1,
+ * C_1 = exp(-alpha)); use_precond = 0 disables it.  tol: stop when
+ * ||b - A psi||_2 / ||b||_2 <= tol, the residual evaluated in FP64.
+ * max_iter: Krylov iteration limit per RHS.  refine_delta: in IOBM_MIXED the
+ * FP64 residual replaces the FP32 recurrence residual whenever the latter has
+ * fallen by this factor since the last replacement (0 < delta < 1).
+ * chunk: iterations per captured CUDA graph between convergence checks. */
+typedef struct {
+    double alpha;
+    int use_precond;
+    double tol;
+    int max_iter;
+    int precision;
+    double refine_delta;
+    int chunk;
+} iobm_options;
+
+/* Per right-hand-side report, in solve order (energy-major, then incident
+ * channel in the canonical open-channel order). */
+typedef struct {
+    int energy_index;
+    int channel;        /* index into the open channels of that energy      */
+    int side;           /* 0: incident from the left, 1: from the right      */
+    int status;         /* IOBM_OK, IOBM_E_NOCONV or IOBM_E_BREAKDOWN         */
+    int iterations;     /* Krylov iterations                                  */
+    int replacements;   /* FP64 residual replacements                         */
+    double residual;    /* final ||b - A psi|| / ||b|| in FP64                */
+} iobm_report;
+
+/* Fill opts with the defaults: alpha 1.8, use_precond 1, tol 1e-8,
+ * max_iter 20000, precision IOBM_MIXED, refine_delta 0.1, chunk 32. */
+void iobm_default_options(iobm_options* opts);
+
+/* Create a solver for one junction.  V_loc: host [nz][ny][nx] local
+ * potential (Ha), copied.  proj: KB projectors (host arrays, copied; NULL
+ * for none).  rs: Wigner-Seitz radius of the jellium electrodes (bohr); it
+ * only sets iobm_fermi_energy.  opts: NULL for defaults.  cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).  Errors: IOBM_E_ARG for bad
+ * sizes / non-finite V, IOBM_E_PROJ_BOUNDARY if a projector reaches the nf
+ * outermost planes, IOBM_E_UNSUPPORTED for lateral sizes whose FFT does not
+ * fit this build, IOBM_E_CUDA. */
+int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projectors* proj,
+                double rs, const iobm_options* opts, void* cuda_stream, iobm_handle** out);
+
+void iobm_destroy(iobm_handle* h);
+
+const char* iobm_status_string(int status);
+const char* iobm_last_error(const iobm_handle* h);
+
+/* Jellium Fermi energy (9 pi / 4)^(2/3) / (2 rs^2) of the handle's electrodes. */
+double iobm_fermi_energy(const iobm_handle* h);
+
+/* Number of open (propagating, right-going) electrode channels at energy E,
+ * and optionally their lateral indices (nu_x, nu_y) pairs and group
+ * velocities in the canonical order (nu_y major, then nu_x, each from
+ * -N/2 upward).  nu and vel may be NULL; otherwise they hold room for
+ * max_out channels.  Eqs. 8.5-9 generalised to N_f (Appendix). */
+int iobm_open_channels(iobm_handle* h, double E, int* n_open, int max_out, int* nu, double* vel);
+
+/* Workspace: bytes of device memory a solve of nrhs right-hand sides needs
+ * at the handle's precision, and attach caller memory (256-byte aligned,
+ * kept by the handle until replaced or destroyed; the caller must keep it
+ * alive).  Passing NULL detaches it. */
+int iobm_workspace_size(iobm_handle* h, int nrhs, size_t* bytes);
+int iobm_set_workspace(iobm_handle* h, void* dev_ptr, size_t bytes);
+
+/* Solve Eq. 7 for every energy E[0..nE) and incident channel.  channels:
+ * NULL = every open channel of each energy; otherwise nch indices into each
+ * energy's open-channel list (indices beyond that list are skipped).
+ * side: 0 left-incident (Eq. 7 as printed), 1 right-incident.  All RHS are
+ * solved together in one batched launch sequence.  The solution vectors stay
+ * in the workspace for iobm_transmission / iobm_solution.  Returns IOBM_OK
+ * when the batch ran (check iobm_report for per-RHS convergence). */
+int iobm_solve(iobm_handle* h, const double* E, int nE, const int* channels, int nch, int side);
+
+/* Number of RHS of the last solve. */
+int iobm_num_rhs(const iobm_handle* h);
+
+/* Transmission/reflection of the last solve (Eq. 6, Landauer-Buttiker of
+ * Sec. III).  T, R: host [rhs][max_open] with T[rhs][o] = |t_o|^2 v_o / v_in
+ * for out-channel o of that RHS's energy (zero past its n_open); pass NULL to
+ * skip.  G: host [nE], conductance in G_0 summed over the solved incident
+ * channels of each energy.  nopen: host [nE] (may be NULL).  reports: host
+ * [nrhs] (may be NULL).  max_open: row stride of T and R. */
+int iobm_transmission(iobm_handle* h, double* T, double* R, int max_open, double* G,
+                      int* nopen, iobm_report* reports);
+
+/* Copy the FP64 solution of RHS `rhs` of the last solve ([z][y][x] complex
+ * double) to dst (host or device). */
+int iobm_solution(iobm_handle* h, int rhs, void* dst, int dst_is_device);
+
+/* dG/dV(r) (G_0 per Ha) at energy E for left-incident waves: solves the
+ * n_open forward waves and the n_open adjoint waves A lambda_o = w_o (same
+ * operator, A = A^T) in one batch, then accumulates
+ * dG/dV(r) = sum_{o,i} 2 (v_o/v_i) Re[conj(t_oi) lambda_o(r) psi_i(r)] in FP64.
+ * dGdV: [nz][ny][nx] double, host or device.  G_out (may be NULL): the
+ * conductance of the same solve. */
+int iobm_grad_V(iobm_handle* h, double E, double* dGdV, int dst_is_device, double* G_out);
+
+/* y = (E - H_T - H~) x for nrhs vectors (Eqs. 1-4, 7-2, 8 via FFT),
+ * x and y device buffers [nrhs][nz][ny][nx] of element type `elem`
+ * (IOBM_ELEM_C64 computes in FP64, IOBM_ELEM_C32 in FP32).  Uses the
+ * workspace for the projector scratch. */
+int iobm_apply(iobm_handle* h, double E, int elem, const void* x, void* y, int nrhs);
+
+/* y = P x with the preconditioner of Eq. 10 (six face neighbours, C_0 = 1,
+ * C_1 = exp(-alpha), zero beyond the end planes). */
+int iobm_apply_precond(iobm_handle* h, int elem, const void* x, void* y, int nrhs);
+
+/* Device-side time (ms) of the last iobm_solve's iteration phase, measured
+ * with CUDA events on the handle's stream, and the number of kernel launches
+ * it issued. */
+int iobm_last_solve_stats(const iobm_handle* h, double* ms, long long* launches,
+                          long long* iterations_total);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IOBM_H */
