@@ -135,7 +135,8 @@ void iobm_default_options(iobm_options* opts);
  * cudaStream_t (NULL = legacy default stream).  Errors: IOBM_E_ARG for bad
  * sizes / non-finite V, IOBM_E_PROJ_BOUNDARY if a projector reaches the nf
  * outermost planes, IOBM_E_UNSUPPORTED for lateral sizes whose FFT does not
- * fit this build, IOBM_E_CUDA. */
+ * fit this build, IOBM_E_CUDA.  On an error *out may still receive a handle
+ * (so that iobm_last_error can explain it); pass it to iobm_destroy. */
 int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projectors* proj,
                 double rs, const iobm_options* opts, void* cuda_stream, iobm_handle** out);
 
@@ -203,6 +204,22 @@ int iobm_apply(iobm_handle* h, double E, int elem, const void* x, void* y, int n
 /* y = P x with the preconditioner of Eq. 10 (six face neighbours, C_0 = 1,
  * C_1 = exp(-alpha), zero beyond the end planes). */
 int iobm_apply_precond(iobm_handle* h, int elem, const void* x, void* y, int nrhs);
+
+/* Replace the local potential V_loc ([nz][ny][nx], Ha; host or device
+ * memory) of an existing handle, e.g. between the forward passes of a
+ * gradient-based optimisation.  Eqs. 2-4: V enters H_T on every plane. */
+int iobm_set_potential(iobm_handle* h, const double* V_loc, int src_is_device);
+
+/* Host-only set-up (needs no GPU and no handle): the electrode channel data
+ * at energy E for a lateral grid, as used by the solver.  n_open: number of
+ * open channels.  nu [max_out][2], vel [max_out], lam [max_out][2] (the
+ * propagating right-going root, re/im), btilde [max_out][nf][2] (incident
+ * source coefficients per depth, Eq. 7 generalised to N_f planes), mrow
+ * [max_out][nf][2] (t = sum_d mrow[d] psi~(depth d)), sigma
+ * [ny][nx][nf][nf][2] (Sigma~ per lateral FFT bin, Eqs. 17, 18-2); any of
+ * them may be NULL.  Returns IOBM_E_THRESHOLD near a channel edge. */
+int iobm_channels_host(const iobm_grid* grid, double E, int* n_open, int max_out, int* nu,
+                       double* vel, double* lam, double* btilde, double* mrow, double* sigma);
 
 /* Device-side time (ms) of the last iobm_solve's iteration phase, measured
  * with CUDA events on the handle's stream, and the number of kernel launches

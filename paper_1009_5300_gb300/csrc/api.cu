@@ -1,0 +1,1135 @@
+// C ABI of the IOBM solver: handle management, the batched COCG driver
+// (plain FP64 and mixed FP32/FP64 with FP64 residual replacement), channel
+// projection, conductance and the adjoint gradient.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <complex>
+#include <type_traits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/iobm.h"
+#include "iobm_internal.cuh"
+#include "setup.h"
+
+namespace iobm {
+cudaError_t sigma_prepare();
+}
+
+using namespace iobm;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+template <typename T>
+cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
+    cudaError_t e = b.ensure(sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (e != cudaSuccess) return e;
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
+}
+
+constexpr int kZChunk = 32;
+
+}  // namespace
+
+struct iobm_handle {
+    iobm_grid g{};
+    int nf = 4;
+    double rs = 0.0;
+    iobm_options opt{};
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;      // private stream (capturable)
+    cudaEvent_t ev_sync = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    std::string err;
+    long long npts = 0;
+    int nxy = 0;
+    std::vector<double> w;              // FD weights
+
+    // persistent device tables
+    DevBuf V32, V64;
+    DevBuf twx32, twy32, twx64, twy64, phx, phy;
+    FftAxis ax{}, ay{};
+    ProjTables pt;
+    DevBuf pptr, pidx, pval32, pval64, pcoup, uidx, uptr, uproj, uval32, uval64;
+
+    // per-solve tables (handle owned)
+    DevBuf sig32, sig64, ediag, rhs_energy, descs, open_ptr, open_bins, proj_out;
+    DevBuf apply_sig32, apply_sig64, apply_ediag;
+    std::vector<ModeTables> energies;
+    std::vector<RhsDesc> hdesc;
+    std::vector<int> hrhs_energy, hrhs_chan;
+    int side = 0;
+    int nrhs = 0;
+    int max_open = 0;
+
+    // workspace
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    DevBuf ws_owned;
+    int ws_nrhs = 0;
+    int ws_prec = -1;
+
+    // layout of the current workspace
+    int slot_stride = 0;
+    int ns_stencil = 0;
+    RhsState* st = nullptr;
+    double2* mu_part = nullptr;
+    double2* rho_part = nullptr;
+    double* rr_part = nullptr;
+    void* vx = nullptr;        // iterate (FP32 in mixed, FP64 in plain)
+    void* vr = nullptr;
+    void* vp[2] = {nullptr, nullptr};
+    void* vq = nullptr;
+    void* vz = nullptr;
+    double2* x64 = nullptr;    // FP64 solution (mixed: separate; plain: == vx)
+    double2* y64 = nullptr;
+    bool solved = false;
+    std::vector<RhsState> hstate;
+
+    // stats
+    double last_ms = 0.0;
+    long long last_launches = 0;
+    long long last_iters = 0;
+};
+
+namespace {
+
+int fail(iobm_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(iobm_handle* h, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, IOBM_E_CUDA, m);
+}
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, #call); \
+    } while (0)
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+int slots_for(const iobm_handle* h) {
+    const int ns = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk);
+    return std::max(ns + 2 * h->nf + 1, 64);
+}
+
+size_t workspace_bytes(const iobm_handle* h, int nrhs, int prec) {
+    const size_t n = (size_t)nrhs * h->npts;
+    const int S = slots_for(h);
+    size_t b = 0;
+    b += align256(sizeof(RhsState) * nrhs);
+    b += 2 * align256(sizeof(double2) * nrhs * S);
+    b += align256(sizeof(double) * nrhs * S);
+    const size_t ce = (prec == IOBM_MIXED) ? sizeof(float2) : sizeof(double2);
+    b += 6 * align256(ce * n);                      // x r p0 p1 q z
+    b += align256(sizeof(double2) * n);             // y64
+    if (prec == IOBM_MIXED) b += align256(sizeof(double2) * n);   // x64
+    return b;
+}
+
+int bind_workspace(iobm_handle* h, int nrhs) {
+    const int prec = h->opt.precision;
+    const size_t need = workspace_bytes(h, nrhs, prec);
+    unsigned char* base = nullptr;
+    if (h->ws && h->ws_bytes >= need) {
+        base = reinterpret_cast<unsigned char*>(h->ws);
+    } else {
+        if (h->ws)
+            return fail(h, IOBM_E_ARG, "attached workspace is smaller than iobm_workspace_size");
+        cudaError_t e = h->ws_owned.ensure(need);
+        if (e != cudaSuccess) return cuda_fail(h, e, "workspace allocation");
+        base = h->ws_owned.as<unsigned char>();
+    }
+    const size_t n = (size_t)nrhs * h->npts;
+    const int S = slots_for(h);
+    h->slot_stride = S;
+    h->ns_stencil = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        void* p = base + off;
+        off += align256(bytes);
+        return p;
+    };
+    h->st = (RhsState*)take(sizeof(RhsState) * nrhs);
+    h->mu_part = (double2*)take(sizeof(double2) * nrhs * S);
+    h->rho_part = (double2*)take(sizeof(double2) * nrhs * S);
+    h->rr_part = (double*)take(sizeof(double) * nrhs * S);
+    const size_t ce = (prec == IOBM_MIXED) ? sizeof(float2) : sizeof(double2);
+    h->vx = take(ce * n);
+    h->vr = take(ce * n);
+    h->vp[0] = take(ce * n);
+    h->vp[1] = take(ce * n);
+    h->vq = take(ce * n);
+    h->vz = take(ce * n);
+    h->y64 = (double2*)take(sizeof(double2) * n);
+    h->x64 = (prec == IOBM_MIXED) ? (double2*)take(sizeof(double2) * n) : (double2*)h->vx;
+    h->ws_nrhs = nrhs;
+    h->ws_prec = prec;
+    return IOBM_OK;
+}
+
+// ---- argument blocks ---------------------------------------------------------
+
+template <typename T>
+StencilArgs<T> op_args(const iobm_handle* h) {
+    StencilArgs<T> a{};
+    a.nx = h->g.nx;
+    a.ny = h->g.ny;
+    a.nz = h->g.nz;
+    a.nf = h->nf;
+    const double ihx = 1.0 / (h->g.hx * h->g.hx), ihy = 1.0 / (h->g.hy * h->g.hy),
+                 ihz = 1.0 / (h->g.hz * h->g.hz);
+    for (int n = 1; n <= h->nf; ++n) {
+        a.cx[n] = (T)(0.5 * h->w[n] * ihx);
+        a.cy[n] = (T)(0.5 * h->w[n] * ihy);
+        a.cz[n] = (T)(0.5 * h->w[n] * ihz);
+    }
+    a.c0 = (T)(0.5 * h->w[0] * (ihx + ihy + ihz));
+    a.vsign = (T)(-1);
+    a.V = std::is_same<T, float>::value ? (const T*)h->V32.p : (const T*)h->V64.p;
+    a.npts = h->npts;
+    a.zchunk = kZChunk;
+    a.mask = M_ALL;
+    return a;
+}
+
+template <typename T>
+StencilArgs<T> precond_args(const iobm_handle* h) {
+    StencilArgs<T> a{};
+    a.nx = h->g.nx;
+    a.ny = h->g.ny;
+    a.nz = h->g.nz;
+    a.nf = 1;
+    const double c1 = h->opt.use_precond ? std::exp(-h->opt.alpha) : 0.0;
+    a.cx[1] = a.cy[1] = a.cz[1] = (T)c1;
+    a.c0 = (T)1;
+    a.vsign = (T)0;
+    a.V = nullptr;
+    a.npts = h->npts;
+    a.zchunk = kZChunk;
+    a.mask = M_ALL;
+    return a;
+}
+
+template <typename T>
+SigmaArgs<T> sigma_args(const iobm_handle* h, const void* sig) {
+    SigmaArgs<T> a{};
+    a.nx = h->g.nx;
+    a.ny = h->g.ny;
+    a.nz = h->g.nz;
+    a.nf = h->nf;
+    a.ax = h->ax;
+    a.ay = h->ay;
+    a.sigma = (const typename Cplx<T>::type*)sig;
+    if (std::is_same<T, float>::value) {
+        a.twx = (const typename Cplx<T>::type*)h->twx32.p;
+        a.twy = (const typename Cplx<T>::type*)h->twy32.p;
+    } else {
+        a.twx = (const typename Cplx<T>::type*)h->twx64.p;
+        a.twy = (const typename Cplx<T>::type*)h->twy64.p;
+    }
+    a.npts = h->npts;
+    a.mask = M_ALL;
+    return a;
+}
+
+template <typename T>
+KbArgs<T> kb_args(const iobm_handle* h) {
+    KbArgs<T> a{};
+    a.nproj = h->pt.nproj;
+    a.pptr = h->pptr.as<int>();
+    a.pidx = h->pidx.as<int>();
+    a.pval = std::is_same<T, float>::value ? (const T*)h->pval32.p : (const T*)h->pval64.p;
+    a.coupling = h->pcoup.as<double>();
+    a.dvol = h->g.hx * h->g.hy * h->g.hz;
+    a.nunion = (int)h->pt.uidx.size();
+    a.uidx = h->uidx.as<int>();
+    a.uptr = h->uptr.as<int>();
+    a.uproj = h->uproj.as<int>();
+    a.uval = std::is_same<T, float>::value ? (const T*)h->uval32.p : (const T*)h->uval64.p;
+    a.npts = h->npts;
+    a.mask = M_ALL;
+    return a;
+}
+
+// y = A x (FP64 or FP32) for the RHS selected by (state, mask); energies per RHS.
+template <typename T>
+int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void* sig,
+                   const double* ediag, const int* rhs_energy, const RhsState* st, int mask,
+                   long long& launches) {
+    using C = typename Cplx<T>::type;
+    StencilArgs<T> a = op_args<T>(h);
+    a.x = (const C*)x;
+    a.y = (C*)y;
+    a.ediag = ediag;
+    a.rhs_energy = rhs_energy;
+    a.state = st;
+    a.mask = mask;
+    CK(launch_stencil<T>(a, nrhs, h->stream));
+    SigmaArgs<T> s = sigma_args<T>(h, sig);
+    s.x = (const C*)x;
+    s.y = (C*)y;
+    s.rhs_energy = rhs_energy;
+    s.state = st;
+    s.mask = mask;
+    CK(launch_sigma<T>(s, nrhs, h->stream));
+    launches += 2;
+    if (h->pt.nproj > 0) {
+        KbArgs<T> k = kb_args<T>(h);
+        k.x = (const C*)x;
+        k.y = (C*)y;
+        k.state = st;
+        k.mask = mask;
+        CK(launch_kb<T>(k, nrhs, h->stream));
+        launches += 1;
+    }
+    return IOBM_OK;
+}
+
+// z = P r with rho = r^T z and rr = |r|^2 partials, for RHS in mask.
+template <typename T>
+int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) {
+    using C = typename Cplx<T>::type;
+    StencilArgs<T> a = precond_args<T>(h);
+    a.x = (const C*)h->vr;
+    a.y = (C*)h->vz;
+    a.state = h->st;
+    a.mask = mask;
+    a.dot_mode = 1;
+    a.dot_part = h->rho_part;
+    a.nrm_part = h->rr_part;
+    a.slot_stride = h->slot_stride;
+    a.slot_base = 0;
+    CK(launch_stencil<T>(a, nrhs, h->stream));
+    launches += 1;
+    return IOBM_OK;
+}
+
+// One COCG iteration for every ACTIVE RHS; reads p[cur], writes p[1-cur].
+template <typename T>
+int cocg_iteration(iobm_handle* h, int nrhs, int cur, bool mixed, long long& launches) {
+    using C = typename Cplx<T>::type;
+    const double tol2 = h->opt.tol * h->opt.tol;
+    const double delta2 = h->opt.refine_delta * h->opt.refine_delta;
+    const int ns = h->ns_stencil;
+    CK(launch_beta(h->st, h->rho_part, h->rr_part, ns, h->slot_stride, nrhs, h->opt.max_iter, tol2,
+                   delta2, mixed ? 1 : 0, h->stream));
+    const void* sig = std::is_same<T, float>::value ? h->sig32.p : h->sig64.p;
+    StencilArgs<T> a = op_args<T>(h);
+    a.x = (const C*)h->vz;
+    a.pold = (const C*)h->vp[cur];
+    a.pout = (C*)h->vp[1 - cur];
+    a.y = (C*)h->vq;
+    a.fused_p = 1;
+    a.ediag = h->ediag.as<double>();
+    a.rhs_energy = h->rhs_energy.as<int>();
+    a.state = h->st;
+    a.mask = M_ACTIVE;
+    a.dot_mode = 1;
+    a.dot_part = h->mu_part;
+    a.nrm_part = nullptr;
+    a.slot_stride = h->slot_stride;
+    a.slot_base = 0;
+    CK(launch_stencil<T>(a, nrhs, h->stream));
+    SigmaArgs<T> s = sigma_args<T>(h, sig);
+    s.x = (const C*)h->vp[1 - cur];
+    s.y = (C*)h->vq;
+    s.rhs_energy = h->rhs_energy.as<int>();
+    s.state = h->st;
+    s.mask = M_ACTIVE;
+    s.dot_part = h->mu_part;
+    s.slot_stride = h->slot_stride;
+    s.slot_base = ns;
+    CK(launch_sigma<T>(s, nrhs, h->stream));
+    int nslots_mu = ns + 2 * h->nf;
+    launches += 3;
+    if (h->pt.nproj > 0) {
+        KbArgs<T> k = kb_args<T>(h);
+        k.x = (const C*)h->vp[1 - cur];
+        k.y = (C*)h->vq;
+        k.state = h->st;
+        k.mask = M_ACTIVE;
+        k.dot_part = h->mu_part;
+        k.slot_stride = h->slot_stride;
+        k.slot_base = nslots_mu;
+        CK(launch_kb<T>(k, nrhs, h->stream));
+        nslots_mu += 1;
+        launches += 1;
+    }
+    CK(launch_alpha(h->st, h->mu_part, nslots_mu, h->slot_stride, nrhs, h->stream));
+    CK(launch_axpy_update<T>((C*)h->vx, (C*)h->vr, (const C*)h->vp[1 - cur], (const C*)h->vq, h->st,
+                             M_ACTIVE, h->npts, nrhs, h->stream));
+    launches += 2;
+    return apply_precond_dots<T>(h, nrhs, M_ACTIVE, launches);
+}
+
+// FP64 residual replacement for RHS in `mask` (PENDING): x64 (+)= x, r = b - A x64.
+template <typename T>
+int residual_replacement(iobm_handle* h, int nrhs, int mask, bool mixed, long long& launches) {
+    using C = typename Cplx<T>::type;
+    if (mixed) {
+        CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
+        launches += 1;
+    }
+    int rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
+                                    h->rhs_energy.as<int>(), h->st, mask, launches);
+    if (rc) return rc;
+    int nslots = 0;
+    CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
+                          h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, h->st, mask,
+                          h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
+    const double tol2 = h->opt.tol * h->opt.tol;
+    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, tol2, 0, h->stream));
+    launches += 2;
+    rc = apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
+    if (rc) return rc;
+    CK(launch_restart_scalars(h->st, h->rho_part, h->rr_part, h->ns_stencil, h->slot_stride, nrhs,
+                              h->stream));
+    launches += 1;
+    return IOBM_OK;
+}
+
+template <typename T>
+int run_solver(iobm_handle* h, int nrhs) {
+    using C = typename Cplx<T>::type;
+    const bool mixed = std::is_same<T, float>::value;
+    const size_t ce = sizeof(C);
+    const size_t n = (size_t)nrhs * h->npts;
+    long long launches = 0;
+    CK(cudaEventRecord(h->ev_t0, h->stream));
+    CK(cudaMemsetAsync(h->vx, 0, ce * n, h->stream));
+    CK(cudaMemsetAsync(h->vp[0], 0, ce * n, h->stream));
+    CK(cudaMemsetAsync(h->vp[1], 0, ce * n, h->stream));
+    if (mixed) CK(cudaMemsetAsync(h->x64, 0, sizeof(double2) * n, h->stream));
+    // r = b, ||b||^2
+    int nslots = 0;
+    CK(launch_residual<T>(nullptr, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
+                          h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, nullptr, M_ALL,
+                          h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
+    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, 0.0, 1, h->stream));
+    launches += 2;
+    int rc = apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
+    if (rc) return rc;
+    CK(launch_restart_scalars(h->st, h->rho_part, h->rr_part, h->ns_stencil, h->slot_stride, nrhs,
+                              h->stream));
+    launches += 1;
+
+    // capture one chunk of iterations (even length: p buffers return to p[0])
+    int chunk = std::max(2, h->opt.chunk);
+    if (chunk & 1) ++chunk;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long per_chunk = 0;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < chunk; ++it) {
+        rc = cocg_iteration<T>(h, nrhs, it & 1, mixed, per_chunk);
+        if (rc) {
+            cudaStreamEndCapture(h->stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+    }
+    CK(cudaStreamEndCapture(h->stream, &graph));
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    cudaGraphDestroy(graph);
+
+    h->hstate.resize(nrhs);
+    const int max_chunks = h->opt.max_iter / chunk + 4;
+    int chunks = 0;
+    for (; chunks < max_chunks; ++chunks) {
+        cudaError_t e = cudaGraphLaunch(exec, h->stream);
+        if (e != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            return cuda_fail(h, e, "cudaGraphLaunch");
+        }
+        launches += per_chunk;
+        e = cudaMemcpyAsync(h->hstate.data(), h->st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost,
+                            h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            return cuda_fail(h, e, "state readback");
+        }
+        int active = 0, pending = 0;
+        for (const RhsState& S : h->hstate) {
+            active += (S.status == ST_ACTIVE || S.status == ST_RESTART);
+            pending += (S.status == ST_PENDING);
+        }
+        if (pending) {
+            rc = residual_replacement<T>(h, nrhs, M_PENDING, mixed, launches);
+            if (rc) {
+                cudaGraphExecDestroy(exec);
+                return rc;
+            }
+            e = cudaMemcpyAsync(h->hstate.data(), h->st, sizeof(RhsState) * nrhs,
+                                cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return cuda_fail(h, e, "state readback");
+            }
+            active = 0;
+            for (const RhsState& S : h->hstate) active += (S.status == ST_ACTIVE);
+        }
+        if (!active) break;
+    }
+    cudaGraphExecDestroy(exec);
+    // RHS that stopped without converging: fold their FP32 progress and record the FP64 residual
+    {
+        const int mask = (1 << ST_NOCONV) | (1 << ST_BREAKDOWN) | (1 << ST_ACTIVE);
+        if (mixed) {
+            CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
+        }
+        rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
+                                    h->rhs_energy.as<int>(), h->st, mask, launches);
+        if (rc) return rc;
+        CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(),
+                              h->phx.as<double2>(), h->phy.as<double2>(), h->g.nx, h->g.ny,
+                              h->g.nz, h->nf, h->st, mask, h->rr_part, h->slot_stride, nrhs,
+                              h->stream, &nslots));
+        CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, 0.0, 2, h->stream));
+    }
+    CK(cudaEventRecord(h->ev_t1, h->stream));
+    CK(cudaMemcpyAsync(h->hstate.data(), h->st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
+    h->last_ms = ms;
+    h->last_launches = launches;
+    long long it = 0;
+    for (const RhsState& S : h->hstate) it += S.iters;
+    h->last_iters = it;
+    return IOBM_OK;
+}
+
+// Build the per-energy tables and RHS list for energies E[0..nE).
+// kind 0: incident channels (channels/nch), kind 1: forward + adjoint at one energy.
+int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, int nch, int side,
+                int kind) {
+    h->energies.clear();
+    h->hdesc.clear();
+    h->hrhs_energy.clear();
+    h->hrhs_chan.clear();
+    h->side = side;
+    const int nf = h->nf;
+    std::vector<std::complex<double>> sig_all;
+    for (int e = 0; e < nE; ++e) {
+        ModeTables mt;
+        std::string msg;
+        if (!std::isfinite(E[e])) return fail(h, IOBM_E_ARG, "non-finite energy");
+        const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, nf, E[e], true,
+                                         mt, msg);
+        if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
+        sig_all.insert(sig_all.end(), mt.sigma.begin(), mt.sigma.end());
+        if (kind == 0) {
+            std::vector<int> list;
+            if (!channels) {
+                for (int c = 0; c < mt.nopen; ++c) list.push_back(c);
+            } else {
+                for (int c = 0; c < nch; ++c)
+                    if (channels[c] >= 0 && channels[c] < mt.nopen) list.push_back(channels[c]);
+            }
+            for (int c : list) {
+                RhsDesc d{};
+                d.energy = e;
+                d.kx = mt.open_kx[c];
+                d.ky = mt.open_ky[c];
+                d.side = side;
+                d.sign = 1;
+                for (int k = 0; k < nf; ++k) {
+                    const auto b = mt.btilde[(size_t)c * nf + k];
+                    d.coef[k] = make_double2(b.real(), b.imag());
+                }
+                h->hdesc.push_back(d);
+                h->hrhs_energy.push_back(e);
+                h->hrhs_chan.push_back(c);
+            }
+        } else {
+            // forward waves, then adjoint functionals w_o on the exit planes
+            for (int c = 0; c < mt.nopen; ++c) {
+                RhsDesc d{};
+                d.energy = e;
+                d.kx = mt.open_kx[c];
+                d.ky = mt.open_ky[c];
+                d.side = 0;
+                d.sign = 1;
+                for (int k = 0; k < nf; ++k) {
+                    const auto b = mt.btilde[(size_t)c * nf + k];
+                    d.coef[k] = make_double2(b.real(), b.imag());
+                }
+                h->hdesc.push_back(d);
+                h->hrhs_energy.push_back(e);
+                h->hrhs_chan.push_back(c);
+            }
+            const double inv = 1.0 / h->nxy;
+            for (int c = 0; c < mt.nopen; ++c) {
+                RhsDesc d{};
+                d.energy = e;
+                d.kx = mt.open_kx[c];
+                d.ky = mt.open_ky[c];
+                d.side = 1;
+                d.sign = -1;
+                for (int k = 0; k < nf; ++k) {
+                    const auto m = mt.mrow[(size_t)c * nf + k] * inv;
+                    d.coef[k] = make_double2(m.real(), m.imag());
+                }
+                h->hdesc.push_back(d);
+                h->hrhs_energy.push_back(e);
+                h->hrhs_chan.push_back(c);
+            }
+        }
+        h->energies.push_back(std::move(mt));
+    }
+    h->nrhs = (int)h->hdesc.size();
+    // device tables
+    std::vector<double2> s64(sig_all.size());
+    std::vector<float2> s32(sig_all.size());
+    for (size_t i = 0; i < sig_all.size(); ++i) {
+        s64[i] = make_double2(sig_all[i].real(), sig_all[i].imag());
+        s32[i] = make_float2((float)sig_all[i].real(), (float)sig_all[i].imag());
+    }
+    std::vector<double> ed(nE);
+    std::vector<int> optr(nE + 1, 0);
+    std::vector<int2> obins;
+    h->max_open = 0;
+    for (int e = 0; e < nE; ++e) {
+        ed[e] = E[e];
+        const ModeTables& mt = h->energies[e];
+        optr[e + 1] = optr[e] + mt.nopen;
+        h->max_open = std::max(h->max_open, mt.nopen);
+        for (int c = 0; c < mt.nopen; ++c) obins.push_back(make_int2(mt.open_kx[c], mt.open_ky[c]));
+    }
+    CK(upload(h->sig64, s64, h->stream));
+    CK(upload(h->sig32, s32, h->stream));
+    CK(upload(h->ediag, ed, h->stream));
+    CK(upload(h->rhs_energy, h->hrhs_energy, h->stream));
+    CK(upload(h->descs, h->hdesc, h->stream));
+    CK(upload(h->open_ptr, optr, h->stream));
+    CK(upload(h->open_bins, obins, h->stream));
+    return IOBM_OK;
+}
+
+int run_batch(iobm_handle* h) {
+    if (h->nrhs == 0) {
+        h->solved = true;
+        h->hstate.clear();
+        return IOBM_OK;
+    }
+    int rc = bind_workspace(h, h->nrhs);
+    if (rc) return rc;
+    rc = (h->opt.precision == IOBM_MIXED) ? run_solver<float>(h, h->nrhs)
+                                          : run_solver<double>(h, h->nrhs);
+    if (rc) return rc;
+    // projections of the FP64 solutions
+    const size_t pbytes = sizeof(double2) * (size_t)h->nrhs * std::max(h->max_open, 1) * 2 * kMaxNf;
+    CK(h->proj_out.ensure(pbytes));
+    CK(launch_projection(h->x64, h->descs.as<RhsDesc>(), h->open_ptr.as<int>(), h->open_bins.as<int2>(),
+                         h->phx.as<double2>(), h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz,
+                         h->nf, h->max_open, h->proj_out.as<double2>(), h->nrhs, h->stream));
+    h->solved = true;
+    return IOBM_OK;
+}
+
+// t and r of every RHS (host, FP64) from the projection sums.
+int compute_tr(iobm_handle* h, std::vector<std::complex<double>>& t,
+               std::vector<std::complex<double>>& r) {
+    const int nf = h->nf;
+    const int mo = std::max(h->max_open, 1);
+    std::vector<double2> out((size_t)h->nrhs * mo * 2 * kMaxNf);
+    CK(cudaMemcpyAsync(out.data(), h->proj_out.p, sizeof(double2) * out.size(),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    t.assign((size_t)h->nrhs * mo, 0.0);
+    r.assign((size_t)h->nrhs * mo, 0.0);
+    for (int i = 0; i < h->nrhs; ++i) {
+        const RhsDesc& D = h->hdesc[i];
+        const ModeTables& mt = h->energies[D.energy];
+        const int side = D.side;
+        const int c_in = h->hrhs_chan[i];
+        for (int o = 0; o < mt.nopen; ++o) {
+            const double2* S = &out[(((size_t)i * mo + o) * 2) * kMaxNf];
+            std::complex<double> tt = 0.0, rr = 0.0;
+            for (int d = 0; d < nf; ++d) {
+                const double2 se = S[(1 - side) * kMaxNf + d];
+                const double2 sn = S[side * kMaxNf + d];
+                std::complex<double> entry(sn.x, sn.y);
+                if (o == c_in) entry -= std::pow(mt.lam_in[c_in], d);
+                tt += mt.mrow[(size_t)o * nf + d] * std::complex<double>(se.x, se.y);
+                rr += mt.mrow[(size_t)o * nf + d] * entry;
+            }
+            t[(size_t)i * mo + o] = tt;
+            r[(size_t)i * mo + o] = rr;
+        }
+    }
+    return IOBM_OK;
+}
+
+int status_of(const RhsState& S) {
+    switch (S.status) {
+        case ST_CONVERGED: return IOBM_OK;
+        case ST_BREAKDOWN: return IOBM_E_BREAKDOWN;
+        default: return IOBM_E_NOCONV;
+    }
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void iobm_default_options(iobm_options* o) {
+    if (!o) return;
+    o->alpha = 1.8;
+    o->use_precond = 1;
+    o->tol = 1e-8;
+    o->max_iter = 20000;
+    o->precision = IOBM_MIXED;
+    o->refine_delta = 0.1;
+    o->chunk = 32;
+}
+
+const char* iobm_status_string(int s) {
+    switch (s) {
+        case IOBM_OK: return "ok";
+        case IOBM_E_ARG: return "invalid argument";
+        case IOBM_E_THRESHOLD: return "energy at a channel threshold";
+        case IOBM_E_PROJ_BOUNDARY: return "projector touches the self-energy planes";
+        case IOBM_E_NOCONV: return "not converged";
+        case IOBM_E_BREAKDOWN: return "COCG breakdown";
+        case IOBM_E_TIMEOUT: return "device wait timed out";
+        case IOBM_E_CUDA: return "CUDA error";
+        case IOBM_E_STATE: return "call out of order";
+        case IOBM_E_UNSUPPORTED: return "unsupported size";
+        default: return "unknown status";
+    }
+}
+
+const char* iobm_last_error(const iobm_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+double iobm_fermi_energy(const iobm_handle* h) {
+    if (!h) return 0.0;
+    return std::pow(9.0 * M_PI / 4.0, 2.0 / 3.0) / (2.0 * h->rs * h->rs);
+}
+
+int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projectors* proj, double rs,
+                const iobm_options* opts, void* cuda_stream, iobm_handle** out) {
+    if (!out) return IOBM_E_ARG;
+    *out = nullptr;
+    if (!grid || !V_loc) return IOBM_E_ARG;
+    iobm_handle* h = new iobm_handle();
+    h->g = *grid;
+    h->nf = grid->nf;
+    h->rs = rs;
+    iobm_default_options(&h->opt);
+    if (opts) h->opt = *opts;
+    auto bad = [&](int code, const std::string& m) {
+        h->err = m;
+        *out = h;   // returned so that iobm_last_error can be read; caller destroys
+        return code;
+    };
+    const iobm_grid& g = h->g;
+    if (g.nx < 1 || g.ny < 1 || g.nf < 1 || g.nf > kMaxNf || g.nz < 2 * g.nf + 1 ||
+        !(g.hx > 0) || !(g.hy > 0) || !(g.hz > 0))
+        return bad(IOBM_E_ARG, "grid sizes or spacings out of range (need nf in 1..4, nz >= 2 nf + 1)");
+    if (!(rs > 0)) return bad(IOBM_E_ARG, "rs must be positive");
+    if (!(h->opt.tol > 0) || h->opt.max_iter < 1 || !(h->opt.refine_delta > 0 && h->opt.refine_delta < 1) ||
+        (h->opt.precision != IOBM_FP64 && h->opt.precision != IOBM_MIXED) || !(h->opt.alpha > 0))
+        return bad(IOBM_E_ARG, "invalid solver options");
+    h->nxy = g.nx * g.ny;
+    h->npts = (long long)h->nxy * g.nz;
+    if (h->npts > (1LL << 31) - 1) return bad(IOBM_E_UNSUPPORTED, "grid larger than 2^31 points");
+    if (h->nxy > 4096)
+        return bad(IOBM_E_UNSUPPORTED, "lateral planes above 4096 points are not supported by the "
+                                       "shared-memory FFT of this build");
+    std::vector<int> rx, ry;
+    if (!fft_plan(g.nx, rx) || !fft_plan(g.ny, ry))
+        return bad(IOBM_E_UNSUPPORTED, "lateral sizes must have prime factors <= 13");
+    if ((int)rx.size() > kMaxRadixPasses || (int)ry.size() > kMaxRadixPasses)
+        return bad(IOBM_E_UNSUPPORTED, "too many FFT passes");
+    h->ax.n = g.nx;
+    h->ax.npass = (int)rx.size();
+    for (size_t i = 0; i < rx.size(); ++i) h->ax.radix[i] = rx[i];
+    h->ay.n = g.ny;
+    h->ay.npass = (int)ry.size();
+    for (size_t i = 0; i < ry.size(); ++i) h->ay.radix[i] = ry[i];
+    for (long long i = 0; i < h->npts; ++i)
+        if (!std::isfinite(V_loc[i])) return bad(IOBM_E_ARG, "non-finite V_loc");
+    std::string msg;
+    int rc = build_projectors(proj ? proj->nproj : 0, proj ? proj->row_ptr : nullptr,
+                              proj ? proj->idx : nullptr, proj ? proj->val : nullptr,
+                              proj ? proj->coupling : nullptr, g.nx, g.ny, g.nz, g.nf, h->pt, msg);
+    if (rc) return bad(rc, msg);
+    h->w = fd_weights(g.nf);
+
+    h->user_stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sync, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t1);
+    if (e == cudaSuccess) e = sigma_prepare();
+    if (e != cudaSuccess) return bad(IOBM_E_CUDA, std::string("stream/event setup: ") + cudaGetErrorString(e));
+
+    std::vector<float> v32(h->npts);
+    std::vector<double> v64(V_loc, V_loc + h->npts);
+    for (long long i = 0; i < h->npts; ++i) v32[i] = (float)V_loc[i];
+    auto tw = [](int n, double sign, std::vector<double2>& t64, std::vector<float2>& t32) {
+        t64.resize(n);
+        t32.resize(n);
+        for (int k = 0; k < n; ++k) {
+            const double a = sign * 2.0 * M_PI * k / n;
+            t64[k] = make_double2(std::cos(a), std::sin(a));
+            t32[k] = make_float2((float)t64[k].x, (float)t64[k].y);
+        }
+    };
+    std::vector<double2> tx64, ty64, px64, py64;
+    std::vector<float2> tx32, ty32, px32, py32;
+    tw(g.nx, -1.0, tx64, tx32);
+    tw(g.ny, -1.0, ty64, ty32);
+    tw(g.nx, +1.0, px64, px32);
+    tw(g.ny, +1.0, py64, py32);
+    std::vector<float> pv32(h->pt.pval.begin(), h->pt.pval.end());
+    std::vector<float> uv32(h->pt.uval.begin(), h->pt.uval.end());
+    cudaStream_t s = h->stream;
+    if ((e = upload(h->V32, v32, s)) || (e = upload(h->V64, v64, s)) || (e = upload(h->twx32, tx32, s)) ||
+        (e = upload(h->twy32, ty32, s)) || (e = upload(h->twx64, tx64, s)) ||
+        (e = upload(h->twy64, ty64, s)) || (e = upload(h->phx, px64, s)) || (e = upload(h->phy, py64, s)) ||
+        (e = upload(h->pptr, h->pt.pptr, s)) || (e = upload(h->pidx, h->pt.pidx, s)) ||
+        (e = upload(h->pval32, pv32, s)) || (e = upload(h->pval64, h->pt.pval, s)) ||
+        (e = upload(h->pcoup, h->pt.coupling, s)) || (e = upload(h->uidx, h->pt.uidx, s)) ||
+        (e = upload(h->uptr, h->pt.uptr, s)) || (e = upload(h->uproj, h->pt.uproj, s)) ||
+        (e = upload(h->uval32, uv32, s)) || (e = upload(h->uval64, h->pt.uval, s)))
+        return bad(IOBM_E_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bad(IOBM_E_CUDA, std::string("create: ") + cudaGetErrorString(e));
+    *out = h;
+    return IOBM_OK;
+}
+
+void iobm_destroy(iobm_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    DevBuf* bufs[] = {&h->V32, &h->V64, &h->twx32, &h->twy32, &h->twx64, &h->twy64, &h->phx,
+                      &h->phy, &h->pptr, &h->pidx, &h->pval32, &h->pval64, &h->pcoup, &h->uidx,
+                      &h->uptr, &h->uproj, &h->uval32, &h->uval64, &h->sig32, &h->sig64, &h->ediag,
+                      &h->rhs_energy, &h->descs, &h->open_ptr, &h->open_bins, &h->proj_out,
+                      &h->apply_sig32, &h->apply_sig64, &h->apply_ediag, &h->ws_owned};
+    for (DevBuf* b : bufs) b->release();
+    if (h->ev_sync) cudaEventDestroy(h->ev_sync);
+    if (h->ev_t0) cudaEventDestroy(h->ev_t0);
+    if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int iobm_open_channels(iobm_handle* h, double E, int* n_open, int max_out, int* nu, double* vel) {
+    if (!h || !n_open) return IOBM_E_ARG;
+    ModeTables mt;
+    std::string msg;
+    const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, h->nf, E, false, mt,
+                                     msg);
+    if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
+    *n_open = mt.nopen;
+    for (int c = 0; c < mt.nopen && c < max_out; ++c) {
+        if (nu) {
+            nu[2 * c] = mt.open_nux[c];
+            nu[2 * c + 1] = mt.open_nuy[c];
+        }
+        if (vel) vel[c] = mt.vel[c];
+    }
+    return IOBM_OK;
+}
+
+int iobm_workspace_size(iobm_handle* h, int nrhs, size_t* bytes) {
+    if (!h || !bytes || nrhs < 0) return IOBM_E_ARG;
+    *bytes = workspace_bytes(h, nrhs, h->opt.precision);
+    return IOBM_OK;
+}
+
+int iobm_set_workspace(iobm_handle* h, void* dev_ptr, size_t bytes) {
+    if (!h) return IOBM_E_ARG;
+    if (dev_ptr && (reinterpret_cast<uintptr_t>(dev_ptr) & 255))
+        return fail(h, IOBM_E_ARG, "workspace must be 256-byte aligned");
+    h->ws = dev_ptr;
+    h->ws_bytes = dev_ptr ? bytes : 0;
+    h->solved = false;
+    return IOBM_OK;
+}
+
+int iobm_solve(iobm_handle* h, const double* E, int nE, const int* channels, int nch, int side) {
+    if (!h || !E || nE < 1 || (channels && nch < 0) || (side != 0 && side != 1))
+        return h ? fail(h, IOBM_E_ARG, "invalid solve arguments") : IOBM_E_ARG;
+    h->solved = false;
+    // order after the caller's stream
+    if (cudaEventRecord(h->ev_sync, h->user_stream) == cudaSuccess)
+        cudaStreamWaitEvent(h->stream, h->ev_sync, 0);
+    int rc = prepare_rhs(h, E, nE, channels, nch, side, 0);
+    if (rc) return rc;
+    rc = run_batch(h);
+    if (rc) return rc;
+    CK(cudaEventRecord(h->ev_sync, h->stream));
+    CK(cudaStreamWaitEvent(h->user_stream, h->ev_sync, 0));
+    return IOBM_OK;
+}
+
+int iobm_num_rhs(const iobm_handle* h) { return h ? h->nrhs : 0; }
+
+int iobm_transmission(iobm_handle* h, double* T, double* R, int max_open, double* G, int* nopen,
+                      iobm_report* reports) {
+    if (!h) return IOBM_E_ARG;
+    if (!h->solved) return fail(h, IOBM_E_STATE, "no solve to report on");
+    if ((T || R) && max_open < h->max_open)
+        return fail(h, IOBM_E_ARG, "max_open is smaller than the largest open-channel count");
+    std::vector<std::complex<double>> t, r;
+    if (h->nrhs > 0) {
+        const int rc = compute_tr(h, t, r);
+        if (rc) return rc;
+    }
+    const int mo = std::max(h->max_open, 1);
+    const int nE = (int)h->energies.size();
+    if (G)
+        for (int e = 0; e < nE; ++e) G[e] = 0.0;
+    if (nopen)
+        for (int e = 0; e < nE; ++e) nopen[e] = h->energies[e].nopen;
+    for (int i = 0; i < h->nrhs; ++i) {
+        const int e = h->hrhs_energy[i];
+        const ModeTables& mt = h->energies[e];
+        const double vin = mt.vel[h->hrhs_chan[i]];
+        for (int o = 0; o < max_open && (T || R); ++o) {
+            double Tv = 0.0, Rv = 0.0;
+            if (o < mt.nopen) {
+                Tv = std::norm(t[(size_t)i * mo + o]) * mt.vel[o] / vin;
+                Rv = std::norm(r[(size_t)i * mo + o]) * mt.vel[o] / vin;
+            }
+            if (T) T[(size_t)i * max_open + o] = Tv;
+            if (R) R[(size_t)i * max_open + o] = Rv;
+        }
+        if (G)
+            for (int o = 0; o < mt.nopen; ++o)
+                G[e] += std::norm(t[(size_t)i * mo + o]) * mt.vel[o] / vin;
+        if (reports) {
+            const RhsState& S = h->hstate[i];
+            iobm_report& rp = reports[i];
+            rp.energy_index = e;
+            rp.channel = h->hrhs_chan[i];
+            rp.side = h->hdesc[i].side;
+            rp.status = status_of(S);
+            rp.iterations = S.iters;
+            rp.replacements = S.replacements;
+            rp.residual = S.res64;
+        }
+    }
+    return IOBM_OK;
+}
+
+int iobm_solution(iobm_handle* h, int rhs, void* dst, int dst_is_device) {
+    if (!h || !dst) return IOBM_E_ARG;
+    if (!h->solved || rhs < 0 || rhs >= h->nrhs) return fail(h, IOBM_E_STATE, "no such solved RHS");
+    const size_t bytes = sizeof(double2) * h->npts;
+    CK(cudaMemcpyAsync(dst, h->x64 + (size_t)rhs * h->npts, bytes,
+                       dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return IOBM_OK;
+}
+
+int iobm_grad_V(iobm_handle* h, double E, double* dGdV, int dst_is_device, double* G_out) {
+    if (!h || !dGdV) return IOBM_E_ARG;
+    if (cudaEventRecord(h->ev_sync, h->user_stream) == cudaSuccess)
+        cudaStreamWaitEvent(h->stream, h->ev_sync, 0);
+    int rc = prepare_rhs(h, &E, 1, nullptr, 0, 0, 1);
+    if (rc) return rc;
+    rc = run_batch(h);
+    if (rc) return rc;
+    const ModeTables& mt = h->energies[0];
+    const int n = mt.nopen;
+    std::vector<std::complex<double>> t, r;
+    rc = compute_tr(h, t, r);
+    if (rc) return rc;
+    const int mo = std::max(h->max_open, 1);
+    std::vector<double2> C((size_t)std::max(n * n, 1));
+    double G = 0.0;
+    for (int o = 0; o < n; ++o)
+        for (int i = 0; i < n; ++i) {
+            const std::complex<double> toi = t[(size_t)i * mo + o];
+            const std::complex<double> c = (mt.vel[o] / mt.vel[i]) * std::conj(toi);
+            C[(size_t)o * n + i] = make_double2(c.real(), c.imag());
+            G += std::norm(toi) * mt.vel[o] / mt.vel[i];
+        }
+    if (G_out) *G_out = G;
+    DevBuf dC, dg;
+    CK(upload(dC, C, h->stream));
+    double* gdev = dGdV;
+    if (!dst_is_device) {
+        CK(dg.ensure(sizeof(double) * h->npts));
+        gdev = dg.as<double>();
+    }
+    if (n > 0) {
+        CK(launch_gradient(h->x64, n, h->x64 + (size_t)n * h->npts, n, dC.as<double2>(), h->npts, gdev,
+                           h->stream));
+    } else {
+        CK(cudaMemsetAsync(gdev, 0, sizeof(double) * h->npts, h->stream));
+    }
+    if (!dst_is_device)
+        CK(cudaMemcpyAsync(dGdV, gdev, sizeof(double) * h->npts, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    dC.release();
+    dg.release();
+    CK(cudaEventRecord(h->ev_sync, h->stream));
+    CK(cudaStreamWaitEvent(h->user_stream, h->ev_sync, 0));
+    return IOBM_OK;
+}
+
+static int apply_common(iobm_handle* h, double E, int elem, const void* x, void* y, int nrhs,
+                        bool precond) {
+    if (!h || !x || !y || nrhs < 0 || (elem != IOBM_ELEM_C64 && elem != IOBM_ELEM_C32))
+        return h ? fail(h, IOBM_E_ARG, "invalid apply arguments") : IOBM_E_ARG;
+    if (nrhs == 0) return IOBM_OK;
+    if (cudaEventRecord(h->ev_sync, h->user_stream) == cudaSuccess)
+        cudaStreamWaitEvent(h->stream, h->ev_sync, 0);
+    long long launches = 0;
+    if (precond) {
+        if (elem == IOBM_ELEM_C64) {
+            StencilArgs<double> a = precond_args<double>(h);
+            a.x = (const double2*)x;
+            a.y = (double2*)y;
+            CK(launch_stencil<double>(a, nrhs, h->stream));
+        } else {
+            StencilArgs<float> a = precond_args<float>(h);
+            a.x = (const float2*)x;
+            a.y = (float2*)y;
+            CK(launch_stencil<float>(a, nrhs, h->stream));
+        }
+    } else {
+        ModeTables mt;
+        std::string msg;
+        const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, h->nf, E, true,
+                                         mt, msg);
+        if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
+        std::vector<double2> s64(mt.sigma.size());
+        std::vector<float2> s32(mt.sigma.size());
+        for (size_t i = 0; i < mt.sigma.size(); ++i) {
+            s64[i] = make_double2(mt.sigma[i].real(), mt.sigma[i].imag());
+            s32[i] = make_float2((float)s64[i].x, (float)s64[i].y);
+        }
+        std::vector<double> ed(1, E);
+        CK(upload(h->apply_sig64, s64, h->stream));
+        CK(upload(h->apply_sig32, s32, h->stream));
+        CK(upload(h->apply_ediag, ed, h->stream));
+        int rc2;
+        if (elem == IOBM_ELEM_C64)
+            rc2 = apply_operator<double>(h, x, y, nrhs, h->apply_sig64.p, h->apply_ediag.as<double>(),
+                                         nullptr, nullptr, M_ALL, launches);
+        else
+            rc2 = apply_operator<float>(h, x, y, nrhs, h->apply_sig32.p, h->apply_ediag.as<double>(),
+                                        nullptr, nullptr, M_ALL, launches);
+        if (rc2) return rc2;
+    }
+    CK(cudaEventRecord(h->ev_sync, h->stream));
+    CK(cudaStreamWaitEvent(h->user_stream, h->ev_sync, 0));
+    CK(cudaStreamSynchronize(h->stream));
+    return IOBM_OK;
+}
+
+int iobm_apply(iobm_handle* h, double E, int elem, const void* x, void* y, int nrhs) {
+    return apply_common(h, E, elem, x, y, nrhs, false);
+}
+
+int iobm_apply_precond(iobm_handle* h, int elem, const void* x, void* y, int nrhs) {
+    return apply_common(h, 0.0, elem, x, y, nrhs, true);
+}
+
+int iobm_set_potential(iobm_handle* h, const double* V_loc, int src_is_device) {
+    if (!h || !V_loc) return IOBM_E_ARG;
+    std::vector<double> v64(h->npts);
+    if (src_is_device) {
+        CK(cudaMemcpy(v64.data(), V_loc, sizeof(double) * h->npts, cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(v64.data(), V_loc, sizeof(double) * h->npts);
+    }
+    for (long long i = 0; i < h->npts; ++i)
+        if (!std::isfinite(v64[i])) return fail(h, IOBM_E_ARG, "non-finite V_loc");
+    std::vector<float> v32(h->npts);
+    for (long long i = 0; i < h->npts; ++i) v32[i] = (float)v64[i];
+    CK(upload(h->V64, v64, h->stream));
+    CK(upload(h->V32, v32, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->solved = false;
+    return IOBM_OK;
+}
+
+int iobm_channels_host(const iobm_grid* g, double E, int* n_open, int max_out, int* nu,
+                       double* vel, double* lam, double* btilde, double* mrow, double* sigma) {
+    if (!g || !n_open || g->nx < 1 || g->ny < 1 || g->nf < 1 || g->nf > kMaxNf) return IOBM_E_ARG;
+    ModeTables mt;
+    std::string msg;
+    const int rc = build_mode_tables(g->nx, g->ny, g->hx, g->hy, g->hz, g->nf, E, sigma != nullptr,
+                                     mt, msg);
+    if (rc) return rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED;
+    const int nf = g->nf;
+    *n_open = mt.nopen;
+    for (int c = 0; c < mt.nopen && c < max_out; ++c) {
+        if (nu) {
+            nu[2 * c] = mt.open_nux[c];
+            nu[2 * c + 1] = mt.open_nuy[c];
+        }
+        if (vel) vel[c] = mt.vel[c];
+        if (lam) {
+            lam[2 * c] = mt.lam_in[c].real();
+            lam[2 * c + 1] = mt.lam_in[c].imag();
+        }
+        for (int d = 0; d < nf; ++d) {
+            if (btilde) {
+                btilde[2 * (c * nf + d)] = mt.btilde[(size_t)c * nf + d].real();
+                btilde[2 * (c * nf + d) + 1] = mt.btilde[(size_t)c * nf + d].imag();
+            }
+            if (mrow) {
+                mrow[2 * (c * nf + d)] = mt.mrow[(size_t)c * nf + d].real();
+                mrow[2 * (c * nf + d) + 1] = mt.mrow[(size_t)c * nf + d].imag();
+            }
+        }
+    }
+    if (sigma)
+        for (size_t i = 0; i < mt.sigma.size(); ++i) {
+            sigma[2 * i] = mt.sigma[i].real();
+            sigma[2 * i + 1] = mt.sigma[i].imag();
+        }
+    return IOBM_OK;
+}
+
+int iobm_last_solve_stats(const iobm_handle* h, double* ms, long long* launches,
+                          long long* iterations_total) {
+    if (!h) return IOBM_E_ARG;
+    if (ms) *ms = h->last_ms;
+    if (launches) *launches = h->last_launches;
+    if (iterations_total) *iterations_total = h->last_iters;
+    return IOBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Internal declarations shared by the IOBM CUDA translation units.
+//
+// Device data layout (all in HBM, one junction per handle):
+//   vectors      [rhs][z][y][x] interleaved complex (float2 / double2)
+//   V            [z][y][x] real (float and double copies)
+//   sigma table  [energy][ky][kx][d][d'] complex, lateral FFT-bin order
+//   partials     [rhs][slot] FP64 partial sums of the Krylov dot products
+//   scalars      [rhs] RhsState (alpha, beta, rho, norms, status, counters)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace iobm {
+
+constexpr int kMaxNf = 4;          // FD half-width supported by the kernels
+constexpr int kMaxRadixPasses = 12;
+constexpr int kMaxRadix = 13;
+
+// ---- per-RHS solver status (device) ---------------------------------
+enum RhsStatusCode : int {
+    ST_ACTIVE = 0,        // iterating
+    ST_PENDING = 1,       // recurrence residual fell: FP64 residual replacement due
+    ST_RESTART = 2,       // residual replaced, z/rho must be recomputed
+    ST_CONVERGED = 3,
+    ST_NOCONV = 4,
+    ST_BREAKDOWN = 5,
+    ST_IDLE = 6,          // slot not used
+};
+
+// status masks selecting which RHS a launch works on
+enum : int {
+    M_ACTIVE = 1 << ST_ACTIVE,
+    M_PENDING = 1 << ST_PENDING,
+    M_RESTART = 1 << ST_RESTART,
+    M_ALL = 0x7fffffff,
+};
+
+struct RhsState {
+    double2 rho;        // r^T z of the current iterate
+    double2 rho_prev;   // previous r^T z (for beta)
+    double2 alpha;
+    double2 beta;
+    double rr;          // ||r||^2 (recurrence)
+    double rr_ref;      // ||r||^2 at the last residual replacement
+    double bb;          // ||b||^2
+    double res64;       // last FP64 relative residual
+    int status;
+    int iters;
+    int replacements;
+    int first;          // 1: next direction update uses beta = 0
+};
+
+// Source / functional descriptor of one RHS: on the entry planes (depth d),
+// b(l, d) = coef[d] * exp(sign * i * G_mode . r_l).
+struct RhsDesc {
+    int energy;
+    int kx, ky;           // FFT bins of the lateral mode (nu mod N)
+    int side;             // planes: 0 -> plane d, 1 -> plane nz-1-d
+    int sign;             // +1 or -1
+    int pad;
+    double2 coef[kMaxNf];
+};
+
+// Lateral FFT plan of one axis
+struct FftAxis {
+    int n;
+    int npass;
+    int radix[kMaxRadixPasses];
+};
+
+// ---- kernel parameter blocks -------------------------------------------
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+template <typename T>
+struct StencilArgs {
+    using C = typename Cplx<T>::type;
+    const C* x;            // operand (COCG: z, with p = z + beta p_old)
+    const C* pold;         // COCG: previous direction (read), may alias pout
+    C* pout;               // COCG: new direction (write)
+    C* y;                  // result
+    const T* V;            // potential or nullptr
+    int nx, ny, nz;
+    int nf;                // taps per side (1 for the preconditioner)
+    T cx[kMaxNf + 1];      // coefficients of x-shifts +-n (index n >= 1)
+    T cy[kMaxNf + 1];
+    T cz[kMaxNf + 1];
+    T c0;                  // constant part of the centre coefficient
+    T vsign;               // centre += vsign * V(r)
+    const double* ediag;   // per-RHS additive centre term (energy) or nullptr
+    const int* rhs_energy; // RHS -> energy index (for ediag)
+    const RhsState* state; // status / beta
+    int mask;              // process RHS whose status bit is in mask
+    int fused_p;           // 1: x is z and p = z + beta*pold is formed and stored
+    int dot_mode;          // 0 none, 1: slots += x^T y (and |x|^2 to nrm)
+    double2* dot_part;     // [rhs][slot_stride]
+    double* nrm_part;      // [rhs][slot_stride] or nullptr
+    int slot_stride;
+    int slot_base;
+    int zchunk;            // planes per CTA
+    int tiles_x, tiles_y;  // lateral tiling
+    long long npts;
+};
+
+// Self-energy (boundary) application, one cluster of nf CTAs per (rhs, end)
+template <typename T>
+struct SigmaArgs {
+    using C = typename Cplx<T>::type;
+    const C* x;             // operand planes are read from here
+    C* y;                   // y[end planes] -= Sigma x
+    const C* sigma;         // [energy][ky][kx][nf][nf]
+    const int* rhs_energy;
+    const RhsState* state;
+    int mask;
+    int nx, ny, nz, nf;
+    FftAxis ax, ay;
+    const C* twx;           // [nx] exp(-2 pi i k / nx)
+    const C* twy;           // [ny]
+    double2* dot_part;      // slot_base + end*nf + d
+    int slot_stride, slot_base;
+    long long npts;
+};
+
+template <typename T>
+struct KbArgs {
+    using C = typename Cplx<T>::type;
+    const C* x;
+    C* y;                    // y[support] -= V_NL x
+    int nproj;
+    const int* pptr;         // [nproj+1] projector CSR
+    const int* pidx;
+    const T* pval;
+    const double* coupling;  // E_p
+    double dvol;
+    int nunion;
+    const int* uidx;         // union of supports (sorted grid indices)
+    const int* uptr;         // [nunion+1]
+    const int* uproj;        // projector of each entry
+    const T* uval;           // value of each entry
+    const RhsState* state;
+    int mask;
+    double2* dot_part;
+    int slot_stride, slot_base;
+    long long npts;
+};
+
+// ---- launchers (defined in the .cu files) ----------------------------------
+
+template <typename T> cudaError_t launch_stencil(const StencilArgs<T>& a, int nrhs, cudaStream_t s);
+template <typename T> cudaError_t launch_sigma(const SigmaArgs<T>& a, int nrhs, cudaStream_t s);
+template <typename T> size_t sigma_smem_bytes(int nx, int ny, int threads);
+template <typename T> cudaError_t launch_kb(const KbArgs<T>& a, int nrhs, cudaStream_t s);
+
+// Krylov scalar and vector kernels
+cudaError_t launch_beta(RhsState* st, const double2* rho_part, const double* rr_part, int nslots,
+                        int slot_stride, int nrhs, int max_iter, double tol2, double delta2,
+                        int mixed, cudaStream_t s);
+cudaError_t launch_alpha(RhsState* st, const double2* mu_part, int nslots, int slot_stride,
+                         int nrhs, cudaStream_t s);
+cudaError_t launch_restart_scalars(RhsState* st, const double2* rho_part, const double* rr_part,
+                                   int nslots, int slot_stride, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_axpy_update(typename Cplx<T>::type* x, typename Cplx<T>::type* r,
+                               const typename Cplx<T>::type* p, const typename Cplx<T>::type* q,
+                               const RhsState* st, int mask, long long npts, int nrhs,
+                               cudaStream_t s);
+// x64 += x32; x32 = 0 (mixed-precision fold before the FP64 residual)
+cudaError_t launch_fold(double2* x64, float2* x32, const RhsState* st, int mask, long long npts,
+                        int nrhs, cudaStream_t s);
+// r = b - y (y may be null) in FP64; writes r64 (may be null) and rT (element type T);
+// rr partials per block.
+template <typename T>
+cudaError_t launch_residual(const double2* y, double2* r64, typename Cplx<T>::type* rT,
+                            const RhsDesc* desc, const double2* phx, const double2* phy,
+                            int nx, int ny, int nz, int nf, const RhsState* st, int mask,
+                            double* rr_part, int slot_stride, int nrhs, cudaStream_t s,
+                            int* nslots_out);
+cudaError_t launch_check(RhsState* st, const double* rr_part, int nslots, int slot_stride,
+                         int nrhs, double tol2, int init, cudaStream_t s);
+cudaError_t launch_projection(const double2* psi, const RhsDesc* desc, const int* open_ptr,
+                              const int2* open_bins, const double2* phx, const double2* phy,
+                              int nx, int ny, int nz, int nf, int max_open, double2* out,
+                              int nrhs, cudaStream_t s);
+cudaError_t launch_gradient(const double2* psi, int n_in, const double2* lam, int n_out,
+                            const double2* C, long long npts, double* g, cudaStream_t s);
+
+}  // namespace iobm
+
+namespace iobm {
+int stencil_slots(int nx, int ny, int nz, int zchunk);
+}  // namespace iobm

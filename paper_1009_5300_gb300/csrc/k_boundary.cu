@@ -1,0 +1,335 @@
+// Boundary self-energy through lateral 2D FFTs (Eqs. 8, 18-1, 18-2, 19) and the
+// Kleinman-Bylander nonlocal term.
+//
+// Self-energy: one thread-block cluster of N_f CTAs per (RHS, electrode end).
+// CTA d loads the operand plane at depth d into shared memory and transforms
+// it with a mixed-radix Stockham FFT (one warp per line, rows then columns;
+// the forward transform carries the 1/N_xy of Eq. 19).  After a cluster
+// barrier every CTA reads the N_f spectra of its cluster through distributed
+// shared memory and forms, per lateral mode nu, sum_d' Sigma~_nu[d][d'] psi~_nu(d')
+// (for N_f = 1 this is the diagonal product of Eq. 18-2), transforms back and
+// subtracts the result from the operator output on its plane.  The
+// unconjugated product x^T (-Sigma x) over the plane goes to a dot slot.
+//
+// KB term: one CTA per RHS.  Warps first form s_p = dvol * sum_r p(r) x(r) for
+// every projector (fixed per-lane order plus a fixed shuffle tree), then the
+// CTA walks the union of the supports point by point and subtracts
+// sum_p E_p p(r) s_p, so the result does not depend on scheduling.
+#include <cooperative_groups.h>
+
+#include "iobm_internal.cuh"
+#include "complex_ops.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace iobm {
+
+// ---------------------------------------------------------------------------
+// Stockham mixed-radix FFT of one line held in shared memory, by one warp.
+// Pass with radix R over current sub-transform size Ns: for j < N/R,
+//   v_r = src[j + r N/R] * W^(r * (j mod Ns) * N/(Ns R)),  W = exp(-+2 pi i / N)
+//   out = R-point DFT of v
+//   dst[(j / Ns) Ns R + (j mod Ns) + r Ns] = out_r
+// followed by a swap of src and dst.
+template <typename C, int R>
+__device__ __forceinline__ void radix_pass(const C* src, int ss, C* dst, int ds, int N, int Ns,
+                                           const C* __restrict__ tw, bool inv, int lane) {
+    const int NR = N / R;
+    const int tscale = N / (Ns * R);
+    for (int j = lane; j < NR; j += 32) {
+        const int k = j % Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            C u = src[(j + r * NR) * ss];
+            const int t = (r * k * tscale) % N;
+            C w = tw[t];
+            if (inv) w.y = -w.y;
+            v[r] = (r == 0) ? u : cmul(u, w);
+        }
+        C o[R];
+        if constexpr (R == 2) {
+            o[0] = cadd(v[0], v[1]);
+            o[1] = csub(v[0], v[1]);
+        } else if constexpr (R == 4) {
+            C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+            C a2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+            // a3 = -i d (forward) or +i d (inverse)
+            C a3;
+            if (inv) { a3.x = -d.y; a3.y = d.x; } else { a3.x = d.y; a3.y = -d.x; }
+            o[0] = cadd(a0, a2);
+            o[2] = csub(a0, a2);
+            o[1] = cadd(a1, a3);
+            o[3] = csub(a1, a3);
+        } else {
+            // generic R-point DFT, roots exp(-+2 pi i a b / R) = tw[(a b mod R) N/R]
+#pragma unroll
+            for (int aa = 0; aa < R; ++aa) {
+                C acc = v[0];
+#pragma unroll
+                for (int b = 1; b < R; ++b) {
+                    C w = tw[((aa * b) % R) * NR];
+                    if (inv) w.y = -w.y;
+                    acc = cfma(v[b], w, acc);
+                }
+                o[aa] = acc;
+            }
+        }
+        const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[(base + r * Ns) * ds] = o[r];
+    }
+}
+
+template <typename C>
+__device__ void fft_line(C* data, int stride, C* scratch, const FftAxis& ax,
+                         const C* __restrict__ tw, bool inv, int lane) {
+    const int N = ax.n;
+    C* src = data;
+    int ss = stride;
+    C* dst = scratch;
+    int ds = 1;
+    int Ns = 1;
+    for (int p = 0; p < ax.npass; ++p) {
+        const int R = ax.radix[p];
+        switch (R) {
+            case 2: radix_pass<C, 2>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
+            case 3: radix_pass<C, 3>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
+            case 4: radix_pass<C, 4>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
+            case 5: radix_pass<C, 5>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
+            case 7: radix_pass<C, 7>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
+            case 11: radix_pass<C, 11>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
+            case 13: radix_pass<C, 13>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
+            default: break;   // plans only hold the radices above (checked on the host)
+        }
+        __syncwarp();
+        C* t = src; src = dst; dst = t;
+        int tt = ss; ss = ds; ds = tt;
+        Ns *= R;
+    }
+    if (src != data) {
+        for (int i = lane; i < N; i += 32) data[i * stride] = src[i];
+        __syncwarp();
+    }
+}
+
+// 2D FFT of an ny x nx plane (x fastest) in shared memory.  scratch: per warp
+// max(nx, ny) elements.
+template <typename C>
+__device__ void fft2(C* plane, C* scratch, const FftAxis& ax, const FftAxis& ay,
+                     const C* __restrict__ twx, const C* __restrict__ twy, bool inv) {
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int nx = ax.n, ny = ay.n;
+    const int smax = nx > ny ? nx : ny;
+    C* my = scratch + warp * smax;
+    for (int row = warp; row < ny; row += nwarps) fft_line(plane + row * nx, 1, my, ax, twx, inv, lane);
+    __syncthreads();
+    for (int col = warp; col < nx; col += nwarps) fft_line(plane + col, nx, my, ay, twy, inv, lane);
+    __syncthreads();
+}
+
+constexpr int kSigmaPer = 16;   // lateral modes per thread in the multiply step
+constexpr int kSigmaMaxThreads = 256;
+constexpr size_t kSigmaMaxSmem = 200 * 1024;
+
+template <typename T>
+size_t sigma_smem_bytes(int nx, int ny, int threads) {
+    using C = typename Cplx<T>::type;
+    const int smax = nx > ny ? nx : ny;
+    return sizeof(C) * ((size_t)nx * ny + (size_t)(threads / 32) * smax) + 3 * 32 * sizeof(double);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSigmaMaxThreads) k_sigma(const SigmaArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int d = blockIdx.x;         // depth of this CTA's plane (= rank in cluster)
+    const int end = blockIdx.y;       // 0 left, 1 right
+    const int rhs = blockIdx.z;
+    const int st = a.state ? a.state[rhs].status : ST_ACTIVE;
+    if (!((1 << st) & a.mask)) return;   // uniform over the cluster
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = a.nx, ny = a.ny, nf = a.nf;
+    const int nxy = nx * ny;
+    const int smax = nx > ny ? nx : ny;
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* scratch = buf + nxy;
+    double* red = reinterpret_cast<double*>(scratch + (blockDim.x / 32) * smax);
+
+    const int plane = (end == 0) ? d : (a.nz - 1 - d);
+    const long long off = (long long)rhs * a.npts + (long long)plane * nxy;
+    const C* __restrict__ X = a.x + off;
+    for (int i = threadIdx.x; i < nxy; i += blockDim.x) buf[i] = X[i];
+    __syncthreads();
+    fft2(buf, scratch, a.ax, a.ay, a.twx, a.twy, false);
+
+    cluster.sync();   // every spectrum of the cluster is complete
+
+    const int e = a.rhs_energy ? a.rhs_energy[rhs] : 0;
+    const C* __restrict__ S = a.sigma + (size_t)e * nxy * nf * nf;
+    const T inv_n = (T)1 / (T)nxy;
+    C out[kSigmaPer];
+#pragma unroll
+    for (int j = 0; j < kSigmaPer; ++j) {
+        const int m = threadIdx.x + j * blockDim.x;
+        C acc = czero<C>();
+        if (m < nxy) {
+            for (int dp = 0; dp < nf; ++dp) {
+                const C* remote = cluster.map_shared_rank(buf, dp);
+                acc = cfma(S[((size_t)m * nf + d) * nf + dp], remote[m], acc);
+            }
+            acc = cscale(acc, inv_n);
+        }
+        out[j] = acc;
+    }
+    cluster.sync();   // all remote reads done before spectra are overwritten
+#pragma unroll
+    for (int j = 0; j < kSigmaPer; ++j) {
+        const int m = threadIdx.x + j * blockDim.x;
+        if (m < nxy) buf[m] = out[j];
+    }
+    __syncthreads();
+    fft2(buf, scratch, a.ax, a.ay, a.twx, a.twy, true);
+
+    C* __restrict__ Y = a.y + off;
+    T tre = 0, tim = 0;   // per-thread partials in the working precision
+    for (int i = threadIdx.x; i < nxy; i += blockDim.x) {
+        const C s = buf[i];
+        const C xv = X[i];
+        Y[i] = csub(Y[i], s);
+        tre -= xv.x * s.x - xv.y * s.y;
+        tim -= xv.x * s.y + xv.y * s.x;
+    }
+    double sre = tre, sim = tim, dummy = 0.0;
+    if (a.dot_part) {
+        block_reduce_3(sre, sim, dummy, red);
+        if (threadIdx.x == 0)
+            a.dot_part[(long long)rhs * a.slot_stride + a.slot_base + end * nf + d] =
+                make_double2(sre, sim);
+    }
+}
+
+static int sigma_threads(int nxy) {
+    int t = (nxy + kSigmaPer - 1) / kSigmaPer;
+    t = ((t + 31) / 32) * 32;
+    if (t < 128) t = 128;
+    return t;   // <= kSigmaMaxThreads when nxy <= 4096 (checked on the host)
+}
+
+template <typename T>
+cudaError_t launch_sigma(const SigmaArgs<T>& a, int nrhs, cudaStream_t s) {
+    const int nxy = a.nx * a.ny;
+    const int threads = sigma_threads(nxy);
+    if (threads > kSigmaMaxThreads) return cudaErrorInvalidValue;
+    const size_t smem = sigma_smem_bytes<T>(a.nx, a.ny, threads);
+    if (smem > kSigmaMaxSmem) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.nf, 2, nrhs);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = a.nf;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_sigma<T>, a);
+}
+
+// ---------------------------------------------------------------------------
+// KB nonlocal term.
+template <typename T>
+__global__ void __launch_bounds__(256) k_kb(const KbArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);                   // [nproj] E_p-weighted projections
+    double* red = reinterpret_cast<double*>(s + a.nproj);   // block reduction scratch
+
+    const int rhs = blockIdx.x;
+    const int st = a.state ? a.state[rhs].status : ST_ACTIVE;
+    if (!((1 << st) & a.mask)) return;
+    const long long base = (long long)rhs * a.npts;
+    const C* __restrict__ X = a.x + base;
+    C* __restrict__ Y = a.y + base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+    // phase 1: s_p = E_p * dvol * sum_r p(r) x(r), one warp per projector
+    for (int p = warp; p < a.nproj; p += nw) {
+        T tre = 0, tim = 0;
+        for (int i = a.pptr[p] + lane; i < a.pptr[p + 1]; i += 32) {
+            const C xv = X[a.pidx[i]];
+            const T v = a.pval[i];
+            tre += v * xv.x;
+            tim += v * xv.y;
+        }
+        double re = tre, im = tim;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_down_sync(0xffffffffu, re, o);
+            im += __shfl_down_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) {
+            const double f = a.coupling[p] * a.dvol;
+            s[p] = from_d2<C>(make_double2(re * f, im * f));
+        }
+    }
+    __syncthreads();
+
+    // phase 2: y(r) -= sum_p p(r) s_p over the union of supports
+    T tre = 0, tim = 0;
+    for (int u = threadIdx.x; u < a.nunion; u += blockDim.x) {
+        C acc = czero<C>();
+        for (int e = a.uptr[u]; e < a.uptr[u + 1]; ++e) acc = caxpy(a.uval[e], s[a.uproj[e]], acc);
+        const int g = a.uidx[u];
+        Y[g] = csub(Y[g], acc);
+        const C xv = X[g];
+        tre -= xv.x * acc.x - xv.y * acc.y;
+        tim -= xv.x * acc.y + xv.y * acc.x;
+    }
+    double dre = tre, dim = tim, dummy = 0.0;
+    if (a.dot_part) {
+        block_reduce_3(dre, dim, dummy, red);
+        if (threadIdx.x == 0)
+            a.dot_part[(long long)rhs * a.slot_stride + a.slot_base] = make_double2(dre, dim);
+    }
+}
+
+template <typename T>
+cudaError_t launch_kb(const KbArgs<T>& a, int nrhs, cudaStream_t s) {
+    using C = typename Cplx<T>::type;
+    if (a.nproj == 0) return cudaSuccess;
+    const size_t smem = sizeof(C) * a.nproj + 3 * 8 * sizeof(double) + 16;
+    if (smem > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(k_kb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    k_kb<T><<<nrhs, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// One-time attribute set-up (outside any stream capture): the self-energy
+// kernel may use up to kSigmaMaxSmem bytes of dynamic shared memory.
+cudaError_t sigma_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_sigma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSigmaMaxSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sigma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSigmaMaxSmem);
+    return e;
+}
+
+template size_t sigma_smem_bytes<float>(int, int, int);
+template size_t sigma_smem_bytes<double>(int, int, int);
+template cudaError_t launch_sigma<float>(const SigmaArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_sigma<double>(const SigmaArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_kb<float>(const KbArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_kb<double>(const KbArgs<double>&, int, cudaStream_t);
+
+}  // namespace iobm

@@ -1,0 +1,387 @@
+// Preconditioned COCG scalars and vector updates, FP64 residual replacement,
+// source construction, channel projection and the dG/dV accumulation.
+//
+// COCG (the CG method for the complex-symmetric matrix of Eq. 7, with the
+// unconjugated bilinear form x^T y and the symmetric preconditioner P of
+// Eq. 10):
+//     rho_i = r_i^T z_i,  beta_i = rho_i / rho_{i-1},  p_i = z_i + beta_i p_{i-1}
+//     mu_i  = p_i^T A p_i, alpha_i = rho_i / mu_i
+//     x_{i+1} = x_i + alpha_i p_i,  r_{i+1} = r_i - alpha_i A p_i,  z_{i+1} = P r_{i+1}
+// The scalar kernels run one thread per RHS and sum the per-CTA partials in a
+// fixed order, so every RHS of a batch gets the same arithmetic as when it is
+// solved alone.
+#include "iobm_internal.cuh"
+#include "complex_ops.cuh"
+
+namespace iobm {
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double den = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+__global__ void k_beta(RhsState* st, const double2* rho_part, const double* rr_part, int nslots,
+                       int stride, int nrhs, int max_iter, double tol2, double delta2, int mixed) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrhs) return;
+    RhsState S = st[i];
+    if (S.status != ST_ACTIVE) return;
+    double2 rho = make_double2(0.0, 0.0);
+    double rr = 0.0;
+    for (int j = 0; j < nslots; ++j) {
+        const double2 v = rho_part[(long long)i * stride + j];
+        rho.x += v.x;
+        rho.y += v.y;
+        rr += rr_part[(long long)i * stride + j];
+    }
+    S.rr = rr;
+    if (!isfinite(rr)) {
+        S.status = ST_BREAKDOWN;
+    } else if (rr <= tol2 * S.bb || (mixed && rr <= delta2 * S.rr_ref)) {
+        S.status = ST_PENDING;             // FP64 residual replacement / final check
+    } else if (S.iters >= max_iter) {
+        S.status = ST_NOCONV;
+    } else if (!finite2(rho) || (rho.x == 0.0 && rho.y == 0.0)) {
+        S.status = ST_BREAKDOWN;
+    } else {
+        S.beta = S.first ? make_double2(0.0, 0.0) : cdiv(rho, S.rho);
+        S.rho_prev = S.rho;
+        S.rho = rho;
+        S.iters += 1;
+    }
+    st[i] = S;
+}
+
+__global__ void k_alpha(RhsState* st, const double2* mu_part, int nslots, int stride, int nrhs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrhs) return;
+    RhsState S = st[i];
+    if (S.status != ST_ACTIVE) return;
+    double2 mu = make_double2(0.0, 0.0);
+    for (int j = 0; j < nslots; ++j) {
+        const double2 v = mu_part[(long long)i * stride + j];
+        mu.x += v.x;
+        mu.y += v.y;
+    }
+    if (!finite2(mu) || (mu.x == 0.0 && mu.y == 0.0)) {
+        S.status = ST_BREAKDOWN;
+    } else {
+        S.alpha = cdiv(S.rho, mu);
+    }
+    S.first = 0;
+    st[i] = S;
+}
+
+__global__ void k_restart_scalars(RhsState* st, const double2* rho_part, const double* rr_part,
+                                  int nslots, int stride, int nrhs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrhs) return;
+    if (st[i].status != ST_RESTART) return;
+    st[i].status = ST_ACTIVE;
+    (void)rho_part; (void)rr_part; (void)nslots; (void)stride;
+}
+
+cudaError_t launch_beta(RhsState* st, const double2* rho_part, const double* rr_part, int nslots,
+                        int slot_stride, int nrhs, int max_iter, double tol2, double delta2,
+                        int mixed, cudaStream_t s) {
+    k_beta<<<(nrhs + 127) / 128, 128, 0, s>>>(st, rho_part, rr_part, nslots, slot_stride, nrhs,
+                                              max_iter, tol2, delta2, mixed);
+    return cudaGetLastError();
+}
+cudaError_t launch_alpha(RhsState* st, const double2* mu_part, int nslots, int slot_stride,
+                         int nrhs, cudaStream_t s) {
+    k_alpha<<<(nrhs + 127) / 128, 128, 0, s>>>(st, mu_part, nslots, slot_stride, nrhs);
+    return cudaGetLastError();
+}
+cudaError_t launch_restart_scalars(RhsState* st, const double2* rho_part, const double* rr_part,
+                                   int nslots, int slot_stride, int nrhs, cudaStream_t s) {
+    k_restart_scalars<<<(nrhs + 127) / 128, 128, 0, s>>>(st, rho_part, rr_part, nslots,
+                                                         slot_stride, nrhs);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_axpy_update(typename Cplx<T>::type* __restrict__ x,
+                              typename Cplx<T>::type* __restrict__ r,
+                              const typename Cplx<T>::type* __restrict__ p,
+                              const typename Cplx<T>::type* __restrict__ q,
+                              const RhsState* st, int mask, long long npts) {
+    using C = typename Cplx<T>::type;
+    const int rhs = blockIdx.y;
+    if (!((1 << st[rhs].status) & mask)) return;
+    const C al = from_d2<C>(st[rhs].alpha);
+    const long long base = (long long)rhs * npts;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long g = base + i;
+        x[g] = cfma(al, p[g], x[g]);
+        r[g] = csub(r[g], cmul(al, q[g]));
+    }
+}
+
+static int vec_blocks(long long npts) {
+    long long b = (npts + 255) / 256;
+    if (b > 1024) b = 1024;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+cudaError_t launch_axpy_update(typename Cplx<T>::type* x, typename Cplx<T>::type* r,
+                               const typename Cplx<T>::type* p, const typename Cplx<T>::type* q,
+                               const RhsState* st, int mask, long long npts, int nrhs,
+                               cudaStream_t s) {
+    dim3 grid(vec_blocks(npts), nrhs);
+    k_axpy_update<T><<<grid, 256, 0, s>>>(x, r, p, q, st, mask, npts);
+    return cudaGetLastError();
+}
+template cudaError_t launch_axpy_update<float>(float2*, float2*, const float2*, const float2*,
+                                               const RhsState*, int, long long, int, cudaStream_t);
+template cudaError_t launch_axpy_update<double>(double2*, double2*, const double2*, const double2*,
+                                                const RhsState*, int, long long, int, cudaStream_t);
+
+__global__ void k_fold(double2* __restrict__ x64, float2* __restrict__ x32, const RhsState* st,
+                       int mask, long long npts) {
+    const int rhs = blockIdx.y;
+    if (!((1 << st[rhs].status) & mask)) return;
+    const long long base = (long long)rhs * npts;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = x32[base + i];
+        double2 w = x64[base + i];
+        w.x += v.x;
+        w.y += v.y;
+        x64[base + i] = w;
+        x32[base + i] = make_float2(0.f, 0.f);
+    }
+}
+
+cudaError_t launch_fold(double2* x64, float2* x32, const RhsState* st, int mask, long long npts,
+                        int nrhs, cudaStream_t s) {
+    dim3 grid(vec_blocks(npts), nrhs);
+    k_fold<<<grid, 256, 0, s>>>(x64, x32, st, mask, npts);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// r = b - y in FP64, b(l, d) = coef[d] exp(sign i G.r_l) on the entry planes.
+__device__ __forceinline__ double2 source_value(const RhsDesc& D, const double2* phx,
+                                                const double2* phy, int nx, int ny, int nz, int nf,
+                                                int k, int ix, int iy) {
+    int d = -1;
+    if (D.side == 0) {
+        if (k < nf) d = k;
+    } else {
+        if (k >= nz - nf) d = nz - 1 - k;
+    }
+    if (d < 0) return make_double2(0.0, 0.0);
+    const double2 ex = phx[(int)(((long long)D.kx * ix) % nx)];
+    const double2 ey = phy[(int)(((long long)D.ky * iy) % ny)];
+    double2 ph = cmul(ex, ey);
+    if (D.sign < 0) ph.y = -ph.y;
+    return cmul(D.coef[d], ph);
+}
+
+template <typename T>
+__global__ void k_residual(const double2* __restrict__ y, double2* __restrict__ r64,
+                           typename Cplx<T>::type* __restrict__ rT, const RhsDesc* desc,
+                           const double2* phx, const double2* phy, int nx, int ny, int nz, int nf,
+                           const RhsState* st, int mask, double* rr_part, int stride) {
+    using C = typename Cplx<T>::type;
+    __shared__ double red[3 * 8];
+    const int rhs = blockIdx.y;
+    if (st && !((1 << st[rhs].status) & mask)) return;
+    const long long plane = (long long)nx * ny;
+    const long long npts = plane * nz;
+    const long long base = (long long)rhs * npts;
+    const RhsDesc D = desc[rhs];
+    double acc = 0.0, z1 = 0.0, z2 = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / plane);
+        const int lat = (int)(i - (long long)k * plane);
+        const int iy = lat / nx, ix = lat - iy * nx;
+        double2 v = source_value(D, phx, phy, nx, ny, nz, nf, k, ix, iy);
+        if (y) v = csub(v, y[base + i]);
+        if (r64) r64[base + i] = v;
+        if (rT) rT[base + i] = from_d2<C>(v);
+        acc += v.x * v.x + v.y * v.y;
+    }
+    block_reduce_3(acc, z1, z2, red);
+    if (threadIdx.x == 0) rr_part[(long long)rhs * stride + blockIdx.x] = acc;
+}
+
+constexpr int kResidualBlocks = 64;
+
+template <typename T>
+cudaError_t launch_residual(const double2* y, double2* r64, typename Cplx<T>::type* rT,
+                            const RhsDesc* desc, const double2* phx, const double2* phy,
+                            int nx, int ny, int nz, int nf, const RhsState* st, int mask,
+                            double* rr_part, int slot_stride, int nrhs, cudaStream_t s,
+                            int* nslots_out) {
+    dim3 grid(kResidualBlocks, nrhs);
+    k_residual<T><<<grid, 256, 0, s>>>(y, r64, rT, desc, phx, phy, nx, ny, nz, nf, st, mask,
+                                       rr_part, slot_stride);
+    if (nslots_out) *nslots_out = kResidualBlocks;
+    return cudaGetLastError();
+}
+template cudaError_t launch_residual<float>(const double2*, double2*, float2*, const RhsDesc*,
+                                            const double2*, const double2*, int, int, int, int,
+                                            const RhsState*, int, double*, int, int, cudaStream_t,
+                                            int*);
+template cudaError_t launch_residual<double>(const double2*, double2*, double2*, const RhsDesc*,
+                                             const double2*, const double2*, int, int, int, int,
+                                             const RhsState*, int, double*, int, int, cudaStream_t,
+                                             int*);
+
+// init = 1: record ||b||^2 and start every RHS; init = 0: judge the FP64
+// residual of the PENDING RHS; init = 2: record the residual of RHS that stopped.
+__global__ void k_check(RhsState* st, const double* rr_part, int nslots, int stride, int nrhs,
+                        double tol2, int init) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrhs) return;
+    RhsState S = st[i];
+    double rr = 0.0;
+    if (init) {
+        for (int j = 0; j < nslots; ++j) rr += rr_part[(long long)i * stride + j];
+        S.bb = rr;
+        S.rr_ref = rr;
+        S.rr = rr;
+        S.res64 = 1.0;
+        S.iters = 0;
+        S.replacements = 0;
+        S.first = 1;
+        S.beta = make_double2(0.0, 0.0);
+        S.rho = make_double2(0.0, 0.0);
+        S.status = (rr > 0.0) ? ST_RESTART : ST_CONVERGED;
+        if (rr == 0.0) S.res64 = 0.0;
+    } else if (init == 2) {
+        // record the FP64 residual of RHS that stopped without converging
+        if (S.status != ST_NOCONV && S.status != ST_BREAKDOWN && S.status != ST_ACTIVE) return;
+        for (int j = 0; j < nslots; ++j) rr += rr_part[(long long)i * stride + j];
+        S.res64 = sqrt(rr / S.bb);
+        if (S.status == ST_ACTIVE) S.status = ST_NOCONV;
+    } else {
+        if (S.status != ST_PENDING) return;
+        for (int j = 0; j < nslots; ++j) rr += rr_part[(long long)i * stride + j];
+        S.res64 = sqrt(rr / S.bb);
+        S.replacements += 1;
+        if (rr <= tol2 * S.bb) {
+            S.status = ST_CONVERGED;
+        } else if (!isfinite(rr)) {
+            S.status = ST_BREAKDOWN;
+        } else {
+            S.rr_ref = rr;
+            S.status = ST_RESTART;
+        }
+    }
+    st[i] = S;
+}
+
+cudaError_t launch_check(RhsState* st, const double* rr_part, int nslots, int slot_stride,
+                         int nrhs, double tol2, int init, cudaStream_t s) {
+    k_check<<<(nrhs + 127) / 128, 128, 0, s>>>(st, rr_part, nslots, slot_stride, nrhs, tol2, init);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Channel projection (Eq. 19 on the N_f outermost planes of both ends):
+// out[rhs][o][side][d] = (1/N_xy) sum_l exp(-i G_o . r_l) psi(l, plane(side, d))
+// for every open channel o of the RHS's energy.  FP64 throughout.
+__global__ void k_projection(const double2* __restrict__ psi, const RhsDesc* desc,
+                             const int* open_ptr, const int2* open_bins, const double2* phx,
+                             const double2* phy, int nx, int ny, int nz, int nf, int max_open,
+                             double2* out) {
+    __shared__ double red[2 * kMaxNf * 2][8];
+    const int o = blockIdx.x;
+    const int rhs = blockIdx.y;
+    const int e = desc[rhs].energy;
+    const int nopen = open_ptr[e + 1] - open_ptr[e];
+    if (o >= nopen) return;
+    const int2 bin = open_bins[open_ptr[e] + o];
+    const long long plane = (long long)nx * ny;
+    const long long npts = plane * nz;
+    const double2* P = psi + (long long)rhs * npts;
+    double acc[2 * kMaxNf][2];
+    for (int s = 0; s < 2 * kMaxNf; ++s) acc[s][0] = acc[s][1] = 0.0;
+    for (int l = threadIdx.x; l < (int)plane; l += blockDim.x) {
+        const int iy = l / nx, ix = l - iy * nx;
+        double2 ph = cmul(phx[(int)(((long long)bin.x * ix) % nx)], phy[(int)(((long long)bin.y * iy) % ny)]);
+        ph.y = -ph.y;   // exp(-i G.r)
+        for (int side = 0; side < 2; ++side) {
+            for (int d = 0; d < nf; ++d) {
+                const int k = side == 0 ? d : nz - 1 - d;
+                const double2 v = cmul(ph, P[(long long)k * plane + l]);
+                acc[side * kMaxNf + d][0] += v.x;
+                acc[side * kMaxNf + d][1] += v.y;
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = 0; s < 2 * kMaxNf; ++s) {
+        for (int c = 0; c < 2; ++c) {
+            double v = acc[s][c];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) red[s * 2 + c][warp] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kMaxNf * 2) {
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += red[threadIdx.x][w];
+        const int s = threadIdx.x >> 1, c = threadIdx.x & 1;
+        const int side = s / kMaxNf, d = s % kMaxNf;
+        if (d < nf) {
+            double* dst = reinterpret_cast<double*>(
+                out + (((long long)rhs * max_open + o) * 2 + side) * kMaxNf + d);
+            dst[c] = v / (double)plane;
+        }
+    }
+}
+
+cudaError_t launch_projection(const double2* psi, const RhsDesc* desc, const int* open_ptr,
+                              const int2* open_bins, const double2* phx, const double2* phy,
+                              int nx, int ny, int nz, int nf, int max_open, double2* out,
+                              int nrhs, cudaStream_t s) {
+    if (max_open <= 0) return cudaSuccess;
+    dim3 grid(max_open, nrhs);
+    k_projection<<<grid, 256, 0, s>>>(psi, desc, open_ptr, open_bins, phx, phy, nx, ny, nz, nf,
+                                      max_open, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// dG/dV(r) = sum_o 2 Re[ lambda_o(r) * sum_i C[o][i] psi_i(r) ],
+// C[o][i] = (v_o / v_i) conj(t_oi).
+__global__ void k_gradient(const double2* __restrict__ psi, int n_in, const double2* __restrict__ lam,
+                           int n_out, const double2* __restrict__ C, long long npts, double* g) {
+    extern __shared__ double2 Cs[];
+    for (int i = threadIdx.x; i < n_in * n_out; i += blockDim.x) Cs[i] = C[i];
+    __syncthreads();
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < npts;
+         r += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int o = 0; o < n_out; ++o) {
+            double2 u = make_double2(0.0, 0.0);
+            for (int i = 0; i < n_in; ++i) u = cfma(Cs[o * n_in + i], psi[(long long)i * npts + r], u);
+            const double2 w = cmul(lam[(long long)o * npts + r], u);
+            acc += 2.0 * w.x;
+        }
+        g[r] = acc;
+    }
+}
+
+cudaError_t launch_gradient(const double2* psi, int n_in, const double2* lam, int n_out,
+                            const double2* C, long long npts, double* g, cudaStream_t s) {
+    const size_t smem = sizeof(double2) * (size_t)n_in * n_out;
+    if (smem > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(k_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    k_gradient<<<vec_blocks(npts), 256, smem, s>>>(psi, n_in, lam, n_out, C, npts, g);
+    return cudaGetLastError();
+}
+
+}  // namespace iobm

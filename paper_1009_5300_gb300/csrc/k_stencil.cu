@@ -1,0 +1,165 @@
+// Complex 3D finite-difference stencil (Eq. 1 kinetic term + local potential,
+// Eqs. 2-4) and the truncated-Laplacian-Green preconditioner (Eq. 10), as one
+// z-marching kernel template.
+//
+// Each CTA owns a TX x TY lateral tile of one RHS and a chunk of z-planes.  It
+// marches through its planes keeping the 2*NF+1 z-neighbours of its own
+// points in a register queue (the z taps cost no memory traffic) and stages
+// the current plane, with an NF-point periodic halo in x and y, in shared
+// memory for the lateral taps.  Planes beyond 0 and nz-1 are zero (Eq. 4:
+// the truncated operator; the self-energy kernel adds the boundary term).
+//
+// In the fused COCG mode the operand is p = z + beta * p_old, formed on the
+// fly wherever p is read and stored once per point by its owning CTA; the
+// epilogue accumulates the unconjugated product p^T (A p) (FP32 per thread
+// over its planes, FP64 across the CTA) into a per-CTA slot.
+#include "iobm_internal.cuh"
+#include "complex_ops.cuh"
+
+namespace iobm {
+
+constexpr int kTX = 32;
+constexpr int kTY = 8;
+
+template <typename T, int NF>
+__global__ void __launch_bounds__(kTX* kTY) k_stencil(const StencilArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    constexpr int W = kTX + 2 * NF;
+    constexpr int H = kTY + 2 * NF;
+    __shared__ C tile[H][W];
+    __shared__ double red[3 * (kTX * kTY / 32)];
+
+    const int rhs = blockIdx.z;
+    int st = ST_ACTIVE;
+    C beta = czero<C>();
+    bool first_dir = false;   // first direction: p = z, p_old is not read
+    if (a.state) {
+        st = a.state[rhs].status;
+        if (a.fused_p && !a.state[rhs].first) beta = from_d2<C>(a.state[rhs].beta);
+        else if (a.fused_p) first_dir = true;
+    }
+    if (!((1 << st) & a.mask)) return;
+
+    const int tile_id = blockIdx.x;
+    const int tx0 = (tile_id % a.tiles_x) * kTX;
+    const int ty0 = (tile_id / a.tiles_x) * kTY;
+    const int k0 = blockIdx.y * a.zchunk;
+    const int k1 = min(k0 + a.zchunk, a.nz);
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int tid = ly * kTX + lx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int gx = tx0 + lx, gy = ty0 + ly;
+    const bool own = (gx < nx) && (gy < ny);
+    const long long plane = (long long)nx * ny;
+    const long long base = (long long)rhs * a.npts;
+    const C* __restrict__ X = a.x + base;
+    const C* __restrict__ PO = (a.fused_p && !first_dir) ? a.pold + base : nullptr;
+    C* __restrict__ Y = a.y + base;
+    C* __restrict__ PN = a.fused_p ? a.pout + base : nullptr;
+    const T ed = a.ediag ? (T)a.ediag[a.rhs_energy ? a.rhs_energy[rhs] : 0] : (T)0;
+    const T cen = a.c0 + ed;
+
+    auto ld = [&](int k, long long lat) -> C {
+        if (k < 0 || k >= nz) return czero<C>();
+        const long long i = (long long)k * plane + lat;
+        C v = X[i];
+        if (PO) v = cfma(beta, PO[i], v);
+        return v;
+    };
+
+    const long long own_lat = own ? (long long)gy * nx + gx : 0;
+    C q[2 * NF + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * NF; ++j) {
+        const int kk = k0 - NF + j;
+        q[j] = own ? ld(kk, own_lat) : czero<C>();
+        if (PN && own && kk >= k0 && kk < k1) PN[(long long)kk * plane + own_lat] = q[j];
+    }
+
+    float dre = 0.f, dim = 0.f, nrm = 0.f;   // per-thread partials (FP32 over own planes)
+    double dre64 = 0.0, dim64 = 0.0, nrm64 = 0.0;
+
+    for (int k = k0; k < k1; ++k) {
+        // own value of plane k+NF enters the queue
+        {
+            const int kk = k + NF;
+            q[2 * NF] = own ? ld(kk, own_lat) : czero<C>();
+            if (PN && own && kk < k1) PN[(long long)kk * plane + own_lat] = q[2 * NF];
+        }
+        __syncthreads();   // previous plane's lateral taps are done
+        for (int i = tid; i < W * H; i += kTX * kTY) {
+            const int sx = i % W, sy = i / W;
+            int ix = tx0 + sx - NF, iy = ty0 + sy - NF;
+            ix %= nx; if (ix < 0) ix += nx;
+            iy %= ny; if (iy < 0) iy += ny;
+            tile[sy][sx] = ld(k, (long long)iy * nx + ix);
+        }
+        __syncthreads();
+        if (own) {
+            T d = cen;
+            if (a.V) d += a.vsign * a.V[(long long)k * plane + own_lat];
+            C acc = cscale(q[NF], d);
+#pragma unroll
+            for (int n = 1; n <= NF; ++n) {
+                acc = caxpy(a.cz[n], cadd(q[NF - n], q[NF + n]), acc);
+                acc = caxpy(a.cx[n], cadd(tile[ly + NF][lx + NF - n], tile[ly + NF][lx + NF + n]), acc);
+                acc = caxpy(a.cy[n], cadd(tile[ly + NF - n][lx + NF], tile[ly + NF + n][lx + NF]), acc);
+            }
+            Y[(long long)k * plane + own_lat] = acc;
+            if (a.dot_mode) {
+                const C p = q[NF];
+                if constexpr (sizeof(T) == 4) {
+                    dre = fmaf((float)p.x, (float)acc.x, fmaf(-(float)p.y, (float)acc.y, dre));
+                    dim = fmaf((float)p.x, (float)acc.y, fmaf((float)p.y, (float)acc.x, dim));
+                    nrm = fmaf((float)p.x, (float)p.x, fmaf((float)p.y, (float)p.y, nrm));
+                } else {
+                    dre64 += (double)p.x * acc.x - (double)p.y * acc.y;
+                    dim64 += (double)p.x * acc.y + (double)p.y * acc.x;
+                    nrm64 += (double)p.x * p.x + (double)p.y * p.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * NF; ++j) q[j] = q[j + 1];
+    }
+
+    if (a.dot_mode) {
+        double r0 = dre64 + (double)dre, r1 = dim64 + (double)dim, r2 = nrm64 + (double)nrm;
+        block_reduce_3(r0, r1, r2, red);
+        if (tid == 0) {
+            const int slot = a.slot_base + blockIdx.x + blockIdx.y * gridDim.x;
+            a.dot_part[(long long)rhs * a.slot_stride + slot] = make_double2(r0, r1);
+            if (a.nrm_part) a.nrm_part[(long long)rhs * a.slot_stride + slot] = r2;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_stencil(const StencilArgs<T>& a0, int nrhs, cudaStream_t s) {
+    StencilArgs<T> a = a0;
+    a.tiles_x = (a.nx + kTX - 1) / kTX;
+    a.tiles_y = (a.ny + kTY - 1) / kTY;
+    if (a.zchunk <= 0) a.zchunk = 32;
+    const int nzc = (a.nz + a.zchunk - 1) / a.zchunk;
+    dim3 grid(a.tiles_x * a.tiles_y, nzc, nrhs);
+    dim3 block(kTX, kTY);
+    switch (a.nf) {
+        case 1: k_stencil<T, 1><<<grid, block, 0, s>>>(a); break;
+        case 2: k_stencil<T, 2><<<grid, block, 0, s>>>(a); break;
+        case 3: k_stencil<T, 3><<<grid, block, 0, s>>>(a); break;
+        case 4: k_stencil<T, 4><<<grid, block, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// number of dot slots a stencil launch writes per RHS
+int stencil_slots(int nx, int ny, int nz, int zchunk) {
+    if (zchunk <= 0) zchunk = 32;
+    return ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY) * ((nz + zchunk - 1) / zchunk);
+}
+
+template cudaError_t launch_stencil<float>(const StencilArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_stencil<double>(const StencilArgs<double>&, int, cudaStream_t);
+
+}  // namespace iobm

@@ -1,0 +1,367 @@
+// Host-side FP64 set-up: FD weights, electrode channels and self-energy per
+// lateral mode, incident sources, lateral FFT plans and projector tables.
+//
+// Electrode channels.  In a flat jellium electrode the lateral plane waves
+// exp(i G_nu . r) decouple Eq. 2 into one recurrence per mode nu,
+//     (E - eps_perp) psi_k + (1 / (2 h_z^2)) sum_{|n| <= N_f} w_|n| psi_{k+n} = 0.
+// With psi_k = lambda^k and u = (lambda + 1/lambda) / 2, lambda^n + lambda^-n =
+// 2 T_n(u) (Chebyshev), so the 2 N_f roots come in pairs (lambda, 1/lambda)
+// over the N_f roots u of the real degree-N_f polynomial
+//     2 h_z^2 (E - eps_perp) + w_0 + 2 sum_n w_n T_n(u) = 0.
+// For N_f = 1 this is u = -chi with chi of Eq. 9 and lambda = exp(i k_z h_z)
+// of Eq. 8.5.  Of each pair the right-going root is kept: |lambda| < 1, or
+// |lambda| = 1 with positive group velocity.
+//
+// Self-energy per mode (Eqs. 17-1/17-2 in the lateral Fourier basis): with
+// depth d = 0 .. N_f-1 inward from the outermost plane and electrode planes
+// e = 1 .. N_f outward, Sigma~ = -K Q_out Q_in^{-1}, K[d][e] = w_{d+e} / (2 h_z^2),
+// Q_in[d][j] = lambda_j^-d, Q_out[e][j] = lambda_j^e.  Columns are scaled by
+// lambda_j^(N_f-1) (which cancels in the product) to keep every entry <= 1.
+// For N_f = 1: Sigma~ = -exp(i k_z h_z) / (2 h_z^2) (Eq. 18-2).
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <sstream>
+
+namespace iobm {
+
+std::vector<double> fd_weights(int nf) {
+    const int n = nf + 1;
+    std::vector<long double> M((size_t)n * n), b(n);
+    for (int m = 0; m < n; ++m) {
+        M[(size_t)m * n + 0] = (m == 0) ? 1.0L : 0.0L;
+        for (int j = 1; j <= nf; ++j) M[(size_t)m * n + j] = 2.0L * std::pow((long double)j, 2 * m);
+        b[m] = (m == 1) ? 2.0L : 0.0L;
+    }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(M[(size_t)r * n + c]) > std::fabs(M[(size_t)piv * n + c])) piv = r;
+        for (int j = 0; j < n; ++j) std::swap(M[(size_t)c * n + j], M[(size_t)piv * n + j]);
+        std::swap(b[c], b[piv]);
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const long double f = M[(size_t)r * n + c] / M[(size_t)c * n + c];
+            for (int j = 0; j < n; ++j) M[(size_t)r * n + j] -= f * M[(size_t)c * n + j];
+            b[r] -= f * b[c];
+        }
+    }
+    std::vector<double> w(n);
+    for (int c = 0; c < n; ++c) w[c] = (double)(b[c] / M[(size_t)c * n + c]);
+    return w;
+}
+
+// roots of sum_k a[k] u^k (real coefficients, a.back() != 0)
+static std::vector<cd> poly_roots(const std::vector<double>& a) {
+    const int n = (int)a.size() - 1;
+    std::vector<cd> z(n);
+    if (n == 1) {
+        z[0] = cd(-a[0] / a[1], 0.0);
+        return z;
+    }
+    std::vector<double> c(a.size());
+    for (int k = 0; k <= n; ++k) c[k] = a[k] / a[n];
+    double R = 0.0;
+    for (int k = 0; k < n; ++k) R = std::max(R, std::fabs(c[k]));
+    R = 1.0 + R;   // Cauchy bound
+    for (int k = 0; k < n; ++k) z[k] = std::polar(0.7 * R, 2.0 * M_PI * k / n + 0.4);
+    auto eval = [&](cd x, cd& p, cd& dp) {
+        p = cd(1.0, 0.0);
+        dp = cd(0.0, 0.0);
+        for (int k = n - 1; k >= 0; --k) {
+            dp = dp * x + p;
+            p = p * x + c[k];
+        }
+    };
+    for (int it = 0; it < 500; ++it) {
+        double maxstep = 0.0;
+        for (int k = 0; k < n; ++k) {
+            cd p, dp;
+            eval(z[k], p, dp);
+            if (p == cd(0.0, 0.0)) continue;
+            const cd ratio = p / dp;
+            cd s(0.0, 0.0);
+            for (int j = 0; j < n; ++j)
+                if (j != k) s += 1.0 / (z[k] - z[j]);
+            const cd w = ratio / (1.0 - ratio * s);
+            z[k] -= w;
+            maxstep = std::max(maxstep, std::abs(w) / std::max(1.0, std::abs(z[k])));
+        }
+        if (maxstep < 1e-16) break;
+    }
+    for (int k = 0; k < n; ++k) {   // Newton polish on the same polynomial
+        for (int it = 0; it < 3; ++it) {
+            cd p, dp;
+            eval(z[k], p, dp);
+            if (dp == cd(0.0, 0.0)) break;
+            z[k] -= p / dp;
+        }
+    }
+    return z;
+}
+
+static double velocity(double theta, const std::vector<double>& w, double hz) {
+    double v = 0.0;
+    for (int n = 1; n < (int)w.size(); ++n) v += n * w[n] * std::sin(n * theta);
+    return v / hz;
+}
+
+// Gauss-Jordan inverse of an n x n complex matrix (row-major), partial pivoting.
+static bool cinv(std::vector<cd>& A, int n) {
+    std::vector<cd> I((size_t)n * n, cd(0.0, 0.0));
+    for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::abs(A[(size_t)r * n + c]) > std::abs(A[(size_t)piv * n + c])) piv = r;
+        if (std::abs(A[(size_t)piv * n + c]) == 0.0) return false;
+        for (int j = 0; j < n; ++j) {
+            std::swap(A[(size_t)c * n + j], A[(size_t)piv * n + j]);
+            std::swap(I[(size_t)c * n + j], I[(size_t)piv * n + j]);
+        }
+        const cd inv = 1.0 / A[(size_t)c * n + c];
+        for (int j = 0; j < n; ++j) {
+            A[(size_t)c * n + j] *= inv;
+            I[(size_t)c * n + j] *= inv;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const cd f = A[(size_t)r * n + c];
+            if (f == cd(0.0, 0.0)) continue;
+            for (int j = 0; j < n; ++j) {
+                A[(size_t)r * n + j] -= f * A[(size_t)c * n + j];
+                I[(size_t)r * n + j] -= f * I[(size_t)c * n + j];
+            }
+        }
+    }
+    A.swap(I);
+    return true;
+}
+
+static inline int nu_of_index(int i, int n) { return i - n / 2; }          // canonical nu
+static inline int bin_of_nu(int nu, int n) { return ((nu % n) + n) % n; }   // FFT bin
+
+int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, double E,
+                      bool want_sigma, ModeTables& out, std::string& msg) {
+    const std::vector<double> w = fd_weights(nf);
+    const double two_pi = 2.0 * M_PI;
+    auto eps1d = [&](int nu, int n, double h) {
+        const double G = two_pi * nu / (n * h);
+        double s = w[0];
+        for (int k = 1; k <= nf; ++k) s += 2.0 * w[k] * std::cos(k * G * h);
+        return -0.5 * s / (h * h);
+    };
+    double top_s = w[0];
+    for (int k = 1; k <= nf; ++k) top_s += 2.0 * w[k] * ((k & 1) ? -1.0 : 1.0);
+    const double band_top = -0.5 * top_s / (hz * hz);
+
+    // Chebyshev coefficients T_n(u) = sum_k tc[n][k] u^k
+    std::vector<std::vector<double>> tc(nf + 1, std::vector<double>(nf + 1, 0.0));
+    tc[0][0] = 1.0;
+    if (nf >= 1) tc[1][1] = 1.0;
+    for (int n = 2; n <= nf; ++n)
+        for (int k = 0; k <= nf; ++k)
+            tc[n][k] = (k > 0 ? 2.0 * tc[n - 1][k - 1] : 0.0) - tc[n - 2][k];
+
+    std::vector<double> K((size_t)nf * nf, 0.0);   // K[d][e-1]
+    for (int d = 0; d < nf; ++d)
+        for (int e = 1; e <= nf; ++e)
+            if (d + e <= nf) K[(size_t)d * nf + (e - 1)] = w[d + e] / (2.0 * hz * hz);
+
+    out = ModeTables();
+    out.E = E;
+    if (want_sigma) out.sigma.assign((size_t)nx * ny * nf * nf, cd(0.0, 0.0));
+    const int nxy = nx * ny;
+    for (int iy = 0; iy < ny; ++iy) {
+        const int nuy = nu_of_index(iy, ny);
+        const double ey = eps1d(nuy, ny, hy);
+        for (int ix = 0; ix < nx; ++ix) {
+            const int nux = nu_of_index(ix, nx);
+            const double eperp = eps1d(nux, nx, hx) + ey;
+            if (std::fabs(E - eperp) < 1e-9 || std::fabs(E - eperp - band_top) < 1e-9) {
+                std::ostringstream os;
+                os << "energy " << E << " Ha lies within 1e-9 Ha of the threshold of lateral mode ("
+                   << nux << "," << nuy << ")";
+                msg = os.str();
+                return 2;
+            }
+            // polynomial in u
+            std::vector<double> a(nf + 1, 0.0);
+            a[0] = 2.0 * hz * hz * (E - eperp) + w[0];
+            for (int n = 1; n <= nf; ++n)
+                for (int k = 0; k <= n; ++k) a[k] += 2.0 * w[n] * tc[n][k];
+            const std::vector<cd> us = poly_roots(a);
+            std::vector<cd> lam(nf);
+            int prop = -1;
+            double vprop = 0.0;
+            for (int j = 0; j < nf; ++j) {
+                cd u = us[j];
+                if (std::fabs(u.imag()) <= 1e-12 * std::max(1.0, std::abs(u))) u = cd(u.real(), 0.0);
+                if (u.imag() == 0.0 && std::fabs(u.real()) < 1.0) {
+                    const double th = std::acos(u.real());   // (0, pi)
+                    const double v = velocity(th, w, hz);
+                    const double sgn = v > 0.0 ? 1.0 : -1.0;
+                    lam[j] = std::polar(1.0, sgn * th);
+                    if (prop >= 0) {
+                        msg = "more than one propagating root in one lateral mode";
+                        return 9;
+                    }
+                    prop = j;
+                    vprop = std::fabs(v);
+                } else {
+                    const cd sq = std::sqrt(u * u - 1.0);
+                    const cd l1 = u - sq, l2 = u + sq;
+                    lam[j] = (std::abs(l1) < std::abs(l2)) ? l1 : l2;
+                }
+            }
+            const int canon = iy * nx + ix;
+            const int kx = bin_of_nu(nux, nx), ky = bin_of_nu(nuy, ny);
+            // scaled Q_in[d][j] = lam_j^(nf-1-d); Q_out[e-1][j] = lam_j^(e+nf-1)
+            std::vector<cd> Qin((size_t)nf * nf), Qout((size_t)nf * nf);
+            for (int d = 0; d < nf; ++d)
+                for (int j = 0; j < nf; ++j) Qin[(size_t)d * nf + j] = std::pow(lam[j], nf - 1 - d);
+            for (int e = 1; e <= nf; ++e)
+                for (int j = 0; j < nf; ++j) Qout[(size_t)(e - 1) * nf + j] = std::pow(lam[j], e + nf - 1);
+            std::vector<cd> Qinv = Qin;
+            if (!cinv(Qinv, nf)) {
+                msg = "singular Bloch-state matrix";
+                return 9;
+            }
+            std::vector<cd> S((size_t)nf * nf, cd(0.0, 0.0));
+            if (want_sigma || prop >= 0) {
+                // S = -K Qout Qinv
+                std::vector<cd> KQ((size_t)nf * nf, cd(0.0, 0.0));
+                for (int d = 0; d < nf; ++d)
+                    for (int j = 0; j < nf; ++j)
+                        for (int e = 0; e < nf; ++e) KQ[(size_t)d * nf + j] += K[(size_t)d * nf + e] * Qout[(size_t)e * nf + j];
+                for (int d = 0; d < nf; ++d)
+                    for (int dp = 0; dp < nf; ++dp)
+                        for (int j = 0; j < nf; ++j) S[(size_t)d * nf + dp] -= KQ[(size_t)d * nf + j] * Qinv[(size_t)j * nf + dp];
+            }
+            if (want_sigma) {
+                cd* dst = &out.sigma[((size_t)ky * nx + kx) * nf * nf];
+                for (int i = 0; i < nf * nf; ++i) dst[i] = S[i];
+            }
+            if (prop >= 0) {
+                const cd li = lam[prop];
+                out.open_canon.push_back(canon);
+                out.open_kx.push_back(kx);
+                out.open_ky.push_back(ky);
+                out.open_nux.push_back(nux);
+                out.open_nuy.push_back(nuy);
+                out.vel.push_back(vprop);
+                out.lam_in.push_back(li);
+                const cd scale = std::pow(li, nf - 1);
+                for (int d = 0; d < nf; ++d) out.mrow.push_back(scale * Qinv[(size_t)prop * nf + d]);
+                for (int d = 0; d < nf; ++d) {
+                    cd b(0.0, 0.0);
+                    for (int e = 1; e <= nf; ++e) b -= K[(size_t)d * nf + (e - 1)] * std::pow(li, -e);
+                    for (int dp = 0; dp < nf; ++dp) b -= S[(size_t)d * nf + dp] * std::pow(li, dp);
+                    out.btilde.push_back(b);
+                }
+            }
+        }
+    }
+    out.nopen = (int)out.open_canon.size();
+    (void)nxy;
+    return 0;
+}
+
+bool fft_plan(int n, std::vector<int>& radices) {
+    radices.clear();
+    if (n < 1) return false;
+    static const int order[] = {4, 2, 3, 5, 7, 11, 13};
+    for (int r : order) {
+        while (n % r == 0) {
+            radices.push_back(r);
+            n /= r;
+        }
+    }
+    return n == 1;
+}
+
+int build_projectors(int nproj, const int64_t* row_ptr, const int32_t* idx, const double* val,
+                     const double* coupling, int nx, int ny, int nz, int nf, ProjTables& out,
+                     std::string& msg) {
+    out = ProjTables();
+    out.nproj = nproj;
+    if (nproj == 0) {
+        out.pptr.assign(1, 0);
+        out.uptr.assign(1, 0);
+        return 0;
+    }
+    if (!row_ptr || !idx || !val || !coupling || nproj < 0) {
+        msg = "projector arrays are NULL";
+        return 1;
+    }
+    const long long plane = (long long)nx * ny;
+    const long long npts = plane * nz;
+    if (row_ptr[0] != 0) {
+        msg = "projector row_ptr[0] must be 0";
+        return 1;
+    }
+    struct Entry { int g, p; double v; };
+    std::vector<Entry> all;
+    out.pptr.assign(nproj + 1, 0);
+    for (int p = 0; p < nproj; ++p) {
+        const int64_t b = row_ptr[p], e = row_ptr[p + 1];
+        if (e < b || e - b > (int64_t)npts) {
+            msg = "projector row_ptr is not non-decreasing";
+            return 1;
+        }
+        if (!std::isfinite(coupling[p])) {
+            msg = "non-finite projector coupling";
+            return 1;
+        }
+        std::vector<int> seen;
+        for (int64_t i = b; i < e; ++i) {
+            const long long g = idx[i];
+            if (g < 0 || g >= npts) {
+                msg = "projector index outside the grid";
+                return 1;
+            }
+            if (!std::isfinite(val[i])) {
+                msg = "non-finite projector value";
+                return 1;
+            }
+            const long long k = g / plane;
+            if (k < nf || k >= nz - nf) {
+                std::ostringstream os;
+                os << "projector " << p << " reaches plane " << k << " (the self-energy acts on planes < "
+                   << nf << " and >= " << nz - nf << ")";
+                msg = os.str();
+                return 3;
+            }
+            out.pidx.push_back((int)g);
+            out.pval.push_back(val[i]);
+            all.push_back({(int)g, p, val[i]});
+            seen.push_back((int)g);
+        }
+        std::sort(seen.begin(), seen.end());
+        if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) {
+            msg = "projector lists a grid point twice";
+            return 1;
+        }
+        out.pptr[p + 1] = (int)out.pidx.size();
+        out.coupling.push_back(coupling[p]);
+    }
+    std::stable_sort(all.begin(), all.end(), [](const Entry& a, const Entry& b) {
+        return a.g != b.g ? a.g < b.g : a.p < b.p;
+    });
+    out.uptr.push_back(0);
+    for (size_t i = 0; i < all.size(); ++i) {
+        if (i == 0 || all[i].g != all[i - 1].g) {
+            if (i > 0) out.uptr.push_back((int)i);
+            out.uidx.push_back(all[i].g);
+        }
+        out.uproj.push_back(all[i].p);
+        out.uval.push_back(all[i].v);
+    }
+    out.uptr.push_back((int)all.size());
+    if (all.empty()) out.uptr.assign(1, 0);
+    return 0;
+}
+
+}  // namespace iobm

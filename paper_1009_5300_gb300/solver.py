@@ -1,0 +1,266 @@
+"""Python front end of the IOBM C ABI (same names, argument marshalling only).
+
+PyTorch provides device memory (the solve workspace, operand tensors) and the
+CUDA stream; every step of the transport solve runs in libiobm.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+@dataclasses.dataclass
+class SolveResult:
+    energies: np.ndarray          # [nE]
+    G: np.ndarray                 # [nE] conductance (G_0), summed over solved incident channels
+    n_open: np.ndarray            # [nE]
+    T: np.ndarray                 # [nrhs][max_open]
+    R: np.ndarray                 # [nrhs][max_open]
+    energy_index: np.ndarray      # [nrhs]
+    channel: np.ndarray           # [nrhs]
+    status: np.ndarray            # [nrhs]
+    iterations: np.ndarray        # [nrhs]
+    replacements: np.ndarray      # [nrhs]
+    residual: np.ndarray          # [nrhs] FP64 ||b - A psi|| / ||b||
+    device_ms: float              # device time of the iteration phase
+    launches: int                 # kernel launches of the iteration phase
+    iterations_total: int
+
+    @property
+    def nrhs(self) -> int:
+        return len(self.status)
+
+    @property
+    def converged(self) -> bool:
+        return bool(np.all(self.status == _lib.IOBM_OK))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_options(**kw) -> _lib.Options:
+    lib = _lib.load()
+    o = _lib.Options()
+    lib.iobm_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": _lib.IOBM_FP64, "mixed": _lib.IOBM_MIXED}[v]
+        setattr(o, k, v)
+    return o
+
+
+def channels_host(nx, ny, hx, hy, hz, nf, E, max_out=None, want_sigma=False):
+    """Host-side channel tables of the library (no GPU needed): iobm_channels_host."""
+    lib = _lib.load()
+    g = _lib.Grid(nx, ny, 2 * nf + 1, hx, hy, hz, nf)
+    n = C.c_int(0)
+    if max_out is None:
+        check(lib.iobm_channels_host(C.byref(g), E, C.byref(n), 0, None, None, None, None, None,
+                                     None))
+        max_out = n.value
+    nu = np.zeros((max(max_out, 1), 2), np.int32)
+    vel = np.zeros(max(max_out, 1))
+    lam = np.zeros((max(max_out, 1), 2))
+    bt = np.zeros((max(max_out, 1), nf, 2))
+    mrow = np.zeros((max(max_out, 1), nf, 2))
+    sig = np.zeros((ny, nx, nf, nf, 2)) if want_sigma else None
+    check(lib.iobm_channels_host(C.byref(g), E, C.byref(n), max_out, _ptr(nu), _ptr(vel),
+                                 _ptr(lam), _ptr(bt), _ptr(mrow),
+                                 _ptr(sig) if want_sigma else None))
+    k = n.value
+    out = dict(n_open=k, nu=nu[:k], vel=vel[:k], lam=lam[:k, 0] + 1j * lam[:k, 1],
+               btilde=bt[:k, :, 0] + 1j * bt[:k, :, 1], mrow=mrow[:k, :, 0] + 1j * mrow[:k, :, 1])
+    if want_sigma:
+        out["sigma"] = sig[..., 0] + 1j * sig[..., 1]
+    return out
+
+
+class IOBMSolver:
+    """One junction: iobm_create / iobm_solve / iobm_transmission / iobm_grad_V."""
+
+    def __init__(self, nx, ny, nz, hx, hy, hz, nf, V, rs, projectors=None, options=None,
+                 device="cuda", **option_kw):
+        self.lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("IOBMSolver needs a CUDA device")
+        self.device = torch.device(device)
+        self.shape = (nz, ny, nx)
+        self.nf = nf
+        self.grid = _lib.Grid(nx, ny, nz, hx, hy, hz, nf)
+        self.opts = options if options is not None else default_options(**option_kw)
+        V = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(nz, ny, nx))
+        self._keep = []
+        if projectors is not None:
+            row_ptr, idx, val, coupling = projectors
+            row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+            idx = np.ascontiguousarray(idx, np.int32)
+            val = np.ascontiguousarray(val, np.float64)
+            coupling = np.ascontiguousarray(coupling, np.float64)
+            self._keep += [row_ptr, idx, val, coupling]
+            proj = _lib.Projectors(len(coupling), row_ptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   idx.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   val.ctypes.data_as(C.POINTER(C.c_double)),
+                                   coupling.ctypes.data_as(C.POINTER(C.c_double)))
+            pproj = C.byref(proj)
+        else:
+            pproj = None
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            rc = self.lib.iobm_create(C.byref(self.grid), _ptr(V), pproj, float(rs),
+                                      C.byref(self.opts), C.c_void_p(stream), C.byref(h))
+        if rc != _lib.IOBM_OK:
+            msg = self.lib.iobm_last_error(h).decode() if h.value else ""
+            if h.value:
+                self.lib.iobm_destroy(h)
+            raise _lib.IOBMError(rc, self.lib.iobm_status_string(rc).decode() + ": " + msg)
+        self.h = h
+        self._ws = None
+
+    @classmethod
+    def from_junction(cls, jn, **kw):
+        proj = jn.projector_csr() if jn.projectors else None
+        return cls(jn.nx, jn.ny, jn.nz, jn.hx, jn.hy, jn.hz, jn.nf, jn.V, jn.rs, projectors=proj,
+                   **kw)
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            torch.cuda.synchronize(self.device)
+            self.lib.iobm_destroy(self.h)
+            self.h = C.c_void_p()
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- queries -------------------------------------------------------
+    @property
+    def fermi_energy(self) -> float:
+        return self.lib.iobm_fermi_energy(self.h)
+
+    def open_channels(self, E: float):
+        n = C.c_int(0)
+        check(self.lib.iobm_open_channels(self.h, float(E), C.byref(n), 0, None, None), self.h)
+        nu = np.zeros((max(n.value, 1), 2), np.int32)
+        vel = np.zeros(max(n.value, 1))
+        check(self.lib.iobm_open_channels(self.h, float(E), C.byref(n), n.value, _ptr(nu),
+                                          _ptr(vel)), self.h)
+        return nu[: n.value], vel[: n.value]
+
+    def workspace_size(self, nrhs: int) -> int:
+        b = C.c_size_t(0)
+        check(self.lib.iobm_workspace_size(self.h, int(nrhs), C.byref(b)), self.h)
+        return b.value
+
+    def _ensure_workspace(self, nrhs: int):
+        need = self.workspace_size(nrhs)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = None
+            self._ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        check(self.lib.iobm_set_workspace(self.h, C.c_void_p(self._ws.data_ptr()),
+                                          self._ws.numel()), self.h)
+
+    def _count_rhs(self, energies, channels):
+        n = 0
+        for E in energies:
+            k = self.open_channels(E)[0].shape[0]
+            n += k if channels is None else sum(1 for c in channels if 0 <= c < k)
+        return n
+
+    # ---- solves --------------------------------------------------------
+    def solve(self, energies: Sequence[float], channels: Optional[Sequence[int]] = None,
+              side: int = 0) -> SolveResult:
+        E = np.ascontiguousarray(np.atleast_1d(np.asarray(energies, np.float64)))
+        nrhs = self._count_rhs(E, channels)
+        self._ensure_workspace(max(nrhs, 1))
+        ch = None if channels is None else np.ascontiguousarray(channels, np.int32)
+        with torch.cuda.device(self.device):
+            check(self.lib.iobm_solve(self.h, _ptr(E), len(E), _ptr(ch) if ch is not None else None,
+                                      0 if ch is None else len(ch), int(side)), self.h)
+        return self.transmission(E)
+
+    def transmission(self, E) -> SolveResult:
+        nrhs = self.lib.iobm_num_rhs(self.h)
+        nE = len(E)
+        n_open = np.zeros(nE, np.int32)
+        G = np.zeros(nE)
+        max_open = max(1, max((self.open_channels(e)[0].shape[0] for e in E), default=1))
+        T = np.zeros((max(nrhs, 1), max_open))
+        R = np.zeros((max(nrhs, 1), max_open))
+        reps = (_lib.Report * max(nrhs, 1))()
+        check(self.lib.iobm_transmission(self.h, _ptr(T), _ptr(R), max_open, _ptr(G), _ptr(n_open),
+                                         reps), self.h)
+        ms = C.c_double(0)
+        la = C.c_longlong(0)
+        it = C.c_longlong(0)
+        self.lib.iobm_last_solve_stats(self.h, C.byref(ms), C.byref(la), C.byref(it))
+        rep = list(reps)[:nrhs]
+        return SolveResult(
+            energies=np.asarray(E), G=G, n_open=n_open, T=T[:nrhs], R=R[:nrhs],
+            energy_index=np.array([r.energy_index for r in rep], np.int32),
+            channel=np.array([r.channel for r in rep], np.int32),
+            status=np.array([r.status for r in rep], np.int32),
+            iterations=np.array([r.iterations for r in rep], np.int32),
+            replacements=np.array([r.replacements for r in rep], np.int32),
+            residual=np.array([r.residual for r in rep]),
+            device_ms=ms.value, launches=la.value, iterations_total=it.value)
+
+    def solution(self, rhs: int) -> torch.Tensor:
+        out = torch.empty(self.shape, dtype=torch.complex128, device=self.device)
+        check(self.lib.iobm_solution(self.h, int(rhs), C.c_void_p(out.data_ptr()), 1), self.h)
+        return out
+
+    def grad_V(self, E: float):
+        """(dG/dV as a [nz][ny][nx] float64 CUDA tensor, G) at energy E."""
+        n = self.open_channels(E)[0].shape[0]
+        self._ensure_workspace(max(2 * n, 1))
+        g = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        G = C.c_double(0)
+        with torch.cuda.device(self.device):
+            check(self.lib.iobm_grad_V(self.h, float(E), C.c_void_p(g.data_ptr()), 1, C.byref(G)),
+                  self.h)
+        return g, G.value
+
+    def set_potential(self, V):
+        if isinstance(V, torch.Tensor):
+            Vt = V.detach().to(device=self.device, dtype=torch.float64).contiguous()
+            torch.cuda.current_stream(self.device).synchronize()
+            check(self.lib.iobm_set_potential(self.h, C.c_void_p(Vt.data_ptr()), 1), self.h)
+        else:
+            Vn = np.ascontiguousarray(np.asarray(V, np.float64).reshape(self.shape))
+            check(self.lib.iobm_set_potential(self.h, _ptr(Vn), 0), self.h)
+
+    # ---- operator access -------------------------------------------------
+    def apply(self, E: float, x: torch.Tensor) -> torch.Tensor:
+        """y = (E - H_T - H~) x for x [nrhs][nz][ny][nx] complex64/complex128 on the device."""
+        x = x.contiguous()
+        elem = _lib.IOBM_ELEM_C64 if x.dtype == torch.complex128 else _lib.IOBM_ELEM_C32
+        if x.dtype not in (torch.complex64, torch.complex128):
+            raise TypeError("x must be complex64 or complex128")
+        nrhs = x.numel() // int(np.prod(self.shape))
+        y = torch.empty_like(x)
+        with torch.cuda.device(self.device):
+            check(self.lib.iobm_apply(self.h, float(E), elem, C.c_void_p(x.data_ptr()),
+                                      C.c_void_p(y.data_ptr()), nrhs), self.h)
+        return y
+
+    def apply_precond(self, x: torch.Tensor) -> torch.Tensor:
+        x = x.contiguous()
+        elem = _lib.IOBM_ELEM_C64 if x.dtype == torch.complex128 else _lib.IOBM_ELEM_C32
+        nrhs = x.numel() // int(np.prod(self.shape))
+        y = torch.empty_like(x)
+        with torch.cuda.device(self.device):
+            check(self.lib.iobm_apply_precond(self.h, elem, C.c_void_p(x.data_ptr()),
+                                              C.c_void_p(y.data_ptr()), nrhs), self.h)
+        return y

@@ -1,0 +1,39 @@
+"""The C-ABI library loads and exports every entry point include/iobm.h declares
+(no compute call: runs without a GPU)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "iobm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(iobm_[A-Za-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1009_5300_gb300 import build_library, load
+    build_library()
+    return load()
+
+
+def test_header_declares_the_core_calls():
+    names = declared_functions()
+    for core in ("iobm_create", "iobm_solve", "iobm_transmission", "iobm_grad_V", "iobm_destroy"):
+        assert core in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1009_5300_gb300._lib import SIGNATURES
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in SIGNATURES, f"binding lacks {name}"
+
+
+def test_status_strings(lib):
+    for code in range(0, 10):
+        assert lib.iobm_status_string(code)

@@ -1,0 +1,93 @@
+"""GPU parity of the operator kernels against the oracle (called through the C ABI).
+
+(E - H_T - H~) x: the z-marching FD stencil + local potential, the KB term and
+the self-energy applied with lateral FFTs in clusters of N_f CTAs; P x: the
+preconditioner of Eq. 10.  Sizes span several lateral tiles and z-chunks with
+ragged tails."""
+import numpy as np
+import pytest
+import torch
+
+import iobm_synth as S
+from oracle import modes, operator
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1009_5300_gb300 import build_library
+    build_library()
+
+
+def make(nx, ny, nz, nf, kb, h=0.45, seed=3):
+    natom = 2 if nz >= 30 else 1
+    return S.small_wire(nx=nx, ny=ny, nz=nz, h=h, natom=natom, spacing=3.0, depth=0.7, width=1.0,
+                        rs=2.0, kb_kinds=S.SP if kb else None, nf=nf, seed=seed)
+
+
+CASES = [
+    (40, 12, 70, 4, True),     # 2 x 2 tiles with ragged x/y tails, 3 z-chunks (ragged)
+    (6, 5, 9, 1, False),       # N_f = 1, one partial tile, odd lateral sizes
+    (48, 48, 40, 4, True),     # the 48 x 48 lateral plane of the wire workload
+    (25, 27, 36, 2, False),    # radix-5 and radix-3 FFTs, N_f = 2
+    (64, 64, 12, 3, False),    # largest supported plane
+]
+
+
+@pytest.mark.parametrize("nx,ny,nz,nf,kb", CASES)
+def test_apply_matches_oracle(nx, ny, nz, nf, kb):
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = make(nx, ny, nz, nf, kb)
+    E = jn.e_fermi + 0.013
+    sol = IOBMSolver.from_junction(jn, precision="fp64")
+    md = modes.mode_data(nx, ny, jn.hx, jn.hy, jn.hz, nf, E)
+    nrhs = 3
+    x = np.stack([S.random_field((nz, ny, nx), 100 + i) for i in range(nrhs)])
+    ref = np.stack([operator.apply_A(jn, E, md, x[i]) for i in range(nrhs)])
+    xd = torch.from_numpy(x).cuda()
+    y64 = sol.apply(E, xd).cpu().numpy()
+    err64 = np.max(np.abs(y64 - ref)) / np.max(np.abs(ref))
+    assert err64 < 1e-12, err64
+    y32 = sol.apply(E, xd.to(torch.complex64)).cpu().numpy()
+    err32 = np.max(np.abs(y32 - ref)) / np.max(np.abs(ref))
+    assert err32 < 2e-5, err32
+    sol.close()
+
+
+@pytest.mark.parametrize("nx,ny,nz,nf,kb", CASES[:3])
+def test_precond_matches_oracle(nx, ny, nz, nf, kb):
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = make(nx, ny, nz, nf, kb)
+    for alpha in (1.8, 3.0):
+        sol = IOBMSolver.from_junction(jn, precision="fp64", alpha=alpha)
+        x = np.stack([S.random_field((nz, ny, nx), 7 + i) for i in range(2)])
+        ref = np.stack([operator.apply_P(jn, alpha, x[i]) for i in range(2)])
+        y = sol.apply_precond(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert np.max(np.abs(y - ref)) < 1e-13 * np.max(np.abs(ref))
+        y32 = sol.apply_precond(torch.from_numpy(x).cuda().to(torch.complex64)).cpu().numpy()
+        assert np.max(np.abs(y32 - ref)) < 1e-6 * np.max(np.abs(ref))
+        sol.close()
+
+
+def test_projector_on_end_planes_rejected():
+    from paper_1009_5300_gb300 import IOBMSolver
+    from paper_1009_5300_gb300._lib import IOBMError, IOBM_E_PROJ_BOUNDARY
+    jn = make(12, 12, 30, 4, True)
+    p = jn.projectors[0]
+    bad = S.Projector(idx=np.array([5], np.int32), val=np.array([1.0]), coupling=0.1, atom=0)
+    jn2 = jn.copy_with(projectors=[p, bad])
+    with pytest.raises(IOBMError) as ei:
+        IOBMSolver.from_junction(jn2)
+    assert ei.value.code == IOBM_E_PROJ_BOUNDARY
+
+
+def test_nonfinite_potential_rejected():
+    from paper_1009_5300_gb300 import IOBMSolver
+    from paper_1009_5300_gb300._lib import IOBMError, IOBM_E_ARG
+    jn = make(8, 8, 12, 1, False)
+    V = jn.V.copy()
+    V[3, 2, 1] = np.nan
+    with pytest.raises(IOBMError) as ei:
+        IOBMSolver.from_junction(jn.copy_with(V=V))
+    assert ei.value.code == IOBM_E_ARG

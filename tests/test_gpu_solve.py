@@ -1,0 +1,146 @@
+"""GPU solves against the oracle's exact (sparse-LU) solutions, through the C ABI.
+
+Bar: conductance within 1e-6 G_0 of the oracle, every T and R entry within
+1e-6, FP64 relative residual <= 1e-8 for every RHS, in both the plain FP64
+solver and the mixed FP32/FP64 solver."""
+import numpy as np
+import pytest
+import torch
+
+import iobm_synth as S
+from oracle import operator, transport
+
+pytestmark = pytest.mark.gpu
+
+G_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1009_5300_gb300 import build_library
+    build_library()
+
+
+def kb_junction(nf=4):
+    return S.small_wire(nx=12, ny=12, nz=26, h=0.5, natom=2, spacing=3.4, depth=0.7, width=0.9,
+                        rs=1.6, kb_kinds=S.SP, nf=nf, seed=77)
+
+
+def compare(res, sol_or, tol=G_TOL):
+    n = sol_or.n_open
+    assert res.n_open[0] == n
+    assert np.all(res.status == 0), res.status
+    assert np.all(res.residual <= 1e-8), res.residual
+    T = res.T[:, :n].T          # [out][in]
+    R = res.R[:, :n].T
+    assert np.max(np.abs(T - sol_or.T)) < tol
+    assert np.max(np.abs(R - sol_or.R)) < tol
+    assert abs(res.G[0] - sol_or.G) < tol
+
+
+@pytest.fixture(scope="module")
+def wire16_oracle():
+    jn = S.wire16()
+    return jn, transport.solve(jn, jn.energies[0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_wire16(wire16_oracle, precision):
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn, ref = wire16_oracle
+    sol = IOBMSolver.from_junction(jn, precision=precision)
+    res = sol.solve(jn.energies)
+    compare(res, ref)
+    # the solution itself against the oracle's
+    psi = sol.solution(0).cpu().numpy()
+    assert np.max(np.abs(psi - ref.psi[0])) < 1e-6 * np.max(np.abs(ref.psi[0]))
+    sol.close()
+
+
+@pytest.mark.parametrize("nf", [1, 4])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multichannel_kb(nf, precision):
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = kb_junction(nf)
+    E = jn.e_fermi
+    ref = transport.solve(jn, E)
+    sol = IOBMSolver.from_junction(jn, precision=precision)
+    res = sol.solve([E])
+    assert ref.n_open >= 3
+    compare(res, ref)
+    # current conservation on the GPU result alone
+    assert np.max(np.abs(res.T.sum(1) + res.R.sum(1) - 1.0)) < 1e-6
+    sol.close()
+
+
+def test_right_incidence_and_reciprocity():
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = kb_junction(4)
+    E = jn.e_fermi - 0.02
+    refR = transport.solve(jn, E, side="R")
+    sol = IOBMSolver.from_junction(jn, precision="mixed")
+    resR = sol.solve([E], side=1)
+    compare(resR, refR)
+    resL = sol.solve([E], side=0)
+    assert abs(resL.G[0] - resR.G[0]) < 2 * G_TOL
+    sol.close()
+
+
+def test_flat_potential_integer_conductance():
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = S.small_wire(nx=12, ny=10, nz=20, h=0.6, natom=1, depth=0.0, rs=1.5, nf=4)
+    jn = jn.copy_with(V=np.zeros_like(jn.V))
+    sol = IOBMSolver.from_junction(jn, precision="mixed")
+    res = sol.solve([jn.e_fermi])
+    n = res.n_open[0]
+    assert n >= 3
+    assert abs(res.G[0] - n) < G_TOL
+    assert np.max(np.abs(res.T[:, :n] - np.eye(n))) < G_TOL
+    sol.close()
+
+
+def test_several_energies_and_batch_independence():
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = kb_junction(4)
+    Es = [jn.e_fermi - 0.05, jn.e_fermi, jn.e_fermi + 0.03]
+    sol = IOBMSolver.from_junction(jn, precision="mixed")
+    res = sol.solve(Es)
+    for e, E in enumerate(Es):
+        ref = transport.solve(jn, E)
+        assert abs(res.G[e] - ref.G) < G_TOL
+    # the same RHS solved alone gives bit-identical results
+    k = int(np.nonzero(res.energy_index == 1)[0][1])
+    single = sol.solve([Es[1]], channels=[int(res.channel[k])])
+    assert np.array_equal(single.T[0], res.T[k][: single.T.shape[1]])
+    assert single.iterations[0] == res.iterations[k]
+    sol.close()
+
+
+def test_gradient_matches_oracle_and_fd():
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = S.small_wire(nx=8, ny=8, nz=20, h=0.6, natom=2, spacing=3.0, depth=0.6, width=0.9,
+                      rs=1.4, kb_kinds=S.SP, nf=4, seed=5)
+    E = jn.e_fermi
+    ref = transport.grad_V(jn, E)
+    sol = IOBMSolver.from_junction(jn, precision="mixed")
+    g, G = sol.grad_V(E)
+    g = g.cpu().numpy()
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(g - ref)) < 1e-5 * scale
+    assert abs(G - transport.conductance(jn, E)) < G_TOL
+    sol.close()
+
+
+def test_autograd_function():
+    from paper_1009_5300_gb300 import IOBMSolver, conductance
+    jn = S.small_wire(nx=8, ny=8, nz=20, h=0.6, natom=2, spacing=3.0, depth=0.6, width=0.9,
+                      rs=1.4, nf=4, seed=9)
+    E = jn.e_fermi
+    sol = IOBMSolver.from_junction(jn, precision="mixed")
+    V = torch.tensor(jn.V, device="cuda", requires_grad=True)
+    G = conductance(V, sol, E)
+    G.backward()
+    ref = transport.grad_V(jn, E)
+    assert abs(G.item() - transport.conductance(jn, E)) < G_TOL
+    assert np.max(np.abs(V.grad.cpu().numpy() - ref)) < 1e-5 * np.max(np.abs(ref))
+    sol.close()
