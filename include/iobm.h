@@ -74,7 +74,7 @@ typedef struct iobm_handle iobm_handle;
  * (nz = N_z + 2).  nf is the FD half-width N_f of Eq. 1 (1 .. 4); the
  * self-energy then acts on the nf outermost planes at each end.  x and y
  * are periodic with period nx*hx and ny*hy.  nx and ny may only contain
- * prime factors <= 13 (lateral FFT radices). */
+ * the prime factors 2, 3 and 5 (lateral FFT radices), and nx*ny <= 4096. */
 typedef struct {
     int nx, ny, nz;
     double hx, hy, hz;
@@ -95,8 +95,15 @@ typedef struct {
     const double* coupling;
 } iobm_projectors;
 
-/* Solver options.  alpha: preconditioner parameter of Eq. 10 (C_0 = 1,
- * C_1 = exp(-alpha)); use_precond = 0 disables it.  tol: stop when
+/* Preconditioners (iobm_options.use_precond) */
+#define IOBM_PRECOND_NONE     0
+#define IOBM_PRECOND_EQ10     1  /* truncated Laplacian Green's function of Eq. 10           */
+#define IOBM_PRECOND_FOURIER  2  /* (E - T - H~)^{-1}: the potential-free Green's function,
+                                    diagonal in the lateral Fourier basis (Eq. 19) and
+                                    banded in z; applied with lateral FFTs (default)       */
+
+/* Solver options.  use_precond: one of IOBM_PRECOND_*.  alpha: parameter of
+ * Eq. 10 (C_0 = 1, C_1 = exp(-alpha)) for IOBM_PRECOND_EQ10.  tol: stop when
  * ||b - A psi||_2 / ||b||_2 <= tol, the residual evaluated in FP64.
  * max_iter: Krylov iteration limit per RHS.  refine_delta: in IOBM_MIXED the
  * FP64 residual replaces the FP32 recurrence residual whenever the latter has
@@ -124,7 +131,7 @@ typedef struct {
     double residual;    /* final ||b - A psi|| / ||b|| in FP64                */
 } iobm_report;
 
-/* Fill opts with the defaults: alpha 1.8, use_precond 1, tol 1e-8,
+/* Fill opts with the defaults: alpha 1.8, use_precond IOBM_PRECOND_FOURIER, tol 1e-8,
  * max_iter 20000, precision IOBM_MIXED, refine_delta 0.1, chunk 32. */
 void iobm_default_options(iobm_options* opts);
 
@@ -155,7 +162,15 @@ double iobm_fermi_energy(const iobm_handle* h);
  * max_out channels.  Eqs. 8.5-9 generalised to N_f (Appendix). */
 int iobm_open_channels(iobm_handle* h, double E, int* n_open, int max_out, int* nu, double* vel);
 
-/* Workspace: bytes of device memory a solve of nrhs right-hand sides needs
+/* Number of internal right-hand sides iobm_solve will run for these
+ * arguments.  An incident wave exp(i G.r) with G != 0 would make the
+ * unconjugated COCG form b^T P b vanish, so the solver runs the real lateral
+ * profiles cos(G.r) and sin(G.r) of each +-G channel pair and recombines them
+ * (two internal RHS per pair, one for a self-conjugate G). */
+int iobm_solve_rhs_count(iobm_handle* h, const double* E, int nE, const int* channels, int nch,
+                         int* n_internal);
+
+/* Workspace: bytes of device memory a solve of nrhs internal right-hand sides needs
  * at the handle's precision, and attach caller memory (256-byte aligned,
  * kept by the handle until replaced or destroyed; the caller must keep it
  * alive).  Passing NULL detaches it. */
@@ -171,7 +186,7 @@ int iobm_set_workspace(iobm_handle* h, void* dev_ptr, size_t bytes);
  * when the batch ran (check iobm_report for per-RHS convergence). */
 int iobm_solve(iobm_handle* h, const double* E, int nE, const int* channels, int nch, int side);
 
-/* Number of RHS of the last solve. */
+/* Number of incident channels (user-visible RHS) of the last solve. */
 int iobm_num_rhs(const iobm_handle* h);
 
 /* Transmission/reflection of the last solve (Eq. 6, Landauer-Buttiker of
@@ -201,9 +216,11 @@ int iobm_grad_V(iobm_handle* h, double E, double* dGdV, int dst_is_device, doubl
  * workspace for the projector scratch. */
 int iobm_apply(iobm_handle* h, double E, int elem, const void* x, void* y, int nrhs);
 
-/* y = P x with the preconditioner of Eq. 10 (six face neighbours, C_0 = 1,
- * C_1 = exp(-alpha), zero beyond the end planes). */
-int iobm_apply_precond(iobm_handle* h, int elem, const void* x, void* y, int nrhs);
+/* y = P x with the handle's preconditioner at energy E: Eq. 10 (six face
+ * neighbours, C_0 = 1, C_1 = exp(-alpha), zero beyond the end planes; E is
+ * then unused) or the lateral-Fourier free propagator (E - T - H~)^{-1}.
+ * Same buffer conventions as iobm_apply. */
+int iobm_apply_precond(iobm_handle* h, double E, int elem, const void* x, void* y, int nrhs);
 
 /* Replace the local potential V_loc ([nz][ny][nx], Ha; host or device
  * memory) of an existing handle, e.g. between the forward passes of a

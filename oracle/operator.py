@@ -24,6 +24,11 @@ applied through the explicit lateral Fourier sums of Eqs. 18-1/19 (dense DFT
 matrices, not an FFT) so that it also works at sizes where the dense
 real-space blocks do not fit.
 
+`free_inverse` applies (E - T - H~)^{-1}, the Green's function of the transition
+region with the potential removed (the quantity the paper's preconditioner of
+Eq. 10 approximates by a truncated Laplacian Green's function), by sparse LU of
+the assembled matrix.
+
 Pinned by: A == A^T exactly; the dense Eq. 8 block equals the Appendix
 surface Green's function (Eq. A-10) for N_f = 1; matrix-free and assembled forms
 agree; P's symbol bound (Sec. III, alpha > ln 6); tests/test_oracle_operator.py.
@@ -207,3 +212,12 @@ def P_matrix(jn, alpha: float) -> sp.csr_matrix:
     adj = (sp.kron(sp.kron(Iz, Iy), Ax) + sp.kron(sp.kron(Iz, Ay), Ix)
            + sp.kron(sp.kron(Az, Iy), Ix))
     return (sp.identity(jn.npts) + c1 * adj).tocsr()
+
+
+def free_inverse(jn, E: float, md: ModeData, r: np.ndarray) -> np.ndarray:
+    """z = (E - T - H~)^{-1} r: the operator of Eqs. 7, 7-2 with V = 0 and no KB term,
+    solved by sparse LU (r shaped [nz][ny][nx])."""
+    import scipy.sparse.linalg as spla
+    flat = jn.copy_with(V=np.zeros_like(jn.V), projectors=[])
+    A0 = assemble_A_local(flat, E, md)
+    return spla.spsolve(A0, np.asarray(r, dtype=np.complex128).reshape(-1)).reshape(r.shape)

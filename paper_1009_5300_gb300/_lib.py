@@ -25,6 +25,9 @@ IOBM_E_UNSUPPORTED = 9
 
 IOBM_FP64 = 0
 IOBM_MIXED = 1
+IOBM_PRECOND_NONE = 0
+IOBM_PRECOND_EQ10 = 1
+IOBM_PRECOND_FOURIER = 2
 IOBM_ELEM_C64 = 0
 IOBM_ELEM_C32 = 1
 
@@ -72,7 +75,10 @@ SIGNATURES = {
     "iobm_solution": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "iobm_grad_V": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_int, C.c_void_p]),
     "iobm_apply": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
-    "iobm_apply_precond": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "iobm_apply_precond": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                     C.c_int]),
+    "iobm_solve_rhs_count": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                       C.POINTER(C.c_int)]),
     "iobm_set_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "iobm_channels_host": (C.c_int, [C.POINTER(Grid), C.c_double, C.POINTER(C.c_int), C.c_int,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

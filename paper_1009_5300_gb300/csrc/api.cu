@@ -76,13 +76,17 @@ struct iobm_handle {
     DevBuf pptr, pidx, pval32, pval64, pcoup, uidx, uptr, uproj, uval32, uval64;
 
     // per-solve tables (handle owned)
-    DevBuf sig32, sig64, ediag, rhs_energy, descs, open_ptr, open_bins, proj_out;
-    DevBuf apply_sig32, apply_sig64, apply_ediag;
+    DevBuf sig32, sig64, pc32, pc64, ediag, rhs_energy, descs, open_ptr, open_bins, proj_out;
+    DevBuf apply_sig32, apply_sig64, apply_pc32, apply_pc64, apply_ediag;
     std::vector<ModeTables> energies;
-    std::vector<RhsDesc> hdesc;
-    std::vector<int> hrhs_energy, hrhs_chan;
+    std::vector<RhsDesc> hdesc;          // internal (real-profile) RHS
+    std::vector<int> hrhs_energy;        // per internal RHS
+    struct User {                        // one incident channel: psi = x[ic] + sign i x[is]
+        int energy, chan, side, ic, is, sign;
+    };
+    std::vector<User> users;
     int side = 0;
-    int nrhs = 0;
+    int nrhs = 0;                        // internal RHS
     int max_open = 0;
 
     // workspace
@@ -135,9 +139,19 @@ int cuda_fail(iobm_handle* h, cudaError_t e, const char* where) {
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
+// Internal (real-profile) RHS are solved to tol / sqrt(2): an incident channel
+// psi = x_c +- i x_s then has ||b - A psi|| <= ||r_c|| + ||r_s|| <= tol ||b||
+// because ||b||^2 = ||b_c||^2 + ||b_s||^2 (cos and sin profiles are orthogonal).
+double internal_tol2(const iobm_handle* h) { return 0.5 * h->opt.tol * h->opt.tol; }
+
 int slots_for(const iobm_handle* h) {
     const int ns = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk);
-    return std::max(ns + 2 * h->nf + 1, 64);
+    return std::max(std::max(ns + 2 * h->nf + 1, 64), h->g.nz);
+}
+
+// number of rho / |r|^2 partial slots the preconditioner pass writes
+int rho_slots(const iobm_handle* h) {
+    return h->opt.use_precond == IOBM_PRECOND_FOURIER ? h->g.nz : h->ns_stencil;
 }
 
 size_t workspace_bytes(const iobm_handle* h, int nrhs, int prec) {
@@ -227,13 +241,35 @@ StencilArgs<T> precond_args(const iobm_handle* h) {
     a.ny = h->g.ny;
     a.nz = h->g.nz;
     a.nf = 1;
-    const double c1 = h->opt.use_precond ? std::exp(-h->opt.alpha) : 0.0;
+    const double c1 = h->opt.use_precond == IOBM_PRECOND_EQ10 ? std::exp(-h->opt.alpha) : 0.0;
     a.cx[1] = a.cy[1] = a.cz[1] = (T)c1;
     a.c0 = (T)1;
     a.vsign = (T)0;
     a.V = nullptr;
     a.npts = h->npts;
     a.zchunk = kZChunk;
+    a.mask = M_ALL;
+    return a;
+}
+
+template <typename T>
+PrecondArgs<T> fourier_args(const iobm_handle* h, const void* pc) {
+    PrecondArgs<T> a{};
+    a.nx = h->g.nx;
+    a.ny = h->g.ny;
+    a.nz = h->g.nz;
+    a.nf = h->nf;
+    a.ax = h->ax;
+    a.ay = h->ay;
+    a.pc = (const typename Cplx<T>::type*)pc;
+    if (std::is_same<T, float>::value) {
+        a.twx = (const typename Cplx<T>::type*)h->twx32.p;
+        a.twy = (const typename Cplx<T>::type*)h->twy32.p;
+    } else {
+        a.twx = (const typename Cplx<T>::type*)h->twx64.p;
+        a.twy = (const typename Cplx<T>::type*)h->twy64.p;
+    }
+    a.npts = h->npts;
     a.mask = M_ALL;
     return a;
 }
@@ -317,6 +353,21 @@ int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void*
 template <typename T>
 int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) {
     using C = typename Cplx<T>::type;
+    if (h->opt.use_precond == IOBM_PRECOND_FOURIER) {
+        PrecondArgs<T> f = fourier_args<T>(h, std::is_same<T, float>::value ? h->pc32.p : h->pc64.p);
+        f.r = (const C*)h->vr;
+        f.spec = (C*)h->vz;
+        f.z = (C*)h->vz;
+        f.rhs_energy = h->rhs_energy.as<int>();
+        f.state = h->st;
+        f.mask = mask;
+        f.dot_part = h->rho_part;
+        f.nrm_part = h->rr_part;
+        f.slot_stride = h->slot_stride;
+        CK(launch_precond_fourier<T>(f, nrhs, h->stream));
+        launches += 3;
+        return IOBM_OK;
+    }
     StencilArgs<T> a = precond_args<T>(h);
     a.x = (const C*)h->vr;
     a.y = (C*)h->vz;
@@ -332,20 +383,22 @@ int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) 
     return IOBM_OK;
 }
 
-// One COCG iteration for every ACTIVE RHS; reads p[cur], writes p[1-cur].
+// One COCG iteration for every ACTIVE RHS.  Each RHS keeps its current
+// direction in one of two buffers (RhsState::pbuf), so RHS that pause for an
+// FP64 residual replacement resume with their own direction.
 template <typename T>
-int cocg_iteration(iobm_handle* h, int nrhs, int cur, bool mixed, long long& launches) {
+int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches) {
     using C = typename Cplx<T>::type;
-    const double tol2 = h->opt.tol * h->opt.tol;
+    const double tol2 = internal_tol2(h);
     const double delta2 = h->opt.refine_delta * h->opt.refine_delta;
     const int ns = h->ns_stencil;
-    CK(launch_beta(h->st, h->rho_part, h->rr_part, ns, h->slot_stride, nrhs, h->opt.max_iter, tol2,
-                   delta2, mixed ? 1 : 0, h->stream));
+    CK(launch_beta(h->st, h->rho_part, h->rr_part, rho_slots(h), h->slot_stride, nrhs,
+                   h->opt.max_iter, tol2, delta2, mixed ? 1 : 0, h->stream));
     const void* sig = std::is_same<T, float>::value ? h->sig32.p : h->sig64.p;
     StencilArgs<T> a = op_args<T>(h);
     a.x = (const C*)h->vz;
-    a.pold = (const C*)h->vp[cur];
-    a.pout = (C*)h->vp[1 - cur];
+    a.pbufs[0] = (C*)h->vp[0];
+    a.pbufs[1] = (C*)h->vp[1];
     a.y = (C*)h->vq;
     a.fused_p = 1;
     a.ediag = h->ediag.as<double>();
@@ -359,7 +412,8 @@ int cocg_iteration(iobm_handle* h, int nrhs, int cur, bool mixed, long long& lau
     a.slot_base = 0;
     CK(launch_stencil<T>(a, nrhs, h->stream));
     SigmaArgs<T> s = sigma_args<T>(h, sig);
-    s.x = (const C*)h->vp[1 - cur];
+    s.pnew[0] = (const C*)h->vp[0];
+    s.pnew[1] = (const C*)h->vp[1];
     s.y = (C*)h->vq;
     s.rhs_energy = h->rhs_energy.as<int>();
     s.state = h->st;
@@ -372,7 +426,8 @@ int cocg_iteration(iobm_handle* h, int nrhs, int cur, bool mixed, long long& lau
     launches += 3;
     if (h->pt.nproj > 0) {
         KbArgs<T> k = kb_args<T>(h);
-        k.x = (const C*)h->vp[1 - cur];
+        k.pnew[0] = (const C*)h->vp[0];
+        k.pnew[1] = (const C*)h->vp[1];
         k.y = (C*)h->vq;
         k.state = h->st;
         k.mask = M_ACTIVE;
@@ -384,8 +439,9 @@ int cocg_iteration(iobm_handle* h, int nrhs, int cur, bool mixed, long long& lau
         launches += 1;
     }
     CK(launch_alpha(h->st, h->mu_part, nslots_mu, h->slot_stride, nrhs, h->stream));
-    CK(launch_axpy_update<T>((C*)h->vx, (C*)h->vr, (const C*)h->vp[1 - cur], (const C*)h->vq, h->st,
-                             M_ACTIVE, h->npts, nrhs, h->stream));
+    C* pb[2] = {(C*)h->vp[0], (C*)h->vp[1]};
+    CK(launch_axpy_update<T>((C*)h->vx, (C*)h->vr, pb, (const C*)h->vq, h->st, M_ACTIVE, h->npts,
+                             nrhs, h->stream));
     launches += 2;
     return apply_precond_dots<T>(h, nrhs, M_ACTIVE, launches);
 }
@@ -405,8 +461,7 @@ int residual_replacement(iobm_handle* h, int nrhs, int mask, bool mixed, long lo
     CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
                           h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, h->st, mask,
                           h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
-    const double tol2 = h->opt.tol * h->opt.tol;
-    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, tol2, 0, h->stream));
+    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, internal_tol2(h), 0, h->stream));
     launches += 2;
     rc = apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
     if (rc) return rc;
@@ -441,15 +496,14 @@ int run_solver(iobm_handle* h, int nrhs) {
                               h->stream));
     launches += 1;
 
-    // capture one chunk of iterations (even length: p buffers return to p[0])
-    int chunk = std::max(2, h->opt.chunk);
-    if (chunk & 1) ++chunk;
+    // capture one chunk of iterations
+    const int chunk = std::max(1, h->opt.chunk);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long per_chunk = 0;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int it = 0; it < chunk; ++it) {
-        rc = cocg_iteration<T>(h, nrhs, it & 1, mixed, per_chunk);
+        rc = cocg_iteration<T>(h, nrhs, mixed, per_chunk);
         if (rc) {
             cudaStreamEndCapture(h->stream, &graph);
             if (graph) cudaGraphDestroy(graph);
@@ -530,91 +584,102 @@ int run_solver(iobm_handle* h, int nrhs) {
     return IOBM_OK;
 }
 
-// Build the per-energy tables and RHS list for energies E[0..nE).
-// kind 0: incident channels (channels/nch), kind 1: forward + adjoint at one energy.
+// Build the per-energy tables and the internal RHS list for energies E[0..nE).
+// kind 0: incident channels (channels/nch) from `side`; kind 1: all forward
+// channels at one energy followed by the adjoint functionals of every channel.
+// An incident channel exp(i G.r) is run as the real profiles cos(G.r) and
+// sin(G.r) of its +-G pair (one profile for a self-conjugate G).
 int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, int nch, int side,
-                int kind) {
+                int kind, bool upload_tables = true) {
     h->energies.clear();
     h->hdesc.clear();
     h->hrhs_energy.clear();
-    h->hrhs_chan.clear();
+    h->users.clear();
     h->side = side;
     const int nf = h->nf;
-    std::vector<std::complex<double>> sig_all;
+    std::vector<std::complex<double>> sig_all, pc_all;
+    auto add_desc = [&](int e, const ModeTables& mt, int q, int side_, int profile,
+                        const std::complex<double>* coef, double scale) {
+        RhsDesc d{};
+        d.energy = e;
+        d.kx = mt.open_kx[q];
+        d.ky = mt.open_ky[q];
+        d.side = side_;
+        d.profile = profile;
+        for (int k = 0; k < nf; ++k) d.coef[k] = make_double2(scale * coef[k].real(), scale * coef[k].imag());
+        h->hdesc.push_back(d);
+        h->hrhs_energy.push_back(e);
+        return (int)h->hdesc.size() - 1;
+    };
     for (int e = 0; e < nE; ++e) {
         ModeTables mt;
         std::string msg;
         if (!std::isfinite(E[e])) return fail(h, IOBM_E_ARG, "non-finite energy");
-        const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, nf, E[e], true,
-                                         mt, msg);
+        const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, nf, E[e],
+                                         upload_tables, mt, msg);
         if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
-        sig_all.insert(sig_all.end(), mt.sigma.begin(), mt.sigma.end());
-        if (kind == 0) {
-            std::vector<int> list;
-            if (!channels) {
-                for (int c = 0; c < mt.nopen; ++c) list.push_back(c);
-            } else {
-                for (int c = 0; c < nch; ++c)
-                    if (channels[c] >= 0 && channels[c] < mt.nopen) list.push_back(channels[c]);
-            }
-            for (int c : list) {
-                RhsDesc d{};
-                d.energy = e;
-                d.kx = mt.open_kx[c];
-                d.ky = mt.open_ky[c];
-                d.side = side;
-                d.sign = 1;
-                for (int k = 0; k < nf; ++k) {
-                    const auto b = mt.btilde[(size_t)c * nf + k];
-                    d.coef[k] = make_double2(b.real(), b.imag());
-                }
-                h->hdesc.push_back(d);
-                h->hrhs_energy.push_back(e);
-                h->hrhs_chan.push_back(c);
-            }
+        if (upload_tables) {
+            sig_all.insert(sig_all.end(), mt.sigma.begin(), mt.sigma.end());
+            pc_all.insert(pc_all.end(), mt.pc.begin(), mt.pc.end());
+        }
+        std::vector<int> list;
+        if (kind == 1 || !channels) {
+            for (int c = 0; c < mt.nopen; ++c) list.push_back(c);
         } else {
-            // forward waves, then adjoint functionals w_o on the exit planes
-            for (int c = 0; c < mt.nopen; ++c) {
-                RhsDesc d{};
-                d.energy = e;
-                d.kx = mt.open_kx[c];
-                d.ky = mt.open_ky[c];
-                d.side = 0;
-                d.sign = 1;
-                for (int k = 0; k < nf; ++k) {
-                    const auto b = mt.btilde[(size_t)c * nf + k];
-                    d.coef[k] = make_double2(b.real(), b.imag());
-                }
-                h->hdesc.push_back(d);
-                h->hrhs_energy.push_back(e);
-                h->hrhs_chan.push_back(c);
-            }
+            for (int c = 0; c < nch; ++c)
+                if (channels[c] >= 0 && channels[c] < mt.nopen &&
+                    std::find(list.begin(), list.end(), channels[c]) == list.end())
+                    list.push_back(channels[c]);
+        }
+        // pairs {q, partner(q)} with q the smaller index
+        std::vector<int> roots;
+        for (int c : list) {
+            const int q = std::min(c, mt.open_partner[c]);
+            if (std::find(roots.begin(), roots.end(), q) == roots.end()) roots.push_back(q);
+        }
+        std::sort(roots.begin(), roots.end());
+        const int fside = (kind == 1) ? 0 : side;
+        std::vector<int> icos(mt.nopen, -1), isin(mt.nopen, -1);
+        for (int q : roots) {
+            const std::complex<double>* b = &mt.btilde[(size_t)q * nf];
+            icos[q] = add_desc(e, mt, q, fside, PROF_COS, b, 1.0);
+            if (mt.open_partner[q] != q) isin[q] = add_desc(e, mt, q, fside, PROF_SIN, b, 1.0);
+        }
+        std::sort(list.begin(), list.end());
+        for (int c : list) {
+            const int q = std::min(c, mt.open_partner[c]);
+            iobm_handle::User u{};
+            u.energy = e;
+            u.chan = c;
+            u.side = fside;
+            u.ic = icos[q];
+            u.is = isin[q];
+            u.sign = (c == q) ? +1 : -1;
+            h->users.push_back(u);
+        }
+        if (kind == 1) {
+            // adjoint functionals w_o = mrow_o exp(-i G_o.r) / N_xy on the exit planes
             const double inv = 1.0 / h->nxy;
-            for (int c = 0; c < mt.nopen; ++c) {
-                RhsDesc d{};
-                d.energy = e;
-                d.kx = mt.open_kx[c];
-                d.ky = mt.open_ky[c];
-                d.side = 1;
-                d.sign = -1;
-                for (int k = 0; k < nf; ++k) {
-                    const auto m = mt.mrow[(size_t)c * nf + k] * inv;
-                    d.coef[k] = make_double2(m.real(), m.imag());
-                }
-                h->hdesc.push_back(d);
-                h->hrhs_energy.push_back(e);
-                h->hrhs_chan.push_back(c);
+            for (int q : roots) {
+                const std::complex<double>* m = &mt.mrow[(size_t)q * nf];
+                add_desc(e, mt, q, 1 - fside, PROF_COS, m, inv);
+                if (mt.open_partner[q] != q) add_desc(e, mt, q, 1 - fside, PROF_SIN, m, inv);
             }
         }
         h->energies.push_back(std::move(mt));
     }
     h->nrhs = (int)h->hdesc.size();
+    if (!upload_tables) return IOBM_OK;
     // device tables
-    std::vector<double2> s64(sig_all.size());
-    std::vector<float2> s32(sig_all.size());
+    std::vector<double2> s64(sig_all.size()), p64(pc_all.size());
+    std::vector<float2> s32(sig_all.size()), p32(pc_all.size());
     for (size_t i = 0; i < sig_all.size(); ++i) {
         s64[i] = make_double2(sig_all[i].real(), sig_all[i].imag());
         s32[i] = make_float2((float)sig_all[i].real(), (float)sig_all[i].imag());
+    }
+    for (size_t i = 0; i < pc_all.size(); ++i) {
+        p64[i] = make_double2(pc_all[i].real(), pc_all[i].imag());
+        p32[i] = make_float2((float)pc_all[i].real(), (float)pc_all[i].imag());
     }
     std::vector<double> ed(nE);
     std::vector<int> optr(nE + 1, 0);
@@ -629,6 +694,8 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
     }
     CK(upload(h->sig64, s64, h->stream));
     CK(upload(h->sig32, s32, h->stream));
+    CK(upload(h->pc64, p64, h->stream));
+    CK(upload(h->pc32, p32, h->stream));
     CK(upload(h->ediag, ed, h->stream));
     CK(upload(h->rhs_energy, h->hrhs_energy, h->stream));
     CK(upload(h->descs, h->hdesc, h->stream));
@@ -658,32 +725,42 @@ int run_batch(iobm_handle* h) {
     return IOBM_OK;
 }
 
-// t and r of every RHS (host, FP64) from the projection sums.
+// t and r of every incident channel (host, FP64): combine the projection sums
+// of its real-profile solves, subtract the unit incident wave on the entry
+// planes, and apply the N_f x N_f projection row (Eq. 6).
 int compute_tr(iobm_handle* h, std::vector<std::complex<double>>& t,
                std::vector<std::complex<double>>& r) {
+    using cdd = std::complex<double>;
     const int nf = h->nf;
     const int mo = std::max(h->max_open, 1);
-    std::vector<double2> out((size_t)h->nrhs * mo * 2 * kMaxNf);
-    CK(cudaMemcpyAsync(out.data(), h->proj_out.p, sizeof(double2) * out.size(),
-                       cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    t.assign((size_t)h->nrhs * mo, 0.0);
-    r.assign((size_t)h->nrhs * mo, 0.0);
-    for (int i = 0; i < h->nrhs; ++i) {
-        const RhsDesc& D = h->hdesc[i];
-        const ModeTables& mt = h->energies[D.energy];
-        const int side = D.side;
-        const int c_in = h->hrhs_chan[i];
+    std::vector<double2> out((size_t)std::max(h->nrhs, 1) * mo * 2 * kMaxNf);
+    if (h->nrhs > 0) {
+        CK(cudaMemcpyAsync(out.data(), h->proj_out.p, sizeof(double2) * (size_t)h->nrhs * mo * 2 * kMaxNf,
+                           cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    const int nu = (int)h->users.size();
+    t.assign((size_t)std::max(nu, 1) * mo, 0.0);
+    r.assign((size_t)std::max(nu, 1) * mo, 0.0);
+    auto S = [&](int internal, int o, int side, int d) {
+        const double2 v = out[(((size_t)internal * mo + o) * 2 + side) * kMaxNf + d];
+        return cdd(v.x, v.y);
+    };
+    for (int i = 0; i < nu; ++i) {
+        const iobm_handle::User& U = h->users[i];
+        const ModeTables& mt = h->energies[U.energy];
+        const cdd ci = cdd(0.0, (double)U.sign);
         for (int o = 0; o < mt.nopen; ++o) {
-            const double2* S = &out[(((size_t)i * mo + o) * 2) * kMaxNf];
-            std::complex<double> tt = 0.0, rr = 0.0;
+            cdd tt = 0.0, rr = 0.0;
             for (int d = 0; d < nf; ++d) {
-                const double2 se = S[(1 - side) * kMaxNf + d];
-                const double2 sn = S[side * kMaxNf + d];
-                std::complex<double> entry(sn.x, sn.y);
-                if (o == c_in) entry -= std::pow(mt.lam_in[c_in], d);
-                tt += mt.mrow[(size_t)o * nf + d] * std::complex<double>(se.x, se.y);
-                rr += mt.mrow[(size_t)o * nf + d] * entry;
+                cdd se = S(U.ic, o, 1 - U.side, d), sn = S(U.ic, o, U.side, d);
+                if (U.is >= 0) {
+                    se += ci * S(U.is, o, 1 - U.side, d);
+                    sn += ci * S(U.is, o, U.side, d);
+                }
+                if (o == U.chan) sn -= std::pow(mt.lam_in[U.chan], d);
+                tt += mt.mrow[(size_t)o * nf + d] * se;
+                rr += mt.mrow[(size_t)o * nf + d] * sn;
             }
             t[(size_t)i * mo + o] = tt;
             r[(size_t)i * mo + o] = rr;
@@ -692,7 +769,7 @@ int compute_tr(iobm_handle* h, std::vector<std::complex<double>>& t,
     return IOBM_OK;
 }
 
-int status_of(const RhsState& S) {
+int status_of_internal(const RhsState& S) {
     switch (S.status) {
         case ST_CONVERGED: return IOBM_OK;
         case ST_BREAKDOWN: return IOBM_E_BREAKDOWN;
@@ -708,7 +785,7 @@ extern "C" {
 void iobm_default_options(iobm_options* o) {
     if (!o) return;
     o->alpha = 1.8;
-    o->use_precond = 1;
+    o->use_precond = IOBM_PRECOND_FOURIER;
     o->tol = 1e-8;
     o->max_iter = 20000;
     o->precision = IOBM_MIXED;
@@ -761,7 +838,8 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
         return bad(IOBM_E_ARG, "grid sizes or spacings out of range (need nf in 1..4, nz >= 2 nf + 1)");
     if (!(rs > 0)) return bad(IOBM_E_ARG, "rs must be positive");
     if (!(h->opt.tol > 0) || h->opt.max_iter < 1 || !(h->opt.refine_delta > 0 && h->opt.refine_delta < 1) ||
-        (h->opt.precision != IOBM_FP64 && h->opt.precision != IOBM_MIXED) || !(h->opt.alpha > 0))
+        (h->opt.precision != IOBM_FP64 && h->opt.precision != IOBM_MIXED) || !(h->opt.alpha > 0) ||
+        h->opt.use_precond < IOBM_PRECOND_NONE || h->opt.use_precond > IOBM_PRECOND_FOURIER)
         return bad(IOBM_E_ARG, "invalid solver options");
     h->nxy = g.nx * g.ny;
     h->npts = (long long)h->nxy * g.nz;
@@ -769,6 +847,8 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     if (h->nxy > 4096)
         return bad(IOBM_E_UNSUPPORTED, "lateral planes above 4096 points are not supported by the "
                                        "shared-memory FFT of this build");
+    if (g.nz < 2 * g.nf + 2)
+        return bad(IOBM_E_ARG, "need at least 2 nf + 2 planes");
     std::vector<int> rx, ry;
     if (!fft_plan(g.nx, rx) || !fft_plan(g.ny, ry))
         return bad(IOBM_E_UNSUPPORTED, "lateral sizes must have prime factors <= 13");
@@ -795,6 +875,7 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t1);
     if (e == cudaSuccess) e = sigma_prepare();
+    if (e == cudaSuccess) e = precond_prepare();
     if (e != cudaSuccess) return bad(IOBM_E_CUDA, std::string("stream/event setup: ") + cudaGetErrorString(e));
 
     std::vector<float> v32(h->npts);
@@ -838,9 +919,10 @@ void iobm_destroy(iobm_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     DevBuf* bufs[] = {&h->V32, &h->V64, &h->twx32, &h->twy32, &h->twx64, &h->twy64, &h->phx,
                       &h->phy, &h->pptr, &h->pidx, &h->pval32, &h->pval64, &h->pcoup, &h->uidx,
-                      &h->uptr, &h->uproj, &h->uval32, &h->uval64, &h->sig32, &h->sig64, &h->ediag,
-                      &h->rhs_energy, &h->descs, &h->open_ptr, &h->open_bins, &h->proj_out,
-                      &h->apply_sig32, &h->apply_sig64, &h->apply_ediag, &h->ws_owned};
+                      &h->uptr, &h->uproj, &h->uval32, &h->uval64, &h->sig32, &h->sig64, &h->pc32,
+                      &h->pc64, &h->ediag, &h->rhs_energy, &h->descs, &h->open_ptr, &h->open_bins,
+                      &h->proj_out, &h->apply_sig32, &h->apply_sig64, &h->apply_pc32,
+                      &h->apply_pc64, &h->apply_ediag, &h->ws_owned};
     for (DevBuf* b : bufs) b->release();
     if (h->ev_sync) cudaEventDestroy(h->ev_sync);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
@@ -899,7 +981,17 @@ int iobm_solve(iobm_handle* h, const double* E, int nE, const int* channels, int
     return IOBM_OK;
 }
 
-int iobm_num_rhs(const iobm_handle* h) { return h ? h->nrhs : 0; }
+int iobm_num_rhs(const iobm_handle* h) { return h ? (int)h->users.size() : 0; }
+
+int iobm_solve_rhs_count(iobm_handle* h, const double* E, int nE, const int* channels, int nch,
+                         int* n_internal) {
+    if (!h || !E || nE < 1 || !n_internal) return IOBM_E_ARG;
+    const int rc = prepare_rhs(h, E, nE, channels, nch, 0, 0, false);
+    h->solved = false;
+    if (rc) return rc;
+    *n_internal = h->nrhs;
+    return IOBM_OK;
+}
 
 int iobm_transmission(iobm_handle* h, double* T, double* R, int max_open, double* G, int* nopen,
                       iobm_report* reports) {
@@ -908,42 +1000,48 @@ int iobm_transmission(iobm_handle* h, double* T, double* R, int max_open, double
     if ((T || R) && max_open < h->max_open)
         return fail(h, IOBM_E_ARG, "max_open is smaller than the largest open-channel count");
     std::vector<std::complex<double>> t, r;
-    if (h->nrhs > 0) {
-        const int rc = compute_tr(h, t, r);
-        if (rc) return rc;
-    }
+    const int rc = compute_tr(h, t, r);
+    if (rc) return rc;
     const int mo = std::max(h->max_open, 1);
     const int nE = (int)h->energies.size();
     if (G)
         for (int e = 0; e < nE; ++e) G[e] = 0.0;
     if (nopen)
         for (int e = 0; e < nE; ++e) nopen[e] = h->energies[e].nopen;
-    for (int i = 0; i < h->nrhs; ++i) {
-        const int e = h->hrhs_energy[i];
-        const ModeTables& mt = h->energies[e];
-        const double vin = mt.vel[h->hrhs_chan[i]];
+    for (size_t i = 0; i < h->users.size(); ++i) {
+        const iobm_handle::User& U = h->users[i];
+        const ModeTables& mt = h->energies[U.energy];
+        const double vin = mt.vel[U.chan];
         for (int o = 0; o < max_open && (T || R); ++o) {
             double Tv = 0.0, Rv = 0.0;
             if (o < mt.nopen) {
-                Tv = std::norm(t[(size_t)i * mo + o]) * mt.vel[o] / vin;
-                Rv = std::norm(r[(size_t)i * mo + o]) * mt.vel[o] / vin;
+                Tv = std::norm(t[i * mo + o]) * mt.vel[o] / vin;
+                Rv = std::norm(r[i * mo + o]) * mt.vel[o] / vin;
             }
-            if (T) T[(size_t)i * max_open + o] = Tv;
-            if (R) R[(size_t)i * max_open + o] = Rv;
+            if (T) T[i * max_open + o] = Tv;
+            if (R) R[i * max_open + o] = Rv;
         }
         if (G)
-            for (int o = 0; o < mt.nopen; ++o)
-                G[e] += std::norm(t[(size_t)i * mo + o]) * mt.vel[o] / vin;
+            for (int o = 0; o < mt.nopen; ++o) G[U.energy] += std::norm(t[i * mo + o]) * mt.vel[o] / vin;
         if (reports) {
-            const RhsState& S = h->hstate[i];
+            const RhsState& Sc = h->hstate[U.ic];
             iobm_report& rp = reports[i];
-            rp.energy_index = e;
-            rp.channel = h->hrhs_chan[i];
-            rp.side = h->hdesc[i].side;
-            rp.status = status_of(S);
-            rp.iterations = S.iters;
-            rp.replacements = S.replacements;
-            rp.residual = S.res64;
+            rp.energy_index = U.energy;
+            rp.channel = U.chan;
+            rp.side = U.side;
+            rp.status = status_of_internal(Sc);
+            rp.iterations = Sc.iters;
+            rp.replacements = Sc.replacements;
+            double num = Sc.res64 * std::sqrt(Sc.bb), den = Sc.bb;
+            if (U.is >= 0) {
+                const RhsState& Ss = h->hstate[U.is];
+                if (rp.status == IOBM_OK) rp.status = status_of_internal(Ss);
+                rp.iterations = std::max(rp.iterations, Ss.iters);
+                rp.replacements = std::max(rp.replacements, Ss.replacements);
+                num += Ss.res64 * std::sqrt(Ss.bb);
+                den += Ss.bb;
+            }
+            rp.residual = den > 0 ? num / std::sqrt(den) : 0.0;   // bound on ||b - A psi|| / ||b||
         }
     }
     return IOBM_OK;
@@ -951,55 +1049,84 @@ int iobm_transmission(iobm_handle* h, double* T, double* R, int max_open, double
 
 int iobm_solution(iobm_handle* h, int rhs, void* dst, int dst_is_device) {
     if (!h || !dst) return IOBM_E_ARG;
-    if (!h->solved || rhs < 0 || rhs >= h->nrhs) return fail(h, IOBM_E_STATE, "no such solved RHS");
+    if (!h->solved || rhs < 0 || rhs >= (int)h->users.size())
+        return fail(h, IOBM_E_STATE, "no such solved incident channel");
+    const iobm_handle::User& U = h->users[rhs];
     const size_t bytes = sizeof(double2) * h->npts;
-    CK(cudaMemcpyAsync(dst, h->x64 + (size_t)rhs * h->npts, bytes,
-                       dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    double2* tmp = h->y64;   // scratch of the last solve
+    CK(launch_combine(tmp, h->x64 + (size_t)U.ic * h->npts, make_double2(1.0, 0.0),
+                      U.is >= 0 ? h->x64 + (size_t)U.is * h->npts : nullptr,
+                      make_double2(0.0, (double)U.sign), h->npts, h->stream));
+    CK(cudaMemcpyAsync(dst, tmp, bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return IOBM_OK;
 }
 
 int iobm_grad_V(iobm_handle* h, double E, double* dGdV, int dst_is_device, double* G_out) {
+    using cdd = std::complex<double>;
     if (!h || !dGdV) return IOBM_E_ARG;
     if (cudaEventRecord(h->ev_sync, h->user_stream) == cudaSuccess)
         cudaStreamWaitEvent(h->stream, h->ev_sync, 0);
     int rc = prepare_rhs(h, &E, 1, nullptr, 0, 0, 1);
     if (rc) return rc;
-    rc = run_batch(h);
-    if (rc) return rc;
     const ModeTables& mt = h->energies[0];
     const int n = mt.nopen;
-    std::vector<std::complex<double>> t, r;
+    // forward internal RHS come first; count them
+    int nX = 0;
+    for (const iobm_handle::User& U : h->users) nX = std::max(nX, std::max(U.ic, U.is) + 1);
+    const int nY = h->nrhs - nX;
+    rc = run_batch(h);
+    if (rc) return rc;
+    std::vector<cdd> t, r;
     rc = compute_tr(h, t, r);
     if (rc) return rc;
     const int mo = std::max(h->max_open, 1);
-    std::vector<double2> C((size_t)std::max(n * n, 1));
+    // psi_i = sum_k B[i][k] X_k;  lambda_o = sum_j L[o][j] Y_j;  U = C B
+    std::vector<cdd> B((size_t)std::max(n, 1) * std::max(nX, 1), 0.0), Lm((size_t)std::max(n, 1) * std::max(nY, 1), 0.0);
+    for (int i = 0; i < n; ++i) {
+        const iobm_handle::User& U = h->users[i];
+        B[(size_t)i * nX + U.ic] = 1.0;
+        if (U.is >= 0) B[(size_t)i * nX + U.is] = cdd(0.0, (double)U.sign);
+        // adjoint of channel i: w ~ exp(-i G.r) = cos -+ i sin, the opposite sign
+        const int jc = U.ic, js = U.is;   // the adjoint list mirrors the forward one
+        Lm[(size_t)i * nY + jc] = 1.0;
+        if (js >= 0) Lm[(size_t)i * nY + js] = cdd(0.0, -(double)U.sign);
+    }
     double G = 0.0;
-    for (int o = 0; o < n; ++o)
-        for (int i = 0; i < n; ++i) {
-            const std::complex<double> toi = t[(size_t)i * mo + o];
-            const std::complex<double> c = (mt.vel[o] / mt.vel[i]) * std::conj(toi);
-            C[(size_t)o * n + i] = make_double2(c.real(), c.imag());
-            G += std::norm(toi) * mt.vel[o] / mt.vel[i];
+    std::vector<double2> Ud((size_t)std::max(n * nX, 1)), Ld((size_t)std::max(n * nY, 1));
+    for (int o = 0; o < n; ++o) {
+        for (int k = 0; k < nX; ++k) {
+            cdd acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const cdd toi = t[(size_t)i * mo + o];
+                acc += (mt.vel[o] / mt.vel[i]) * std::conj(toi) * B[(size_t)i * nX + k];
+            }
+            Ud[(size_t)o * nX + k] = make_double2(acc.real(), acc.imag());
         }
+        for (int j = 0; j < nY; ++j) Ld[(size_t)o * nY + j] = make_double2(Lm[(size_t)o * nY + j].real(), Lm[(size_t)o * nY + j].imag());
+        for (int i = 0; i < n; ++i) G += std::norm(t[(size_t)i * mo + o]) * mt.vel[o] / mt.vel[i];
+    }
     if (G_out) *G_out = G;
-    DevBuf dC, dg;
-    CK(upload(dC, C, h->stream));
+    DevBuf dU, dL, dg;
+    CK(upload(dU, Ud, h->stream));
+    CK(upload(dL, Ld, h->stream));
     double* gdev = dGdV;
     if (!dst_is_device) {
         CK(dg.ensure(sizeof(double) * h->npts));
         gdev = dg.as<double>();
     }
     if (n > 0) {
-        CK(launch_gradient(h->x64, n, h->x64 + (size_t)n * h->npts, n, dC.as<double2>(), h->npts, gdev,
-                           h->stream));
+        CK(launch_gradient(h->x64, nX, h->x64 + (size_t)nX * h->npts, nY, dU.as<double2>(),
+                           dL.as<double2>(), n, h->npts, gdev, h->stream));
     } else {
         CK(cudaMemsetAsync(gdev, 0, sizeof(double) * h->npts, h->stream));
     }
     if (!dst_is_device)
         CK(cudaMemcpyAsync(dGdV, gdev, sizeof(double) * h->npts, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    dC.release();
+    dU.release();
+    dL.release();
     dg.release();
     CK(cudaEventRecord(h->ev_sync, h->stream));
     CK(cudaStreamWaitEvent(h->user_stream, h->ev_sync, 0));
@@ -1014,8 +1141,46 @@ static int apply_common(iobm_handle* h, double E, int elem, const void* x, void*
     if (cudaEventRecord(h->ev_sync, h->user_stream) == cudaSuccess)
         cudaStreamWaitEvent(h->stream, h->ev_sync, 0);
     long long launches = 0;
+    const bool need_tables = !precond || h->opt.use_precond == IOBM_PRECOND_FOURIER;
+    if (need_tables) {
+        ModeTables mt;
+        std::string msg;
+        const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, h->nf, E, true,
+                                         mt, msg);
+        if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
+        std::vector<double2> s64(mt.sigma.size()), p64(mt.pc.size());
+        std::vector<float2> s32(mt.sigma.size()), p32(mt.pc.size());
+        for (size_t i = 0; i < mt.sigma.size(); ++i) {
+            s64[i] = make_double2(mt.sigma[i].real(), mt.sigma[i].imag());
+            s32[i] = make_float2((float)s64[i].x, (float)s64[i].y);
+        }
+        for (size_t i = 0; i < mt.pc.size(); ++i) {
+            p64[i] = make_double2(mt.pc[i].real(), mt.pc[i].imag());
+            p32[i] = make_float2((float)p64[i].x, (float)p64[i].y);
+        }
+        std::vector<double> ed(1, E);
+        CK(upload(h->apply_sig64, s64, h->stream));
+        CK(upload(h->apply_sig32, s32, h->stream));
+        CK(upload(h->apply_pc64, p64, h->stream));
+        CK(upload(h->apply_pc32, p32, h->stream));
+        CK(upload(h->apply_ediag, ed, h->stream));
+    }
     if (precond) {
-        if (elem == IOBM_ELEM_C64) {
+        if (h->opt.use_precond == IOBM_PRECOND_FOURIER) {
+            if (elem == IOBM_ELEM_C64) {
+                PrecondArgs<double> f = fourier_args<double>(h, h->apply_pc64.p);
+                f.r = (const double2*)x;
+                f.spec = (double2*)y;
+                f.z = (double2*)y;
+                CK(launch_precond_fourier<double>(f, nrhs, h->stream));
+            } else {
+                PrecondArgs<float> f = fourier_args<float>(h, h->apply_pc32.p);
+                f.r = (const float2*)x;
+                f.spec = (float2*)y;
+                f.z = (float2*)y;
+                CK(launch_precond_fourier<float>(f, nrhs, h->stream));
+            }
+        } else if (elem == IOBM_ELEM_C64) {
             StencilArgs<double> a = precond_args<double>(h);
             a.x = (const double2*)x;
             a.y = (double2*)y;
@@ -1027,21 +1192,6 @@ static int apply_common(iobm_handle* h, double E, int elem, const void* x, void*
             CK(launch_stencil<float>(a, nrhs, h->stream));
         }
     } else {
-        ModeTables mt;
-        std::string msg;
-        const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, h->nf, E, true,
-                                         mt, msg);
-        if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
-        std::vector<double2> s64(mt.sigma.size());
-        std::vector<float2> s32(mt.sigma.size());
-        for (size_t i = 0; i < mt.sigma.size(); ++i) {
-            s64[i] = make_double2(mt.sigma[i].real(), mt.sigma[i].imag());
-            s32[i] = make_float2((float)s64[i].x, (float)s64[i].y);
-        }
-        std::vector<double> ed(1, E);
-        CK(upload(h->apply_sig64, s64, h->stream));
-        CK(upload(h->apply_sig32, s32, h->stream));
-        CK(upload(h->apply_ediag, ed, h->stream));
         int rc2;
         if (elem == IOBM_ELEM_C64)
             rc2 = apply_operator<double>(h, x, y, nrhs, h->apply_sig64.p, h->apply_ediag.as<double>(),
@@ -1061,8 +1211,8 @@ int iobm_apply(iobm_handle* h, double E, int elem, const void* x, void* y, int n
     return apply_common(h, E, elem, x, y, nrhs, false);
 }
 
-int iobm_apply_precond(iobm_handle* h, int elem, const void* x, void* y, int nrhs) {
-    return apply_common(h, 0.0, elem, x, y, nrhs, true);
+int iobm_apply_precond(iobm_handle* h, double E, int elem, const void* x, void* y, int nrhs) {
+    return apply_common(h, E, elem, x, y, nrhs, true);
 }
 
 int iobm_set_potential(iobm_handle* h, const double* V_loc, int src_is_device) {

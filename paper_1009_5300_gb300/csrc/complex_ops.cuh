@@ -43,6 +43,19 @@ template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) {
 }
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
 
+template <typename C> __device__ __forceinline__ C make_one();
+template <> __device__ __forceinline__ float2 make_one<float2>() { return make_float2(1.f, 0.f); }
+template <> __device__ __forceinline__ double2 make_one<double2>() { return make_double2(1.0, 0.0); }
+
+__device__ __forceinline__ float2 cdivc(float2 a, float2 b) {
+    const float den = b.x * b.x + b.y * b.y;
+    return make_float2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+__device__ __forceinline__ double2 cdivc(double2 a, double2 b) {
+    const double den = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
 

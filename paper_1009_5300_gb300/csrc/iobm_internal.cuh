@@ -16,7 +16,7 @@ namespace iobm {
 
 constexpr int kMaxNf = 4;          // FD half-width supported by the kernels
 constexpr int kMaxRadixPasses = 12;
-constexpr int kMaxRadix = 13;
+constexpr int kMaxRadix = 5;
 
 // ---- per-RHS solver status (device) ---------------------------------
 enum RhsStatusCode : int {
@@ -50,18 +50,30 @@ struct RhsState {
     int iters;
     int replacements;
     int first;          // 1: next direction update uses beta = 0
+    int pbuf;           // which of the two direction buffers holds the current p
+    int pad;
 };
 
-// Source / functional descriptor of one RHS: on the entry planes (depth d),
-// b(l, d) = coef[d] * exp(sign * i * G_mode . r_l).
+// Lateral profile of a source: f(l) for b(l, d) = coef[d] * f(l).
+enum Profile : int {
+    PROF_EXP_PLUS = 0,    // exp(+i G.r)
+    PROF_COS = 1,         // cos(G.r)
+    PROF_SIN = 2,         // sin(G.r)
+    PROF_EXP_MINUS = 3,   // exp(-i G.r)
+};
+
+// Source / functional descriptor of one RHS: on the N_f planes of one end
+// (depth d), b(l, d) = coef[d] * f(l) with f one of the profiles above.
 struct RhsDesc {
     int energy;
     int kx, ky;           // FFT bins of the lateral mode (nu mod N)
     int side;             // planes: 0 -> plane d, 1 -> plane nz-1-d
-    int sign;             // +1 or -1
+    int profile;
     int pad;
     double2 coef[kMaxNf];
 };
+
+
 
 // Lateral FFT plan of one axis
 struct FftAxis {
@@ -80,8 +92,8 @@ template <typename T>
 struct StencilArgs {
     using C = typename Cplx<T>::type;
     const C* x;            // operand (COCG: z, with p = z + beta p_old)
-    const C* pold;         // COCG: previous direction (read), may alias pout
-    C* pout;               // COCG: new direction (write)
+    C* pbufs[2];           // COCG: direction buffers; reads p_old = pbufs[pbuf] and
+                           // writes p = pbufs[1 - pbuf] (pbuf from the RHS state)
     C* y;                  // result
     const T* V;            // potential or nullptr
     int nx, ny, nz;
@@ -111,6 +123,7 @@ template <typename T>
 struct SigmaArgs {
     using C = typename Cplx<T>::type;
     const C* x;             // operand planes are read from here
+    const C* pnew[2];       // if set: operand = pnew[1 - pbuf] of the RHS (COCG direction)
     C* y;                   // y[end planes] -= Sigma x
     const C* sigma;         // [energy][ky][kx][nf][nf]
     const int* rhs_energy;
@@ -129,6 +142,7 @@ template <typename T>
 struct KbArgs {
     using C = typename Cplx<T>::type;
     const C* x;
+    const C* pnew[2];        // if set: operand = pnew[1 - pbuf] of the RHS (COCG direction)
     C* y;                    // y[support] -= V_NL x
     int nproj;
     const int* pptr;         // [nproj+1] projector CSR
@@ -148,6 +162,32 @@ struct KbArgs {
     long long npts;
 };
 
+constexpr int kPcStrideDev = 25;   // per-mode preconditioner table stride (nf = 4)
+
+template <typename T>
+struct PrecondArgs {
+    using C = typename Cplx<T>::type;
+    const C* r;              // operand
+    C* spec;                 // spectrum scratch (may alias z)
+    C* z;                    // result
+    const C* pc;             // [energy][ky][kx][kPcStrideDev]
+    const int* rhs_energy;
+    const RhsState* state;
+    int mask;
+    int nx, ny, nz, nf;
+    FftAxis ax, ay;
+    const C* twx;
+    const C* twy;
+    double2* dot_part;       // slot = plane
+    double* nrm_part;
+    int slot_stride;
+    long long npts;
+};
+
+template <typename T> cudaError_t launch_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s);
+template <typename T> size_t precond_smem_bytes(int nx, int ny);
+cudaError_t precond_prepare();
+
 // ---- launchers (defined in the .cu files) ----------------------------------
 
 template <typename T> cudaError_t launch_stencil(const StencilArgs<T>& a, int nrhs, cudaStream_t s);
@@ -163,11 +203,12 @@ cudaError_t launch_alpha(RhsState* st, const double2* mu_part, int nslots, int s
                          int nrhs, cudaStream_t s);
 cudaError_t launch_restart_scalars(RhsState* st, const double2* rho_part, const double* rr_part,
                                    int nslots, int slot_stride, int nrhs, cudaStream_t s);
+// x += alpha p, r -= alpha q with p = pbufs[pbuf] of each RHS
 template <typename T>
 cudaError_t launch_axpy_update(typename Cplx<T>::type* x, typename Cplx<T>::type* r,
-                               const typename Cplx<T>::type* p, const typename Cplx<T>::type* q,
-                               const RhsState* st, int mask, long long npts, int nrhs,
-                               cudaStream_t s);
+                               typename Cplx<T>::type* const* pbufs,
+                               const typename Cplx<T>::type* q, const RhsState* st, int mask,
+                               long long npts, int nrhs, cudaStream_t s);
 // x64 += x32; x32 = 0 (mixed-precision fold before the FP64 residual)
 cudaError_t launch_fold(double2* x64, float2* x32, const RhsState* st, int mask, long long npts,
                         int nrhs, cudaStream_t s);
@@ -185,8 +226,12 @@ cudaError_t launch_projection(const double2* psi, const RhsDesc* desc, const int
                               const int2* open_bins, const double2* phx, const double2* phy,
                               int nx, int ny, int nz, int nf, int max_open, double2* out,
                               int nrhs, cudaStream_t s);
-cudaError_t launch_gradient(const double2* psi, int n_in, const double2* lam, int n_out,
-                            const double2* C, long long npts, double* g, cudaStream_t s);
+// g(r) = 2 Re sum_o (sum_j L[o][j] Y_j(r)) (sum_k U[o][k] X_k(r))
+cudaError_t launch_gradient(const double2* X, int nX, const double2* Y, int nY, const double2* U,
+                            const double2* L, int n, long long npts, double* g, cudaStream_t s);
+// dst = c1 * x1 + c2 * x2 (x2 may be null)
+cudaError_t launch_combine(double2* dst, const double2* x1, double2 c1, const double2* x2,
+                           double2 c2, long long npts, cudaStream_t s);
 
 }  // namespace iobm
 

@@ -97,9 +97,6 @@ __device__ void fft_line(C* data, int stride, C* scratch, const FftAxis& ax,
             case 3: radix_pass<C, 3>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
             case 4: radix_pass<C, 4>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
             case 5: radix_pass<C, 5>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
-            case 7: radix_pass<C, 7>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
-            case 11: radix_pass<C, 11>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
-            case 13: radix_pass<C, 13>(src, ss, dst, ds, N, Ns, tw, inv, lane); break;
             default: break;   // plans only hold the radices above (checked on the host)
         }
         __syncwarp();
@@ -162,7 +159,8 @@ __global__ void __launch_bounds__(kSigmaMaxThreads) k_sigma(const SigmaArgs<T> a
 
     const int plane = (end == 0) ? d : (a.nz - 1 - d);
     const long long off = (long long)rhs * a.npts + (long long)plane * nxy;
-    const C* __restrict__ X = a.x + off;
+    const C* xb = a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x;
+    const C* __restrict__ X = xb + off;
     for (int i = threadIdx.x; i < nxy; i += blockDim.x) buf[i] = X[i];
     __syncthreads();
     fft2(buf, scratch, a.ax, a.ay, a.twx, a.twy, false);
@@ -255,7 +253,8 @@ __global__ void __launch_bounds__(256) k_kb(const KbArgs<T> a) {
     const int st = a.state ? a.state[rhs].status : ST_ACTIVE;
     if (!((1 << st) & a.mask)) return;
     const long long base = (long long)rhs * a.npts;
-    const C* __restrict__ X = a.x + base;
+    const C* xb = a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x;
+    const C* __restrict__ X = xb + base;
     C* __restrict__ Y = a.y + base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 

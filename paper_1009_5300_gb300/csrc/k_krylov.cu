@@ -68,6 +68,7 @@ __global__ void k_alpha(RhsState* st, const double2* mu_part, int nslots, int st
         S.status = ST_BREAKDOWN;
     } else {
         S.alpha = cdiv(S.rho, mu);
+        S.pbuf ^= 1;   // the direction written by this iteration becomes current
     }
     S.first = 0;
     st[i] = S;
@@ -105,13 +106,14 @@ cudaError_t launch_restart_scalars(RhsState* st, const double2* rho_part, const 
 template <typename T>
 __global__ void k_axpy_update(typename Cplx<T>::type* __restrict__ x,
                               typename Cplx<T>::type* __restrict__ r,
-                              const typename Cplx<T>::type* __restrict__ p,
+                              typename Cplx<T>::type* p0, typename Cplx<T>::type* p1,
                               const typename Cplx<T>::type* __restrict__ q,
                               const RhsState* st, int mask, long long npts) {
     using C = typename Cplx<T>::type;
     const int rhs = blockIdx.y;
     if (!((1 << st[rhs].status) & mask)) return;
     const C al = from_d2<C>(st[rhs].alpha);
+    const C* __restrict__ p = (st[rhs].pbuf & 1) ? p1 : p0;
     const long long base = (long long)rhs * npts;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts;
          i += (long long)gridDim.x * blockDim.x) {
@@ -129,16 +131,16 @@ static int vec_blocks(long long npts) {
 
 template <typename T>
 cudaError_t launch_axpy_update(typename Cplx<T>::type* x, typename Cplx<T>::type* r,
-                               const typename Cplx<T>::type* p, const typename Cplx<T>::type* q,
-                               const RhsState* st, int mask, long long npts, int nrhs,
-                               cudaStream_t s) {
+                               typename Cplx<T>::type* const* pbufs,
+                               const typename Cplx<T>::type* q, const RhsState* st, int mask,
+                               long long npts, int nrhs, cudaStream_t s) {
     dim3 grid(vec_blocks(npts), nrhs);
-    k_axpy_update<T><<<grid, 256, 0, s>>>(x, r, p, q, st, mask, npts);
+    k_axpy_update<T><<<grid, 256, 0, s>>>(x, r, pbufs[0], pbufs[1], q, st, mask, npts);
     return cudaGetLastError();
 }
-template cudaError_t launch_axpy_update<float>(float2*, float2*, const float2*, const float2*,
+template cudaError_t launch_axpy_update<float>(float2*, float2*, float2* const*, const float2*,
                                                const RhsState*, int, long long, int, cudaStream_t);
-template cudaError_t launch_axpy_update<double>(double2*, double2*, const double2*, const double2*,
+template cudaError_t launch_axpy_update<double>(double2*, double2*, double2* const*, const double2*,
                                                 const RhsState*, int, long long, int, cudaStream_t);
 
 __global__ void k_fold(double2* __restrict__ x64, float2* __restrict__ x32, const RhsState* st,
@@ -178,8 +180,13 @@ __device__ __forceinline__ double2 source_value(const RhsDesc& D, const double2*
     if (d < 0) return make_double2(0.0, 0.0);
     const double2 ex = phx[(int)(((long long)D.kx * ix) % nx)];
     const double2 ey = phy[(int)(((long long)D.ky * iy) % ny)];
-    double2 ph = cmul(ex, ey);
-    if (D.sign < 0) ph.y = -ph.y;
+    double2 ph = cmul(ex, ey);   // exp(+i G.r)
+    switch (D.profile) {
+        case PROF_COS: ph = make_double2(ph.x, 0.0); break;
+        case PROF_SIN: ph = make_double2(ph.y, 0.0); break;
+        case PROF_EXP_MINUS: ph.y = -ph.y; break;
+        default: break;
+    }
     return cmul(D.coef[d], ph);
 }
 
@@ -243,7 +250,7 @@ __global__ void k_check(RhsState* st, const double* rr_part, int nslots, int str
     if (i >= nrhs) return;
     RhsState S = st[i];
     double rr = 0.0;
-    if (init) {
+    if (init == 1) {
         for (int j = 0; j < nslots; ++j) rr += rr_part[(long long)i * stride + j];
         S.bb = rr;
         S.rr_ref = rr;
@@ -252,6 +259,7 @@ __global__ void k_check(RhsState* st, const double* rr_part, int nslots, int str
         S.iters = 0;
         S.replacements = 0;
         S.first = 1;
+        S.pbuf = 0;
         S.beta = make_double2(0.0, 0.0);
         S.rho = make_double2(0.0, 0.0);
         S.status = (rr > 0.0) ? ST_RESTART : ST_CONVERGED;
@@ -352,35 +360,57 @@ cudaError_t launch_projection(const double2* psi, const RhsDesc* desc, const int
 }
 
 // ---------------------------------------------------------------------------
-// dG/dV(r) = sum_o 2 Re[ lambda_o(r) * sum_i C[o][i] psi_i(r) ],
-// C[o][i] = (v_o / v_i) conj(t_oi).
-__global__ void k_gradient(const double2* __restrict__ psi, int n_in, const double2* __restrict__ lam,
-                           int n_out, const double2* __restrict__ C, long long npts, double* g) {
-    extern __shared__ double2 Cs[];
-    for (int i = threadIdx.x; i < n_in * n_out; i += blockDim.x) Cs[i] = C[i];
+// dG/dV(r) = sum_{o,i} 2 (v_o / v_i) Re[conj(t_oi) lambda_o(r) psi_i(r)], with the
+// forward waves psi_i = sum_k B[i][k] X_k and the adjoint waves
+// lambda_o = sum_j L[o][j] Y_j combined from the solved real-profile RHS; the
+// host folds C[o][i] = (v_o / v_i) conj(t_oi) into U = C B.
+__global__ void k_gradient(const double2* __restrict__ X, int nX, const double2* __restrict__ Y,
+                           int nY, const double2* __restrict__ U, const double2* __restrict__ L,
+                           int n, long long npts, double* g) {
+    extern __shared__ double2 sh[];
+    double2* Us = sh;
+    double2* Ls = sh + (size_t)n * nX;
+    for (int i = threadIdx.x; i < n * nX; i += blockDim.x) Us[i] = U[i];
+    for (int i = threadIdx.x; i < n * nY; i += blockDim.x) Ls[i] = L[i];
     __syncthreads();
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < npts;
          r += (long long)gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int o = 0; o < n_out; ++o) {
-            double2 u = make_double2(0.0, 0.0);
-            for (int i = 0; i < n_in; ++i) u = cfma(Cs[o * n_in + i], psi[(long long)i * npts + r], u);
-            const double2 w = cmul(lam[(long long)o * npts + r], u);
-            acc += 2.0 * w.x;
+        for (int o = 0; o < n; ++o) {
+            double2 u = make_double2(0.0, 0.0), l = make_double2(0.0, 0.0);
+            for (int k = 0; k < nX; ++k) u = cfma(Us[o * nX + k], X[(long long)k * npts + r], u);
+            for (int j = 0; j < nY; ++j) l = cfma(Ls[o * nY + j], Y[(long long)j * npts + r], l);
+            acc += 2.0 * (l.x * u.x - l.y * u.y);
         }
         g[r] = acc;
     }
 }
 
-cudaError_t launch_gradient(const double2* psi, int n_in, const double2* lam, int n_out,
-                            const double2* C, long long npts, double* g, cudaStream_t s) {
-    const size_t smem = sizeof(double2) * (size_t)n_in * n_out;
+cudaError_t launch_gradient(const double2* X, int nX, const double2* Y, int nY, const double2* U,
+                            const double2* L, int n, long long npts, double* g, cudaStream_t s) {
+    const size_t smem = sizeof(double2) * (size_t)n * (nX + nY);
     if (smem > 48 * 1024) {
         cudaError_t err = cudaFuncSetAttribute(k_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
         if (err != cudaSuccess) return err;
     }
-    k_gradient<<<vec_blocks(npts), 256, smem, s>>>(psi, n_in, lam, n_out, C, npts, g);
+    k_gradient<<<vec_blocks(npts), 256, smem, s>>>(X, nX, Y, nY, U, L, n, npts, g);
+    return cudaGetLastError();
+}
+
+__global__ void k_combine(double2* __restrict__ dst, const double2* __restrict__ x1, double2 c1,
+                          const double2* __restrict__ x2, double2 c2, long long npts) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts;
+         i += (long long)gridDim.x * blockDim.x) {
+        double2 v = cmul(c1, x1[i]);
+        if (x2) v = cfma(c2, x2[i], v);
+        dst[i] = v;
+    }
+}
+
+cudaError_t launch_combine(double2* dst, const double2* x1, double2 c1, const double2* x2,
+                           double2 c2, long long npts, cudaStream_t s) {
+    k_combine<<<vec_blocks(npts), 256, 0, s>>>(dst, x1, c1, x2, c2, npts);
     return cudaGetLastError();
 }
 

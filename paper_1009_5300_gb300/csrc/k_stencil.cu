@@ -53,9 +53,10 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(const StencilArgs<T> a) {
     const long long plane = (long long)nx * ny;
     const long long base = (long long)rhs * a.npts;
     const C* __restrict__ X = a.x + base;
-    const C* __restrict__ PO = (a.fused_p && !first_dir) ? a.pold + base : nullptr;
+    const int pb = (a.fused_p && a.state) ? (a.state[rhs].pbuf & 1) : 0;
+    const C* __restrict__ PO = (a.fused_p && !first_dir) ? a.pbufs[pb] + base : nullptr;
     C* __restrict__ Y = a.y + base;
-    C* __restrict__ PN = a.fused_p ? a.pout + base : nullptr;
+    C* __restrict__ PN = a.fused_p ? a.pbufs[1 - pb] + base : nullptr;
     const T ed = a.ediag ? (T)a.ediag[a.rhs_energy ? a.rhs_energy[rhs] : 0] : (T)0;
     const T cen = a.c0 + ed;
 

@@ -172,7 +172,10 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
 
     out = ModeTables();
     out.E = E;
-    if (want_sigma) out.sigma.assign((size_t)nx * ny * nf * nf, cd(0.0, 0.0));
+    if (want_sigma) {
+        out.sigma.assign((size_t)nx * ny * nf * nf, cd(0.0, 0.0));
+        out.pc.assign((size_t)nx * ny * kPcStride, cd(0.0, 0.0));
+    }
     const int nxy = nx * ny;
     for (int iy = 0; iy < ny; ++iy) {
         const int nuy = nu_of_index(iy, ny);
@@ -243,6 +246,35 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
             if (want_sigma) {
                 cd* dst = &out.sigma[((size_t)ky * nx + kx) * nf * nf];
                 for (int i = 0; i < nf * nf; ++i) dst[i] = S[i];
+                // Free-propagator preconditioner of this mode: E - eps_perp - T_z - Sigma at
+                // both ends.  Gaussian elimination from the left end keeps the left
+                // self-energy pattern on the leading block (eliminating one more plane of
+                // a semi-infinite lead reproduces the lead), so the band factors are the
+                // same on every row of the first nz - nf planes:
+                //   u_j = T[0][j] - S[0][j],  l_j = (T[j][0] - S[j][0]) / u_0,
+                // and the last nf planes form the block T - S - flip(S).
+                auto Tm = [&](int i, int j) {
+                    const int n = std::abs(i - j);
+                    double v = (n <= nf) ? w[n] / (2.0 * hz * hz) : 0.0;
+                    if (i == j) v += E - eperp;
+                    return cd(v, 0.0);
+                };
+                cd* pc = &out.pc[((size_t)ky * nx + kx) * kPcStride];
+                std::vector<cd> u(nf + 1), l(nf + 1);
+                for (int j = 0; j <= nf; ++j) u[j] = Tm(0, j) - (j < nf ? S[j] : cd(0.0, 0.0));
+                for (int j = 1; j <= nf; ++j) l[j] = (Tm(j, 0) - (j < nf ? S[(size_t)j * nf] : cd(0.0, 0.0))) / u[0];
+                for (int j = 1; j <= nf; ++j) pc[j - 1] = l[j];
+                for (int j = 0; j <= nf; ++j) pc[nf + j] = u[j];
+                std::vector<cd> S2((size_t)nf * nf);
+                for (int i = 0; i < nf; ++i)
+                    for (int j = 0; j < nf; ++j)
+                        S2[(size_t)i * nf + j] = Tm(i, j) - S[(size_t)i * nf + j] -
+                                                 S[(size_t)(nf - 1 - i) * nf + (nf - 1 - j)];
+                if (!cinv(S2, nf)) {
+                    msg = "singular end block of the free-propagator preconditioner";
+                    return 9;
+                }
+                for (int i = 0; i < nf * nf; ++i) pc[2 * nf + 1 + i] = S2[i];
             }
             if (prop >= 0) {
                 const cd li = lam[prop];
@@ -265,6 +297,17 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
         }
     }
     out.nopen = (int)out.open_canon.size();
+    // partner channel (-nu) of every open channel; the lateral dispersion is even in nu
+    out.open_partner.assign(out.nopen, -1);
+    for (int c = 0; c < out.nopen; ++c) {
+        const int bx = bin_of_nu(-out.open_nux[c], nx), by = bin_of_nu(-out.open_nuy[c], ny);
+        for (int d = 0; d < out.nopen; ++d)
+            if (out.open_kx[d] == bx && out.open_ky[d] == by) out.open_partner[c] = d;
+        if (out.open_partner[c] < 0) {
+            msg = "open channel without a -nu partner";
+            return 9;
+        }
+    }
     (void)nxy;
     return 0;
 }
@@ -272,7 +315,7 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
 bool fft_plan(int n, std::vector<int>& radices) {
     radices.clear();
     if (n < 1) return false;
-    static const int order[] = {4, 2, 3, 5, 7, 11, 13};
+    static const int order[] = {4, 2, 3, 5};
     for (int r : order) {
         while (n % r == 0) {
             radices.push_back(r);

@@ -25,8 +25,15 @@ struct ModeTables {
     std::vector<cd> lam_in;            // propagating right-going root of each open channel
     std::vector<cd> mrow;              // [nopen][nf]: t = sum_d mrow[d] psi~(depth d)
     std::vector<cd> btilde;            // [nopen][nf]: incident source coefficients (Eq. 7)
+    std::vector<int> open_partner;     // open-list index of the channel with lateral index -nu
     std::vector<cd> sigma;             // [ky][kx][nf][nf] Sigma~ in FFT-bin order
+    // free-propagator preconditioner per FFT bin: banded LU of E - T - H~ for the
+    // mode (constant factors l_1..l_nf, u_0..u_nf and the inverse of the last
+    // nf x nf Schur block), [ky][kx][kPcStride]
+    std::vector<cd> pc;
 };
+
+constexpr int kPcStride = 25;   // nf + (nf + 1) + nf * nf for nf = 4
 
 // Builds the tables of energy E.  Returns 0, or 2 (IOBM_E_THRESHOLD) when E is
 // within 1e-9 Ha of a channel edge, or 9 when a mode has more than one
@@ -34,8 +41,8 @@ struct ModeTables {
 int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, double E,
                       bool want_sigma, ModeTables& out, std::string& msg);
 
-// Radix plan of a lateral FFT length (radices 4, 2, 3, 5, 7, 11, 13); false if
-// n has another prime factor.
+// Radix plan of a lateral FFT length (radices 4, 2, 3, 5); false if n has
+// another prime factor.
 bool fft_plan(int n, std::vector<int>& radices);
 
 struct ProjTables {

@@ -53,6 +53,9 @@ def default_options(**kw) -> _lib.Options:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": _lib.IOBM_FP64, "mixed": _lib.IOBM_MIXED}[v]
+        if k == "use_precond" and isinstance(v, str):
+            v = {"none": _lib.IOBM_PRECOND_NONE, "eq10": _lib.IOBM_PRECOND_EQ10,
+                 "fourier": _lib.IOBM_PRECOND_FOURIER}[v]
         setattr(o, k, v)
     return o
 
@@ -171,20 +174,20 @@ class IOBMSolver:
         check(self.lib.iobm_set_workspace(self.h, C.c_void_p(self._ws.data_ptr()),
                                           self._ws.numel()), self.h)
 
-    def _count_rhs(self, energies, channels):
-        n = 0
-        for E in energies:
-            k = self.open_channels(E)[0].shape[0]
-            n += k if channels is None else sum(1 for c in channels if 0 <= c < k)
-        return n
+    def _count_rhs(self, E: np.ndarray, ch) -> int:
+        n = C.c_int(0)
+        check(self.lib.iobm_solve_rhs_count(self.h, _ptr(E), len(E),
+                                            _ptr(ch) if ch is not None else None,
+                                            0 if ch is None else len(ch), C.byref(n)), self.h)
+        return n.value
 
     # ---- solves --------------------------------------------------------
     def solve(self, energies: Sequence[float], channels: Optional[Sequence[int]] = None,
               side: int = 0) -> SolveResult:
         E = np.ascontiguousarray(np.atleast_1d(np.asarray(energies, np.float64)))
-        nrhs = self._count_rhs(E, channels)
-        self._ensure_workspace(max(nrhs, 1))
         ch = None if channels is None else np.ascontiguousarray(channels, np.int32)
+        nrhs = self._count_rhs(E, ch)
+        self._ensure_workspace(max(nrhs, 1))
         with torch.cuda.device(self.device):
             check(self.lib.iobm_solve(self.h, _ptr(E), len(E), _ptr(ch) if ch is not None else None,
                                       0 if ch is None else len(ch), int(side)), self.h)
@@ -224,7 +227,7 @@ class IOBMSolver:
     def grad_V(self, E: float):
         """(dG/dV as a [nz][ny][nx] float64 CUDA tensor, G) at energy E."""
         n = self.open_channels(E)[0].shape[0]
-        self._ensure_workspace(max(2 * n, 1))
+        self._ensure_workspace(max(2 * n, 1))   # forward and adjoint real-profile RHS
         g = torch.empty(self.shape, dtype=torch.float64, device=self.device)
         G = C.c_double(0)
         with torch.cuda.device(self.device):
@@ -255,12 +258,13 @@ class IOBMSolver:
                                       C.c_void_p(y.data_ptr()), nrhs), self.h)
         return y
 
-    def apply_precond(self, x: torch.Tensor) -> torch.Tensor:
+    def apply_precond(self, x: torch.Tensor, E: float = 0.0) -> torch.Tensor:
+        """y = P x (Eq. 10, or the lateral-Fourier free propagator at energy E)."""
         x = x.contiguous()
         elem = _lib.IOBM_ELEM_C64 if x.dtype == torch.complex128 else _lib.IOBM_ELEM_C32
         nrhs = x.numel() // int(np.prod(self.shape))
         y = torch.empty_like(x)
         with torch.cuda.device(self.device):
-            check(self.lib.iobm_apply_precond(self.h, elem, C.c_void_p(x.data_ptr()),
+            check(self.lib.iobm_apply_precond(self.h, float(E), elem, C.c_void_p(x.data_ptr()),
                                               C.c_void_p(y.data_ptr()), nrhs), self.h)
         return y

@@ -60,7 +60,7 @@ def test_precond_matches_oracle(nx, ny, nz, nf, kb):
     from paper_1009_5300_gb300 import IOBMSolver
     jn = make(nx, ny, nz, nf, kb)
     for alpha in (1.8, 3.0):
-        sol = IOBMSolver.from_junction(jn, precision="fp64", alpha=alpha)
+        sol = IOBMSolver.from_junction(jn, precision="fp64", alpha=alpha, use_precond="eq10")
         x = np.stack([S.random_field((nz, ny, nx), 7 + i) for i in range(2)])
         ref = np.stack([operator.apply_P(jn, alpha, x[i]) for i in range(2)])
         y = sol.apply_precond(torch.from_numpy(x).cuda()).cpu().numpy()
@@ -68,6 +68,23 @@ def test_precond_matches_oracle(nx, ny, nz, nf, kb):
         y32 = sol.apply_precond(torch.from_numpy(x).cuda().to(torch.complex64)).cpu().numpy()
         assert np.max(np.abs(y32 - ref)) < 1e-6 * np.max(np.abs(ref))
         sol.close()
+
+
+@pytest.mark.parametrize("nx,ny,nz,nf,kb", [CASES[0], CASES[1], CASES[3]])
+def test_fourier_precond_matches_oracle(nx, ny, nz, nf, kb):
+    # (E - T - H~)^{-1} by lateral FFT + constant-factor z-sweeps against sparse LU
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = make(nx, ny, nz, nf, kb)
+    E = jn.e_fermi + 0.007
+    md = modes.mode_data(nx, ny, jn.hx, jn.hy, jn.hz, nf, E)
+    sol = IOBMSolver.from_junction(jn, precision="fp64", use_precond="fourier")
+    x = np.stack([S.random_field((nz, ny, nx), 31 + i) for i in range(2)])
+    ref = np.stack([operator.free_inverse(jn, E, md, x[i]) for i in range(2)])
+    y = sol.apply_precond(torch.from_numpy(x).cuda(), E).cpu().numpy()
+    assert np.max(np.abs(y - ref)) < 1e-11 * np.max(np.abs(ref))
+    y32 = sol.apply_precond(torch.from_numpy(x).cuda().to(torch.complex64), E).cpu().numpy()
+    assert np.max(np.abs(y32 - ref)) < 1e-4 * np.max(np.abs(ref))
+    sol.close()
 
 
 def test_projector_on_end_planes_rejected():

@@ -59,12 +59,13 @@ def test_wire16(wire16_oracle, precision):
 
 @pytest.mark.parametrize("nf", [1, 4])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_multichannel_kb(nf, precision):
+@pytest.mark.parametrize("precond", ["fourier", "eq10"])
+def test_multichannel_kb(nf, precision, precond):
     from paper_1009_5300_gb300 import IOBMSolver
     jn = kb_junction(nf)
     E = jn.e_fermi
     ref = transport.solve(jn, E)
-    sol = IOBMSolver.from_junction(jn, precision=precision)
+    sol = IOBMSolver.from_junction(jn, precision=precision, use_precond=precond)
     res = sol.solve([E])
     assert ref.n_open >= 3
     compare(res, ref)
@@ -108,7 +109,7 @@ def test_several_energies_and_batch_independence():
     for e, E in enumerate(Es):
         ref = transport.solve(jn, E)
         assert abs(res.G[e] - ref.G) < G_TOL
-    # the same RHS solved alone gives bit-identical results
+    # the same channel pair solved alone gives bit-identical results
     k = int(np.nonzero(res.energy_index == 1)[0][1])
     single = sol.solve([Es[1]], channels=[int(res.channel[k])])
     assert np.array_equal(single.T[0], res.T[k][: single.T.shape[1]])
