@@ -238,6 +238,15 @@ int iobm_set_potential(iobm_handle* h, const double* V_loc, int src_is_device);
 int iobm_channels_host(const iobm_grid* grid, double E, int* n_open, int max_out, int* nu,
                        double* vel, double* lam, double* btilde, double* mrow, double* sigma);
 
+/* Enable (1) or disable (0) CUDA-event timing of every fused stencil launch
+ * (the dominant kernel: p = z + beta p_old, q = (E - T - V) p and the p^T q
+ * partials) inside the captured iteration graphs; resets the counters. */
+int iobm_profile(iobm_handle* h, int enable);
+
+/* Accumulated device time (ms) and count of the timed stencil launches
+ * since iobm_profile(h, 1). */
+int iobm_kernel_stats(const iobm_handle* h, double* stencil_ms, long long* stencil_launches);
+
 /* Device-side time (ms) of the last iobm_solve's iteration phase, measured
  * with CUDA events on the handle's stream, and the number of kernel launches
  * it issued. */

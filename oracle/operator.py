@@ -216,8 +216,10 @@ def P_matrix(jn, alpha: float) -> sp.csr_matrix:
 
 def free_inverse(jn, E: float, md: ModeData, r: np.ndarray) -> np.ndarray:
     """z = (E - T - H~)^{-1} r: the operator of Eqs. 7, 7-2 with V = 0 and no KB term,
-    solved by sparse LU (r shaped [nz][ny][nx])."""
+    solved by sparse LU (r shaped [..., nz][ny][nx]; one factorisation for all)."""
     import scipy.sparse.linalg as spla
     flat = jn.copy_with(V=np.zeros_like(jn.V), projectors=[])
-    A0 = assemble_A_local(flat, E, md)
-    return spla.spsolve(A0, np.asarray(r, dtype=np.complex128).reshape(-1)).reshape(r.shape)
+    lu = spla.splu(assemble_A_local(flat, E, md))
+    r = np.asarray(r, dtype=np.complex128)
+    vecs = r.reshape(-1, jn.npts)
+    return np.stack([lu.solve(v) for v in vecs]).reshape(r.shape)

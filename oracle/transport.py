@@ -72,18 +72,25 @@ def incident_wave_planes(jn, md: ModeData, m: int, depths: np.ndarray) -> np.nda
     return (lam ** depths)[:, None] * f[None, :]
 
 
-def source_vector(jn, md: ModeData, m: int, side: str, S: Optional[np.ndarray] = None) -> np.ndarray:
-    """b for a unit incident wave in mode m from side 'L' or 'R' (Eq. 7)."""
+def source_vector(jn, md: ModeData, m: int, side: str, S: Optional[np.ndarray] = None,
+                  matrix_free: bool = False) -> np.ndarray:
+    """b for a unit incident wave in mode m from side 'L' or 'R' (Eq. 7).  With
+    matrix_free the self-energy term goes through the explicit Eq. 19 sums instead of
+    the dense Eq. 8 block (for lateral grids whose dense block does not fit)."""
+    from .operator import _sigma_apply_end
     nf = jn.nf
     nxy = jn.nx * jn.ny
-    if S is None:
-        S = sigma_dense(jn, md)
     K = md.K
     d = np.arange(nf)
     phi_in = incident_wave_planes(jn, md, m, d)                  # transition planes, depth d
     phi_el = incident_wave_planes(jn, md, m, -(d + 1))            # electrode planes e = 1..nf
     coupling = K @ phi_el                                         # [d][l]
-    sig = (S @ phi_in.reshape(-1)).reshape(nf, nxy)
+    if matrix_free:
+        sig = _sigma_apply_end(jn, md, phi_in)
+    else:
+        if S is None:
+            S = sigma_dense(jn, md)
+        sig = (S @ phi_in.reshape(-1)).reshape(nf, nxy)
     bplanes = -coupling - sig
     b = np.zeros((jn.nz, nxy), dtype=np.complex128)
     b[end_planes(jn, side)] = bplanes

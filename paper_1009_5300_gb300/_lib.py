@@ -83,6 +83,8 @@ SIGNATURES = {
     "iobm_channels_host": (C.c_int, [C.POINTER(Grid), C.c_double, C.POINTER(C.c_int), C.c_int,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "iobm_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "iobm_kernel_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "iobm_last_solve_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
                                         C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
 }

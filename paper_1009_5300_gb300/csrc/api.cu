@@ -117,6 +117,11 @@ struct iobm_handle {
     double last_ms = 0.0;
     long long last_launches = 0;
     long long last_iters = 0;
+    // optional in-graph CUDA-event timing of the fused stencil launches
+    int profile = 0;
+    std::vector<cudaEvent_t> kev;
+    double prof_ms = 0.0;
+    long long prof_launches = 0;
 };
 
 namespace {
@@ -387,7 +392,7 @@ int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) 
 // direction in one of two buffers (RhsState::pbuf), so RHS that pause for an
 // FP64 residual replacement resume with their own direction.
 template <typename T>
-int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches) {
+int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, int slot = -1) {
     using C = typename Cplx<T>::type;
     const double tol2 = internal_tol2(h);
     const double delta2 = h->opt.refine_delta * h->opt.refine_delta;
@@ -410,7 +415,9 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches) {
     a.nrm_part = nullptr;
     a.slot_stride = h->slot_stride;
     a.slot_base = 0;
+    if (slot >= 0) CK(cudaEventRecord(h->kev[2 * slot], h->stream));
     CK(launch_stencil<T>(a, nrhs, h->stream));
+    if (slot >= 0) CK(cudaEventRecord(h->kev[2 * slot + 1], h->stream));
     SigmaArgs<T> s = sigma_args<T>(h, sig);
     s.pnew[0] = (const C*)h->vp[0];
     s.pnew[1] = (const C*)h->vp[1];
@@ -501,9 +508,16 @@ int run_solver(iobm_handle* h, int nrhs) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long per_chunk = 0;
+    if (h->profile) {
+        while ((int)h->kev.size() < 2 * chunk) {
+            cudaEvent_t ev;
+            CK(cudaEventCreate(&ev));
+            h->kev.push_back(ev);
+        }
+    }
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int it = 0; it < chunk; ++it) {
-        rc = cocg_iteration<T>(h, nrhs, mixed, per_chunk);
+        rc = cocg_iteration<T>(h, nrhs, mixed, per_chunk, h->profile ? it : -1);
         if (rc) {
             cudaStreamEndCapture(h->stream, &graph);
             if (graph) cudaGraphDestroy(graph);
@@ -530,6 +544,14 @@ int run_solver(iobm_handle* h, int nrhs) {
         if (e != cudaSuccess) {
             cudaGraphExecDestroy(exec);
             return cuda_fail(h, e, "state readback");
+        }
+        if (h->profile) {
+            for (int it = 0; it < chunk; ++it) {
+                float kms = 0.f;
+                if (cudaEventElapsedTime(&kms, h->kev[2 * it], h->kev[2 * it + 1]) == cudaSuccess)
+                    h->prof_ms += kms;
+            }
+            h->prof_launches += chunk;
         }
         int active = 0, pending = 0;
         for (const RhsState& S : h->hstate) {
@@ -611,13 +633,17 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
         h->hrhs_energy.push_back(e);
         return (int)h->hdesc.size() - 1;
     };
-    for (int e = 0; e < nE; ++e) {
-        ModeTables mt;
-        std::string msg;
+    for (int e = 0; e < nE; ++e)
         if (!std::isfinite(E[e])) return fail(h, IOBM_E_ARG, "non-finite energy");
-        const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, nf, E[e],
-                                         upload_tables, mt, msg);
+    std::vector<ModeTables> tables;
+    {
+        std::string msg;
+        const int rc = build_mode_tables_many(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, nf, E, nE,
+                                              upload_tables, tables, msg);
         if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
+    }
+    for (int e = 0; e < nE; ++e) {
+        ModeTables& mt = tables[e];
         if (upload_tables) {
             sig_all.insert(sig_all.end(), mt.sigma.begin(), mt.sigma.end());
             pc_all.insert(pc_all.end(), mt.pc.begin(), mt.pc.end());
@@ -927,6 +953,7 @@ void iobm_destroy(iobm_handle* h) {
     if (h->ev_sync) cudaEventDestroy(h->ev_sync);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+    for (cudaEvent_t ev : h->kev) cudaEventDestroy(ev);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -1270,6 +1297,21 @@ int iobm_channels_host(const iobm_grid* g, double E, int* n_open, int max_out, i
             sigma[2 * i] = mt.sigma[i].real();
             sigma[2 * i + 1] = mt.sigma[i].imag();
         }
+    return IOBM_OK;
+}
+
+int iobm_profile(iobm_handle* h, int enable) {
+    if (!h) return IOBM_E_ARG;
+    h->profile = enable ? 1 : 0;
+    h->prof_ms = 0.0;
+    h->prof_launches = 0;
+    return IOBM_OK;
+}
+
+int iobm_kernel_stats(const iobm_handle* h, double* stencil_ms, long long* stencil_launches) {
+    if (!h) return IOBM_E_ARG;
+    if (stencil_ms) *stencil_ms = h->prof_ms;
+    if (stencil_launches) *stencil_launches = h->prof_launches;
     return IOBM_OK;
 }
 

@@ -23,9 +23,13 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <atomic>
 #include <sstream>
+#include <thread>
 
 namespace iobm {
+
+constexpr int kMaxNfHost = 4;
 
 std::vector<double> fd_weights(int nf) {
     const int n = nf + 1;
@@ -75,7 +79,7 @@ static std::vector<cd> poly_roots(const std::vector<double>& a) {
             p = p * x + c[k];
         }
     };
-    for (int it = 0; it < 500; ++it) {
+    for (int it = 0; it < 80; ++it) {
         double maxstep = 0.0;
         for (int k = 0; k < n; ++k) {
             cd p, dp;
@@ -89,7 +93,7 @@ static std::vector<cd> poly_roots(const std::vector<double>& a) {
             z[k] -= w;
             maxstep = std::max(maxstep, std::abs(w) / std::max(1.0, std::abs(z[k])));
         }
-        if (maxstep < 1e-16) break;
+        if (maxstep < 1e-13) break;   // the Newton polish below finishes the digits
     }
     for (int k = 0; k < n; ++k) {   // Newton polish on the same polynomial
         for (int it = 0; it < 3; ++it) {
@@ -108,40 +112,175 @@ static double velocity(double theta, const std::vector<double>& w, double hz) {
     return v / hz;
 }
 
-// Gauss-Jordan inverse of an n x n complex matrix (row-major), partial pivoting.
-static bool cinv(std::vector<cd>& A, int n) {
-    std::vector<cd> I((size_t)n * n, cd(0.0, 0.0));
-    for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+static inline int nu_of_index(int i, int n) { return i - n / 2; }          // canonical nu
+static inline int bin_of_nu(int nu, int n) { return ((nu % n) + n) % n; }   // FFT bin
+
+namespace {
+
+// Everything the solver needs about one lateral mode depends on E - eps_perp
+// only, so it is computed once per distinct eps_perp.
+struct ModeSolution {
+    bool open = false;
+    double vel = 0.0;
+    cd lam_in;
+    cd sigma[kMaxNfHost * kMaxNfHost];
+    cd pc[kPcStride];
+    cd mrow[kMaxNfHost];
+    cd btilde[kMaxNfHost];
+};
+
+// Gauss-Jordan inverse of an n x n complex matrix (row-major, n <= 4), partial pivoting.
+bool cinv_small(cd* A, int n) {
+    cd I[kMaxNfHost * kMaxNfHost];
+    for (int i = 0; i < n * n; ++i) I[i] = 0.0;
+    for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
     for (int c = 0; c < n; ++c) {
         int piv = c;
         for (int r = c + 1; r < n; ++r)
-            if (std::abs(A[(size_t)r * n + c]) > std::abs(A[(size_t)piv * n + c])) piv = r;
-        if (std::abs(A[(size_t)piv * n + c]) == 0.0) return false;
+            if (std::abs(A[r * n + c]) > std::abs(A[piv * n + c])) piv = r;
+        if (std::abs(A[piv * n + c]) == 0.0) return false;
         for (int j = 0; j < n; ++j) {
-            std::swap(A[(size_t)c * n + j], A[(size_t)piv * n + j]);
-            std::swap(I[(size_t)c * n + j], I[(size_t)piv * n + j]);
+            std::swap(A[c * n + j], A[piv * n + j]);
+            std::swap(I[c * n + j], I[piv * n + j]);
         }
-        const cd inv = 1.0 / A[(size_t)c * n + c];
+        const cd inv = 1.0 / A[c * n + c];
         for (int j = 0; j < n; ++j) {
-            A[(size_t)c * n + j] *= inv;
-            I[(size_t)c * n + j] *= inv;
+            A[c * n + j] *= inv;
+            I[c * n + j] *= inv;
         }
         for (int r = 0; r < n; ++r) {
             if (r == c) continue;
-            const cd f = A[(size_t)r * n + c];
+            const cd f = A[r * n + c];
             if (f == cd(0.0, 0.0)) continue;
             for (int j = 0; j < n; ++j) {
-                A[(size_t)r * n + j] -= f * A[(size_t)c * n + j];
-                I[(size_t)r * n + j] -= f * I[(size_t)c * n + j];
+                A[r * n + j] -= f * A[c * n + j];
+                I[r * n + j] -= f * I[c * n + j];
             }
         }
     }
-    A.swap(I);
+    for (int i = 0; i < n * n; ++i) A[i] = I[i];
     return true;
 }
 
-static inline int nu_of_index(int i, int n) { return i - n / 2; }          // canonical nu
-static inline int bin_of_nu(int nu, int n) { return ((nu % n) + n) % n; }   // FFT bin
+cd ipow(cd x, int n) {
+    cd r(1.0, 0.0);
+    if (n < 0) {
+        x = 1.0 / x;
+        n = -n;
+    }
+    for (int i = 0; i < n; ++i) r *= x;
+    return r;
+}
+
+// Roots, self-energy, preconditioner factors, projection row and source of
+// one lateral mode with E - eps_perp = dE.  Returns 0 or 9 (more than one
+// propagating root / singular block).
+int solve_mode(double dE, int nf, double hz, const std::vector<double>& w,
+               const std::vector<std::vector<double>>& tc, const double* K, bool want_sigma,
+               ModeSolution& m, std::string& msg) {
+    std::vector<double> a(nf + 1, 0.0);
+    a[0] = 2.0 * hz * hz * dE + w[0];
+    for (int n = 1; n <= nf; ++n)
+        for (int k = 0; k <= n; ++k) a[k] += 2.0 * w[n] * tc[n][k];
+    const std::vector<cd> us = poly_roots(a);
+    cd lam[kMaxNfHost];
+    int prop = -1;
+    for (int j = 0; j < nf; ++j) {
+        cd u = us[j];
+        if (std::fabs(u.imag()) <= 1e-12 * std::max(1.0, std::abs(u))) u = cd(u.real(), 0.0);
+        if (u.imag() == 0.0 && std::fabs(u.real()) < 1.0) {
+            const double th = std::acos(u.real());
+            const double v = velocity(th, w, hz);
+            lam[j] = std::polar(1.0, (v > 0.0 ? 1.0 : -1.0) * th);
+            if (prop >= 0) {
+                msg = "more than one propagating root in one lateral mode";
+                return 9;
+            }
+            prop = j;
+            m.vel = std::fabs(v);
+        } else {
+            const cd sq = std::sqrt(u * u - 1.0);
+            const cd l1 = u - sq, l2 = u + sq;
+            lam[j] = (std::abs(l1) < std::abs(l2)) ? l1 : l2;
+        }
+    }
+    // scaled Q_in[d][j] = lam_j^(nf-1-d); Q_out[e-1][j] = lam_j^(e+nf-1)
+    cd Qinv[kMaxNfHost * kMaxNfHost], Qout[kMaxNfHost * kMaxNfHost];
+    for (int j = 0; j < nf; ++j) {
+        cd p = 1.0;
+        cd pw[2 * kMaxNfHost];
+        for (int k = 0; k < 2 * nf; ++k) {
+            pw[k] = p;
+            p *= lam[j];
+        }
+        for (int d = 0; d < nf; ++d) Qinv[d * nf + j] = pw[nf - 1 - d];
+        for (int e = 1; e <= nf; ++e) Qout[(e - 1) * nf + j] = pw[e + nf - 1];
+    }
+    if (!cinv_small(Qinv, nf)) {
+        msg = "singular Bloch-state matrix";
+        return 9;
+    }
+    // S = -K Qout Qinv
+    cd KQ[kMaxNfHost * kMaxNfHost], S[kMaxNfHost * kMaxNfHost];
+    for (int d = 0; d < nf; ++d)
+        for (int j = 0; j < nf; ++j) {
+            cd acc = 0.0;
+            for (int e = 0; e < nf; ++e) acc += K[d * nf + e] * Qout[e * nf + j];
+            KQ[d * nf + j] = acc;
+        }
+    for (int d = 0; d < nf; ++d)
+        for (int dp = 0; dp < nf; ++dp) {
+            cd acc = 0.0;
+            for (int j = 0; j < nf; ++j) acc -= KQ[d * nf + j] * Qinv[j * nf + dp];
+            S[d * nf + dp] = acc;
+        }
+    for (int i = 0; i < nf * nf; ++i) m.sigma[i] = S[i];
+    if (want_sigma) {
+        // Free-propagator preconditioner of this mode: E - eps_perp - T_z - Sigma at
+        // both ends.  Gaussian elimination from the left end keeps the left
+        // self-energy pattern on the leading block (eliminating one more plane of
+        // a semi-infinite lead reproduces the lead), so the band factors are the
+        // same on every row of the first nz - nf planes:
+        //   u_j = T[0][j] - S[0][j],  l_j = (T[j][0] - S[j][0]) / u_0,
+        // and the last nf planes form the block T - S - flip(S).
+        auto Tm = [&](int i, int j) {
+            const int n = std::abs(i - j);
+            double v = (n <= nf) ? w[n] / (2.0 * hz * hz) : 0.0;
+            if (i == j) v += dE;
+            return cd(v, 0.0);
+        };
+        cd u[kMaxNfHost + 1];
+        for (int j = 0; j <= nf; ++j) u[j] = Tm(0, j) - (j < nf ? S[j] : cd(0.0, 0.0));
+        for (int j = 1; j <= nf; ++j)
+            m.pc[j - 1] = (Tm(j, 0) - (j < nf ? S[j * nf] : cd(0.0, 0.0))) / u[0];
+        for (int j = 0; j <= nf; ++j) m.pc[nf + j] = u[j];
+        cd S2[kMaxNfHost * kMaxNfHost];
+        for (int i = 0; i < nf; ++i)
+            for (int j = 0; j < nf; ++j)
+                S2[i * nf + j] = Tm(i, j) - S[i * nf + j] - S[(nf - 1 - i) * nf + (nf - 1 - j)];
+        if (!cinv_small(S2, nf)) {
+            msg = "singular end block of the free-propagator preconditioner";
+            return 9;
+        }
+        for (int i = 0; i < nf * nf; ++i) m.pc[2 * nf + 1 + i] = S2[i];
+    }
+    m.open = prop >= 0;
+    if (m.open) {
+        const cd li = lam[prop];
+        m.lam_in = li;
+        const cd scale = ipow(li, nf - 1);
+        for (int d = 0; d < nf; ++d) m.mrow[d] = scale * Qinv[prop * nf + d];
+        for (int d = 0; d < nf; ++d) {
+            cd b(0.0, 0.0);
+            for (int e = 1; e <= nf; ++e) b -= K[d * nf + (e - 1)] * ipow(li, -e);
+            for (int dp = 0; dp < nf; ++dp) b -= S[d * nf + dp] * ipow(li, dp);
+            m.btilde[d] = b;
+        }
+    }
+    return 0;
+}
+
+}  // namespace
 
 int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, double E,
                       bool want_sigma, ModeTables& out, std::string& msg) {
@@ -165,10 +304,10 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
         for (int k = 0; k <= nf; ++k)
             tc[n][k] = (k > 0 ? 2.0 * tc[n - 1][k - 1] : 0.0) - tc[n - 2][k];
 
-    std::vector<double> K((size_t)nf * nf, 0.0);   // K[d][e-1]
+    double K[kMaxNfHost * kMaxNfHost] = {};
     for (int d = 0; d < nf; ++d)
         for (int e = 1; e <= nf; ++e)
-            if (d + e <= nf) K[(size_t)d * nf + (e - 1)] = w[d + e] / (2.0 * hz * hz);
+            if (d + e <= nf) K[d * nf + (e - 1)] = w[d + e] / (2.0 * hz * hz);
 
     out = ModeTables();
     out.E = E;
@@ -176,123 +315,53 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
         out.sigma.assign((size_t)nx * ny * nf * nf, cd(0.0, 0.0));
         out.pc.assign((size_t)nx * ny * kPcStride, cd(0.0, 0.0));
     }
-    const int nxy = nx * ny;
+    std::vector<double> ex(nx), ey(ny);
+    for (int ix = 0; ix < nx; ++ix) ex[ix] = eps1d(nu_of_index(ix, nx), nx, hx);
+    for (int iy = 0; iy < ny; ++iy) ey[iy] = eps1d(nu_of_index(iy, ny), ny, hy);
+    // distinct lateral energies (the dispersion is even in nu, and symmetric in
+    // x <-> y on square cells), each solved once
+    std::vector<double> eperp((size_t)nx * ny);
+    for (int iy = 0; iy < ny; ++iy)
+        for (int ix = 0; ix < nx; ++ix) eperp[(size_t)iy * nx + ix] = ex[ix] + ey[iy];
+    std::vector<double> uniq(eperp);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    std::vector<ModeSolution> sol(uniq.size());
+    for (size_t u = 0; u < uniq.size(); ++u) {
+        if (std::fabs(E - uniq[u]) < 1e-9 || std::fabs(E - uniq[u] - band_top) < 1e-9) {
+            std::ostringstream os;
+            os << "energy " << E << " Ha lies within 1e-9 Ha of the threshold of a lateral mode "
+               << "with eps_perp = " << uniq[u] << " Ha";
+            msg = os.str();
+            return 2;
+        }
+        const int rc = solve_mode(E - uniq[u], nf, hz, w, tc, K, want_sigma, sol[u], msg);
+        if (rc) return rc;
+    }
     for (int iy = 0; iy < ny; ++iy) {
         const int nuy = nu_of_index(iy, ny);
-        const double ey = eps1d(nuy, ny, hy);
         for (int ix = 0; ix < nx; ++ix) {
             const int nux = nu_of_index(ix, nx);
-            const double eperp = eps1d(nux, nx, hx) + ey;
-            if (std::fabs(E - eperp) < 1e-9 || std::fabs(E - eperp - band_top) < 1e-9) {
-                std::ostringstream os;
-                os << "energy " << E << " Ha lies within 1e-9 Ha of the threshold of lateral mode ("
-                   << nux << "," << nuy << ")";
-                msg = os.str();
-                return 2;
-            }
-            // polynomial in u
-            std::vector<double> a(nf + 1, 0.0);
-            a[0] = 2.0 * hz * hz * (E - eperp) + w[0];
-            for (int n = 1; n <= nf; ++n)
-                for (int k = 0; k <= n; ++k) a[k] += 2.0 * w[n] * tc[n][k];
-            const std::vector<cd> us = poly_roots(a);
-            std::vector<cd> lam(nf);
-            int prop = -1;
-            double vprop = 0.0;
-            for (int j = 0; j < nf; ++j) {
-                cd u = us[j];
-                if (std::fabs(u.imag()) <= 1e-12 * std::max(1.0, std::abs(u))) u = cd(u.real(), 0.0);
-                if (u.imag() == 0.0 && std::fabs(u.real()) < 1.0) {
-                    const double th = std::acos(u.real());   // (0, pi)
-                    const double v = velocity(th, w, hz);
-                    const double sgn = v > 0.0 ? 1.0 : -1.0;
-                    lam[j] = std::polar(1.0, sgn * th);
-                    if (prop >= 0) {
-                        msg = "more than one propagating root in one lateral mode";
-                        return 9;
-                    }
-                    prop = j;
-                    vprop = std::fabs(v);
-                } else {
-                    const cd sq = std::sqrt(u * u - 1.0);
-                    const cd l1 = u - sq, l2 = u + sq;
-                    lam[j] = (std::abs(l1) < std::abs(l2)) ? l1 : l2;
-                }
-            }
             const int canon = iy * nx + ix;
+            const size_t u = std::lower_bound(uniq.begin(), uniq.end(), eperp[canon]) - uniq.begin();
+            const ModeSolution& m = sol[u];
             const int kx = bin_of_nu(nux, nx), ky = bin_of_nu(nuy, ny);
-            // scaled Q_in[d][j] = lam_j^(nf-1-d); Q_out[e-1][j] = lam_j^(e+nf-1)
-            std::vector<cd> Qin((size_t)nf * nf), Qout((size_t)nf * nf);
-            for (int d = 0; d < nf; ++d)
-                for (int j = 0; j < nf; ++j) Qin[(size_t)d * nf + j] = std::pow(lam[j], nf - 1 - d);
-            for (int e = 1; e <= nf; ++e)
-                for (int j = 0; j < nf; ++j) Qout[(size_t)(e - 1) * nf + j] = std::pow(lam[j], e + nf - 1);
-            std::vector<cd> Qinv = Qin;
-            if (!cinv(Qinv, nf)) {
-                msg = "singular Bloch-state matrix";
-                return 9;
-            }
-            std::vector<cd> S((size_t)nf * nf, cd(0.0, 0.0));
-            if (want_sigma || prop >= 0) {
-                // S = -K Qout Qinv
-                std::vector<cd> KQ((size_t)nf * nf, cd(0.0, 0.0));
-                for (int d = 0; d < nf; ++d)
-                    for (int j = 0; j < nf; ++j)
-                        for (int e = 0; e < nf; ++e) KQ[(size_t)d * nf + j] += K[(size_t)d * nf + e] * Qout[(size_t)e * nf + j];
-                for (int d = 0; d < nf; ++d)
-                    for (int dp = 0; dp < nf; ++dp)
-                        for (int j = 0; j < nf; ++j) S[(size_t)d * nf + dp] -= KQ[(size_t)d * nf + j] * Qinv[(size_t)j * nf + dp];
-            }
             if (want_sigma) {
                 cd* dst = &out.sigma[((size_t)ky * nx + kx) * nf * nf];
-                for (int i = 0; i < nf * nf; ++i) dst[i] = S[i];
-                // Free-propagator preconditioner of this mode: E - eps_perp - T_z - Sigma at
-                // both ends.  Gaussian elimination from the left end keeps the left
-                // self-energy pattern on the leading block (eliminating one more plane of
-                // a semi-infinite lead reproduces the lead), so the band factors are the
-                // same on every row of the first nz - nf planes:
-                //   u_j = T[0][j] - S[0][j],  l_j = (T[j][0] - S[j][0]) / u_0,
-                // and the last nf planes form the block T - S - flip(S).
-                auto Tm = [&](int i, int j) {
-                    const int n = std::abs(i - j);
-                    double v = (n <= nf) ? w[n] / (2.0 * hz * hz) : 0.0;
-                    if (i == j) v += E - eperp;
-                    return cd(v, 0.0);
-                };
+                for (int i = 0; i < nf * nf; ++i) dst[i] = m.sigma[i];
                 cd* pc = &out.pc[((size_t)ky * nx + kx) * kPcStride];
-                std::vector<cd> u(nf + 1), l(nf + 1);
-                for (int j = 0; j <= nf; ++j) u[j] = Tm(0, j) - (j < nf ? S[j] : cd(0.0, 0.0));
-                for (int j = 1; j <= nf; ++j) l[j] = (Tm(j, 0) - (j < nf ? S[(size_t)j * nf] : cd(0.0, 0.0))) / u[0];
-                for (int j = 1; j <= nf; ++j) pc[j - 1] = l[j];
-                for (int j = 0; j <= nf; ++j) pc[nf + j] = u[j];
-                std::vector<cd> S2((size_t)nf * nf);
-                for (int i = 0; i < nf; ++i)
-                    for (int j = 0; j < nf; ++j)
-                        S2[(size_t)i * nf + j] = Tm(i, j) - S[(size_t)i * nf + j] -
-                                                 S[(size_t)(nf - 1 - i) * nf + (nf - 1 - j)];
-                if (!cinv(S2, nf)) {
-                    msg = "singular end block of the free-propagator preconditioner";
-                    return 9;
-                }
-                for (int i = 0; i < nf * nf; ++i) pc[2 * nf + 1 + i] = S2[i];
+                for (int i = 0; i < kPcStride; ++i) pc[i] = m.pc[i];
             }
-            if (prop >= 0) {
-                const cd li = lam[prop];
+            if (m.open) {
                 out.open_canon.push_back(canon);
                 out.open_kx.push_back(kx);
                 out.open_ky.push_back(ky);
                 out.open_nux.push_back(nux);
                 out.open_nuy.push_back(nuy);
-                out.vel.push_back(vprop);
-                out.lam_in.push_back(li);
-                const cd scale = std::pow(li, nf - 1);
-                for (int d = 0; d < nf; ++d) out.mrow.push_back(scale * Qinv[(size_t)prop * nf + d]);
-                for (int d = 0; d < nf; ++d) {
-                    cd b(0.0, 0.0);
-                    for (int e = 1; e <= nf; ++e) b -= K[(size_t)d * nf + (e - 1)] * std::pow(li, -e);
-                    for (int dp = 0; dp < nf; ++dp) b -= S[(size_t)d * nf + dp] * std::pow(li, dp);
-                    out.btilde.push_back(b);
-                }
+                out.vel.push_back(m.vel);
+                out.lam_in.push_back(m.lam_in);
+                for (int d = 0; d < nf; ++d) out.mrow.push_back(m.mrow[d]);
+                for (int d = 0; d < nf; ++d) out.btilde.push_back(m.btilde[d]);
             }
         }
     }
@@ -308,7 +377,29 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
             return 9;
         }
     }
-    (void)nxy;
+    return 0;
+}
+
+int build_mode_tables_many(int nx, int ny, double hx, double hy, double hz, int nf, const double* E,
+                           int nE, bool want_sigma, std::vector<ModeTables>& out, std::string& msg) {
+    out.assign(nE, ModeTables());
+    std::vector<int> rc(nE, 0);
+    std::vector<std::string> msgs(nE);
+    const int nth = std::max(1, std::min<int>(nE, (int)std::thread::hardware_concurrency()));
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        for (int e = next++; e < nE; e = next++)
+            rc[e] = build_mode_tables(nx, ny, hx, hy, hz, nf, E[e], want_sigma, out[e], msgs[e]);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    for (int e = 0; e < nE; ++e)
+        if (rc[e]) {
+            msg = msgs[e];
+            return rc[e];
+        }
     return 0;
 }
 

@@ -41,6 +41,10 @@ constexpr int kPcStride = 25;   // nf + (nf + 1) + nf * nf for nf = 4
 int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, double E,
                       bool want_sigma, ModeTables& out, std::string& msg);
 
+// The tables of several energies, built in parallel host threads.
+int build_mode_tables_many(int nx, int ny, double hx, double hy, double hz, int nf, const double* E,
+                           int nE, bool want_sigma, std::vector<ModeTables>& out, std::string& msg);
+
 // Radix plan of a lateral FFT length (radices 4, 2, 3, 5); false if n has
 // another prime factor.
 bool fft_plan(int n, std::vector<int>& radices);

@@ -244,6 +244,16 @@ class IOBMSolver:
             Vn = np.ascontiguousarray(np.asarray(V, np.float64).reshape(self.shape))
             check(self.lib.iobm_set_potential(self.h, _ptr(Vn), 0), self.h)
 
+    def profile(self, enable: bool = True):
+        check(self.lib.iobm_profile(self.h, 1 if enable else 0), self.h)
+
+    def kernel_stats(self):
+        """(total ms, launches) of the timed fused-stencil launches since profile(True)."""
+        ms = C.c_double(0)
+        n = C.c_longlong(0)
+        check(self.lib.iobm_kernel_stats(self.h, C.byref(ms), C.byref(n)), self.h)
+        return ms.value, n.value
+
     # ---- operator access -------------------------------------------------
     def apply(self, E: float, x: torch.Tensor) -> torch.Tensor:
         """y = (E - H_T - H~) x for x [nrhs][nz][ny][nx] complex64/complex128 on the device."""

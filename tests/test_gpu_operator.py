@@ -70,7 +70,7 @@ def test_precond_matches_oracle(nx, ny, nz, nf, kb):
         sol.close()
 
 
-@pytest.mark.parametrize("nx,ny,nz,nf,kb", [CASES[0], CASES[1], CASES[3]])
+@pytest.mark.parametrize("nx,ny,nz,nf,kb", [(20, 12, 30, 4, True), CASES[1], (25, 27, 16, 2, False)])
 def test_fourier_precond_matches_oracle(nx, ny, nz, nf, kb):
     # (E - T - H~)^{-1} by lateral FFT + constant-factor z-sweeps against sparse LU
     from paper_1009_5300_gb300 import IOBMSolver
@@ -79,7 +79,7 @@ def test_fourier_precond_matches_oracle(nx, ny, nz, nf, kb):
     md = modes.mode_data(nx, ny, jn.hx, jn.hy, jn.hz, nf, E)
     sol = IOBMSolver.from_junction(jn, precision="fp64", use_precond="fourier")
     x = np.stack([S.random_field((nz, ny, nx), 31 + i) for i in range(2)])
-    ref = np.stack([operator.free_inverse(jn, E, md, x[i]) for i in range(2)])
+    ref = operator.free_inverse(jn, E, md, x)
     y = sol.apply_precond(torch.from_numpy(x).cuda(), E).cpu().numpy()
     assert np.max(np.abs(y - ref)) < 1e-11 * np.max(np.abs(ref))
     y32 = sol.apply_precond(torch.from_numpy(x).cuda().to(torch.complex64), E).cpu().numpy()
