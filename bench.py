@@ -201,13 +201,22 @@ def native_arm(args, rank, world, local_rank):
 
     jn = S.wire48(junction_id=rank, n_energies=args.energies)
     E = jn.energies
-    solver = IOBMSolver.from_junction(jn, precision="mixed", device=dev)
+    opt_kw = {}
+    if args.delta is not None:
+        opt_kw["refine_delta"] = args.delta
+    if args.chunk is not None:
+        opt_kw["chunk"] = args.chunk
+    solver = IOBMSolver.from_junction(jn, precision="mixed", device=dev, **opt_kw)
     nrhs_int = solver._count_rhs(np.ascontiguousarray(E), None)
     ws_bytes = solver.workspace_size(nrhs_int)
 
     # warm-up
     for _ in range(args.warmup):
         res = solver.solve(E)
+        print(f"[bench] warm-up solve: {res.device_ms:.1f} ms device, {res.nrhs} channels, "
+              f"iterations mean {res.iterations.mean():.1f} max {res.iterations.max()}, "
+              f"replacements mean {res.replacements.mean():.1f}, converged {res.converged}",
+              file=sys.stderr, flush=True)
     barrier()
 
     sampler = ClockSampler(local_rank)
@@ -355,6 +364,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--delta", type=float, default=None,
+                    help="FP64 residual replacement factor of the mixed solver (library default)")
+    ap.add_argument("--chunk", type=int, default=None,
+                    help="COCG iterations per captured graph (library default)")
     args = ap.parse_args()
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)

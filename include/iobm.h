@@ -132,7 +132,7 @@ typedef struct {
 } iobm_report;
 
 /* Fill opts with the defaults: alpha 1.8, use_precond IOBM_PRECOND_FOURIER, tol 1e-8,
- * max_iter 20000, precision IOBM_MIXED, refine_delta 0.1, chunk 32. */
+ * max_iter 20000, precision IOBM_MIXED, refine_delta 0.01, chunk 32. */
 void iobm_default_options(iobm_options* opts);
 
 /* Create a solver for one junction.  V_loc: host [nz][ny][nx] local

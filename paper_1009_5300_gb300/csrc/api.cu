@@ -388,6 +388,28 @@ int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) 
     return IOBM_OK;
 }
 
+// FP64 residual replacement for RHS in `mask` (PENDING): x64 (+)= x, r = b - A x64.
+template <typename T>
+int residual_replacement(iobm_handle* h, int nrhs, int mask, bool mixed, long long& launches) {
+    using C = typename Cplx<T>::type;
+    if (mixed) {
+        CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
+        launches += 1;
+    }
+    int rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
+                                    h->rhs_energy.as<int>(), h->st, mask, launches);
+    if (rc) return rc;
+    int nslots = 0;
+    CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
+                          h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, h->st, mask,
+                          h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
+    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, internal_tol2(h), 0, h->stream));
+    launches += 2;
+    // RESTART RHS get z = P r and the rho / |r|^2 partials of the replaced residual;
+    // the next iteration returns them to ACTIVE and forms beta from these partials
+    return apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
+}
+
 // One COCG iteration for every ACTIVE RHS.  Each RHS keeps its current
 // direction in one of two buffers (RhsState::pbuf), so RHS that pause for an
 // FP64 residual replacement resume with their own direction.
@@ -397,8 +419,12 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     const double tol2 = internal_tol2(h);
     const double delta2 = h->opt.refine_delta * h->opt.refine_delta;
     const int ns = h->ns_stencil;
+    // RHS whose residual was replaced in the previous iteration resume here
+    CK(launch_restart_scalars(h->st, h->rho_part, h->rr_part, h->ns_stencil, h->slot_stride, nrhs,
+                              h->stream));
     CK(launch_beta(h->st, h->rho_part, h->rr_part, rho_slots(h), h->slot_stride, nrhs,
                    h->opt.max_iter, tol2, delta2, mixed ? 1 : 0, h->stream));
+    launches += 2;
     const void* sig = std::is_same<T, float>::value ? h->sig32.p : h->sig64.p;
     StencilArgs<T> a = op_args<T>(h);
     a.x = (const C*)h->vz;
@@ -415,9 +441,11 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     a.nrm_part = nullptr;
     a.slot_stride = h->slot_stride;
     a.slot_base = 0;
-    if (slot >= 0) CK(cudaEventRecord(h->kev[2 * slot], h->stream));
+    // event record nodes inside the captured graph (external records execute with the graph)
+    if (slot >= 0) CK(cudaEventRecordWithFlags(h->kev[2 * slot], h->stream, cudaEventRecordExternal));
     CK(launch_stencil<T>(a, nrhs, h->stream));
-    if (slot >= 0) CK(cudaEventRecord(h->kev[2 * slot + 1], h->stream));
+    if (slot >= 0)
+        CK(cudaEventRecordWithFlags(h->kev[2 * slot + 1], h->stream, cudaEventRecordExternal));
     SigmaArgs<T> s = sigma_args<T>(h, sig);
     s.pnew[0] = (const C*)h->vp[0];
     s.pnew[1] = (const C*)h->vp[1];
@@ -450,32 +478,11 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     CK(launch_axpy_update<T>((C*)h->vx, (C*)h->vr, pb, (const C*)h->vq, h->st, M_ACTIVE, h->npts,
                              nrhs, h->stream));
     launches += 2;
-    return apply_precond_dots<T>(h, nrhs, M_ACTIVE, launches);
-}
-
-// FP64 residual replacement for RHS in `mask` (PENDING): x64 (+)= x, r = b - A x64.
-template <typename T>
-int residual_replacement(iobm_handle* h, int nrhs, int mask, bool mixed, long long& launches) {
-    using C = typename Cplx<T>::type;
-    if (mixed) {
-        CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
-        launches += 1;
-    }
-    int rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
-                                    h->rhs_energy.as<int>(), h->st, mask, launches);
+    int rc = apply_precond_dots<T>(h, nrhs, M_ACTIVE, launches);
     if (rc) return rc;
-    int nslots = 0;
-    CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
-                          h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, h->st, mask,
-                          h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
-    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, internal_tol2(h), 0, h->stream));
-    launches += 2;
-    rc = apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
-    if (rc) return rc;
-    CK(launch_restart_scalars(h->st, h->rho_part, h->rr_part, h->ns_stencil, h->slot_stride, nrhs,
-                              h->stream));
-    launches += 1;
-    return IOBM_OK;
+    // FP64 residual replacement of the RHS that became PENDING in this iteration
+    // (masked launches: no work when none is pending)
+    return residual_replacement<T>(h, nrhs, M_PENDING, mixed, launches);
 }
 
 template <typename T>
@@ -499,9 +506,6 @@ int run_solver(iobm_handle* h, int nrhs) {
     launches += 2;
     int rc = apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
     if (rc) return rc;
-    CK(launch_restart_scalars(h->st, h->rho_part, h->rr_part, h->ns_stencil, h->slot_stride, nrhs,
-                              h->stream));
-    launches += 1;
 
     // capture one chunk of iterations
     const int chunk = std::max(1, h->opt.chunk);
@@ -548,38 +552,24 @@ int run_solver(iobm_handle* h, int nrhs) {
         if (h->profile) {
             for (int it = 0; it < chunk; ++it) {
                 float kms = 0.f;
-                if (cudaEventElapsedTime(&kms, h->kev[2 * it], h->kev[2 * it + 1]) == cudaSuccess)
+                if (cudaEventElapsedTime(&kms, h->kev[2 * it], h->kev[2 * it + 1]) == cudaSuccess) {
                     h->prof_ms += kms;
+                    h->prof_launches += 1;
+                } else {
+                    cudaGetLastError();   // do not leave the failed query as the last error
+                }
             }
-            h->prof_launches += chunk;
         }
-        int active = 0, pending = 0;
-        for (const RhsState& S : h->hstate) {
-            active += (S.status == ST_ACTIVE || S.status == ST_RESTART);
-            pending += (S.status == ST_PENDING);
-        }
-        if (pending) {
-            rc = residual_replacement<T>(h, nrhs, M_PENDING, mixed, launches);
-            if (rc) {
-                cudaGraphExecDestroy(exec);
-                return rc;
-            }
-            e = cudaMemcpyAsync(h->hstate.data(), h->st, sizeof(RhsState) * nrhs,
-                                cudaMemcpyDeviceToHost, h->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-            if (e != cudaSuccess) {
-                cudaGraphExecDestroy(exec);
-                return cuda_fail(h, e, "state readback");
-            }
-            active = 0;
-            for (const RhsState& S : h->hstate) active += (S.status == ST_ACTIVE);
-        }
-        if (!active) break;
+        int live = 0;
+        for (const RhsState& S : h->hstate)
+            live += (S.status == ST_ACTIVE || S.status == ST_RESTART || S.status == ST_PENDING);
+        if (!live) break;
     }
     cudaGraphExecDestroy(exec);
     // RHS that stopped without converging: fold their FP32 progress and record the FP64 residual
     {
-        const int mask = (1 << ST_NOCONV) | (1 << ST_BREAKDOWN) | (1 << ST_ACTIVE);
+        const int mask = (1 << ST_NOCONV) | (1 << ST_BREAKDOWN) | (1 << ST_ACTIVE) |
+                         (1 << ST_PENDING) | (1 << ST_RESTART);
         if (mixed) {
             CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
         }
@@ -815,7 +805,7 @@ void iobm_default_options(iobm_options* o) {
     o->tol = 1e-8;
     o->max_iter = 20000;
     o->precision = IOBM_MIXED;
-    o->refine_delta = 0.1;
+    o->refine_delta = 0.01;
     o->chunk = 32;
 }
 

@@ -266,10 +266,10 @@ __global__ void k_check(RhsState* st, const double* rr_part, int nslots, int str
         if (rr == 0.0) S.res64 = 0.0;
     } else if (init == 2) {
         // record the FP64 residual of RHS that stopped without converging
-        if (S.status != ST_NOCONV && S.status != ST_BREAKDOWN && S.status != ST_ACTIVE) return;
+        if (S.status == ST_CONVERGED || S.status == ST_IDLE) return;
         for (int j = 0; j < nslots; ++j) rr += rr_part[(long long)i * stride + j];
         S.res64 = sqrt(rr / S.bb);
-        if (S.status == ST_ACTIVE) S.status = ST_NOCONV;
+        if (S.status != ST_BREAKDOWN) S.status = ST_NOCONV;
     } else {
         if (S.status != ST_PENDING) return;
         for (int j = 0; j < nslots; ++j) rr += rr_part[(long long)i * stride + j];
