@@ -247,6 +247,35 @@ int iobm_profile(iobm_handle* h, int enable);
  * since iobm_profile(h, 1). */
 int iobm_kernel_stats(const iobm_handle* h, double* stencil_ms, long long* stencil_launches);
 
+/* Allocation-free form of the Eq. 10 preconditioner with its COCG dot
+ * products, for callers that cannot allocate device memory: for instance an
+ * application whose memory pool owns the whole GPU, a latency-critical loop
+ * that cannot afford the implicit synchronisation of cudaMalloc/cudaFree, or
+ * code running while a stream is being captured into a CUDA graph.  The paper
+ * has no counterpart; it is the same operation as iobm_apply_precond with
+ * IOBM_PRECOND_EQ10 in FP64, plus the sums the solver forms from it.
+ *
+ * Needs no handle.  r and z: device [nrhs][nz][ny][nx] complex double
+ * (interleaved); z = P r with C_0 = 1, C_1 = exp(-alpha), six face neighbours,
+ * laterally periodic, zero beyond the end planes.  rho: device [nrhs][2]
+ * receives r^T z (unconjugated, re/im); rr: device [nrhs] receives |r|^2.
+ * Everything is enqueued on cuda_stream (a cudaStream_t, NULL = legacy
+ * default stream); the call does not synchronise.
+ *
+ * The per-block partial sums live in a fixed device array compiled into the
+ * library (1.5 MiB per GPU, held by every GPU that loads the library until the
+ * process exits): at most 65536 partial slots, where one RHS uses
+ * ceil(nx/32) * ceil(ny/8) * ceil(nz/32) slots; larger requests return
+ * IOBM_E_UNSUPPORTED.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current, so make the first
+ * call before capturing a stream.  Every call shares the array and overwrites
+ * every slot it reads, so calls need no clearing, but calls that overlap on
+ * the GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: IOBM_E_ARG, IOBM_E_UNSUPPORTED, IOBM_E_CUDA. */
+int iobm_precond_dots_noalloc(const iobm_grid* grid, double alpha, const void* r, void* z,
+                              int nrhs, double* rho, double* rr, void* cuda_stream);
+
 /* Device-side time (ms) of the last iobm_solve's iteration phase, measured
  * with CUDA events on the handle's stream, and the number of kernel launches
  * it issued. */
