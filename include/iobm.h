@@ -264,7 +264,7 @@ int iobm_kernel_stats(const iobm_handle* h, double* stencil_ms, long long* stenc
  *
  * The per-block partial sums live in a fixed device array compiled into the
  * library (1.5 MiB per GPU, held by every GPU that loads the library until the
- * process exits): at most 65536 partial slots, where one RHS uses
+ * process exits): at most 65536 partial slots, where one RHS uses at most
  * ceil(nx/32) * ceil(ny/8) * ceil(nz/32) slots; larger requests return
  * IOBM_E_UNSUPPORTED.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress) with the device current, so make the first

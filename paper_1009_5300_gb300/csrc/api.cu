@@ -150,13 +150,16 @@ size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 double internal_tol2(const iobm_handle* h) { return 0.5 * h->opt.tol * h->opt.tol; }
 
 int slots_for(const iobm_handle* h) {
-    const int ns = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk);
-    return std::max(std::max(ns + 2 * h->nf + 1, 64), h->g.nz);
+    const int ns_op = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk, h->nf);
+    const int ns_pc = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk, 1);
+    return std::max(std::max(ns_op + 2 * h->nf + 1, 64), std::max(h->g.nz, ns_pc));
 }
 
 // number of rho / |r|^2 partial slots the preconditioner pass writes
 int rho_slots(const iobm_handle* h) {
-    return h->opt.use_precond == IOBM_PRECOND_FOURIER ? h->g.nz : h->ns_stencil;
+    return h->opt.use_precond == IOBM_PRECOND_FOURIER
+               ? h->g.nz
+               : stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk, 1);
 }
 
 size_t workspace_bytes(const iobm_handle* h, int nrhs, int prec) {
@@ -189,7 +192,7 @@ int bind_workspace(iobm_handle* h, int nrhs) {
     const size_t n = (size_t)nrhs * h->npts;
     const int S = slots_for(h);
     h->slot_stride = S;
-    h->ns_stencil = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk);
+    h->ns_stencil = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk, h->nf);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         void* p = base + off;
@@ -230,7 +233,8 @@ StencilArgs<T> op_args(const iobm_handle* h) {
         a.cy[n] = (T)(0.5 * h->w[n] * ihy);
         a.cz[n] = (T)(0.5 * h->w[n] * ihz);
     }
-    a.c0 = (T)(0.5 * h->w[0] * (ihx + ihy + ihz));
+    // difference form: the centre weight plus 2 sum_n c_n vanishes for the FD Laplacian
+    a.c0 = (T)0;
     a.vsign = (T)(-1);
     a.V = std::is_same<T, float>::value ? (const T*)h->V32.p : (const T*)h->V64.p;
     a.npts = h->npts;
@@ -248,7 +252,7 @@ StencilArgs<T> precond_args(const iobm_handle* h) {
     a.nf = 1;
     const double c1 = h->opt.use_precond == IOBM_PRECOND_EQ10 ? std::exp(-h->opt.alpha) : 0.0;
     a.cx[1] = a.cy[1] = a.cz[1] = (T)c1;
-    a.c0 = (T)1;
+    a.c0 = (T)(1.0 + 6.0 * c1);   // difference form: C_0 + 2 (3 C_1)
     a.vsign = (T)0;
     a.V = nullptr;
     a.npts = h->npts;
@@ -474,12 +478,37 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
         launches += 1;
     }
     CK(launch_alpha(h->st, h->mu_part, nslots_mu, h->slot_stride, nrhs, h->stream));
+    launches += 1;
     C* pb[2] = {(C*)h->vp[0], (C*)h->vp[1]};
-    CK(launch_axpy_update<T>((C*)h->vx, (C*)h->vr, pb, (const C*)h->vq, h->st, M_ACTIVE, h->npts,
-                             nrhs, h->stream));
-    launches += 2;
-    int rc = apply_precond_dots<T>(h, nrhs, M_ACTIVE, launches);
-    if (rc) return rc;
+    bool fused = false;
+    if (h->opt.use_precond == IOBM_PRECOND_FOURIER) {
+        // x += alpha p, r -= alpha q fused with the forward plane FFTs of the preconditioner
+        PrecondArgs<T> f = fourier_args<T>(h, std::is_same<T, float>::value ? h->pc32.p : h->pc64.p);
+        f.r = (const C*)h->vr;
+        f.spec = (C*)h->vz;
+        f.z = (C*)h->vz;
+        f.rhs_energy = h->rhs_energy.as<int>();
+        f.state = h->st;
+        f.mask = M_ACTIVE;
+        f.dot_part = h->rho_part;
+        f.nrm_part = h->rr_part;
+        f.slot_stride = h->slot_stride;
+        const cudaError_t e = launch_update_precond_fourier<T>(f, nrhs, h->stream, (C*)h->vx,
+                                                               (C*)h->vr, pb, (const C*)h->vq);
+        if (e == cudaSuccess) {
+            fused = true;
+            launches += 3;
+        } else if (e != cudaErrorNotSupported) {
+            return cuda_fail(h, e, "launch_update_precond_fourier");
+        }
+    }
+    if (!fused) {
+        CK(launch_axpy_update<T>((C*)h->vx, (C*)h->vr, pb, (const C*)h->vq, h->st, M_ACTIVE,
+                                 h->npts, nrhs, h->stream));
+        launches += 1;
+        int rc = apply_precond_dots<T>(h, nrhs, M_ACTIVE, launches);
+        if (rc) return rc;
+    }
     // FP64 residual replacement of the RHS that became PENDING in this iteration
     // (masked launches: no work when none is pending)
     return residual_replacement<T>(h, nrhs, M_PENDING, mixed, launches);

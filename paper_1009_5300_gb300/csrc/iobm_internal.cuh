@@ -101,7 +101,8 @@ struct StencilArgs {
     T cx[kMaxNf + 1];      // coefficients of x-shifts +-n (index n >= 1)
     T cy[kMaxNf + 1];
     T cz[kMaxNf + 1];
-    T c0;                  // constant part of the centre coefficient
+    T c0;                  // centre coefficient + 2 sum of the tap weights (taps are
+                           // applied as c_n (x_{+n} + x_{-n} - 2 x_0))
     T vsign;               // centre += vsign * V(r)
     const double* ediag;   // per-RHS additive centre term (energy) or nullptr
     const int* rhs_energy; // RHS -> energy index (for ediag)
@@ -185,6 +186,11 @@ struct PrecondArgs {
 };
 
 template <typename T> cudaError_t launch_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s,
+                                          typename Cplx<T>::type* x, typename Cplx<T>::type* r,
+                                          typename Cplx<T>::type* const* pbufs,
+                                          const typename Cplx<T>::type* q);
 template <typename T> size_t precond_smem_bytes(int nx, int ny);
 cudaError_t precond_prepare();
 
@@ -236,5 +242,5 @@ cudaError_t launch_combine(double2* dst, const double2* x1, double2 c1, const do
 }  // namespace iobm
 
 namespace iobm {
-int stencil_slots(int nx, int ny, int nz, int zchunk);
+int stencil_slots(int nx, int ny, int nz, int zchunk, int nf);
 }  // namespace iobm

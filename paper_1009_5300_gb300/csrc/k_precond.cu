@@ -242,43 +242,414 @@ __global__ void __launch_bounds__(256) k_plane_ifft_dots(const PrecondArgs<T> a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Compile-time plans for square planes of side N (the radix sequence, the
+// sub-transform sizes and every index divisor are constants, so the butterfly
+// index arithmetic reduces to multiplies and shifts).  Twiddles come from a
+// shared-memory copy of the table.
+template <int N>
+struct CtPlan {
+    __host__ __device__ static constexpr int count(int n, int r) {
+        return n % r == 0 ? 1 + count(n / r, r) : 0;
+    }
+    static constexpr int n4 = count(N, 4);
+    static constexpr int n2 = count(N / (n4 == 0 ? 1 : (1 << (2 * n4))), 2);
+    static constexpr int rest2 = N / (1 << (2 * n4)) / (1 << n2);
+    static constexpr int n3 = count(rest2, 3);
+    static constexpr int rest3 = rest2 / (n3 == 0 ? 1 : (n3 == 1 ? 3 : (n3 == 2 ? 9 : 27)));
+    static constexpr int n5 = count(rest3, 5);
+    static constexpr int npass = n4 + n2 + n3 + n5;
+    __host__ __device__ static constexpr int radix(int p) {
+        return p < n4 ? 4 : (p < n4 + n2 ? 2 : (p < n4 + n2 + n3 ? 3 : 5));
+    }
+};
+
+template <typename C, int N, int NS, int R>
+__device__ __forceinline__ void ct_bfly(const C* src, int ss, C* dst, int ds, int j,
+                                        const C* tw, bool inv) {
+    constexpr int NR = N / R;
+    constexpr int TS = N / (NS * R);
+    const int k = j % NS;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        C u = src[(j + r * NR) * ss];
+        if (r) {
+            C w = tw[(r * k * TS) % N];
+            if (inv) w.y = -w.y;
+            u = cmul(u, w);
+        }
+        v[r] = u;
+    }
+    C o[R];
+    if constexpr (R == 2) {
+        o[0] = cadd(v[0], v[1]);
+        o[1] = csub(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        C a2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        C a3;
+        if (inv) { a3.x = -d.y; a3.y = d.x; } else { a3.x = d.y; a3.y = -d.x; }
+        o[0] = cadd(a0, a2);
+        o[2] = csub(a0, a2);
+        o[1] = cadd(a1, a3);
+        o[3] = csub(a1, a3);
+    } else {
+#pragma unroll
+        for (int aa = 0; aa < R; ++aa) {
+            C acc = v[0];
+#pragma unroll
+            for (int b = 1; b < R; ++b) {
+                C w = tw[((aa * b) % R) * NR];
+                if (inv) w.y = -w.y;
+                acc = cfma(v[b], w, acc);
+            }
+            o[aa] = acc;
+        }
+    }
+    const int base = (j / NS) * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(base + r * NS) * ds] = o[r];
+}
+
+// all passes of N-point transforms along `lines` lines (line stride ls, element stride es)
+template <typename C, int N, int P, int NS>
+__device__ __forceinline__ void ct_passes(C*& cur, C*& oth, int ls, int es, const C* tw, bool inv) {
+    if constexpr (P < CtPlan<N>::npass) {
+        constexpr int R = CtPlan<N>::radix(P);
+        constexpr int PER = N / R;
+        for (int t = threadIdx.x; t < N * PER; t += blockDim.x) {
+            const int line = t / PER, j = t - line * PER;
+            ct_bfly<C, N, NS, R>(cur + line * ls, es, oth + line * ls, es, j, tw, inv);
+        }
+        __syncthreads();
+        C* s = cur; cur = oth; oth = s;
+        ct_passes<C, N, P + 1, NS * R>(cur, oth, ls, es, tw, inv);
+    }
+}
+
+// 2D FFT of an N x N plane in shared memory (a), b scratch; returns the result buffer
+template <typename C, int N>
+__device__ __forceinline__ C* ct_fft2(C* a, C* b, const C* tw, bool inv) {
+    C* cur = a;
+    C* oth = b;
+    ct_passes<C, N, 0, 1>(cur, oth, N, 1, tw, inv);   // rows
+    ct_passes<C, N, 0, 1>(cur, oth, 1, N, tw, inv);   // columns
+    return cur;
+}
+
+// x += alpha p, r -= alpha q for one plane (COCG update), then the forward FFT
+// of the new r into the spectrum buffer.  With alpha_from_state = 0 it is the
+// plain forward transform of r.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_update_fft_ct(const PrecondArgs<T> a, typename Cplx<T>::type* x,
+                                                       typename Cplx<T>::type* r_rw,
+                                                       typename Cplx<T>::type* p0,
+                                                       typename Cplx<T>::type* p1,
+                                                       const typename Cplx<T>::type* q, int update) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int plane = blockIdx.x, rhs = blockIdx.y;
+    if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
+    constexpr int NXY = N * N;
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + NXY;
+    C* tw = B + NXY;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.twx[i];
+    const long long off = (long long)rhs * a.npts + (long long)plane * NXY;
+    if (update) {
+        const C al = from_d2<C>(a.state[rhs].alpha);
+        const C* __restrict__ P = ((a.state[rhs].pbuf & 1) ? p1 : p0) + off;
+        C* __restrict__ Xv = x + off;
+        C* __restrict__ R = r_rw + off;
+        const C* __restrict__ Q = q + off;
+        for (int i = threadIdx.x; i < NXY; i += blockDim.x) {
+            const C rn = csub(R[i], cmul(al, Q[i]));
+            Xv[i] = cfma(al, P[i], Xv[i]);
+            R[i] = rn;
+            A[i] = rn;
+        }
+    } else {
+        for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[i] = a.r[off + i];
+    }
+    __syncthreads();
+    C* res = ct_fft2<C, N>(A, B, tw, false);
+    for (int i = threadIdx.x; i < NXY; i += blockDim.x) a.spec[off + i] = res[i];
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_ifft_dots_ct(const PrecondArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[3 * 8];
+    const int plane = blockIdx.x, rhs = blockIdx.y;
+    if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
+    constexpr int NXY = N * N;
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + NXY;
+    C* tw = B + NXY;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.twx[i];
+    const long long off = (long long)rhs * a.npts + (long long)plane * NXY;
+    for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[i] = a.spec[off + i];
+    __syncthreads();
+    C* res = ct_fft2<C, N>(A, B, tw, true);
+    T dre = 0, dim = 0, nrm = 0;
+    for (int i = threadIdx.x; i < NXY; i += blockDim.x) {
+        const C z = res[i];
+        a.z[off + i] = z;
+        if (a.dot_part) {
+            const C r = a.r[off + i];
+            dre += r.x * z.x - r.y * z.y;
+            dim += r.x * z.y + r.y * z.x;
+            nrm += r.x * r.x + r.y * r.y;
+        }
+    }
+    if (a.dot_part) {
+        double d0 = dre, d1 = dim, d2 = nrm;
+        block_reduce_3(d0, d1, d2, red);
+        if (threadIdx.x == 0) {
+            a.dot_part[(long long)rhs * a.slot_stride + plane] = make_double2(d0, d1);
+            a.nrm_part[(long long)rhs * a.slot_stride + plane] = d2;
+        }
+    }
+}
+
+// z-sweeps keeping the intermediate forward-sweep values of each mode in shared
+// memory (the spectrum is read once and written once)
+template <typename T, int NF>
+__global__ void __launch_bounds__(64) k_zsolve_smem(const PrecondArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int rhs = blockIdx.y;
+    if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
+    const int nxy = a.nx * a.ny;
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nz = a.nz, m = nz - NF;
+    C* col = reinterpret_cast<C*>(smem_raw) + threadIdx.x;   // col[k * blockDim.x]
+    const int cs = blockDim.x;
+    if (mode >= nxy) return;
+    const int e = a.rhs_energy ? a.rhs_energy[rhs] : 0;
+    const C* __restrict__ pc = a.pc + ((size_t)e * nxy + mode) * kPcStrideDev;
+    C l[NF + 1], u[NF + 1], S2[NF * NF];
+#pragma unroll
+    for (int j = 1; j <= NF; ++j) l[j] = pc[j - 1];
+#pragma unroll
+    for (int j = 0; j <= NF; ++j) u[j] = pc[NF + j];
+#pragma unroll
+    for (int i = 0; i < NF * NF; ++i) S2[i] = pc[2 * NF + 1 + i];
+    const C uinv = cdivc(make_one<C>(), u[0]);
+    const C* __restrict__ sin_ = a.spec + (long long)rhs * a.npts + mode;
+    C* __restrict__ sout = a.spec + (long long)rhs * a.npts + mode;
+    const T scale = (T)1 / (T)nxy;
+    C hist[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) hist[j] = czero<C>();
+    constexpr int PF = 4;   // loads issued ahead of use
+    C buf[PF];
+#pragma unroll
+    for (int j = 0; j < PF; ++j) buf[j] = (j < nz) ? sin_[(long long)j * nxy] : czero<C>();
+    for (int k0 = 0; k0 < m; k0 += PF) {
+        C cur[PF];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) cur[j] = buf[j];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int kk = k0 + PF + j;
+            buf[j] = (kk < nz) ? sin_[(long long)kk * nxy] : czero<C>();
+        }
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int k = k0 + j;
+            if (k < m) {
+                C y = cscale(cur[j], scale);
+#pragma unroll
+                for (int t = 1; t <= NF; ++t) y = csub(y, cmul(l[t], hist[t - 1]));
+                col[k * cs] = y;
+#pragma unroll
+                for (int t = NF - 1; t > 0; --t) hist[t] = hist[t - 1];
+                hist[0] = y;
+            } else if (k < nz) {
+                col[k * cs] = cur[j];   // last nf planes, still unscaled
+            }
+        }
+    }
+    // planes beyond the last full prefetch block (when m is a multiple of PF the
+    // last nf planes are still in buf)
+    for (int k = ((m + PF - 1) / PF) * PF; k < nz; ++k) col[k * cs] = sin_[(long long)k * nxy];
+    C g[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        C v = cscale(col[(m + i) * cs], scale);
+#pragma unroll
+        for (int j = 1; j <= NF; ++j)
+            if (j > i) v = csub(v, cmul(l[j], hist[j - 1 - i]));
+        g[i] = v;
+    }
+    C nxt[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        C v = czero<C>();
+#pragma unroll
+        for (int j = 0; j < NF; ++j) v = cfma(S2[i * NF + j], g[j], v);
+        nxt[i] = v;
+        sout[(long long)(m + i) * nxy] = v;
+    }
+    for (int k = m - 1; k >= 0; --k) {
+        C v = col[k * cs];
+#pragma unroll
+        for (int j = 1; j <= NF; ++j) v = csub(v, cmul(u[j], nxt[j - 1]));
+        v = cmul(v, uinv);
+        sout[(long long)k * nxy] = v;
+#pragma unroll
+        for (int j = NF - 1; j > 0; --j) nxt[j] = nxt[j - 1];
+        nxt[0] = v;
+    }
+}
+
 template <typename T>
 size_t precond_smem_bytes(int nx, int ny) {
     using C = typename Cplx<T>::type;
     return 2 * sizeof(C) * (size_t)nx * ny;
 }
 
-cudaError_t precond_prepare() {
-    const int lim = 160 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_plane_fft_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_plane_fft_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_plane_ifft_dots<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_plane_ifft_dots<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+constexpr int kPrecondSmemLimit = 160 * 1024;
+
+template <typename T>
+static cudaError_t prepare_type() {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kPrecondSmemLimit);
+    };
+    set((const void*)k_plane_fft_fwd<T>);
+    set((const void*)k_plane_ifft_dots<T>);
+    set((const void*)k_zsolve_smem<T, 1>);
+    set((const void*)k_zsolve_smem<T, 2>);
+    set((const void*)k_zsolve_smem<T, 3>);
+    set((const void*)k_zsolve_smem<T, 4>);
+#define IOBM_CT(N)                                    \
+    set((const void*)k_update_fft_ct<T, N>);          \
+    set((const void*)k_ifft_dots_ct<T, N>);
+    IOBM_CT(12) IOBM_CT(16) IOBM_CT(24) IOBM_CT(32) IOBM_CT(48) IOBM_CT(64)
+#undef IOBM_CT
     return e;
+}
+
+cudaError_t precond_prepare() {
+    cudaError_t e = prepare_type<float>();
+    if (e == cudaSuccess) e = prepare_type<double>();
+    return e;
+}
+
+static bool ct_size(int nx, int ny) {
+    return nx == ny && (nx == 12 || nx == 16 || nx == 24 || nx == 32 || nx == 48 || nx == 64);
+}
+
+template <typename T>
+static cudaError_t launch_zsolve(const PrecondArgs<T>& a, int nrhs, cudaStream_t s) {
+    using C = typename Cplx<T>::type;
+    const int nxy = a.nx * a.ny;
+    dim3 gz((nxy + 63) / 64, nrhs);
+    const size_t smem = sizeof(C) * 64 * (size_t)a.nz;
+    if (smem <= (size_t)kPrecondSmemLimit) {
+        switch (a.nf) {
+            case 1: k_zsolve_smem<T, 1><<<gz, 64, smem, s>>>(a); break;
+            case 2: k_zsolve_smem<T, 2><<<gz, 64, smem, s>>>(a); break;
+            case 3: k_zsolve_smem<T, 3><<<gz, 64, smem, s>>>(a); break;
+            case 4: k_zsolve_smem<T, 4><<<gz, 64, smem, s>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (a.nf) {
+            case 1: k_zsolve<T, 1><<<gz, 64, 0, s>>>(a); break;
+            case 2: k_zsolve<T, 2><<<gz, 64, 0, s>>>(a); break;
+            case 3: k_zsolve<T, 3><<<gz, 64, 0, s>>>(a); break;
+            case 4: k_zsolve<T, 4><<<gz, 64, 0, s>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+// forward transform (optionally fused with the COCG update) for square planes
+template <typename T>
+static cudaError_t launch_fwd_ct(const PrecondArgs<T>& a, int nrhs, cudaStream_t s,
+                                 typename Cplx<T>::type* x, typename Cplx<T>::type* r,
+                                 typename Cplx<T>::type* p0, typename Cplx<T>::type* p1,
+                                 const typename Cplx<T>::type* q, int update) {
+    using C = typename Cplx<T>::type;
+    const int N = a.nx;
+    const size_t smem = sizeof(C) * (2 * (size_t)N * N + N);
+    dim3 gp(a.nz, nrhs);
+    switch (N) {
+#define IOBM_CT(NN) \
+        case NN: k_update_fft_ct<T, NN><<<gp, 256, smem, s>>>(a, x, r, p0, p1, q, update); break;
+        IOBM_CT(12) IOBM_CT(16) IOBM_CT(24) IOBM_CT(32) IOBM_CT(48) IOBM_CT(64)
+#undef IOBM_CT
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_inv_ct(const PrecondArgs<T>& a, int nrhs, cudaStream_t s) {
+    using C = typename Cplx<T>::type;
+    const int N = a.nx;
+    const size_t smem = sizeof(C) * (2 * (size_t)N * N + N);
+    dim3 gp(a.nz, nrhs);
+    switch (N) {
+#define IOBM_CT(NN) case NN: k_ifft_dots_ct<T, NN><<<gp, 256, smem, s>>>(a); break;
+        IOBM_CT(12) IOBM_CT(16) IOBM_CT(24) IOBM_CT(32) IOBM_CT(48) IOBM_CT(64)
+#undef IOBM_CT
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s) {
     const size_t smem = precond_smem_bytes<T>(a.nx, a.ny);
-    if (smem > 160 * 1024) return cudaErrorInvalidValue;
+    if (smem > (size_t)kPrecondSmemLimit) return cudaErrorInvalidValue;
+    cudaError_t e;
     dim3 gp(a.nz, nrhs);
-    k_plane_fft_fwd<T><<<gp, 256, smem, s>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int nxy = a.nx * a.ny;
-    dim3 gz((nxy + 63) / 64, nrhs);
-    switch (a.nf) {
-        case 1: k_zsolve<T, 1><<<gz, 64, 0, s>>>(a); break;
-        case 2: k_zsolve<T, 2><<<gz, 64, 0, s>>>(a); break;
-        case 3: k_zsolve<T, 3><<<gz, 64, 0, s>>>(a); break;
-        case 4: k_zsolve<T, 4><<<gz, 64, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;
+    const bool ct = ct_size(a.nx, a.ny);
+    if (ct) {
+        e = launch_fwd_ct<T>(a, nrhs, s, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+    } else {
+        k_plane_fft_fwd<T><<<gp, 256, smem, s>>>(a);
+        e = cudaGetLastError();
     }
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    e = launch_zsolve<T>(a, nrhs, s);
+    if (e != cudaSuccess) return e;
+    if (ct) return launch_inv_ct<T>(a, nrhs, s);
     k_plane_ifft_dots<T><<<gp, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
+
+// COCG update x += alpha p, r -= alpha q fused with the preconditioner's forward
+// transform of r (square planes with a compile-time plan); returns
+// cudaErrorNotSupported when the size has no fused kernel (the caller then
+// runs the separate update and launch_precond_fourier).
+template <typename T>
+cudaError_t launch_update_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s,
+                                          typename Cplx<T>::type* x, typename Cplx<T>::type* r,
+                                          typename Cplx<T>::type* const* pbufs,
+                                          const typename Cplx<T>::type* q) {
+    if (!ct_size(a.nx, a.ny)) return cudaErrorNotSupported;
+    cudaError_t e = launch_fwd_ct<T>(a, nrhs, s, x, r, pbufs[0], pbufs[1], q, 1);
+    if (e != cudaSuccess) return e;
+    e = launch_zsolve<T>(a, nrhs, s);
+    if (e != cudaSuccess) return e;
+    return launch_inv_ct<T>(a, nrhs, s);
+}
+
+template cudaError_t launch_update_precond_fourier<float>(const PrecondArgs<float>&, int, cudaStream_t,
+                                                          float2*, float2*, float2* const*,
+                                                          const float2*);
+template cudaError_t launch_update_precond_fourier<double>(const PrecondArgs<double>&, int,
+                                                           cudaStream_t, double2*, double2*,
+                                                           double2* const*, const double2*);
 
 template size_t precond_smem_bytes<float>(int, int);
 template size_t precond_smem_bytes<double>(int, int);

@@ -84,7 +84,7 @@ extern "C" int iobm_precond_dots_noalloc(const iobm_grid* grid, double alpha, co
     const iobm_grid& g = *grid;
     if (g.nx < 1 || g.ny < 1 || g.nz < 1) return IOBM_E_ARG;
     if (nrhs == 0) return IOBM_OK;
-    const int per_rhs = stencil_slots(g.nx, g.ny, g.nz, kNoAllocZChunk);
+    const int per_rhs = stencil_slots(g.nx, g.ny, g.nz, kNoAllocZChunk, 1);
     if ((long long)per_rhs * nrhs > kNoAllocSlots) return IOBM_E_UNSUPPORTED;
     DeviceScratch s;
     if (scratch_for_current_device(s) != cudaSuccess) return IOBM_E_CUDA;
@@ -99,7 +99,7 @@ extern "C" int iobm_precond_dots_noalloc(const iobm_grid* grid, double alpha, co
     a.nf = 1;
     const double c1 = std::exp(-alpha);
     a.cx[1] = a.cy[1] = a.cz[1] = c1;
-    a.c0 = 1.0;
+    a.c0 = 1.0 + 6.0 * c1;   // the stencil kernel applies its taps in difference form
     a.vsign = 0.0;
     a.mask = M_ALL;
     a.dot_mode = 1;

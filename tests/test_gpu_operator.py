@@ -32,6 +32,8 @@ CASES = [
     (48, 48, 40, 4, True),     # the 48 x 48 lateral plane of the wire workload
     (25, 27, 36, 2, False),    # radix-5 and radix-3 FFTs, N_f = 2
     (64, 64, 12, 3, False),    # largest supported plane
+    (80, 40, 20, 4, False),    # wider than the full-row stencil tiles: 2-D tiled kernel
+    (3, 20, 12, 1, False),     # narrower than the full-row stencil tiles: 2-D tiled kernel
 ]
 
 
@@ -70,8 +72,10 @@ def test_precond_matches_oracle(nx, ny, nz, nf, kb):
         sol.close()
 
 
-@pytest.mark.parametrize("nx,ny,nz,nf,kb", [(20, 12, 30, 4, True), CASES[1], (25, 27, 16, 2, False)])
+@pytest.mark.parametrize("nx,ny,nz,nf,kb", [(20, 12, 30, 4, True), CASES[1], (25, 27, 16, 2, False),
+                                             (16, 16, 24, 4, True), (12, 12, 30, 1, False)])
 def test_fourier_precond_matches_oracle(nx, ny, nz, nf, kb):
+    # non-square and odd planes take the generic FFT, 16x16 and 12x12 the compile-time plans
     # (E - T - H~)^{-1} by lateral FFT + constant-factor z-sweeps against sparse LU
     from paper_1009_5300_gb300 import IOBMSolver
     jn = make(nx, ny, nz, nf, kb)
