@@ -84,6 +84,7 @@ extern "C" int iobm_precond_dots_noalloc(const iobm_grid* grid, double alpha, co
     const iobm_grid& g = *grid;
     if (g.nx < 1 || g.ny < 1 || g.nz < 1) return IOBM_E_ARG;
     if (nrhs == 0) return IOBM_OK;
+    if (nrhs > kNoAllocSlots) return IOBM_E_UNSUPPORTED;   // at least one slot per RHS
     const int per_rhs = stencil_slots(g.nx, g.ny, g.nz, kNoAllocZChunk, 1);
     if ((long long)per_rhs * nrhs > kNoAllocSlots) return IOBM_E_UNSUPPORTED;
     DeviceScratch s;
