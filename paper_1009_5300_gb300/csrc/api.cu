@@ -52,6 +52,9 @@ cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
 }
 
 constexpr int kZChunk = 32;
+// FP64 residual replacements run after every kReplaceEvery-th captured iteration
+// (RHS that became PENDING wait at most kReplaceEvery - 1 iterations)
+constexpr int kReplaceEvery = 2;
 
 }  // namespace
 
@@ -418,7 +421,8 @@ int residual_replacement(iobm_handle* h, int nrhs, int mask, bool mixed, long lo
 // direction in one of two buffers (RhsState::pbuf), so RHS that pause for an
 // FP64 residual replacement resume with their own direction.
 template <typename T>
-int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, int slot = -1) {
+int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, int slot,
+                   bool replace_now) {
     using C = typename Cplx<T>::type;
     const double tol2 = internal_tol2(h);
     const double delta2 = h->opt.refine_delta * h->opt.refine_delta;
@@ -446,9 +450,10 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     a.slot_stride = h->slot_stride;
     a.slot_base = 0;
     // event record nodes inside the captured graph (external records execute with the graph)
-    if (slot >= 0) CK(cudaEventRecordWithFlags(h->kev[2 * slot], h->stream, cudaEventRecordExternal));
+    const bool timed = h->profile && slot >= 0;
+    if (timed) CK(cudaEventRecordWithFlags(h->kev[2 * slot], h->stream, cudaEventRecordExternal));
     CK(launch_stencil<T>(a, nrhs, h->stream));
-    if (slot >= 0)
+    if (timed)
         CK(cudaEventRecordWithFlags(h->kev[2 * slot + 1], h->stream, cudaEventRecordExternal));
     SigmaArgs<T> s = sigma_args<T>(h, sig);
     s.pnew[0] = (const C*)h->vp[0];
@@ -509,9 +514,11 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
         int rc = apply_precond_dots<T>(h, nrhs, M_ACTIVE, launches);
         if (rc) return rc;
     }
-    // FP64 residual replacement of the RHS that became PENDING in this iteration
-    // (masked launches: no work when none is pending)
-    return residual_replacement<T>(h, nrhs, M_PENDING, mixed, launches);
+    // FP64 residual replacement of the RHS that became PENDING since the last one
+    // (masked launches), every kReplaceEvery-th iteration of the captured chunk
+    if (replace_now)
+        return residual_replacement<T>(h, nrhs, M_PENDING, mixed, launches);
+    return IOBM_OK;
 }
 
 template <typename T>
@@ -537,7 +544,7 @@ int run_solver(iobm_handle* h, int nrhs) {
     if (rc) return rc;
 
     // capture one chunk of iterations
-    const int chunk = std::max(1, h->opt.chunk);
+    const int chunk = ((std::max(1, h->opt.chunk) + kReplaceEvery - 1) / kReplaceEvery) * kReplaceEvery;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long per_chunk = 0;
@@ -550,7 +557,8 @@ int run_solver(iobm_handle* h, int nrhs) {
     }
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int it = 0; it < chunk; ++it) {
-        rc = cocg_iteration<T>(h, nrhs, mixed, per_chunk, h->profile ? it : -1);
+        // iteration index `it` places the event pair (profiling) and the replacement
+        rc = cocg_iteration<T>(h, nrhs, mixed, per_chunk, it, (it + 1) % kReplaceEvery == 0);
         if (rc) {
             cudaStreamEndCapture(h->stream, &graph);
             if (graph) cudaGraphDestroy(graph);

@@ -121,10 +121,11 @@ __device__ void fft2(C* plane, C* scratch, const FftAxis& ax, const FftAxis& ay,
     const int nwarps = blockDim.x >> 5;
     const int nx = ax.n, ny = ay.n;
     const int smax = nx > ny ? nx : ny;
+    const int pitch = nx + 1;   // padded rows: column lines do not share one bank
     C* my = scratch + warp * smax;
-    for (int row = warp; row < ny; row += nwarps) fft_line(plane + row * nx, 1, my, ax, twx, inv, lane);
+    for (int row = warp; row < ny; row += nwarps) fft_line(plane + row * pitch, 1, my, ax, twx, inv, lane);
     __syncthreads();
-    for (int col = warp; col < nx; col += nwarps) fft_line(plane + col, nx, my, ay, twy, inv, lane);
+    for (int col = warp; col < nx; col += nwarps) fft_line(plane + col, pitch, my, ay, twy, inv, lane);
     __syncthreads();
 }
 
@@ -136,7 +137,7 @@ template <typename T>
 size_t sigma_smem_bytes(int nx, int ny, int threads) {
     using C = typename Cplx<T>::type;
     const int smax = nx > ny ? nx : ny;
-    return sizeof(C) * ((size_t)nx * ny + (size_t)(threads / 32) * smax) + 3 * 32 * sizeof(double);
+    return sizeof(C) * ((size_t)(nx + 1) * ny + (size_t)(threads / 32) * smax) + 3 * 32 * sizeof(double);
 }
 
 template <typename T>
@@ -153,15 +154,16 @@ __global__ void __launch_bounds__(kSigmaMaxThreads) k_sigma(const SigmaArgs<T> a
     const int nx = a.nx, ny = a.ny, nf = a.nf;
     const int nxy = nx * ny;
     const int smax = nx > ny ? nx : ny;
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    C* scratch = buf + nxy;
+    const int pitch = nx + 1;
+    C* buf = reinterpret_cast<C*>(smem_raw);   // [ny][pitch]
+    C* scratch = buf + ny * pitch;
     double* red = reinterpret_cast<double*>(scratch + (blockDim.x / 32) * smax);
 
     const int plane = (end == 0) ? d : (a.nz - 1 - d);
     const long long off = (long long)rhs * a.npts + (long long)plane * nxy;
     const C* xb = a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x;
     const C* __restrict__ X = xb + off;
-    for (int i = threadIdx.x; i < nxy; i += blockDim.x) buf[i] = X[i];
+    for (int i = threadIdx.x; i < nxy; i += blockDim.x) buf[(i / nx) * pitch + (i % nx)] = X[i];
     __syncthreads();
     fft2(buf, scratch, a.ax, a.ay, a.twx, a.twy, false);
 
@@ -176,9 +178,10 @@ __global__ void __launch_bounds__(kSigmaMaxThreads) k_sigma(const SigmaArgs<T> a
         const int m = threadIdx.x + j * blockDim.x;
         C acc = czero<C>();
         if (m < nxy) {
+            const int sm = (m / nx) * pitch + (m % nx);
             for (int dp = 0; dp < nf; ++dp) {
                 const C* remote = cluster.map_shared_rank(buf, dp);
-                acc = cfma(S[((size_t)m * nf + d) * nf + dp], remote[m], acc);
+                acc = cfma(S[((size_t)m * nf + d) * nf + dp], remote[sm], acc);
             }
             acc = cscale(acc, inv_n);
         }
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(kSigmaMaxThreads) k_sigma(const SigmaArgs<T> a
 #pragma unroll
     for (int j = 0; j < kSigmaPer; ++j) {
         const int m = threadIdx.x + j * blockDim.x;
-        if (m < nxy) buf[m] = out[j];
+        if (m < nxy) buf[(m / nx) * pitch + (m % nx)] = out[j];
     }
     __syncthreads();
     fft2(buf, scratch, a.ax, a.ay, a.twx, a.twy, true);
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(kSigmaMaxThreads) k_sigma(const SigmaArgs<T> a
     C* __restrict__ Y = a.y + off;
     T tre = 0, tim = 0;   // per-thread partials in the working precision
     for (int i = threadIdx.x; i < nxy; i += blockDim.x) {
-        const C s = buf[i];
+        const C s = buf[(i / nx) * pitch + (i % nx)];
         const C xv = X[i];
         Y[i] = csub(Y[i], s);
         tre -= xv.x * s.x - xv.y * s.y;
@@ -243,7 +246,7 @@ cudaError_t launch_sigma(const SigmaArgs<T>& a, int nrhs, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // KB nonlocal term.
 template <typename T>
-__global__ void __launch_bounds__(256) k_kb(const KbArgs<T> a) {
+__global__ void __launch_bounds__(1024) k_kb(const KbArgs<T> a) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);                   // [nproj] E_p-weighted projections
@@ -303,13 +306,13 @@ template <typename T>
 cudaError_t launch_kb(const KbArgs<T>& a, int nrhs, cudaStream_t s) {
     using C = typename Cplx<T>::type;
     if (a.nproj == 0) return cudaSuccess;
-    const size_t smem = sizeof(C) * a.nproj + 3 * 8 * sizeof(double) + 16;
+    const size_t smem = sizeof(C) * a.nproj + 3 * 32 * sizeof(double) + 16;
     if (smem > 48 * 1024) {
         cudaError_t err = cudaFuncSetAttribute(k_kb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
         if (err != cudaSuccess) return err;
     }
-    k_kb<T><<<nrhs, 256, smem, s>>>(a);
+    k_kb<T><<<nrhs, 1024, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -123,18 +123,22 @@ __global__ void k_axpy_update(typename Cplx<T>::type* __restrict__ x,
     }
 }
 
-static int vec_blocks(long long npts) {
+static int vec_blocks(long long npts, int cap = 1024) {
     long long b = (npts + 255) / 256;
-    if (b > 1024) b = 1024;
+    if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
+
+// per-RHS vector kernels run once per RHS in a batch (grid.y = RHS) and are
+// often masked out; a modest per-RHS block count keeps the empty launches cheap
+constexpr int kPerRhsBlocks = 96;
 
 template <typename T>
 cudaError_t launch_axpy_update(typename Cplx<T>::type* x, typename Cplx<T>::type* r,
                                typename Cplx<T>::type* const* pbufs,
                                const typename Cplx<T>::type* q, const RhsState* st, int mask,
                                long long npts, int nrhs, cudaStream_t s) {
-    dim3 grid(vec_blocks(npts), nrhs);
+    dim3 grid(vec_blocks(npts, kPerRhsBlocks), nrhs);
     k_axpy_update<T><<<grid, 256, 0, s>>>(x, r, pbufs[0], pbufs[1], q, st, mask, npts);
     return cudaGetLastError();
 }
@@ -161,7 +165,7 @@ __global__ void k_fold(double2* __restrict__ x64, float2* __restrict__ x32, cons
 
 cudaError_t launch_fold(double2* x64, float2* x32, const RhsState* st, int mask, long long npts,
                         int nrhs, cudaStream_t s) {
-    dim3 grid(vec_blocks(npts), nrhs);
+    dim3 grid(vec_blocks(npts, kPerRhsBlocks), nrhs);
     k_fold<<<grid, 256, 0, s>>>(x64, x32, st, mask, npts);
     return cudaGetLastError();
 }

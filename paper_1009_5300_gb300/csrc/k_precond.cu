@@ -135,9 +135,13 @@ __global__ void __launch_bounds__(256) k_plane_fft_fwd(const PrecondArgs<T> a) {
 
 // z-sweeps of one lateral mode: forward substitution with the constant band
 // multipliers over planes 0 .. nz-nf-1, a dense nf x nf solve on the last nf
-// planes, backward substitution with the constant band rows.  In place.
+// planes, backward substitution with the constant band rows.  In place on the
+// spectrum; one thread per (RHS, mode), loads issued kZPrefetch planes ahead.
+constexpr int kZPrefetch = 4;
+constexpr int kZThreads = 128;
+
 template <typename T, int NF>
-__global__ void __launch_bounds__(64) k_zsolve(const PrecondArgs<T> a) {
+__global__ void __launch_bounds__(kZThreads) k_zsolve(const PrecondArgs<T> a) {
     using C = typename Cplx<T>::type;
     const int rhs = blockIdx.y;
     if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
@@ -156,19 +160,36 @@ __global__ void __launch_bounds__(64) k_zsolve(const PrecondArgs<T> a) {
     const C uinv = cdivc(make_one<C>(), u[0]);
     const int nz = a.nz, m = nz - NF;
     C* __restrict__ s = a.spec + (long long)rhs * a.npts + mode;
-    const T scale = (T)1 / (T)nxy;   // the forward FFT above carries no 1/N_xy
+    const T scale = (T)1 / (T)nxy;   // the forward FFT carries no 1/N_xy
+    constexpr int PF = kZPrefetch;
     // forward: y_k = r_k - sum_j l_j y_{k-j}
     C hist[NF];
 #pragma unroll
     for (int j = 0; j < NF; ++j) hist[j] = czero<C>();   // hist[j] = y_{k-1-j}
-    for (int k = 0; k < m; ++k) {
-        C y = cscale(s[(long long)k * nxy], scale);
+    C buf[PF];
 #pragma unroll
-        for (int j = 1; j <= NF; ++j) y = csub(y, cmul(l[j], hist[j - 1]));
-        s[(long long)k * nxy] = y;
+    for (int j = 0; j < PF; ++j) buf[j] = (j < m) ? s[(long long)j * nxy] : czero<C>();
+    for (int k0 = 0; k0 < m; k0 += PF) {
+        C cur[PF];
 #pragma unroll
-        for (int j = NF - 1; j > 0; --j) hist[j] = hist[j - 1];
-        hist[0] = y;
+        for (int j = 0; j < PF; ++j) {
+            cur[j] = buf[j];
+            const int kk = k0 + PF + j;
+            buf[j] = (kk < m) ? s[(long long)kk * nxy] : czero<C>();
+        }
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int k = k0 + j;
+            if (k < m) {
+                C y = cscale(cur[j], scale);
+#pragma unroll
+                for (int t = 1; t <= NF; ++t) y = csub(y, cmul(l[t], hist[t - 1]));
+                s[(long long)k * nxy] = y;
+#pragma unroll
+                for (int t = NF - 1; t > 0; --t) hist[t] = hist[t - 1];
+                hist[0] = y;
+            }
+        }
     }
     // last nf planes: g_i = r_i - sum_{j: i-j < m} l_j y_{i-j};  x_2 = S2^{-1} g
     C g[NF];
@@ -176,34 +197,44 @@ __global__ void __launch_bounds__(64) k_zsolve(const PrecondArgs<T> a) {
     for (int i = 0; i < NF; ++i) {
         C v = cscale(s[(long long)(m + i) * nxy], scale);
 #pragma unroll
-        for (int j = 1; j <= NF; ++j) {
-            // y_{m+i-j} is hist[j-1-i] when m+i-j <= m-1, i.e. j > i
+        for (int j = 1; j <= NF; ++j)
             if (j > i) v = csub(v, cmul(l[j], hist[j - 1 - i]));
-        }
         g[i] = v;
     }
-    C xl[NF];
+    C nxt[NF];   // nxt[j] = x_{k+1+j}
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
         C v = czero<C>();
 #pragma unroll
         for (int j = 0; j < NF; ++j) v = cfma(S2[i * NF + j], g[j], v);
-        xl[i] = v;
         s[(long long)(m + i) * nxy] = v;
+        nxt[i] = v;
     }
     // backward: x_k = (y_k - sum_j u_j x_{k+j}) / u_0
-    C nxt[NF];   // nxt[j] = x_{k+1+j}
 #pragma unroll
-    for (int j = 0; j < NF; ++j) nxt[j] = xl[j];
-    for (int k = m - 1; k >= 0; --k) {
-        C v = s[(long long)k * nxy];
+    for (int j = 0; j < PF; ++j) buf[j] = (m - 1 - j >= 0) ? s[(long long)(m - 1 - j) * nxy] : czero<C>();
+    for (int k0 = m - 1; k0 >= 0; k0 -= PF) {
+        C cur[PF];
 #pragma unroll
-        for (int j = 1; j <= NF; ++j) v = csub(v, cmul(u[j], nxt[j - 1]));
-        v = cmul(v, uinv);
-        s[(long long)k * nxy] = v;
+        for (int j = 0; j < PF; ++j) {
+            cur[j] = buf[j];
+            const int kk = k0 - PF - j;
+            buf[j] = (kk >= 0) ? s[(long long)kk * nxy] : czero<C>();
+        }
 #pragma unroll
-        for (int j = NF - 1; j > 0; --j) nxt[j] = nxt[j - 1];
-        nxt[0] = v;
+        for (int j = 0; j < PF; ++j) {
+            const int k = k0 - j;
+            if (k >= 0) {
+                C v = cur[j];
+#pragma unroll
+                for (int t = 1; t <= NF; ++t) v = csub(v, cmul(u[t], nxt[t - 1]));
+                v = cmul(v, uinv);
+                s[(long long)k * nxy] = v;
+#pragma unroll
+                for (int t = NF - 1; t > 0; --t) nxt[t] = nxt[t - 1];
+                nxt[0] = v;
+            }
+        }
     }
 }
 
@@ -328,13 +359,19 @@ __device__ __forceinline__ void ct_passes(C*& cur, C*& oth, int ls, int es, cons
     }
 }
 
-// 2D FFT of an N x N plane in shared memory (a), b scratch; returns the result buffer
+// Shared-memory pitch of a plane row: one element of padding so that the
+// column passes (stride = pitch) spread over the banks instead of hitting one.
+template <int N> struct CtPitch { static constexpr int P = N + 1; };
+
+// 2D FFT of an N x N plane in shared memory (a, rows of pitch N+1), b scratch of
+// the same shape; returns the buffer that holds the result
 template <typename C, int N>
 __device__ __forceinline__ C* ct_fft2(C* a, C* b, const C* tw, bool inv) {
+    constexpr int P = CtPitch<N>::P;
     C* cur = a;
     C* oth = b;
-    ct_passes<C, N, 0, 1>(cur, oth, N, 1, tw, inv);   // rows
-    ct_passes<C, N, 0, 1>(cur, oth, 1, N, tw, inv);   // columns
+    ct_passes<C, N, 0, 1>(cur, oth, P, 1, tw, inv);   // rows
+    ct_passes<C, N, 0, 1>(cur, oth, 1, P, tw, inv);   // columns
     return cur;
 }
 
@@ -352,9 +389,10 @@ __global__ void __launch_bounds__(256) k_update_fft_ct(const PrecondArgs<T> a, t
     const int plane = blockIdx.x, rhs = blockIdx.y;
     if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
     constexpr int NXY = N * N;
+    constexpr int PT = CtPitch<N>::P;
     C* A = reinterpret_cast<C*>(smem_raw);
-    C* B = A + NXY;
-    C* tw = B + NXY;
+    C* B = A + N * PT;
+    C* tw = B + N * PT;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.twx[i];
     const long long off = (long long)rhs * a.npts + (long long)plane * NXY;
     if (update) {
@@ -367,14 +405,14 @@ __global__ void __launch_bounds__(256) k_update_fft_ct(const PrecondArgs<T> a, t
             const C rn = csub(R[i], cmul(al, Q[i]));
             Xv[i] = cfma(al, P[i], Xv[i]);
             R[i] = rn;
-            A[i] = rn;
+            A[(i / N) * PT + (i % N)] = rn;
         }
     } else {
-        for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[i] = a.r[off + i];
+        for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[(i / N) * PT + (i % N)] = a.r[off + i];
     }
     __syncthreads();
     C* res = ct_fft2<C, N>(A, B, tw, false);
-    for (int i = threadIdx.x; i < NXY; i += blockDim.x) a.spec[off + i] = res[i];
+    for (int i = threadIdx.x; i < NXY; i += blockDim.x) a.spec[off + i] = res[(i / N) * PT + (i % N)];
 }
 
 template <typename T, int N>
@@ -385,17 +423,18 @@ __global__ void __launch_bounds__(256) k_ifft_dots_ct(const PrecondArgs<T> a) {
     const int plane = blockIdx.x, rhs = blockIdx.y;
     if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
     constexpr int NXY = N * N;
+    constexpr int PT = CtPitch<N>::P;
     C* A = reinterpret_cast<C*>(smem_raw);
-    C* B = A + NXY;
-    C* tw = B + NXY;
+    C* B = A + N * PT;
+    C* tw = B + N * PT;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.twx[i];
     const long long off = (long long)rhs * a.npts + (long long)plane * NXY;
-    for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[i] = a.spec[off + i];
+    for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[(i / N) * PT + (i % N)] = a.spec[off + i];
     __syncthreads();
     C* res = ct_fft2<C, N>(A, B, tw, true);
     T dre = 0, dim = 0, nrm = 0;
     for (int i = threadIdx.x; i < NXY; i += blockDim.x) {
-        const C z = res[i];
+        const C z = res[(i / N) * PT + (i % N)];
         a.z[off + i] = z;
         if (a.dot_part) {
             const C r = a.r[off + i];
@@ -411,98 +450,6 @@ __global__ void __launch_bounds__(256) k_ifft_dots_ct(const PrecondArgs<T> a) {
             a.dot_part[(long long)rhs * a.slot_stride + plane] = make_double2(d0, d1);
             a.nrm_part[(long long)rhs * a.slot_stride + plane] = d2;
         }
-    }
-}
-
-// z-sweeps keeping the intermediate forward-sweep values of each mode in shared
-// memory (the spectrum is read once and written once)
-template <typename T, int NF>
-__global__ void __launch_bounds__(64) k_zsolve_smem(const PrecondArgs<T> a) {
-    using C = typename Cplx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int rhs = blockIdx.y;
-    if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
-    const int nxy = a.nx * a.ny;
-    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nz = a.nz, m = nz - NF;
-    C* col = reinterpret_cast<C*>(smem_raw) + threadIdx.x;   // col[k * blockDim.x]
-    const int cs = blockDim.x;
-    if (mode >= nxy) return;
-    const int e = a.rhs_energy ? a.rhs_energy[rhs] : 0;
-    const C* __restrict__ pc = a.pc + ((size_t)e * nxy + mode) * kPcStrideDev;
-    C l[NF + 1], u[NF + 1], S2[NF * NF];
-#pragma unroll
-    for (int j = 1; j <= NF; ++j) l[j] = pc[j - 1];
-#pragma unroll
-    for (int j = 0; j <= NF; ++j) u[j] = pc[NF + j];
-#pragma unroll
-    for (int i = 0; i < NF * NF; ++i) S2[i] = pc[2 * NF + 1 + i];
-    const C uinv = cdivc(make_one<C>(), u[0]);
-    const C* __restrict__ sin_ = a.spec + (long long)rhs * a.npts + mode;
-    C* __restrict__ sout = a.spec + (long long)rhs * a.npts + mode;
-    const T scale = (T)1 / (T)nxy;
-    C hist[NF];
-#pragma unroll
-    for (int j = 0; j < NF; ++j) hist[j] = czero<C>();
-    constexpr int PF = 4;   // loads issued ahead of use
-    C buf[PF];
-#pragma unroll
-    for (int j = 0; j < PF; ++j) buf[j] = (j < nz) ? sin_[(long long)j * nxy] : czero<C>();
-    for (int k0 = 0; k0 < m; k0 += PF) {
-        C cur[PF];
-#pragma unroll
-        for (int j = 0; j < PF; ++j) cur[j] = buf[j];
-#pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int kk = k0 + PF + j;
-            buf[j] = (kk < nz) ? sin_[(long long)kk * nxy] : czero<C>();
-        }
-#pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int k = k0 + j;
-            if (k < m) {
-                C y = cscale(cur[j], scale);
-#pragma unroll
-                for (int t = 1; t <= NF; ++t) y = csub(y, cmul(l[t], hist[t - 1]));
-                col[k * cs] = y;
-#pragma unroll
-                for (int t = NF - 1; t > 0; --t) hist[t] = hist[t - 1];
-                hist[0] = y;
-            } else if (k < nz) {
-                col[k * cs] = cur[j];   // last nf planes, still unscaled
-            }
-        }
-    }
-    // planes beyond the last full prefetch block (when m is a multiple of PF the
-    // last nf planes are still in buf)
-    for (int k = ((m + PF - 1) / PF) * PF; k < nz; ++k) col[k * cs] = sin_[(long long)k * nxy];
-    C g[NF];
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-        C v = cscale(col[(m + i) * cs], scale);
-#pragma unroll
-        for (int j = 1; j <= NF; ++j)
-            if (j > i) v = csub(v, cmul(l[j], hist[j - 1 - i]));
-        g[i] = v;
-    }
-    C nxt[NF];
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-        C v = czero<C>();
-#pragma unroll
-        for (int j = 0; j < NF; ++j) v = cfma(S2[i * NF + j], g[j], v);
-        nxt[i] = v;
-        sout[(long long)(m + i) * nxy] = v;
-    }
-    for (int k = m - 1; k >= 0; --k) {
-        C v = col[k * cs];
-#pragma unroll
-        for (int j = 1; j <= NF; ++j) v = csub(v, cmul(u[j], nxt[j - 1]));
-        v = cmul(v, uinv);
-        sout[(long long)k * nxy] = v;
-#pragma unroll
-        for (int j = NF - 1; j > 0; --j) nxt[j] = nxt[j - 1];
-        nxt[0] = v;
     }
 }
 
@@ -523,10 +470,6 @@ static cudaError_t prepare_type() {
     };
     set((const void*)k_plane_fft_fwd<T>);
     set((const void*)k_plane_ifft_dots<T>);
-    set((const void*)k_zsolve_smem<T, 1>);
-    set((const void*)k_zsolve_smem<T, 2>);
-    set((const void*)k_zsolve_smem<T, 3>);
-    set((const void*)k_zsolve_smem<T, 4>);
 #define IOBM_CT(N)                                    \
     set((const void*)k_update_fft_ct<T, N>);          \
     set((const void*)k_ifft_dots_ct<T, N>);
@@ -547,26 +490,14 @@ static bool ct_size(int nx, int ny) {
 
 template <typename T>
 static cudaError_t launch_zsolve(const PrecondArgs<T>& a, int nrhs, cudaStream_t s) {
-    using C = typename Cplx<T>::type;
     const int nxy = a.nx * a.ny;
-    dim3 gz((nxy + 63) / 64, nrhs);
-    const size_t smem = sizeof(C) * 64 * (size_t)a.nz;
-    if (smem <= (size_t)kPrecondSmemLimit) {
-        switch (a.nf) {
-            case 1: k_zsolve_smem<T, 1><<<gz, 64, smem, s>>>(a); break;
-            case 2: k_zsolve_smem<T, 2><<<gz, 64, smem, s>>>(a); break;
-            case 3: k_zsolve_smem<T, 3><<<gz, 64, smem, s>>>(a); break;
-            case 4: k_zsolve_smem<T, 4><<<gz, 64, smem, s>>>(a); break;
-            default: return cudaErrorInvalidValue;
-        }
-    } else {
-        switch (a.nf) {
-            case 1: k_zsolve<T, 1><<<gz, 64, 0, s>>>(a); break;
-            case 2: k_zsolve<T, 2><<<gz, 64, 0, s>>>(a); break;
-            case 3: k_zsolve<T, 3><<<gz, 64, 0, s>>>(a); break;
-            case 4: k_zsolve<T, 4><<<gz, 64, 0, s>>>(a); break;
-            default: return cudaErrorInvalidValue;
-        }
+    dim3 gz((nxy + kZThreads - 1) / kZThreads, nrhs);
+    switch (a.nf) {
+        case 1: k_zsolve<T, 1><<<gz, kZThreads, 0, s>>>(a); break;
+        case 2: k_zsolve<T, 2><<<gz, kZThreads, 0, s>>>(a); break;
+        case 3: k_zsolve<T, 3><<<gz, kZThreads, 0, s>>>(a); break;
+        case 4: k_zsolve<T, 4><<<gz, kZThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
@@ -579,7 +510,7 @@ static cudaError_t launch_fwd_ct(const PrecondArgs<T>& a, int nrhs, cudaStream_t
                                  const typename Cplx<T>::type* q, int update) {
     using C = typename Cplx<T>::type;
     const int N = a.nx;
-    const size_t smem = sizeof(C) * (2 * (size_t)N * N + N);
+    const size_t smem = sizeof(C) * (2 * (size_t)N * (N + 1) + N);
     dim3 gp(a.nz, nrhs);
     switch (N) {
 #define IOBM_CT(NN) \
@@ -595,7 +526,7 @@ template <typename T>
 static cudaError_t launch_inv_ct(const PrecondArgs<T>& a, int nrhs, cudaStream_t s) {
     using C = typename Cplx<T>::type;
     const int N = a.nx;
-    const size_t smem = sizeof(C) * (2 * (size_t)N * N + N);
+    const size_t smem = sizeof(C) * (2 * (size_t)N * (N + 1) + N);
     dim3 gp(a.nz, nrhs);
     switch (N) {
 #define IOBM_CT(NN) case NN: k_ifft_dots_ct<T, NN><<<gp, 256, smem, s>>>(a); break;

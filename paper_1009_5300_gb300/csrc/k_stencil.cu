@@ -239,16 +239,19 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
     double dre64 = 0.0, dim64 = 0.0, nrm64 = 0.0;
     C* row = tile + (NF + ly) * nx;
 
+    // halo values of plane k are loaded one plane ahead
+    C hv[2], hvn[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) hv[t] = (t < nh) ? ld(k0, hlat[t]) : czero<C>();
+
     for (int k = k0; k < k1; ++k) {
         {
             const int kk = k + NF;
             q[2 * NF] = own ? ld(kk, own_lat) : czero<C>();
             if (PN && own && kk < k1) PN[(long long)kk * plane + own_lat] = q[2 * NF];
         }
-        C hv[2];
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
-            if (t < nh) hv[t] = ld(k, hlat[t]);
+        for (int t = 0; t < 2; ++t) hvn[t] = (t < nh && k + 1 < k1) ? ld(k + 1, hlat[t]) : czero<C>();
         __syncthreads();   // previous plane's taps are done
 #pragma unroll
         for (int t = 0; t < 2; ++t)
@@ -283,6 +286,8 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
         }
 #pragma unroll
         for (int j = 0; j < 2 * NF; ++j) q[j] = q[j + 1];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) hv[t] = hvn[t];
     }
 
     if (a.dot_mode) {
