@@ -204,28 +204,21 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
     // shared-memory rows this thread fetches every plane (halo rows and the rows
     // of a partial tile): s = ly and s = ly + kRowTY, skipping own rows
     constexpr int SR = kRowTY + 2 * NF;
-    int hs[2];
+    // the (at most two) shared-memory rows this thread fills from global memory
+    bool hf[2];
+    int hsm[2];
     long long hlat[2];
-    int nh = 0;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const int srow = ly + t * kRowTY;
-        if (srow < SR && !(srow >= NF && srow < NF + rows)) {
-            int gy = ty0 - NF + srow;
-            gy %= ny;
-            if (gy < 0) gy += ny;
-            hs[nh] = srow;
-            hlat[nh] = (long long)gy * nx + x;
-            ++nh;
-        }
+        hf[t] = srow < SR && !(srow >= NF && srow < NF + rows);
+        int gy = ty0 - NF + srow;
+        gy %= ny;
+        if (gy < 0) gy += ny;
+        hsm[t] = srow * nx + x;
+        hlat[t] = (long long)gy * nx + x;
     }
     const long long own_lat = own ? (long long)(ty0 + ly) * nx + x : 0;
-    int xm[NF + 1], xp[NF + 1];
-#pragma unroll
-    for (int n = 1; n <= NF; ++n) {
-        xm[n] = x - n < 0 ? x - n + nx : x - n;
-        xp[n] = x + n >= nx ? x + n - nx : x + n;
-    }
 
     C q[2 * NF + 1];
 #pragma unroll
@@ -242,7 +235,7 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
     // halo values of plane k are loaded one plane ahead
     C hv[2], hvn[2];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) hv[t] = (t < nh) ? ld(k0, hlat[t]) : czero<C>();
+    for (int t = 0; t < 2; ++t) hv[t] = hf[t] ? ld(k0, hlat[t]) : czero<C>();
 
     for (int k = k0; k < k1; ++k) {
         {
@@ -251,11 +244,11 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
             if (PN && own && kk < k1) PN[(long long)kk * plane + own_lat] = q[2 * NF];
         }
 #pragma unroll
-        for (int t = 0; t < 2; ++t) hvn[t] = (t < nh && k + 1 < k1) ? ld(k + 1, hlat[t]) : czero<C>();
+        for (int t = 0; t < 2; ++t) hvn[t] = (hf[t] && k + 1 < k1) ? ld(k + 1, hlat[t]) : czero<C>();
         __syncthreads();   // previous plane's taps are done
 #pragma unroll
         for (int t = 0; t < 2; ++t)
-            if (t < nh) tile[hs[t] * nx + x] = hv[t];
+            if (hf[t]) tile[hsm[t]] = hv[t];
         if (own) row[x] = q[NF];
         __syncthreads();
         if (own) {
@@ -266,8 +259,10 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
             C acc = cscale(x0, d);
 #pragma unroll
             for (int n = 1; n <= NF; ++n) {
+                const int xm = (x - n < 0) ? x - n + nx : x - n;     // periodic in x (nx >= NF)
+                const int xp = (x + n >= nx) ? x + n - nx : x + n;
                 acc = caxpy(a.cz[n], csub(cadd(q[NF - n], q[NF + n]), x2), acc);
-                acc = caxpy(a.cx[n], csub(cadd(row[xm[n]], row[xp[n]]), x2), acc);
+                acc = caxpy(a.cx[n], csub(cadd(row[xm], row[xp]), x2), acc);
                 acc = caxpy(a.cy[n], csub(cadd(row[x - n * nx], row[x + n * nx]), x2), acc);
             }
             Y[(long long)k * plane + own_lat] = acc;
