@@ -379,7 +379,7 @@ __device__ __forceinline__ C* ct_fft2(C* a, C* b, const C* tw, bool inv) {
 // of the new r into the spectrum buffer.  With alpha_from_state = 0 it is the
 // plain forward transform of r.
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_update_fft_ct(const PrecondArgs<T> a, typename Cplx<T>::type* x,
+__global__ void __launch_bounds__(256, 4) k_update_fft_ct(const PrecondArgs<T> a, typename Cplx<T>::type* x,
                                                        typename Cplx<T>::type* r_rw,
                                                        typename Cplx<T>::type* p0,
                                                        typename Cplx<T>::type* p1,
@@ -401,11 +401,28 @@ __global__ void __launch_bounds__(256) k_update_fft_ct(const PrecondArgs<T> a, t
         C* __restrict__ Xv = x + off;
         C* __restrict__ R = r_rw + off;
         const C* __restrict__ Q = q + off;
-        for (int i = threadIdx.x; i < NXY; i += blockDim.x) {
-            const C rn = csub(R[i], cmul(al, Q[i]));
-            Xv[i] = cfma(al, P[i], Xv[i]);
-            R[i] = rn;
-            A[(i / N) * PT + (i % N)] = rn;
+        // all loads of this thread's points first, then the arithmetic and stores
+        constexpr int PER = (NXY + 255) / 256;
+        C rv[PER], qv[PER], xv[PER], pv[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int i = threadIdx.x + j * 256;
+            if (i < NXY) {
+                rv[j] = R[i];
+                qv[j] = Q[i];
+                xv[j] = Xv[i];
+                pv[j] = P[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int i = threadIdx.x + j * 256;
+            if (i < NXY) {
+                const C rn = csub(rv[j], cmul(al, qv[j]));
+                R[i] = rn;
+                A[(i / N) * PT + (i % N)] = rn;
+                Xv[i] = cfma(al, pv[j], xv[j]);
+            }
         }
     } else {
         for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[(i / N) * PT + (i % N)] = a.r[off + i];
@@ -416,7 +433,7 @@ __global__ void __launch_bounds__(256) k_update_fft_ct(const PrecondArgs<T> a, t
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_ifft_dots_ct(const PrecondArgs<T> a) {
+__global__ void __launch_bounds__(256, 4) k_ifft_dots_ct(const PrecondArgs<T> a) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[3 * 8];
@@ -430,14 +447,27 @@ __global__ void __launch_bounds__(256) k_ifft_dots_ct(const PrecondArgs<T> a) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.twx[i];
     const long long off = (long long)rhs * a.npts + (long long)plane * NXY;
     for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[(i / N) * PT + (i % N)] = a.spec[off + i];
+    // r is needed only after the transform: load it now so the loads overlap the FFT
+    constexpr int PER = (NXY + 255) / 256;
+    C rv[PER];
+    if (a.dot_part) {
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int i = threadIdx.x + j * 256;
+            rv[j] = (i < NXY) ? a.r[off + i] : czero<C>();
+        }
+    }
     __syncthreads();
     C* res = ct_fft2<C, N>(A, B, tw, true);
     T dre = 0, dim = 0, nrm = 0;
-    for (int i = threadIdx.x; i < NXY; i += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int i = threadIdx.x + j * 256;
+        if (i >= NXY) continue;
         const C z = res[(i / N) * PT + (i % N)];
         a.z[off + i] = z;
         if (a.dot_part) {
-            const C r = a.r[off + i];
+            const C r = rv[j];
             dre += r.x * z.x - r.y * z.y;
             dim += r.x * z.y + r.y * z.x;
             nrm += r.x * r.x + r.y * r.y;

@@ -232,19 +232,37 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
     double dre64 = 0.0, dim64 = 0.0, nrm64 = 0.0;
     C* row = tile + (NF + ly) * nx;
 
-    // halo values of plane k are loaded one plane ahead
-    C hv[2], hvn[2];
+    // Software pipeline: the raw operands (z and p_old) of the own value of
+    // plane k+1+NF and of the halo of plane k+1 are loaded during plane k and
+    // only combined (p = z + beta p_old) when plane k+1 is processed, so no
+    // load is waited on in the iteration that issues it.
+    auto raw = [&](int k, long long lat, C& zv, C& pv) {
+        if (k < 0 || k >= nz) {
+            zv = czero<C>();
+            pv = czero<C>();
+            return;
+        }
+        const long long i = (long long)k * plane + lat;
+        zv = X[i];
+        pv = PO ? PO[i] : czero<C>();
+    };
+    C oz, op;                 // own, plane k+NF
+    C hz[2], hp[2];           // halo, plane k
+    raw(own ? k0 + NF : -1, own_lat, oz, op);
 #pragma unroll
-    for (int t = 0; t < 2; ++t) hv[t] = hf[t] ? ld(k0, hlat[t]) : czero<C>();
+    for (int t = 0; t < 2; ++t) raw(hf[t] ? k0 : -1, hlat[t], hz[t], hp[t]);
 
     for (int k = k0; k < k1; ++k) {
-        {
-            const int kk = k + NF;
-            q[2 * NF] = own ? ld(kk, own_lat) : czero<C>();
-            if (PN && own && kk < k1) PN[(long long)kk * plane + own_lat] = q[2 * NF];
-        }
+        // combine the operands that arrived during the previous plane
+        q[2 * NF] = cfma(beta, op, oz);
+        if (PN && own && k + NF < k1) PN[(long long)(k + NF) * plane + own_lat] = q[2 * NF];
+        C hv[2];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) hvn[t] = (hf[t] && k + 1 < k1) ? ld(k + 1, hlat[t]) : czero<C>();
+        for (int t = 0; t < 2; ++t) hv[t] = cfma(beta, hp[t], hz[t]);
+        // issue the loads for the next plane
+        raw(own ? k + 1 + NF : -1, own_lat, oz, op);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) raw((hf[t] && k + 1 < k1) ? k + 1 : -1, hlat[t], hz[t], hp[t]);
         __syncthreads();   // previous plane's taps are done
 #pragma unroll
         for (int t = 0; t < 2; ++t)
@@ -281,8 +299,6 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
         }
 #pragma unroll
         for (int j = 0; j < 2 * NF; ++j) q[j] = q[j + 1];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) hv[t] = hvn[t];
     }
 
     if (a.dot_mode) {
