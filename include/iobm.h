@@ -167,6 +167,11 @@ int iobm_open_channels(iobm_handle* h, double E, int* n_open, int max_out, int* 
  * unconjugated COCG form b^T P b vanish, so the solver runs the real lateral
  * profiles cos(G.r) and sin(G.r) of each +-G channel pair and recombines them
  * (two internal RHS per pair, one for a self-conjugate G). */
+/* The per-energy mode tables built for the count are kept in the handle and
+ * taken over by the next iobm_solve if it has the same energies (bit-identical
+ * values, same order), which then skips rebuilding them; a count, solve or
+ * gradient with other energies discards them.  The tables depend on the
+ * lateral grid, N_f and E only, never on the potential. */
 int iobm_solve_rhs_count(iobm_handle* h, const double* E, int nE, const int* channels, int nch,
                          int* n_internal);
 
@@ -188,6 +193,10 @@ int iobm_solve(iobm_handle* h, const double* E, int nE, const int* channels, int
 
 /* Number of incident channels (user-visible RHS) of the last solve. */
 int iobm_num_rhs(const iobm_handle* h);
+
+/* Largest open-channel count over the energies of the last solve (the
+ * smallest max_open iobm_transmission accepts); 0 before any solve. */
+int iobm_max_open(const iobm_handle* h);
 
 /* Transmission/reflection of the last solve (Eq. 6, Landauer-Buttiker of
  * Sec. III).  T, R: host [rhs][max_open] with T[rhs][o] = |t_o|^2 v_o / v_in

@@ -70,6 +70,7 @@ SIGNATURES = {
     "iobm_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "iobm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "iobm_num_rhs": (C.c_int, [C.c_void_p]),
+    "iobm_max_open": (C.c_int, [C.c_void_p]),
     "iobm_transmission": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
     "iobm_solution": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),

@@ -82,6 +82,8 @@ struct iobm_handle {
     DevBuf sig32, sig64, pc32, pc64, ediag, rhs_energy, descs, open_ptr, open_bins, proj_out;
     DevBuf apply_sig32, apply_sig64, apply_pc32, apply_pc64, apply_ediag;
     std::vector<ModeTables> energies;
+    std::vector<double> memo_E;          // energies of the tables kept by the last RHS count
+    std::vector<ModeTables> memo_tables;
     std::vector<RhsDesc> hdesc;          // internal (real-profile) RHS
     std::vector<int> hrhs_energy;        // per internal RHS
     struct User {                        // one incident channel: psi = x[ic] + sign i x[is]
@@ -663,12 +665,19 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
     for (int e = 0; e < nE; ++e)
         if (!std::isfinite(E[e])) return fail(h, IOBM_E_ARG, "non-finite energy");
     std::vector<ModeTables> tables;
-    {
+    const bool memo_hit = upload_tables && (int)h->memo_E.size() == nE &&
+                          std::equal(h->memo_E.begin(), h->memo_E.end(), E);
+    if (memo_hit) {
+        tables = std::move(h->memo_tables);
+    } else {
         std::string msg;
+        // a count (no upload) builds the full tables too, for the solve that follows it
         const int rc = build_mode_tables_many(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, nf, E, nE,
-                                              upload_tables, tables, msg);
+                                              true, tables, msg);
         if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
     }
+    h->memo_E.clear();
+    h->memo_tables.clear();
     for (int e = 0; e < nE; ++e) {
         ModeTables& mt = tables[e];
         if (upload_tables) {
@@ -722,7 +731,13 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
         h->energies.push_back(std::move(mt));
     }
     h->nrhs = (int)h->hdesc.size();
-    if (!upload_tables) return IOBM_OK;
+    if (!upload_tables) {
+        // keep the tables for the solve that normally follows a count
+        h->memo_E.assign(E, E + nE);
+        h->memo_tables = std::move(h->energies);
+        h->energies.clear();
+        return IOBM_OK;
+    }
     // device tables
     std::vector<double2> s64(sig_all.size()), p64(pc_all.size());
     std::vector<float2> s32(sig_all.size()), p32(pc_all.size());
@@ -1036,6 +1051,8 @@ int iobm_solve(iobm_handle* h, const double* E, int nE, const int* channels, int
 }
 
 int iobm_num_rhs(const iobm_handle* h) { return h ? (int)h->users.size() : 0; }
+
+int iobm_max_open(const iobm_handle* h) { return (h && h->solved) ? h->max_open : 0; }
 
 int iobm_solve_rhs_count(iobm_handle* h, const double* E, int nE, const int* channels, int nch,
                          int* n_internal) {

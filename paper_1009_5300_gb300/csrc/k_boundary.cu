@@ -19,6 +19,7 @@
 
 #include "iobm_internal.cuh"
 #include "complex_ops.cuh"
+#include "fft_ct.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -214,6 +215,109 @@ __global__ void __launch_bounds__(kSigmaMaxThreads) k_sigma(const SigmaArgs<T> a
     }
 }
 
+// The same cluster scheme for square N x N planes with a compile-time FFT plan:
+// 256 threads spread every butterfly pass over all lines of the plane, each
+// thread keeps its operand points in registers for the closing dot product.
+constexpr int kSigmaCtThreads = 256;
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kSigmaCtThreads) k_sigma_ct(const SigmaArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int d = blockIdx.x;
+    const int end = blockIdx.y;
+    const int rhs = blockIdx.z;
+    const int st = a.state ? a.state[rhs].status : ST_ACTIVE;
+    if (!((1 << st) & a.mask)) return;   // uniform over the cluster
+
+    constexpr int NXY = N * N;
+    constexpr int PT = CtPitch<N>::P;
+    constexpr int PER = (NXY + kSigmaCtThreads - 1) / kSigmaCtThreads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* A = reinterpret_cast<C*>(smem_raw);   // [N][PT] spectrum (the result of ct_fft2 lands here)
+    C* B = A + N * PT;                       // ping-pong scratch
+    C* tw = B + N * PT;
+    __shared__ double red[3 * (kSigmaCtThreads / 32)];
+    const int nf = a.nf;
+    for (int i = threadIdx.x; i < N; i += kSigmaCtThreads) tw[i] = a.twx[i];
+
+    const int plane = (end == 0) ? d : (a.nz - 1 - d);
+    const long long off = (long long)rhs * a.npts + (long long)plane * NXY;
+    const C* xb = a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x;
+    const C* __restrict__ X = xb + off;
+    C* __restrict__ Y = a.y + off;
+    C xv[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int i = threadIdx.x + j * kSigmaCtThreads;
+        if (i < NXY) {
+            xv[j] = X[i];
+            A[(i / N) * PT + (i % N)] = xv[j];
+        }
+    }
+    __syncthreads();
+    ct_fft2<C, N>(A, B, tw, false);   // an even number of passes: the spectrum is in A
+
+    cluster.sync();   // every spectrum of the cluster is complete
+
+    const int e = a.rhs_energy ? a.rhs_energy[rhs] : 0;
+    const C* __restrict__ S = a.sigma + (size_t)e * NXY * nf * nf;
+    const T inv_n = (T)1 / (T)NXY;
+    C out[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int m = threadIdx.x + j * kSigmaCtThreads;
+        C acc = czero<C>();
+        if (m < NXY) {
+            const int sm = (m / N) * PT + (m % N);
+            const C* Sm = S + ((size_t)m * nf + d) * nf;
+            for (int dp = 0; dp < nf; ++dp) {
+                const C* remote = cluster.map_shared_rank(A, dp);
+                acc = cfma(Sm[dp], remote[sm], acc);
+            }
+            acc = cscale(acc, inv_n);
+        }
+        out[j] = acc;
+    }
+    cluster.sync();   // all remote reads done before the spectra are overwritten
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int m = threadIdx.x + j * kSigmaCtThreads;
+        if (m < NXY) A[(m / N) * PT + (m % N)] = out[j];
+    }
+    __syncthreads();
+    ct_fft2<C, N>(A, B, tw, true);
+
+    T tre = 0, tim = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int i = threadIdx.x + j * kSigmaCtThreads;
+        if (i < NXY) {
+            const C sv = A[(i / N) * PT + (i % N)];
+            Y[i] = csub(Y[i], sv);
+            tre -= xv[j].x * sv.x - xv[j].y * sv.y;
+            tim -= xv[j].x * sv.y + xv[j].y * sv.x;
+        }
+    }
+    if (a.dot_part) {
+        double sre = tre, sim = tim, dummy = 0.0;
+        block_reduce_3(sre, sim, dummy, red);
+        if (threadIdx.x == 0)
+            a.dot_part[(long long)rhs * a.slot_stride + a.slot_base + end * nf + d] =
+                make_double2(sre, sim);
+    }
+}
+
+template <typename T, int N>
+size_t sigma_ct_smem_bytes() {
+    using C = typename Cplx<T>::type;
+    return sizeof(C) * (2 * (size_t)N * CtPitch<N>::P + N);
+}
+
+static bool sigma_ct_size(int nx, int ny) {
+    return nx == ny && (nx == 12 || nx == 16 || nx == 24 || nx == 32 || nx == 48 || nx == 64);
+}
+
 static int sigma_threads(int nxy) {
     int t = (nxy + kSigmaPer - 1) / kSigmaPer;
     t = ((t + 31) / 32) * 32;
@@ -224,14 +328,8 @@ static int sigma_threads(int nxy) {
 template <typename T>
 cudaError_t launch_sigma(const SigmaArgs<T>& a, int nrhs, cudaStream_t s) {
     const int nxy = a.nx * a.ny;
-    const int threads = sigma_threads(nxy);
-    if (threads > kSigmaMaxThreads) return cudaErrorInvalidValue;
-    const size_t smem = sigma_smem_bytes<T>(a.nx, a.ny, threads);
-    if (smem > kSigmaMaxSmem) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.nf, 2, nrhs);
-    cfg.blockDim = dim3(threads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -240,6 +338,24 @@ cudaError_t launch_sigma(const SigmaArgs<T>& a, int nrhs, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (sigma_ct_size(a.nx, a.ny)) {
+        cfg.blockDim = dim3(kSigmaCtThreads, 1, 1);
+        switch (a.nx) {
+#define IOBM_SIG(NN)                                              \
+            case NN:                                              \
+                cfg.dynamicSmemBytes = sigma_ct_smem_bytes<T, NN>(); \
+                return cudaLaunchKernelEx(&cfg, k_sigma_ct<T, NN>, a);
+            IOBM_SIG(12) IOBM_SIG(16) IOBM_SIG(24) IOBM_SIG(32) IOBM_SIG(48) IOBM_SIG(64)
+#undef IOBM_SIG
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    const int threads = sigma_threads(nxy);
+    if (threads > kSigmaMaxThreads) return cudaErrorInvalidValue;
+    const size_t smem = sigma_smem_bytes<T>(a.nx, a.ny, threads);
+    if (smem > kSigmaMaxSmem) return cudaErrorInvalidValue;
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
     return cudaLaunchKernelEx(&cfg, k_sigma<T>, a);
 }
 
@@ -324,6 +440,15 @@ cudaError_t sigma_prepare() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sigma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSigmaMaxSmem);
+#define IOBM_SIG(NN)                                                                              \
+    if (e == cudaSuccess)                                                                         \
+        e = cudaFuncSetAttribute(k_sigma_ct<float, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)sigma_ct_smem_bytes<float, NN>());                          \
+    if (e == cudaSuccess)                                                                         \
+        e = cudaFuncSetAttribute(k_sigma_ct<double, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)sigma_ct_smem_bytes<double, NN>());
+    IOBM_SIG(12) IOBM_SIG(16) IOBM_SIG(24) IOBM_SIG(32) IOBM_SIG(48) IOBM_SIG(64)
+#undef IOBM_SIG
     return e;
 }
 

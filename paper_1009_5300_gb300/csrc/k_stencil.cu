@@ -9,11 +9,12 @@
 // memory for the lateral taps.  Planes beyond 0 and nz-1 are zero (Eq. 4:
 // the truncated operator; the self-energy kernel adds the boundary term).
 //
-// The taps are applied in difference form, c_n (x_{+n} + x_{-n} - 2 x_0): for the
-// kinetic operator the weights sum to zero, so the large diagonal cancels
-// analytically and the FP32 result keeps the precision of the smooth
+// In FP32 the taps are applied in difference form, c_n (x_{+n} + x_{-n} - 2 x_0):
+// for the kinetic operator the weights sum to zero, so the large diagonal
+// cancels analytically and the FP32 result keeps the precision of the smooth
 // components (the centre coefficient c0 passed in is the diagonal plus
-// 2 sum_n c_n, which is zero for the FD Laplacian).
+// 2 sum_n c_n, which is zero for the FD Laplacian).  FP64 has the digits to
+// spare and applies the direct form, one FP64 operation fewer per tap pair.
 //
 // In the fused COCG mode the operand is p = z + beta * p_old, formed on the
 // fly wherever p is read and stored once per point by its owning CTA; the
@@ -65,6 +66,9 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(const StencilArgs<T> a) {
     C* __restrict__ PN = a.fused_p ? a.pbufs[1 - pb] + base : nullptr;
     const T ed = a.ediag ? (T)a.ediag[a.rhs_energy ? a.rhs_energy[rhs] : 0] : (T)0;
     const T cen = a.c0 + ed;
+    T tapsum2 = 0;   // 2 sum_n (c_x,n + c_y,n + c_z,n): moves the taps' diagonal into the direct form
+#pragma unroll
+    for (int n = 1; n <= NF; ++n) tapsum2 += 2 * (a.cx[n] + a.cy[n] + a.cz[n]);
 
     auto ld = [&](int k, long long lat) -> C {
         if (k < 0 || k >= nz) return czero<C>();
@@ -106,14 +110,26 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(const StencilArgs<T> a) {
             T d = cen;
             if (a.V) d += a.vsign * a.V[(long long)k * plane + own_lat];
             const C x0 = q[NF];
-            const C x2 = cadd(x0, x0);
-            C acc = cscale(x0, d);
+            C acc;
+            if constexpr (sizeof(T) == 8) {
+                // FP64: direct form, the diagonal carries -2 sum c_n
+                acc = cscale(x0, d - tapsum2);
 #pragma unroll
-            for (int n = 1; n <= NF; ++n) {
-                // difference form: c_n (x_{+n} + x_{-n} - 2 x_0), the kinetic diagonal cancels
-                acc = caxpy(a.cz[n], csub(cadd(q[NF - n], q[NF + n]), x2), acc);
-                acc = caxpy(a.cx[n], csub(cadd(tile[ly + NF][lx + NF - n], tile[ly + NF][lx + NF + n]), x2), acc);
-                acc = caxpy(a.cy[n], csub(cadd(tile[ly + NF - n][lx + NF], tile[ly + NF + n][lx + NF]), x2), acc);
+                for (int n = 1; n <= NF; ++n) {
+                    acc = caxpy(a.cz[n], cadd(q[NF - n], q[NF + n]), acc);
+                    acc = caxpy(a.cx[n], cadd(tile[ly + NF][lx + NF - n], tile[ly + NF][lx + NF + n]), acc);
+                    acc = caxpy(a.cy[n], cadd(tile[ly + NF - n][lx + NF], tile[ly + NF + n][lx + NF]), acc);
+                }
+            } else {
+                const C x2 = cadd(x0, x0);
+                acc = cscale(x0, d);
+#pragma unroll
+                for (int n = 1; n <= NF; ++n) {
+                    // difference form: c_n (x_{+n} + x_{-n} - 2 x_0), the kinetic diagonal cancels
+                    acc = caxpy(a.cz[n], csub(cadd(q[NF - n], q[NF + n]), x2), acc);
+                    acc = caxpy(a.cx[n], csub(cadd(tile[ly + NF][lx + NF - n], tile[ly + NF][lx + NF + n]), x2), acc);
+                    acc = caxpy(a.cy[n], csub(cadd(tile[ly + NF - n][lx + NF], tile[ly + NF + n][lx + NF]), x2), acc);
+                }
             }
             Y[(long long)k * plane + own_lat] = acc;
             if (a.dot_mode) {
@@ -192,6 +208,9 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
     C* __restrict__ PN = a.fused_p ? a.pbufs[1 - pb] + base : nullptr;
     const T ed = a.ediag ? (T)a.ediag[a.rhs_energy ? a.rhs_energy[rhs] : 0] : (T)0;
     const T cen = a.c0 + ed;
+    T tapsum2 = 0;   // 2 sum_n (c_x,n + c_y,n + c_z,n): moves the taps' diagonal into the direct form
+#pragma unroll
+    for (int n = 1; n <= NF; ++n) tapsum2 += 2 * (a.cx[n] + a.cy[n] + a.cz[n]);
 
     auto ld = [&](int k, long long lat) -> C {
         if (k < 0 || k >= nz) return czero<C>();
@@ -273,15 +292,30 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
             T d = cen;
             if (a.V) d += a.vsign * a.V[(long long)k * plane + own_lat];
             const C x0 = q[NF];
-            const C x2 = cadd(x0, x0);
-            C acc = cscale(x0, d);
+            C acc;
+            if constexpr (sizeof(T) == 8) {
+                // FP64: direct form, the diagonal carries -2 sum c_n (2 instead of 3
+                // FP64 operations per tap pair and component; the FP64 ALU is the limit)
+                acc = cscale(x0, d - tapsum2);
 #pragma unroll
-            for (int n = 1; n <= NF; ++n) {
-                const int xm = (x - n < 0) ? x - n + nx : x - n;     // periodic in x (nx >= NF)
-                const int xp = (x + n >= nx) ? x + n - nx : x + n;
-                acc = caxpy(a.cz[n], csub(cadd(q[NF - n], q[NF + n]), x2), acc);
-                acc = caxpy(a.cx[n], csub(cadd(row[xm], row[xp]), x2), acc);
-                acc = caxpy(a.cy[n], csub(cadd(row[x - n * nx], row[x + n * nx]), x2), acc);
+                for (int n = 1; n <= NF; ++n) {
+                    const int xm = (x - n < 0) ? x - n + nx : x - n;
+                    const int xp = (x + n >= nx) ? x + n - nx : x + n;
+                    acc = caxpy(a.cz[n], cadd(q[NF - n], q[NF + n]), acc);
+                    acc = caxpy(a.cx[n], cadd(row[xm], row[xp]), acc);
+                    acc = caxpy(a.cy[n], cadd(row[x - n * nx], row[x + n * nx]), acc);
+                }
+            } else {
+                const C x2 = cadd(x0, x0);
+                acc = cscale(x0, d);
+#pragma unroll
+                for (int n = 1; n <= NF; ++n) {
+                    const int xm = (x - n < 0) ? x - n + nx : x - n;     // periodic in x (nx >= NF)
+                    const int xp = (x + n >= nx) ? x + n - nx : x + n;
+                    acc = caxpy(a.cz[n], csub(cadd(q[NF - n], q[NF + n]), x2), acc);
+                    acc = caxpy(a.cx[n], csub(cadd(row[xm], row[xp]), x2), acc);
+                    acc = caxpy(a.cy[n], csub(cadd(row[x - n * nx], row[x + n * nx]), x2), acc);
+                }
             }
             Y[(long long)k * plane + own_lat] = acc;
             if (a.dot_mode) {

@@ -198,7 +198,7 @@ class IOBMSolver:
         nE = len(E)
         n_open = np.zeros(nE, np.int32)
         G = np.zeros(nE)
-        max_open = max(1, max((self.open_channels(e)[0].shape[0] for e in E), default=1))
+        max_open = max(1, self.lib.iobm_max_open(self.h))
         T = np.zeros((max(nrhs, 1), max_open))
         R = np.zeros((max(nrhs, 1), max_open))
         reps = (_lib.Report * max(nrhs, 1))()

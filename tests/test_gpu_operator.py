@@ -34,6 +34,8 @@ CASES = [
     (64, 64, 12, 3, False),    # largest supported plane
     (80, 40, 20, 4, False),    # wider than the full-row stencil tiles: 2-D tiled kernel
     (3, 20, 12, 1, False),     # narrower than the full-row stencil tiles: 2-D tiled kernel
+    (16, 16, 14, 1, True),     # compile-time-FFT self-energy with N_f = 1 (cluster of one CTA)
+    (32, 32, 18, 2, False),    # compile-time-FFT self-energy, radix 4 and 2 passes, N_f = 2
 ]
 
 
