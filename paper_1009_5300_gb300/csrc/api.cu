@@ -73,6 +73,7 @@ struct iobm_handle {
 
     // persistent device tables
     DevBuf V32, V64;
+    DevBuf errflag;                     // int, set by a kernel whose bounded wait gave up
     DevBuf twx32, twy32, twx64, twy64, phx, phy;
     FftAxis ax{}, ay{};
     ProjTables pt;
@@ -238,6 +239,8 @@ StencilArgs<T> op_args(const iobm_handle* h) {
         a.cy[n] = (T)(0.5 * h->w[n] * ihy);
         a.cz[n] = (T)(0.5 * h->w[n] * ihz);
     }
+    a.iso = 1;
+    for (int n = 1; n <= h->nf; ++n) a.iso &= (a.cx[n] == a.cy[n] && a.cy[n] == a.cz[n]) ? 1 : 0;
     // difference form: the centre weight plus 2 sum_n c_n vanishes for the FD Laplacian
     a.c0 = (T)0;
     a.vsign = (T)(-1);
@@ -245,6 +248,7 @@ StencilArgs<T> op_args(const iobm_handle* h) {
     a.npts = h->npts;
     a.zchunk = kZChunk;
     a.mask = M_ALL;
+    a.err = h->errflag.as<int>();
     return a;
 }
 
@@ -257,12 +261,14 @@ StencilArgs<T> precond_args(const iobm_handle* h) {
     a.nf = 1;
     const double c1 = h->opt.use_precond == IOBM_PRECOND_EQ10 ? std::exp(-h->opt.alpha) : 0.0;
     a.cx[1] = a.cy[1] = a.cz[1] = (T)c1;
+    a.iso = 1;
     a.c0 = (T)(1.0 + 6.0 * c1);   // difference form: C_0 + 2 (3 C_1)
     a.vsign = (T)0;
     a.V = nullptr;
     a.npts = h->npts;
     a.zchunk = kZChunk;
     a.mask = M_ALL;
+    a.err = h->errflag.as<int>();
     return a;
 }
 
@@ -523,6 +529,17 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     return IOBM_OK;
 }
 
+// Reads (and clears) the kernels' error flag after the stream has drained.
+int check_err_flag(iobm_handle* h) {
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, h->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (v == 0) return IOBM_OK;
+    CK(cudaMemsetAsync(h->errflag.p, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return fail(h, IOBM_E_CUDA, "a kernel's bounded wait on its staged copies timed out");
+}
+
 template <typename T>
 int run_solver(iobm_handle* h, int nrhs) {
     using C = typename Cplx<T>::type;
@@ -632,7 +649,7 @@ int run_solver(iobm_handle* h, int nrhs) {
     long long it = 0;
     for (const RhsState& S : h->hstate) it += S.iters;
     h->last_iters = it;
-    return IOBM_OK;
+    return check_err_flag(h);
 }
 
 // Build the per-energy tables and the internal RHS list for energies E[0..nE).
@@ -944,6 +961,7 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t1);
     if (e == cudaSuccess) e = sigma_prepare();
     if (e == cudaSuccess) e = precond_prepare();
+    if (e == cudaSuccess) e = stencil_prepare();
     if (e != cudaSuccess) return bad(IOBM_E_CUDA, std::string("stream/event setup: ") + cudaGetErrorString(e));
 
     std::vector<float> v32(h->npts);
@@ -974,7 +992,8 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
         (e = upload(h->pval32, pv32, s)) || (e = upload(h->pval64, h->pt.pval, s)) ||
         (e = upload(h->pcoup, h->pt.coupling, s)) || (e = upload(h->uidx, h->pt.uidx, s)) ||
         (e = upload(h->uptr, h->pt.uptr, s)) || (e = upload(h->uproj, h->pt.uproj, s)) ||
-        (e = upload(h->uval32, uv32, s)) || (e = upload(h->uval64, h->pt.uval, s)))
+        (e = upload(h->uval32, uv32, s)) || (e = upload(h->uval64, h->pt.uval, s)) ||
+        (e = h->errflag.ensure(sizeof(int))) || (e = cudaMemsetAsync(h->errflag.p, 0, sizeof(int), s)))
         return bad(IOBM_E_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bad(IOBM_E_CUDA, std::string("create: ") + cudaGetErrorString(e));
@@ -1275,7 +1294,7 @@ static int apply_common(iobm_handle* h, double E, int elem, const void* x, void*
     CK(cudaEventRecord(h->ev_sync, h->stream));
     CK(cudaStreamWaitEvent(h->user_stream, h->ev_sync, 0));
     CK(cudaStreamSynchronize(h->stream));
-    return IOBM_OK;
+    return check_err_flag(h);
 }
 
 int iobm_apply(iobm_handle* h, double E, int elem, const void* x, void* y, int nrhs) {

@@ -103,6 +103,7 @@ struct StencilArgs {
     T cz[kMaxNf + 1];
     T c0;                  // centre coefficient + 2 sum of the tap weights (taps are
                            // applied as c_n (x_{+n} + x_{-n} - 2 x_0))
+    int iso;               // 1: cx[n] == cy[n] == cz[n] for every n (cubic grid spacing)
     T vsign;               // centre += vsign * V(r)
     const double* ediag;   // per-RHS additive centre term (energy) or nullptr
     const int* rhs_energy; // RHS -> energy index (for ediag)
@@ -117,7 +118,11 @@ struct StencilArgs {
     int zchunk;            // planes per CTA
     int tiles_x, tiles_y;  // lateral tiling
     long long npts;
+    int* err;              // set to a nonzero code when a bounded wait gives up (or nullptr)
 };
+
+// codes written to StencilArgs::err
+enum { ERR_STAGE_TIMEOUT = 1 };
 
 // Self-energy (boundary) application, one cluster of nf CTAs per (rhs, end)
 template <typename T>
@@ -193,6 +198,7 @@ cudaError_t launch_update_precond_fourier(const PrecondArgs<T>& a, int nrhs, cud
                                           const typename Cplx<T>::type* q);
 template <typename T> size_t precond_smem_bytes(int nx, int ny);
 cudaError_t precond_prepare();
+cudaError_t stencil_prepare();
 
 // ---- launchers (defined in the .cu files) ----------------------------------
 

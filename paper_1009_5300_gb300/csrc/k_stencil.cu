@@ -22,6 +22,7 @@
 // over its planes, FP64 across the CTA) into a per-CTA slot.
 #include "iobm_internal.cuh"
 #include "complex_ops.cuh"
+#include "bulk_copy.cuh"
 
 namespace iobm {
 
@@ -346,7 +347,320 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Full-row variant with the operands staged by bulk copies (FP32, row widths
+// NX of the compile-time FFT plans).  Same tiling and arithmetic as
+// k_stencil_rows, but the raw operands (z and p_old) of every plane arrive in
+// shared memory through cp.async.bulk copies issued kTmaStages planes ahead
+// into a ring of stages, each completing on its own mbarrier; no thread waits
+// on a global load.  Stage s holds, for plane k, the own rows of plane k+N_f
+// (they enter the register z-queue) and the N_f halo rows above and below of
+// plane k (they go to the row tile): one contiguous copy for the own rows and
+// one per halo row (the periodic wrap in y is a matter of the source row
+// index), issued by the lanes of warp 0 in parallel.  The row tile carries N_f
+// periodic pad columns on each side, so every tap is a constant offset, and is
+// double-buffered: one CTA barrier per plane separates the stage reads and
+// tile writes of plane k from the copies into the freed stage and the taps of
+// plane k.
+constexpr int kTmaStages = 4;
+
+template <int NX, int NF>
+struct RowsTma {
+    static constexpr int SR = kRowTY + 2 * NF;   // tile / stage rows
+    static constexpr int TP = NX + 2 * NF;       // tile pitch (periodic pad columns)
+    static constexpr int TILE = SR * TP;
+    static constexpr int SLAB = SR * NX;
+    static constexpr size_t smem = 128 + sizeof(float2) * (2 * (size_t)TILE + 2 * (size_t)kTmaStages * SLAB);
+};
+
+template <int NX, int NF, int MINB>
+__global__ void __launch_bounds__(NX * kRowTY, MINB) k_stencil_rows_tma(const StencilArgs<float> a) {
+    using T = float;
+    using C = float2;
+    using L = RowsTma<NX, NF>;
+    constexpr int TP = L::TP, TILE = L::TILE, SLAB = L::SLAB;
+    constexpr int D = kTmaStages;
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    __shared__ double red[3 * 16];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_tma);   // [D]
+
+    const int rhs = blockIdx.z;
+    int st = ST_ACTIVE;
+    C beta = czero<C>();
+    bool first_dir = false;
+    if (a.state) {
+        st = a.state[rhs].status;
+        if (a.fused_p && !a.state[rhs].first) beta = from_d2<C>(a.state[rhs].beta);
+        else if (a.fused_p) first_dir = true;
+    }
+    if (!((1 << st) & a.mask)) return;
+
+    const int ny = a.ny, nz = a.nz;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int x = tid % NX;
+    const int ly = tid / NX;
+    const int ty0 = blockIdx.x * kRowTY;
+    const int rows = min(kRowTY, ny - ty0);
+    const bool own = ly < rows;
+    const int k0 = blockIdx.y * a.zchunk;
+    const int k1 = min(k0 + a.zchunk, nz);
+    const long long plane = (long long)NX * ny;
+    const long long base = (long long)rhs * a.npts;
+    const C* __restrict__ X = a.x + base;
+    const int pb = (a.fused_p && a.state) ? (a.state[rhs].pbuf & 1) : 0;
+    const C* __restrict__ PO = (a.fused_p && !first_dir) ? a.pbufs[pb] + base : nullptr;
+    const T ed = a.ediag ? (T)a.ediag[a.rhs_energy ? a.rhs_energy[rhs] : 0] : (T)0;
+    const T cen = a.c0 + ed;
+
+    C* tiles = reinterpret_cast<C*>(smem_tma + 128);   // [2][SR][TP] combined operand rows
+    C* stages = tiles + 2 * TILE;                      // stage s: z at 2 s SLAB, p_old at (2 s + 1) SLAB
+    if (tid == 0) {
+        for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    // copy assignment of warp 0.  A halo side (NF rows above or below the own
+    // rows) whose source rows do not wrap around in y is one copy of NF rows,
+    // otherwise one copy per row.  Lane l < 2 NF: halo row l (row copies of a
+    // wrapping side; for a contiguous side its first lane copies all NF rows);
+    // lane 2 NF: the own rows of z, lane 2 NF + 1: those of p_old.
+    constexpr uint32_t row_bytes = NX * sizeof(C);
+    auto issue = [&](int k, int s) {   // all lanes of warp 0
+        const bool own_plane = k + NF < nz;
+        if (lane == 0) {
+            const uint32_t per = (own_plane ? (uint32_t)rows : 0u) * row_bytes + 2u * NF * row_bytes;
+            mbar_arrive_expect_tx(&bar[s], PO ? 2 * per : per);
+        }
+        __syncwarp();
+        C* sz = stages + 2 * s * SLAB;
+        C* sp = sz + SLAB;
+        if (lane < 2 * NF) {
+            const bool above = lane < NF;
+            const int h = above ? lane : lane - NF;
+            const bool contiguous = above ? (ty0 >= NF) : (ty0 + rows + NF <= ny);
+            const int nrows = contiguous ? (h == 0 ? NF : 0) : 1;
+            if (nrows) {
+                const int srow = above ? lane : NF + rows + h;
+                int gy = (ty0 - NF + srow) % ny;
+                if (gy < 0) gy += ny;
+                fence_proxy_async_smem();
+                const long long src = (long long)k * plane + (long long)gy * NX;
+                bulk_g2s(sz + srow * NX, X + src, nrows * row_bytes, &bar[s]);
+                if (PO) bulk_g2s(sp + srow * NX, PO + src, nrows * row_bytes, &bar[s]);
+            }
+        } else if (own_plane && (lane == 2 * NF || (PO && lane == 2 * NF + 1))) {
+            fence_proxy_async_smem();
+            const long long src = (long long)(k + NF) * plane + (long long)ty0 * NX;
+            if (lane == 2 * NF) bulk_g2s(sz + NF * NX, X + src, rows * row_bytes, &bar[s]);
+            else bulk_g2s(sp + NF * NX, PO + src, rows * row_bytes, &bar[s]);
+        }
+    };
+
+    // tile rows this thread fills from the stage (the halo rows of a full or
+    // partial tile): stage rows ly and ly + kRowTY, stage index tid + t kRowTY NX
+    bool hf[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int srow = ly + t * kRowTY;
+        hf[t] = srow < 2 * NF + rows && !(srow >= NF && srow < NF + rows);
+    }
+    // column of x in the padded tile, and its periodic copy in the pad (or -1;
+    // NX >= 2 NF, so a column has at most one copy)
+    static_assert(NX >= 2 * NF, "pad columns assume NX >= 2 NF");
+    const int tcol = NF + x;
+    const int tpad = (x < NF) ? NF + NX + x : ((x >= NX - NF) ? x - (NX - NF) : -1);
+    const long long own_lat = own ? (long long)(ty0 + ly) * NX + x : 0;
+
+    auto ld = [&](int k, long long lat) -> C {
+        if (k < 0 || k >= nz) return czero<C>();
+        const long long i = (long long)k * plane + lat;
+        C v = X[i];
+        if (PO) v = cfma(beta, PO[i], v);
+        return v;
+    };
+    if (tid < 32)
+        for (int j = 0; j < D && k0 + j < k1; ++j) issue(k0 + j, j);
+
+    C* PN = a.fused_p ? a.pbufs[1 - pb] + base : nullptr;
+    C q[2 * NF + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * NF; ++j) {
+        const int kk = k0 - NF + j;
+        q[j] = own ? ld(kk, own_lat) : czero<C>();
+        if (PN && own && kk >= k0 && kk < k1) PN[(long long)kk * plane + own_lat] = q[j];
+    }
+    // running pointers at plane k (Y, V) and k + NF (PN)
+    C* __restrict__ Yk = a.y + base + (long long)k0 * plane + own_lat;
+    C* __restrict__ PNk = PN ? PN + (long long)(k0 + NF) * plane + own_lat : nullptr;
+    const T* __restrict__ Vk = a.V ? a.V + (long long)k0 * plane + own_lat : nullptr;
+    T vnext = (Vk && own) ? Vk[0] : (T)0;
+
+    float dre = 0.f, dim = 0.f, nrm = 0.f;
+    const int own_st = (NF + ly) * NX + x;
+
+    for (int k = k0; k < k1; ++k) {
+        const unsigned kk = (unsigned)(k - k0);
+        const int s = (int)(kk % D);
+        C* tile = tiles + (kk & 1) * TILE;
+        const T vk = vnext;
+        if (Vk && own && k + 1 < k1) vnext = Vk[plane];
+        const bool ok = mbar_wait_bounded(&bar[s], (kk / D) & 1);
+        const C* sz = stages + 2 * s * SLAB;
+        const C* sp = sz + SLAB;
+        C qn = czero<C>();
+        if (own && k + NF < nz) {
+            const C zv = sz[own_st];
+            qn = PO ? cfma(beta, sp[own_st], zv) : zv;
+        }
+        q[2 * NF] = qn;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (hf[t]) {
+                const int si = tid + t * kRowTY * NX;
+                const C zv = sz[si];
+                const C v = PO ? cfma(beta, sp[si], zv) : zv;
+                C* trow = tile + (ly + t * kRowTY) * TP;
+                trow[tcol] = v;
+                if (tpad >= 0) trow[tpad] = v;
+            }
+        }
+        C* row = tile + (NF + ly) * TP;
+        if (own) {
+            row[tcol] = q[NF];
+            if (tpad >= 0) row[tpad] = q[NF];
+        }
+        // stage s is consumed and tile k is complete; the other tile (plane k-1)
+        // was last read before this barrier
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                if (a.err) atomicExch(a.err, ERR_STAGE_TIMEOUT);
+                for (int j = k; j < k + D && j < k1; ++j)   // this CTA's copies still in flight
+                    mbar_wait_bounded(&bar[(j - k0) % D], ((j - k0) / D) & 1);
+            }
+            __syncthreads();
+            return;
+        }
+        if (tid < 32 && k + D < k1) issue(k + D, s);
+        if (PNk && own && k + NF < k1) PNk[0] = qn;
+        if (own) {
+            T d = cen;
+            if (Vk) d += a.vsign * vk;
+            const C x0 = q[NF];
+            const C* c = row + tcol;
+            C acc;
+            if (a.iso) {
+                // the same difference form in packed two-lane FP32 instructions (one
+                // weight pair per shift n serves all three axes)
+                const C x2 = p2add(x0, x0);
+                acc = p2mul(x0, make_float2(d, d));
+#pragma unroll
+                for (int n = 1; n <= NF; ++n) {
+                    const C cc = make_float2(a.cz[n], a.cz[n]);
+                    acc = p2fma(cc, p2sub(p2add(q[NF - n], q[NF + n]), x2), acc);
+                    acc = p2fma(cc, p2sub(p2add(c[-n], c[n]), x2), acc);
+                    acc = p2fma(cc, p2sub(p2add(c[-n * TP], c[n * TP]), x2), acc);
+                }
+            } else {
+                const C x2 = cadd(x0, x0);
+                acc = cscale(x0, d);
+#pragma unroll
+                for (int n = 1; n <= NF; ++n) {
+                    acc = caxpy(a.cz[n], csub(cadd(q[NF - n], q[NF + n]), x2), acc);
+                    acc = caxpy(a.cx[n], csub(cadd(c[-n], c[n]), x2), acc);
+                    acc = caxpy(a.cy[n], csub(cadd(c[-n * TP], c[n * TP]), x2), acc);
+                }
+            }
+            Yk[0] = acc;
+            if (a.dot_mode) {
+                dre = fmaf(x0.x, acc.x, fmaf(-x0.y, acc.y, dre));
+                dim = fmaf(x0.x, acc.y, fmaf(x0.y, acc.x, dim));
+                nrm = fmaf(x0.x, x0.x, fmaf(x0.y, x0.y, nrm));
+            }
+        }
+        Yk += plane;
+        if (PNk) PNk += plane;
+        if (Vk) Vk += plane;
+#pragma unroll
+        for (int j = 0; j < 2 * NF; ++j) q[j] = q[j + 1];
+    }
+
+    if (a.dot_mode) {
+        double r0 = dre, r1 = dim, r2 = nrm;
+        block_reduce_3(r0, r1, r2, red);
+        if (tid == 0) {
+            const int slot = a.slot_base + blockIdx.x + blockIdx.y * gridDim.x;
+            a.dot_part[(long long)rhs * a.slot_stride + slot] = make_double2(r0, r1);
+            if (a.nrm_part) a.nrm_part[(long long)rhs * a.slot_stride + slot] = r2;
+        }
+    }
+}
+
 static bool use_rows(int nx, int nf) { return nx >= nf && nx >= 4 && nx <= 64; }
+
+// bulk-copy variant: FP32, rows of a multiple of 16 bytes, 16-byte aligned operands
+static bool tma_width(int nx) {
+    return nx == 12 || nx == 16 || nx == 24 || nx == 32 || nx == 48 || nx == 64;
+}
+
+template <typename T>
+static bool use_rows_tma(const StencilArgs<T>& a) {
+    if (sizeof(T) != 4 || !use_rows(a.nx, a.nf) || !tma_width(a.nx)) return false;
+    uintptr_t al = reinterpret_cast<uintptr_t>(a.x);
+    if (a.fused_p) al |= reinterpret_cast<uintptr_t>(a.pbufs[0]) | reinterpret_cast<uintptr_t>(a.pbufs[1]);
+    return (al & 15) == 0;
+}
+
+template <int NX, int NF>
+static cudaError_t prepare_tma() {
+    constexpr int MB = NX * kRowTY <= 384 ? 3 : 2;
+    cudaError_t e = cudaFuncSetAttribute(k_stencil_rows_tma<NX, NF, MB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RowsTma<NX, NF>::smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_stencil_rows_tma<NX, NF, MB>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+template <int NX>
+static cudaError_t prepare_tma_nf() {
+    cudaError_t e = prepare_tma<NX, 1>();
+    if (e == cudaSuccess) e = prepare_tma<NX, 2>();
+    if (e == cudaSuccess) e = prepare_tma<NX, 3>();
+    if (e == cudaSuccess) e = prepare_tma<NX, 4>();
+    return e;
+}
+
+cudaError_t stencil_prepare() {
+    cudaError_t e = prepare_tma_nf<12>();
+    if (e == cudaSuccess) e = prepare_tma_nf<16>();
+    if (e == cudaSuccess) e = prepare_tma_nf<24>();
+    if (e == cudaSuccess) e = prepare_tma_nf<32>();
+    if (e == cudaSuccess) e = prepare_tma_nf<48>();
+    if (e == cudaSuccess) e = prepare_tma_nf<64>();
+    return e;
+}
+
+template <int NX, int NF>
+static void launch_tma(const StencilArgs<float>& a, dim3 grid, cudaStream_t s) {
+    constexpr int MB = NX * kRowTY <= 384 ? 3 : 2;
+    k_stencil_rows_tma<NX, NF, MB><<<grid, NX * kRowTY, RowsTma<NX, NF>::smem, s>>>(a);
+}
+
+template <int NX>
+static cudaError_t launch_tma_nf(const StencilArgs<float>& a, dim3 grid, cudaStream_t s) {
+    switch (a.nf) {
+        case 1: launch_tma<NX, 1>(a, grid, s); break;
+        case 2: launch_tma<NX, 2>(a, grid, s); break;
+        case 3: launch_tma<NX, 3>(a, grid, s); break;
+        case 4: launch_tma<NX, 4>(a, grid, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_stencil(const StencilArgs<T>& a0, int nrhs, cudaStream_t s) {
@@ -359,6 +673,19 @@ cudaError_t launch_stencil(const StencilArgs<T>& a0, int nrhs, cudaStream_t s) {
         dim3 grid(a.tiles_y, nzc, nrhs);
         const int threads = a.nx * kRowTY;
         using C = typename Cplx<T>::type;
+        if constexpr (sizeof(T) == 4) {
+            if (use_rows_tma(a)) {
+                switch (a.nx) {
+                    case 12: return launch_tma_nf<12>(a, grid, s);
+                    case 16: return launch_tma_nf<16>(a, grid, s);
+                    case 24: return launch_tma_nf<24>(a, grid, s);
+                    case 32: return launch_tma_nf<32>(a, grid, s);
+                    case 48: return launch_tma_nf<48>(a, grid, s);
+                    case 64: return launch_tma_nf<64>(a, grid, s);
+                    default: return cudaErrorInvalidValue;
+                }
+            }
+        }
         const size_t smem = sizeof(C) * (size_t)(kRowTY + 2 * a.nf) * a.nx;
         switch (a.nf) {
             case 1: k_stencil_rows<T, 1><<<grid, threads, smem, s>>>(a); break;
