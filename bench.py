@@ -29,6 +29,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "channel-solves/sec at 1e-6 G0 (mixed vs FP64 GPU); stencil HBM GB/s vs peak"
 UNIT = "channel-solves/s"
+# DRAM bytes (read + write) per RHS-point of one k_stencil_rows_tma<48,4,3> launch, from an
+# ncu capture of the 8-energy wire48 case with all 56 RHS active: 695.0 MB / 20.64 M points
+# (the algorithmic figure is 32.07 B); to be re-taken whenever that kernel changes
+STENCIL_DRAM_BYTES_PER_RHS_POINT = 695.0e6 / (56 * 368640)
 WORKLOAD = ("wire48: 6-atom wire, Gaussian wells (0.5 Ha, width 1.5 bohr, spacing 6.8 bohr) "
             "+ s/p KB projectors (radius 3 bohr), 48x48x160 grid, h=0.35 bohr, 9-point FD, "
             "r_s=3.28 jellium, 32 energies in [E_F-2eV, E_F+0.5eV], all open channels, "
@@ -261,9 +265,14 @@ def native_arm(args, rank, world, local_rank):
     roof = None
     if stencil_launches > 0 and stencil_ms > 0:
         achieved = alg_bytes / (stencil_ms / 1000.0) / 1e9
+        rhs_points = npts * iters_total / stencil_launches
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_stencil<float,4> (fused p "
-                "update + operator + p^T q)", "launches": stencil_launches,
+                "frac": achieved / peak,
+                "traffic": STENCIL_DRAM_BYTES_PER_RHS_POINT * rhs_points,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                  "launch on the 8-energy case (56 RHS), scaled by RHS-points",
+                "kernel": "k_stencil_rows_tma<48,4,3> (fused p update + operator + p^T q)",
+                "launches": stencil_launches,
                 "avg_launch_ms": stencil_ms / stencil_launches,
                 "alg_bytes_per_launch": alg_bytes / stencil_launches,
                 "peak_source": f"{peak_kind} hbm_gbs"}
