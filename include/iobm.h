@@ -191,6 +191,35 @@ int iobm_set_workspace(iobm_handle* h, void* dev_ptr, size_t bytes);
  * when the batch ran (check iobm_report for per-RHS convergence). */
 int iobm_solve(iobm_handle* h, const double* E, int nE, const int* channels, int nch, int side);
 
+/* Solve several junctions together (not in the paper, which treats one incident
+ * wave of one junction at a time).  handles[j] (from iobm_create, all on the
+ * current device, distinct, each with its own workspace: attached or owned) is
+ * solved at energies E[j][0..nE[j]) for every open incident channel from `side`.
+ * Each junction's tables, RHS and solver start run on its handle's stream; then
+ * ONE CUDA graph launch runs all junctions concurrently: a conditional WHILE node
+ * per junction repeats that junction's chunk of COCG iterations (with its FP64
+ * residual replacements) on the device until every one of its RHS has stopped or
+ * its iteration limit is reached; then each junction's final FP64 residual and
+ * channel projections run.  Results are read per handle (iobm_transmission,
+ * iobm_solution).  Per RHS the arithmetic is that of iobm_solve on the handle
+ * alone.  Returns IOBM_OK or the first error (the failing handle reports it in
+ * iobm_last_error); per-iteration kernel profiling is not collected here. */
+int iobm_solve_batch(int n, iobm_handle* const* handles, const double* const* E, const int* nE,
+                     int side);
+
+/* Stencil tiling autotuner: times the fused COCG stencil (p = z + beta p_old,
+ * A p, p^T A p) on nrhs RHS of this handle's grid for z-chunks of 16, 32 and 64
+ * planes per CTA and, in the mixed solver, for both FP32 row kernels (bulk-copy
+ * staged or register-pipelined), keeps the fastest for the handle's later solves
+ * and returns it in *zchunk / *variant (either may be NULL).  Binds the workspace
+ * for nrhs RHS (the attached one must be large enough).  The choice changes only
+ * the order of the partial sums of the dot products. */
+int iobm_autotune(iobm_handle* h, int nrhs, int* zchunk, int* variant);
+
+/* Set the stencil tiling explicitly: zchunk >= 16 z-planes per CTA; variant 0 =
+ * the fastest kernel for the shape, 1 = the register-pipelined row kernel. */
+int iobm_set_tiling(iobm_handle* h, int zchunk, int variant);
+
 /* Number of incident channels (user-visible RHS) of the last solve. */
 int iobm_num_rhs(const iobm_handle* h);
 

@@ -8,7 +8,7 @@ builds it and marshals arguments.
 """
 from ._lib import IOBMError, load  # noqa: F401
 
-__all__ = ["IOBMError", "load", "IOBMSolver", "conductance", "build_library"]
+__all__ = ["IOBMError", "load", "IOBMSolver", "solve_batch", "conductance", "build_library"]
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:
@@ -24,6 +24,9 @@ def __getattr__(name):
     if name == "conductance":
         from .autograd import conductance
         return conductance
+    if name == "solve_batch":
+        from .solver import solve_batch
+        return solve_batch
     if name == "channels_host":
         from .solver import channels_host
         return channels_host

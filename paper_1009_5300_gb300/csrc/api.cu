@@ -51,7 +51,8 @@ cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
     return cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
 }
 
-constexpr int kZChunk = 32;
+constexpr int kZChunkDefault = 32;   // z-planes per stencil CTA unless the autotuner picks another
+constexpr int kZChunkMin = 16;       // smallest candidate: sizes the per-CTA partial-sum slots
 // FP64 residual replacements run after every kReplaceEvery-th captured iteration
 // (RHS that became PENDING wait at most kReplaceEvery - 1 iterations)
 constexpr int kReplaceEvery = 2;
@@ -94,6 +95,9 @@ struct iobm_handle {
     int side = 0;
     int nrhs = 0;                        // internal RHS
     int max_open = 0;
+    int zchunk = kZChunkDefault;         // stencil z-planes per CTA (autotuned)
+    int stencil_variant = 0;             // StencilArgs::variant (autotuned)
+    DevBuf batch_ctr;                    // chunk counter of this junction in a batched solve
 
     // workspace
     void* ws = nullptr;
@@ -156,8 +160,8 @@ size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 double internal_tol2(const iobm_handle* h) { return 0.5 * h->opt.tol * h->opt.tol; }
 
 int slots_for(const iobm_handle* h) {
-    const int ns_op = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk, h->nf);
-    const int ns_pc = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk, 1);
+    const int ns_op = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, h->nf);
+    const int ns_pc = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, 1);
     return std::max(std::max(ns_op + 2 * h->nf + 1, 64), std::max(h->g.nz, ns_pc));
 }
 
@@ -165,7 +169,7 @@ int slots_for(const iobm_handle* h) {
 int rho_slots(const iobm_handle* h) {
     return h->opt.use_precond == IOBM_PRECOND_FOURIER
                ? h->g.nz
-               : stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk, 1);
+               : stencil_slots(h->g.nx, h->g.ny, h->g.nz, h->zchunk, 1);
 }
 
 size_t workspace_bytes(const iobm_handle* h, int nrhs, int prec) {
@@ -198,7 +202,7 @@ int bind_workspace(iobm_handle* h, int nrhs) {
     const size_t n = (size_t)nrhs * h->npts;
     const int S = slots_for(h);
     h->slot_stride = S;
-    h->ns_stencil = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunk, h->nf);
+    h->ns_stencil = stencil_slots(h->g.nx, h->g.ny, h->g.nz, h->zchunk, h->nf);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         void* p = base + off;
@@ -246,7 +250,8 @@ StencilArgs<T> op_args(const iobm_handle* h) {
     a.vsign = (T)(-1);
     a.V = std::is_same<T, float>::value ? (const T*)h->V32.p : (const T*)h->V64.p;
     a.npts = h->npts;
-    a.zchunk = kZChunk;
+    a.zchunk = h->zchunk;
+    a.variant = h->stencil_variant;
     a.mask = M_ALL;
     a.err = h->errflag.as<int>();
     return a;
@@ -266,7 +271,8 @@ StencilArgs<T> precond_args(const iobm_handle* h) {
     a.vsign = (T)0;
     a.V = nullptr;
     a.npts = h->npts;
-    a.zchunk = kZChunk;
+    a.zchunk = h->zchunk;
+    a.variant = h->stencil_variant;
     a.mask = M_ALL;
     a.err = h->errflag.as<int>();
     return a;
@@ -540,30 +546,89 @@ int check_err_flag(iobm_handle* h) {
     return fail(h, IOBM_E_CUDA, "a kernel's bounded wait on its staged copies timed out");
 }
 
+// Solver start for every RHS: zero x and the directions, r = b, ||b||^2, z = P r.
 template <typename T>
-int run_solver(iobm_handle* h, int nrhs) {
+int solver_prologue(iobm_handle* h, int nrhs, long long& launches) {
     using C = typename Cplx<T>::type;
     const bool mixed = std::is_same<T, float>::value;
     const size_t ce = sizeof(C);
     const size_t n = (size_t)nrhs * h->npts;
-    long long launches = 0;
     CK(cudaEventRecord(h->ev_t0, h->stream));
     CK(cudaMemsetAsync(h->vx, 0, ce * n, h->stream));
     CK(cudaMemsetAsync(h->vp[0], 0, ce * n, h->stream));
     CK(cudaMemsetAsync(h->vp[1], 0, ce * n, h->stream));
     if (mixed) CK(cudaMemsetAsync(h->x64, 0, sizeof(double2) * n, h->stream));
-    // r = b, ||b||^2
     int nslots = 0;
     CK(launch_residual<T>(nullptr, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
                           h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, nullptr, M_ALL,
                           h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
     CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, 0.0, 1, h->stream));
     launches += 2;
-    int rc = apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
+    return apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
+}
+
+// COCG iterations per captured chunk (a multiple of the replacement period)
+int chunk_length(const iobm_handle* h) {
+    return ((std::max(1, h->opt.chunk) + kReplaceEvery - 1) / kReplaceEvery) * kReplaceEvery;
+}
+
+// Launch one chunk of iterations on h->stream (which is being captured);
+// timed: record the stencil event pairs (plain graphs only).
+template <typename T>
+int launch_chunk(iobm_handle* h, int nrhs, bool timed, long long& per_chunk) {
+    const bool mixed = std::is_same<T, float>::value;
+    const int chunk = chunk_length(h);
+    for (int it = 0; it < chunk; ++it) {
+        // iteration index `it` places the event pair (profiling) and the replacement
+        const int rc = cocg_iteration<T>(h, nrhs, mixed, per_chunk, timed ? it : -1,
+                                         (it + 1) % kReplaceEvery == 0);
+        if (rc) return rc;
+    }
+    return IOBM_OK;
+}
+
+// Solver end: fold the FP32 progress of RHS that stopped without converging,
+// record their FP64 residual, read the per-RHS state back.
+template <typename T>
+int solver_epilogue(iobm_handle* h, int nrhs, long long& launches) {
+    using C = typename Cplx<T>::type;
+    const bool mixed = std::is_same<T, float>::value;
+    const int mask = (1 << ST_NOCONV) | (1 << ST_BREAKDOWN) | (1 << ST_ACTIVE) | (1 << ST_PENDING) |
+                     (1 << ST_RESTART);
+    if (mixed) {
+        CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
+    }
+    int rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
+                                    h->rhs_energy.as<int>(), h->st, mask, launches);
+    if (rc) return rc;
+    int nslots = 0;
+    CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
+                          h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, h->st, mask,
+                          h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
+    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, 0.0, 2, h->stream));
+    CK(cudaEventRecord(h->ev_t1, h->stream));
+    h->hstate.resize(nrhs);
+    CK(cudaMemcpyAsync(h->hstate.data(), h->st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
+    h->last_ms = ms;
+    h->last_launches = launches;
+    long long it = 0;
+    for (const RhsState& S : h->hstate) it += S.iters;
+    h->last_iters = it;
+    return check_err_flag(h);
+}
+
+template <typename T>
+int run_solver(iobm_handle* h, int nrhs) {
+    long long launches = 0;
+    int rc = solver_prologue<T>(h, nrhs, launches);
     if (rc) return rc;
 
     // capture one chunk of iterations
-    const int chunk = ((std::max(1, h->opt.chunk) + kReplaceEvery - 1) / kReplaceEvery) * kReplaceEvery;
+    const int chunk = chunk_length(h);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long per_chunk = 0;
@@ -575,14 +640,11 @@ int run_solver(iobm_handle* h, int nrhs) {
         }
     }
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    for (int it = 0; it < chunk; ++it) {
-        // iteration index `it` places the event pair (profiling) and the replacement
-        rc = cocg_iteration<T>(h, nrhs, mixed, per_chunk, it, (it + 1) % kReplaceEvery == 0);
-        if (rc) {
-            cudaStreamEndCapture(h->stream, &graph);
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
+    rc = launch_chunk<T>(h, nrhs, h->profile, per_chunk);
+    if (rc) {
+        cudaStreamEndCapture(h->stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
     }
     CK(cudaStreamEndCapture(h->stream, &graph));
     CK(cudaGraphInstantiate(&exec, graph, 0));
@@ -622,34 +684,7 @@ int run_solver(iobm_handle* h, int nrhs) {
         if (!live) break;
     }
     cudaGraphExecDestroy(exec);
-    // RHS that stopped without converging: fold their FP32 progress and record the FP64 residual
-    {
-        const int mask = (1 << ST_NOCONV) | (1 << ST_BREAKDOWN) | (1 << ST_ACTIVE) |
-                         (1 << ST_PENDING) | (1 << ST_RESTART);
-        if (mixed) {
-            CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
-        }
-        rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
-                                    h->rhs_energy.as<int>(), h->st, mask, launches);
-        if (rc) return rc;
-        CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(),
-                              h->phx.as<double2>(), h->phy.as<double2>(), h->g.nx, h->g.ny,
-                              h->g.nz, h->nf, h->st, mask, h->rr_part, h->slot_stride, nrhs,
-                              h->stream, &nslots));
-        CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, 0.0, 2, h->stream));
-    }
-    CK(cudaEventRecord(h->ev_t1, h->stream));
-    CK(cudaMemcpyAsync(h->hstate.data(), h->st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost,
-                       h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
-    h->last_ms = ms;
-    h->last_launches = launches;
-    long long it = 0;
-    for (const RhsState& S : h->hstate) it += S.iters;
-    h->last_iters = it;
-    return check_err_flag(h);
+    return solver_epilogue<T>(h, nrhs, launches);
 }
 
 // Build the per-energy tables and the internal RHS list for energies E[0..nE).
@@ -789,6 +824,16 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
     return IOBM_OK;
 }
 
+// projection sums of the FP64 solutions (Eq. 19 on the end planes) after a solve
+int launch_projections(iobm_handle* h) {
+    const size_t pbytes = sizeof(double2) * (size_t)h->nrhs * std::max(h->max_open, 1) * 2 * kMaxNf;
+    CK(h->proj_out.ensure(pbytes));
+    CK(launch_projection(h->x64, h->descs.as<RhsDesc>(), h->open_ptr.as<int>(), h->open_bins.as<int2>(),
+                         h->phx.as<double2>(), h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz,
+                         h->nf, h->max_open, h->proj_out.as<double2>(), h->nrhs, h->stream));
+    return IOBM_OK;
+}
+
 int run_batch(iobm_handle* h) {
     if (h->nrhs == 0) {
         h->solved = true;
@@ -800,14 +845,132 @@ int run_batch(iobm_handle* h) {
     rc = (h->opt.precision == IOBM_MIXED) ? run_solver<float>(h, h->nrhs)
                                           : run_solver<double>(h, h->nrhs);
     if (rc) return rc;
-    // projections of the FP64 solutions
-    const size_t pbytes = sizeof(double2) * (size_t)h->nrhs * std::max(h->max_open, 1) * 2 * kMaxNf;
-    CK(h->proj_out.ensure(pbytes));
-    CK(launch_projection(h->x64, h->descs.as<RhsDesc>(), h->open_ptr.as<int>(), h->open_bins.as<int2>(),
-                         h->phx.as<double2>(), h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz,
-                         h->nf, h->max_open, h->proj_out.as<double2>(), h->nrhs, h->stream));
+    rc = launch_projections(h);
+    if (rc) return rc;
     h->solved = true;
     return IOBM_OK;
+}
+
+// ---- several junctions in one graph ------------------------------------------
+
+// Capture the body of a junction's WHILE node: one chunk of its iterations and
+// the kernel that sets the loop condition.
+template <typename T>
+int capture_batch_body(iobm_handle* h, cudaGraph_t body, cudaGraphConditionalHandle cond,
+                       long long& per_chunk) {
+    CK(cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    int rc = launch_chunk<T>(h, h->nrhs, false, per_chunk);
+    if (rc == IOBM_OK) {
+        const int max_chunks = h->opt.max_iter / chunk_length(h) + 4;
+        const cudaError_t e = launch_batch_cond(cond, h->st, h->nrhs, h->batch_ctr.as<int>(),
+                                                max_chunks, h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "batch loop condition");
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch body capture");
+    return IOBM_OK;
+}
+
+// Solve every junction of the batch: per-junction set-up and start on each
+// handle's stream, then ONE graph launch holding a WHILE node per junction
+// (its chunk of COCG iterations repeated on the device until the junction's
+// RHS have all stopped), then the per-junction ends and projections.
+int solve_batch(int n, iobm_handle* const* hs, const double* const* E, const int* nE, int side) {
+    std::vector<long long> launches(n, 0), per_chunk(n, 0);
+    std::vector<int> active;
+    for (int j = 0; j < n; ++j) {
+        iobm_handle* h = hs[j];
+        h->solved = false;
+        int rc = prepare_rhs(h, E[j], nE[j], nullptr, 0, side, 0);
+        if (rc) return rc;
+        if (h->nrhs == 0) {
+            h->solved = true;
+            h->hstate.clear();
+            continue;
+        }
+        rc = bind_workspace(h, h->nrhs);
+        if (rc) return rc;
+        CK(h->batch_ctr.ensure(sizeof(int)));
+        CK(cudaMemsetAsync(h->batch_ctr.p, 0, sizeof(int), h->stream));
+        rc = (h->opt.precision == IOBM_MIXED) ? solver_prologue<float>(h, h->nrhs, launches[j])
+                                              : solver_prologue<double>(h, h->nrhs, launches[j]);
+        if (rc) return rc;
+        active.push_back(j);
+    }
+    if (active.empty()) return IOBM_OK;
+    iobm_handle* h0 = hs[active[0]];
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (done) cudaEventDestroy(done);
+    };
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(h0, e, "batch graph set-up");
+    }
+    for (int j : active) {
+        iobm_handle* h = hs[j];
+        cudaGraphConditionalHandle cond;
+        e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = cond;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(h, e, "batch WHILE node");
+        }
+        const int rc = (h->opt.precision == IOBM_MIXED)
+                           ? capture_batch_body<float>(h, p.conditional.phGraph_out[0], cond, per_chunk[j])
+                           : capture_batch_body<double>(h, p.conditional.phGraph_out[0], cond, per_chunk[j]);
+        if (rc) {
+            cleanup();
+            return rc;
+        }
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    // the graph starts when every junction's start has finished, and every
+    // junction's end waits for the graph
+    for (int j : active) {
+        if (e == cudaSuccess) e = cudaEventRecord(hs[j]->ev_sync, hs[j]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h0->stream, hs[j]->ev_sync, 0);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, h0->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(done, h0->stream);
+    for (int j : active)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hs[j]->stream, done, 0);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(h0, e, "batch graph launch");
+    }
+    int first_rc = IOBM_OK;
+    for (int j : active) {
+        iobm_handle* h = hs[j];
+        int chunks = 0;
+        e = cudaMemcpyAsync(&chunks, h->batch_ctr.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        int rc = (e == cudaSuccess) ? IOBM_OK : cuda_fail(h, e, "batch chunk count");
+        launches[j] += (long long)chunks * (per_chunk[j] + 1);
+        if (!rc)
+            rc = (h->opt.precision == IOBM_MIXED) ? solver_epilogue<float>(h, h->nrhs, launches[j])
+                                                  : solver_epilogue<double>(h, h->nrhs, launches[j]);
+        if (!rc) rc = launch_projections(h);
+        if (!rc) h->solved = true;
+        if (rc && !first_rc) first_rc = rc;
+    }
+    cleanup();
+    return first_rc;
 }
 
 // t and r of every incident channel (host, FP64): combine the projection sums
@@ -865,6 +1028,61 @@ int status_of_internal(const RhsState& S) {
 }  // namespace
 
 // ============================================================================
+// Time the fused COCG stencil (p = z + beta p_old, A p, p^T A p) on nrhs RHS of
+// this grid for every candidate z-chunk and stencil kernel, keep the fastest.
+template <typename T>
+int autotune_stencil(iobm_handle* h, int nrhs, int* zchunk_out, int* variant_out) {
+    using C = typename Cplx<T>::type;
+    int rc = bind_workspace(h, nrhs);
+    if (rc) return rc;
+    const size_t bytes = sizeof(C) * (size_t)nrhs * h->npts;
+    CK(cudaMemsetAsync(h->vz, 0, bytes, h->stream));
+    CK(cudaMemsetAsync(h->vp[0], 0, bytes, h->stream));
+    StencilArgs<T> a = op_args<T>(h);
+    a.x = (const C*)h->vz;
+    a.pbufs[0] = (C*)h->vp[0];
+    a.pbufs[1] = (C*)h->vp[1];
+    a.y = (C*)h->vq;
+    a.fused_p = 1;
+    a.state = nullptr;   // every RHS active, beta = 0
+    a.dot_mode = 1;
+    a.dot_part = h->mu_part;
+    a.slot_stride = h->slot_stride;
+    const int zcands[3] = {kZChunkMin, 32, 64};
+    const int nvar = std::is_same<T, float>::value ? 2 : 1;
+    float best = -1.f;
+    int best_z = h->zchunk, best_v = h->stencil_variant;
+    for (int zi = 0; zi < 3; ++zi) {
+        const int zc = zcands[zi];
+        if (zi > 0 && zcands[zi - 1] >= h->g.nz) break;   // larger chunks are all the same launch
+        for (int v = 0; v < nvar; ++v) {
+            a.zchunk = zc;
+            a.variant = v;
+            CK(launch_stencil<T>(a, nrhs, h->stream));   // warm-up
+            CK(cudaEventRecord(h->ev_t0, h->stream));
+            for (int r = 0; r < 3; ++r) CK(launch_stencil<T>(a, nrhs, h->stream));
+            CK(cudaEventRecord(h->ev_t1, h->stream));
+            CK(cudaEventSynchronize(h->ev_t1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
+            if (best < 0.f || ms < best) {
+                best = ms;
+                best_z = zc;
+                best_v = v;
+            }
+        }
+    }
+    h->zchunk = best_z;
+    h->stencil_variant = best_v;
+    rc = bind_workspace(h, nrhs);   // slot counts follow the chosen z-chunk
+    if (rc) return rc;
+    rc = check_err_flag(h);
+    if (rc) return rc;
+    if (zchunk_out) *zchunk_out = best_z;
+    if (variant_out) *variant_out = best_v;
+    return IOBM_OK;
+}
+
 extern "C" {
 
 void iobm_default_options(iobm_options* o) {
@@ -1067,6 +1285,32 @@ int iobm_solve(iobm_handle* h, const double* E, int nE, const int* channels, int
     CK(cudaEventRecord(h->ev_sync, h->stream));
     CK(cudaStreamWaitEvent(h->user_stream, h->ev_sync, 0));
     return IOBM_OK;
+}
+
+int iobm_autotune(iobm_handle* h, int nrhs, int* zchunk, int* variant) {
+    if (!h || nrhs < 1) return h ? fail(h, IOBM_E_ARG, "autotune needs nrhs >= 1") : IOBM_E_ARG;
+    return (h->opt.precision == IOBM_MIXED) ? autotune_stencil<float>(h, nrhs, zchunk, variant)
+                                            : autotune_stencil<double>(h, nrhs, zchunk, variant);
+}
+
+int iobm_set_tiling(iobm_handle* h, int zchunk, int variant) {
+    if (!h) return IOBM_E_ARG;
+    if (zchunk < kZChunkMin || (variant != 0 && variant != 1))
+        return fail(h, IOBM_E_ARG, "z-chunk below the minimum or unknown stencil variant");
+    h->zchunk = zchunk;
+    h->stencil_variant = variant;
+    return IOBM_OK;
+}
+
+int iobm_solve_batch(int n, iobm_handle* const* handles, const double* const* E, const int* nE,
+                     int side) {
+    if (n < 1 || !handles || !E || !nE || (side != 0 && side != 1)) return IOBM_E_ARG;
+    for (int j = 0; j < n; ++j) {
+        if (!handles[j] || !E[j] || nE[j] < 1) return IOBM_E_ARG;
+        for (int i = 0; i < j; ++i)
+            if (handles[i] == handles[j]) return fail(handles[j], IOBM_E_ARG, "a handle appears twice in the batch");
+    }
+    return solve_batch(n, handles, E, nE, side);
 }
 
 int iobm_num_rhs(const iobm_handle* h) { return h ? (int)h->users.size() : 0; }

@@ -119,6 +119,7 @@ struct StencilArgs {
     int tiles_x, tiles_y;  // lateral tiling
     long long npts;
     int* err;              // set to a nonzero code when a bounded wait gives up (or nullptr)
+    int variant;           // 0: the fastest kernel for the shape, 1: the register-pipelined row kernel
 };
 
 // codes written to StencilArgs::err
@@ -232,6 +233,8 @@ cudaError_t launch_residual(const double2* y, double2* r64, typename Cplx<T>::ty
                             int nx, int ny, int nz, int nf, const RhsState* st, int mask,
                             double* rr_part, int slot_stride, int nrhs, cudaStream_t s,
                             int* nslots_out);
+cudaError_t launch_batch_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
+                              int* counter, int max_chunks, cudaStream_t s);
 cudaError_t launch_check(RhsState* st, const double* rr_part, int nslots, int slot_stride,
                          int nrhs, double tol2, int init, cudaStream_t s);
 cudaError_t launch_projection(const double2* psi, const RhsDesc* desc, const int* open_ptr,

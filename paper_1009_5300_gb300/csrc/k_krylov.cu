@@ -418,4 +418,32 @@ cudaError_t launch_combine(double2* dst, const double2* x1, double2 c1, const do
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Loop condition of one junction in a batched solve (the WHILE node around its
+// chunk of iterations): continue while any RHS is ACTIVE, PENDING or
+// RESTART and fewer than max_chunks chunks have run.  The chunk counter makes
+// the loop end even if a status never settles.
+__global__ void k_batch_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
+                             int* counter, int max_chunks) {
+    __shared__ int live;
+    if (threadIdx.x == 0) live = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nrhs; i += blockDim.x) {
+        const int s = st[i].status;
+        if (s == ST_ACTIVE || s == ST_PENDING || s == ST_RESTART) live = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int c = *counter + 1;
+        *counter = c;
+        cudaGraphSetConditional(cond, (live && c < max_chunks) ? 1u : 0u);
+    }
+}
+
+cudaError_t launch_batch_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
+                              int* counter, int max_chunks, cudaStream_t s) {
+    k_batch_cond<<<1, 256, 0, s>>>(cond, st, nrhs, counter, max_chunks);
+    return cudaGetLastError();
+}
+
 }  // namespace iobm

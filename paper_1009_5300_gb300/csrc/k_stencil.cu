@@ -606,7 +606,7 @@ static bool tma_width(int nx) {
 
 template <typename T>
 static bool use_rows_tma(const StencilArgs<T>& a) {
-    if (sizeof(T) != 4 || !use_rows(a.nx, a.nf) || !tma_width(a.nx)) return false;
+    if (sizeof(T) != 4 || a.variant == 1 || !use_rows(a.nx, a.nf) || !tma_width(a.nx)) return false;
     uintptr_t al = reinterpret_cast<uintptr_t>(a.x);
     if (a.fused_p) al |= reinterpret_cast<uintptr_t>(a.pbufs[0]) | reinterpret_cast<uintptr_t>(a.pbufs[1]);
     return (al & 15) == 0;

@@ -193,6 +193,18 @@ class IOBMSolver:
                                       0 if ch is None else len(ch), int(side)), self.h)
         return self.transmission(E)
 
+    def autotune(self, nrhs: int):
+        """Pick the stencil tiling for nrhs RHS on this grid (iobm_autotune); (zchunk, variant)."""
+        self._ensure_workspace(max(int(nrhs), 1))
+        z = C.c_int(0)
+        v = C.c_int(0)
+        with torch.cuda.device(self.device):
+            check(self.lib.iobm_autotune(self.h, int(nrhs), C.byref(z), C.byref(v)), self.h)
+        return z.value, v.value
+
+    def set_tiling(self, zchunk: int, variant: int = 0):
+        check(self.lib.iobm_set_tiling(self.h, int(zchunk), int(variant)), self.h)
+
     def transmission(self, E) -> SolveResult:
         nrhs = self.lib.iobm_num_rhs(self.h)
         nE = len(E)
@@ -278,3 +290,32 @@ class IOBMSolver:
             check(self.lib.iobm_apply_precond(self.h, float(E), elem, C.c_void_p(x.data_ptr()),
                                               C.c_void_p(y.data_ptr()), nrhs), self.h)
         return y
+
+
+def solve_batch(solvers: Sequence["IOBMSolver"], energies: Sequence[Sequence[float]], side: int = 0,
+                autotune: bool = False):
+    """Solve several junctions together (iobm_solve_batch): one CUDA graph launch runs
+    every junction's COCG iterations concurrently.  energies[j] are the energies of
+    solvers[j]; every open incident channel is solved.  With autotune, each junction's
+    stencil tiling is picked for its RHS count first.  Returns one SolveResult per solver."""
+    lib = _lib.load()
+    n = len(solvers)
+    if n == 0:
+        return []
+    Es = [np.ascontiguousarray(np.atleast_1d(np.asarray(e, np.float64))) for e in energies]
+    if len(Es) != n:
+        raise ValueError("one energy list per solver")
+    for sol, E in zip(solvers, Es):
+        nrhs = sol._count_rhs(E, None)
+        sol._ensure_workspace(max(nrhs, 1))
+        if autotune and nrhs > 0:
+            sol.autotune(nrhs)
+    handles = (C.c_void_p * n)(*[sol.h.value for sol in solvers])
+    eptrs = (C.c_void_p * n)(*[E.ctypes.data for E in Es])
+    ne = (C.c_int * n)(*[len(E) for E in Es])
+    with torch.cuda.device(solvers[0].device):
+        code = lib.iobm_solve_batch(n, handles, eptrs, ne, int(side))
+    if code != _lib.IOBM_OK:
+        failing = next((sol.h for sol in solvers if lib.iobm_last_error(sol.h)), solvers[0].h)
+        check(code, failing)
+    return [sol.transmission(E) for sol, E in zip(solvers, Es)]
