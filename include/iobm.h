@@ -101,9 +101,12 @@ typedef struct {
 #define IOBM_PRECOND_FOURIER  2  /* (E - T - H~)^{-1}: the potential-free Green's function,
                                     diagonal in the lateral Fourier basis (Eq. 19) and
                                     banded in z; applied with lateral FFTs (default)       */
+#define IOBM_PRECOND_EQ10_FOURIER 3  /* Eq. 10 applied in the lateral Fourier basis: plane
+                                    FFT, per-mode tridiagonal multiply in z, inverse FFT;
+                                    the same operator as IOBM_PRECOND_EQ10 up to rounding  */
 
 /* Solver options.  use_precond: one of IOBM_PRECOND_*.  alpha: parameter of
- * Eq. 10 (C_0 = 1, C_1 = exp(-alpha)) for IOBM_PRECOND_EQ10.  tol: stop when
+ * Eq. 10 (C_0 = 1, C_1 = exp(-alpha)) for IOBM_PRECOND_EQ10(_FOURIER).  tol: stop when
  * ||b - A psi||_2 / ||b||_2 <= tol, the residual evaluated in FP64.
  * max_iter: Krylov iteration limit per RHS.  refine_delta: in IOBM_MIXED the
  * FP64 residual replaces the FP32 recurrence residual whenever the latter has

@@ -28,6 +28,7 @@ IOBM_MIXED = 1
 IOBM_PRECOND_NONE = 0
 IOBM_PRECOND_EQ10 = 1
 IOBM_PRECOND_FOURIER = 2
+IOBM_PRECOND_EQ10_FOURIER = 3
 IOBM_ELEM_C64 = 0
 IOBM_ELEM_C32 = 1
 

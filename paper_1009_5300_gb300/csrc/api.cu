@@ -159,6 +159,11 @@ size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 // because ||b||^2 = ||b_c||^2 + ||b_s||^2 (cos and sin profiles are orthogonal).
 double internal_tol2(const iobm_handle* h) { return 0.5 * h->opt.tol * h->opt.tol; }
 
+// preconditioner applied through lateral plane FFTs (free propagator or Eq. 10)
+bool fourier_precond(const iobm_handle* h) {
+    return h->opt.use_precond == IOBM_PRECOND_FOURIER || h->opt.use_precond == IOBM_PRECOND_EQ10_FOURIER;
+}
+
 int slots_for(const iobm_handle* h) {
     const int ns_op = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, h->nf);
     const int ns_pc = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, 1);
@@ -167,7 +172,7 @@ int slots_for(const iobm_handle* h) {
 
 // number of rho / |r|^2 partial slots the preconditioner pass writes
 int rho_slots(const iobm_handle* h) {
-    return h->opt.use_precond == IOBM_PRECOND_FOURIER
+    return fourier_precond(h)
                ? h->g.nz
                : stencil_slots(h->g.nx, h->g.ny, h->g.nz, h->zchunk, 1);
 }
@@ -297,6 +302,8 @@ PrecondArgs<T> fourier_args(const iobm_handle* h, const void* pc) {
     }
     a.npts = h->npts;
     a.mask = M_ALL;
+    a.eq10 = (h->opt.use_precond == IOBM_PRECOND_EQ10_FOURIER) ? 1 : 0;
+    a.c1 = std::exp(-h->opt.alpha);
     return a;
 }
 
@@ -379,7 +386,7 @@ int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void*
 template <typename T>
 int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) {
     using C = typename Cplx<T>::type;
-    if (h->opt.use_precond == IOBM_PRECOND_FOURIER) {
+    if (fourier_precond(h)) {
         PrecondArgs<T> f = fourier_args<T>(h, std::is_same<T, float>::value ? h->pc32.p : h->pc64.p);
         f.r = (const C*)h->vr;
         f.spec = (C*)h->vz;
@@ -500,7 +507,7 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     launches += 1;
     C* pb[2] = {(C*)h->vp[0], (C*)h->vp[1]};
     bool fused = false;
-    if (h->opt.use_precond == IOBM_PRECOND_FOURIER) {
+    if (fourier_precond(h)) {
         // x += alpha p, r -= alpha q fused with the forward plane FFTs of the preconditioner
         PrecondArgs<T> f = fourier_args<T>(h, std::is_same<T, float>::value ? h->pc32.p : h->pc64.p);
         f.r = (const C*)h->vr;
@@ -1142,7 +1149,7 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     if (!(rs > 0)) return bad(IOBM_E_ARG, "rs must be positive");
     if (!(h->opt.tol > 0) || h->opt.max_iter < 1 || !(h->opt.refine_delta > 0 && h->opt.refine_delta < 1) ||
         (h->opt.precision != IOBM_FP64 && h->opt.precision != IOBM_MIXED) || !(h->opt.alpha > 0) ||
-        h->opt.use_precond < IOBM_PRECOND_NONE || h->opt.use_precond > IOBM_PRECOND_FOURIER)
+        h->opt.use_precond < IOBM_PRECOND_NONE || h->opt.use_precond > IOBM_PRECOND_EQ10_FOURIER)
         return bad(IOBM_E_ARG, "invalid solver options");
     h->nxy = g.nx * g.ny;
     h->npts = (long long)h->nxy * g.nz;
@@ -1500,7 +1507,7 @@ static int apply_common(iobm_handle* h, double E, int elem, const void* x, void*
         CK(upload(h->apply_ediag, ed, h->stream));
     }
     if (precond) {
-        if (h->opt.use_precond == IOBM_PRECOND_FOURIER) {
+        if (fourier_precond(h)) {
             if (elem == IOBM_ELEM_C64) {
                 PrecondArgs<double> f = fourier_args<double>(h, h->apply_pc64.p);
                 f.r = (const double2*)x;

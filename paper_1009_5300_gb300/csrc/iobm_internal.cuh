@@ -189,6 +189,8 @@ struct PrecondArgs {
     double* nrm_part;
     int slot_stride;
     long long npts;
+    int eq10;                // 0: free-propagator z-sweeps (pc tables); 1: Eq. 10 per mode
+    double c1;               // Eq. 10 weight exp(-alpha) (eq10 = 1)
 };
 
 template <typename T> cudaError_t launch_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s);

@@ -14,7 +14,9 @@
 // memory ping-pong Stockham passes over all lines at once); (2) per-mode
 // z-sweeps in place on the spectrum (one thread per mode, coalesced across
 // modes); (3) inverse 2D FFT of every plane, fused with the Krylov dot
-// products r^T z and |r|^2 of that plane.
+// products r^T z and |r|^2 of that plane.  The same transforms also apply the
+// Eq. 10 preconditioner in its lateral Fourier form (step 2 then being a
+// per-mode tridiagonal multiply in z).
 #include "iobm_internal.cuh"
 #include "complex_ops.cuh"
 #include "fft_ct.cuh"
@@ -239,6 +241,35 @@ __global__ void __launch_bounds__(kZThreads) k_zsolve(const PrecondArgs<T> a) {
     }
 }
 
+// Eq. 10 in the lateral Fourier basis: with r~ the (unnormalised) plane
+// spectrum of mode (kx, ky), z~(k) = (1 + 2 C_1 (cos th_x + cos th_y)) r~(k)
+//   + C_1 (r~(k-1) + r~(k+1)), th = 2 pi k / N, zero beyond the end planes.
+// One thread per (RHS, mode), in place: r~(k+1) is read before z~(k) is written
+// and r~(k-1) is kept in a register.  Carries the 1/N_xy of the transform pair.
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) k_zmul_eq10(const PrecondArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    const int rhs = blockIdx.y;
+    if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
+    const int nxy = a.nx * a.ny;
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= nxy) return;
+    const int kx = mode % a.nx, ky = mode / a.nx;
+    const double pi2 = 6.283185307179586476925286766559;
+    const double d = 1.0 + 2.0 * a.c1 * (cos(pi2 * kx / a.nx) + cos(pi2 * ky / a.ny));
+    const T scale = (T)1 / (T)nxy;
+    const T dd = (T)d * scale, cc = (T)a.c1 * scale;
+    C* __restrict__ s = a.spec + (long long)rhs * a.npts + mode;
+    C prev = czero<C>();
+    C cur = s[0];
+    for (int k = 0; k < a.nz; ++k) {
+        const C next = (k + 1 < a.nz) ? s[(long long)(k + 1) * nxy] : czero<C>();
+        s[(long long)k * nxy] = caxpy(cc, cadd(prev, next), cscale(cur, dd));
+        prev = cur;
+        cur = next;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_plane_ifft_dots(const PrecondArgs<T> a) {
     using C = typename Cplx<T>::type;
@@ -421,6 +452,10 @@ template <typename T>
 static cudaError_t launch_zsolve(const PrecondArgs<T>& a, int nrhs, cudaStream_t s) {
     const int nxy = a.nx * a.ny;
     dim3 gz((nxy + kZThreads - 1) / kZThreads, nrhs);
+    if (a.eq10) {
+        k_zmul_eq10<T><<<gz, kZThreads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     switch (a.nf) {
         case 1: k_zsolve<T, 1><<<gz, kZThreads, 0, s>>>(a); break;
         case 2: k_zsolve<T, 2><<<gz, kZThreads, 0, s>>>(a); break;

@@ -55,7 +55,8 @@ def default_options(**kw) -> _lib.Options:
             v = {"fp64": _lib.IOBM_FP64, "mixed": _lib.IOBM_MIXED}[v]
         if k == "use_precond" and isinstance(v, str):
             v = {"none": _lib.IOBM_PRECOND_NONE, "eq10": _lib.IOBM_PRECOND_EQ10,
-                 "fourier": _lib.IOBM_PRECOND_FOURIER}[v]
+                 "fourier": _lib.IOBM_PRECOND_FOURIER,
+                 "eq10_fourier": _lib.IOBM_PRECOND_EQ10_FOURIER}[v]
         setattr(o, k, v)
     return o
 

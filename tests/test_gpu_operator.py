@@ -74,6 +74,30 @@ def test_precond_matches_oracle(nx, ny, nz, nf, kb):
         sol.close()
 
 
+@pytest.mark.parametrize("nx,ny,nz,nf,kb", [(20, 12, 30, 4, True), (16, 16, 24, 4, False),
+                                             (25, 27, 16, 2, False), CASES[1]])
+def test_eq10_fourier_form_matches_stencil(nx, ny, nz, nf, kb):
+    # Eq. 10 applied through the lateral FFT (per-mode tridiagonal z-multiply) is the
+    # operator of the real-space stencil form, to rounding; both against the oracle
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = make(nx, ny, nz, nf, kb)
+    for alpha in (1.8, 3.0):
+        st = IOBMSolver.from_junction(jn, precision="fp64", alpha=alpha, use_precond="eq10")
+        ft = IOBMSolver.from_junction(jn, precision="fp64", alpha=alpha, use_precond="eq10_fourier")
+        x = np.stack([S.random_field((nz, ny, nx), 11 + i) for i in range(2)])
+        ref = np.stack([operator.apply_P(jn, alpha, x[i]) for i in range(2)])
+        xd = torch.from_numpy(x).cuda()
+        y_st = st.apply_precond(xd).cpu().numpy()
+        y_ft = ft.apply_precond(xd).cpu().numpy()
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(y_ft - y_st)) < 1e-13 * scale
+        assert np.max(np.abs(y_ft - ref)) < 1e-13 * scale
+        y32 = ft.apply_precond(xd.to(torch.complex64)).cpu().numpy()
+        assert np.max(np.abs(y32 - ref)) < 1e-6 * scale
+        st.close()
+        ft.close()
+
+
 @pytest.mark.parametrize("nx,ny,nz,nf,kb", [(20, 12, 30, 4, True), CASES[1], (25, 27, 16, 2, False),
                                              (16, 16, 24, 4, True), (12, 12, 30, 1, False)])
 def test_fourier_precond_matches_oracle(nx, ny, nz, nf, kb):

@@ -74,6 +74,23 @@ def test_multichannel_kb(nf, precision, precond):
     sol.close()
 
 
+def test_eq10_fourier_form_solve():
+    # the Fourier form of Eq. 10 drives the same Krylov iteration as the stencil form
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = kb_junction(4)
+    E = jn.e_fermi
+    ref = transport.solve(jn, E)
+    its = []
+    for precond in ("eq10", "eq10_fourier"):
+        sol = IOBMSolver.from_junction(jn, precision="fp64", use_precond=precond, alpha=1.8)
+        res = sol.solve([E])
+        compare(res, ref)
+        its.append(res.iterations)
+        sol.close()
+    # different rounding over ~200 Krylov steps moves the counts by a few per cent
+    assert np.max(np.abs(its[0] - its[1])) <= 0.05 * np.max(its[0])
+
+
 def test_right_incidence_and_reciprocity():
     from paper_1009_5300_gb300 import IOBMSolver
     jn = kb_junction(4)
