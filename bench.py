@@ -363,6 +363,107 @@ def native_arm(args, rank, world, local_rank):
     return 0
 
 
+BATCH_WORKLOAD = ("uneven batch: {n} junctions (lateral N from the 2,3,5-smooth set in [24, 64], "
+                  "N_z in [96, 256], h=0.35 bohr, 2-8 Gaussian wells, r_s in [2, 4]), {e} energies "
+                  "each in [E_F-1eV, E_F+0.5eV], all open channels, mixed precision, Fourier "
+                  "preconditioner, autotuned stencil tiling, one graph launch per group")
+
+
+def batch_arm(args, rank, world, local_rank):
+    """Many junctions of uneven size: groups sized to the free device memory, each
+    group solved by one iobm_solve_batch (one graph launch, a device-side WHILE loop
+    per junction).  Junctions are dealt round-robin to the ranks."""
+    import numpy as np
+    import torch
+
+    import iobm_synth as S
+    from paper_1009_5300_gb300 import IOBMSolver, build_library, solve_batch
+
+    build_library()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    ids = list(range(rank, args.junctions, world))
+    jns = [S.batch_junction(j, n_energies=args.batch_energies) for j in ids]
+
+    # warm-up: the first junction at two energies, untimed
+    w = IOBMSolver.from_junction(jns[0], precision="mixed", device=dev)
+    solve_batch([w], [jns[0].energies[:2]], autotune=True)
+    w.close()
+    torch.cuda.synchronize(dev)
+
+    # RHS counts and workspace sizes decide the groups (host-side, untimed)
+    sols = [IOBMSolver.from_junction(jn, precision="mixed", device=dev) for jn in jns]
+    need = []
+    for sol, jn in zip(sols, jns):
+        nrhs = sol._count_rhs(np.ascontiguousarray(jn.energies), None)
+        need.append(sol.workspace_size(max(nrhs, 1)))
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = 0.7 * free
+    groups, cur, cur_b = [], [], 0
+    for i, b in enumerate(need):
+        if cur and cur_b + b > budget:
+            groups.append(cur)
+            cur, cur_b = [], 0
+        cur.append(i)
+        cur_b += b
+    if cur:
+        groups.append(cur)
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    stream = torch.cuda.current_stream(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    solves, converged, iters = 0, True, 0
+    ev0.record(stream)
+    for g in groups:
+        res = solve_batch([sols[i] for i in g], [jns[i].energies for i in g], autotune=True)
+        for r in res:
+            solves += r.nrhs
+            converged &= bool(r.converged)
+            iters += r.iterations_total
+        for i in g:
+            sols[i].release_workspace()   # free this group's workspace before the next one
+        torch.cuda.empty_cache()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms, float(solves)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms, solves_all = float(tmax[0]), float(t[1])
+    else:
+        solves_all = float(solves)
+    if rank == 0:
+        line = {"metric": METRIC, "value": solves_all / (ms / 1000.0), "unit": UNIT,
+                "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "c64+f64", "data": "synthetic",
+                "config": {"workload": BATCH_WORKLOAD.format(n=args.junctions, e=args.batch_energies),
+                           "junctions": args.junctions, "channel_solves": int(solves_all),
+                           "groups_rank0": len(groups), "l2": "inputs larger than L2",
+                           "parallelism": f"junctions dealt to {world} replica(s)"},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clocks,
+                "iterations_mean": iters / max(1, solves), "converged": converged}
+        print(json.dumps(line), flush=True)
+    for sol in sols:
+        sol.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,12 +478,19 @@ def main():
                     help="FP64 residual replacement factor of the mixed solver (library default)")
     ap.add_argument("--chunk", type=int, default=None,
                     help="COCG iterations per captured graph (library default)")
+    ap.add_argument("--workload", choices=["wire48", "batch"], default="wire48",
+                    help="wire48: the 48x48x160 wire (default line); batch: the uneven "
+                         "many-junction workload solved in grouped graph launches")
+    ap.add_argument("--junctions", type=int, default=256)
+    ap.add_argument("--batch-energies", type=int, default=16)
     args = ap.parse_args()
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)
     local_rank = env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload == "batch":
+        return batch_arm(args, rank, world, local_rank)
     return native_arm(args, rank, world, local_rank)
 
 

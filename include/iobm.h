@@ -111,7 +111,12 @@ typedef struct {
  * max_iter: Krylov iteration limit per RHS.  refine_delta: in IOBM_MIXED the
  * FP64 residual replaces the FP32 recurrence residual whenever the latter has
  * fallen by this factor since the last replacement (0 < delta < 1).
- * chunk: iterations per captured CUDA graph between convergence checks. */
+ * chunk: iterations per captured CUDA graph between convergence checks.
+ * max_iter_mixed: in IOBM_MIXED, FP32 iteration limit per RHS; an RHS that
+ * stops there (or breaks down) without converging is continued with FP64
+ * iterations from its FP64 iterate, up to max_iter more (precision escalation:
+ * once cond(A) times the FP32 rounding unit is no longer small, the FP32 inner
+ * iteration stops making progress while FP64 still converges). */
 typedef struct {
     double alpha;
     int use_precond;
@@ -120,6 +125,7 @@ typedef struct {
     int precision;
     double refine_delta;
     int chunk;
+    int max_iter_mixed;
 } iobm_options;
 
 /* Per right-hand-side report, in solve order (energy-major, then incident
@@ -135,7 +141,8 @@ typedef struct {
 } iobm_report;
 
 /* Fill opts with the defaults: alpha 1.8, use_precond IOBM_PRECOND_FOURIER, tol 1e-8,
- * max_iter 20000, precision IOBM_MIXED, refine_delta 0.01, chunk 32. */
+ * max_iter 20000, precision IOBM_MIXED, refine_delta 0.01, chunk 32,
+ * max_iter_mixed 1000. */
 void iobm_default_options(iobm_options* opts);
 
 /* Create a solver for one junction.  V_loc: host [nz][ny][nx] local

@@ -98,6 +98,7 @@ struct iobm_handle {
     int zchunk = kZChunkDefault;         // stencil z-planes per CTA (autotuned)
     int stencil_variant = 0;             // StencilArgs::variant (autotuned)
     DevBuf batch_ctr;                    // chunk counter of this junction in a batched solve
+    DevBuf esc_ws, esc_descs, esc_rhs_energy;   // FP64 continuation of stalled mixed RHS
 
     // workspace
     void* ws = nullptr;
@@ -158,6 +159,13 @@ size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 // psi = x_c +- i x_s then has ||b - A psi|| <= ||r_c|| + ||r_s|| <= tol ||b||
 // because ||b||^2 = ||b_c||^2 + ||b_s||^2 (cos and sin profiles are orthogonal).
 double internal_tol2(const iobm_handle* h) { return 0.5 * h->opt.tol * h->opt.tol; }
+
+// per-RHS iteration limit of the current solve (the FP32 phase of a mixed solve
+// stops at max_iter_mixed; the FP64 continuation gets max_iter)
+int iter_cap(const iobm_handle* h) {
+    return h->opt.precision == IOBM_MIXED ? std::min(h->opt.max_iter, h->opt.max_iter_mixed)
+                                          : h->opt.max_iter;
+}
 
 // preconditioner applied through lateral plane FFTs (free propagator or Eq. 10)
 bool fourier_precond(const iobm_handle* h) {
@@ -452,7 +460,7 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     CK(launch_restart_scalars(h->st, h->rho_part, h->rr_part, h->ns_stencil, h->slot_stride, nrhs,
                               h->stream));
     CK(launch_beta(h->st, h->rho_part, h->rr_part, rho_slots(h), h->slot_stride, nrhs,
-                   h->opt.max_iter, tol2, delta2, mixed ? 1 : 0, h->stream));
+                   iter_cap(h), tol2, delta2, mixed ? 1 : 0, h->stream));
     launches += 2;
     const void* sig = std::is_same<T, float>::value ? h->sig32.p : h->sig64.p;
     StencilArgs<T> a = op_args<T>(h);
@@ -574,6 +582,25 @@ int solver_prologue(iobm_handle* h, int nrhs, long long& launches) {
     return apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
 }
 
+// Solver start from the iterate already in x (FP64 solver only, where x64 is x):
+// ||b||^2 from r = b, then an FP64 residual replacement gives r = b - A x and
+// z = P r for every RHS that is not already converged.
+int solver_prologue_warm(iobm_handle* h, int nrhs, long long& launches) {
+    using C = double2;
+    const size_t n = (size_t)nrhs * h->npts;
+    CK(cudaEventRecord(h->ev_t0, h->stream));
+    CK(cudaMemsetAsync(h->vp[0], 0, sizeof(C) * n, h->stream));
+    CK(cudaMemsetAsync(h->vp[1], 0, sizeof(C) * n, h->stream));
+    int nslots = 0;
+    CK(launch_residual<double>(nullptr, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
+                               h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, nullptr, M_ALL,
+                               h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
+    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, 0.0, 1, h->stream));
+    CK(launch_set_status(h->st, nrhs, ST_RESTART, ST_PENDING, h->stream));
+    launches += 3;
+    return residual_replacement<double>(h, nrhs, M_PENDING, false, launches);
+}
+
 // COCG iterations per captured chunk (a multiple of the replacement period)
 int chunk_length(const iobm_handle* h) {
     return ((std::max(1, h->opt.chunk) + kReplaceEvery - 1) / kReplaceEvery) * kReplaceEvery;
@@ -629,9 +656,10 @@ int solver_epilogue(iobm_handle* h, int nrhs, long long& launches) {
 }
 
 template <typename T>
-int run_solver(iobm_handle* h, int nrhs) {
+int run_solver(iobm_handle* h, int nrhs, bool warm = false) {
     long long launches = 0;
-    int rc = solver_prologue<T>(h, nrhs, launches);
+    int rc = (warm && !std::is_same<T, float>::value) ? solver_prologue_warm(h, nrhs, launches)
+                                                      : solver_prologue<T>(h, nrhs, launches);
     if (rc) return rc;
 
     // capture one chunk of iterations
@@ -658,7 +686,7 @@ int run_solver(iobm_handle* h, int nrhs) {
     cudaGraphDestroy(graph);
 
     h->hstate.resize(nrhs);
-    const int max_chunks = h->opt.max_iter / chunk + 4;
+    const int max_chunks = iter_cap(h) / chunk + 4;
     int chunks = 0;
     for (; chunks < max_chunks; ++chunks) {
         cudaError_t e = cudaGraphLaunch(exec, h->stream);
@@ -831,6 +859,96 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
     return IOBM_OK;
 }
 
+// Precision escalation after a mixed solve: the RHS that stopped without
+// converging (FP32 iteration limit or breakdown) are solved again with FP64
+// COCG, starting from their FP64 iterate, in a separate FP64 workspace; their
+// solutions, states and counts are merged back.  The handle's workspace
+// bindings are swapped for the sub-solve and restored afterwards.
+int escalate_fp64(iobm_handle* h) {
+    std::vector<int> idx;
+    for (int i = 0; i < h->nrhs; ++i) {
+        const int st = h->hstate[i].status;
+        if (st == ST_NOCONV || st == ST_BREAKDOWN) idx.push_back(i);
+    }
+    if (idx.empty()) return IOBM_OK;
+    const int m = (int)idx.size();
+    std::vector<RhsDesc> sd(m);
+    std::vector<int> se(m);
+    for (int k = 0; k < m; ++k) {
+        sd[k] = h->hdesc[idx[k]];
+        se[k] = h->hrhs_energy[idx[k]];
+    }
+    CK(upload(h->esc_descs, sd, h->stream));
+    CK(upload(h->esc_rhs_energy, se, h->stream));
+    const size_t need = workspace_bytes(h, m, IOBM_FP64);
+    CK(h->esc_ws.ensure(need));
+
+    struct Saved {
+        void* ws; size_t ws_bytes; int ws_nrhs, ws_prec, slot_stride, ns_stencil, nrhs, precision;
+        RhsState* st; double2 *mu_part, *rho_part; double* rr_part;
+        void *vx, *vr, *vp0, *vp1, *vq, *vz; double2 *x64, *y64;
+        double last_ms; long long last_launches, last_iters; int profile;
+    } sv{h->ws, h->ws_bytes, h->ws_nrhs, h->ws_prec, h->slot_stride, h->ns_stencil, h->nrhs,
+         h->opt.precision, h->st, h->mu_part, h->rho_part, h->rr_part, h->vx, h->vr, h->vp[0],
+         h->vp[1], h->vq, h->vz, h->x64, h->y64, h->last_ms, h->last_launches, h->last_iters,
+         h->profile};
+    std::vector<RhsState> main_state = h->hstate;
+    auto restore = [&]() {
+        h->ws = sv.ws; h->ws_bytes = sv.ws_bytes; h->ws_nrhs = sv.ws_nrhs; h->ws_prec = sv.ws_prec;
+        h->slot_stride = sv.slot_stride; h->ns_stencil = sv.ns_stencil; h->nrhs = sv.nrhs;
+        h->opt.precision = sv.precision; h->st = sv.st; h->mu_part = sv.mu_part;
+        h->rho_part = sv.rho_part; h->rr_part = sv.rr_part; h->vx = sv.vx; h->vr = sv.vr;
+        h->vp[0] = sv.vp0; h->vp[1] = sv.vp1; h->vq = sv.vq; h->vz = sv.vz; h->x64 = sv.x64;
+        h->y64 = sv.y64; h->profile = sv.profile;
+        std::swap(h->descs, h->esc_descs);
+        std::swap(h->rhs_energy, h->esc_rhs_energy);
+    };
+    std::swap(h->descs, h->esc_descs);
+    std::swap(h->rhs_energy, h->esc_rhs_energy);
+    h->ws = h->esc_ws.p;
+    h->ws_bytes = need;
+    h->opt.precision = IOBM_FP64;
+    h->nrhs = m;
+    h->profile = 0;
+    int rc = bind_workspace(h, m);
+    // the FP64 iterate of every stalled RHS is the starting point
+    for (int k = 0; !rc && k < m; ++k) {
+        const cudaError_t e = cudaMemcpyAsync((double2*)h->vx + (size_t)k * h->npts,
+                                              sv.x64 + (size_t)idx[k] * h->npts,
+                                              sizeof(double2) * h->npts, cudaMemcpyDeviceToDevice,
+                                              h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "escalation start");
+    }
+    if (!rc) rc = run_solver<double>(h, m, true);
+    for (int k = 0; !rc && k < m; ++k) {
+        const cudaError_t e = cudaMemcpyAsync(sv.x64 + (size_t)idx[k] * h->npts,
+                                              (double2*)h->vx + (size_t)k * h->npts,
+                                              sizeof(double2) * h->npts, cudaMemcpyDeviceToDevice,
+                                              h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "escalation result");
+    }
+    const std::vector<RhsState> sub = h->hstate;
+    const double sub_ms = h->last_ms;
+    const long long sub_launches = h->last_launches, sub_iters = h->last_iters;
+    restore();
+    h->hstate = main_state;
+    if (rc) return rc;
+    for (int k = 0; k < m; ++k) {
+        RhsState& S = h->hstate[idx[k]];
+        const int iters = S.iters, reps = S.replacements;
+        S = sub[k];
+        S.iters += iters;
+        S.replacements += reps;
+    }
+    CK(cudaMemcpyAsync(h->st, h->hstate.data(), sizeof(RhsState) * h->nrhs, cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->last_ms += sub_ms;
+    h->last_launches += sub_launches;
+    h->last_iters += sub_iters;
+    return IOBM_OK;
+}
+
 // projection sums of the FP64 solutions (Eq. 19 on the end planes) after a solve
 int launch_projections(iobm_handle* h) {
     const size_t pbytes = sizeof(double2) * (size_t)h->nrhs * std::max(h->max_open, 1) * 2 * kMaxNf;
@@ -852,6 +970,10 @@ int run_batch(iobm_handle* h) {
     rc = (h->opt.precision == IOBM_MIXED) ? run_solver<float>(h, h->nrhs)
                                           : run_solver<double>(h, h->nrhs);
     if (rc) return rc;
+    if (h->opt.precision == IOBM_MIXED) {
+        rc = escalate_fp64(h);
+        if (rc) return rc;
+    }
     rc = launch_projections(h);
     if (rc) return rc;
     h->solved = true;
@@ -869,7 +991,7 @@ int capture_batch_body(iobm_handle* h, cudaGraph_t body, cudaGraphConditionalHan
                                      cudaStreamCaptureModeThreadLocal));
     int rc = launch_chunk<T>(h, h->nrhs, false, per_chunk);
     if (rc == IOBM_OK) {
-        const int max_chunks = h->opt.max_iter / chunk_length(h) + 4;
+        const int max_chunks = iter_cap(h) / chunk_length(h) + 4;
         const cudaError_t e = launch_batch_cond(cond, h->st, h->nrhs, h->batch_ctr.as<int>(),
                                                 max_chunks, h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "batch loop condition");
@@ -972,6 +1094,7 @@ int solve_batch(int n, iobm_handle* const* hs, const double* const* E, const int
         if (!rc)
             rc = (h->opt.precision == IOBM_MIXED) ? solver_epilogue<float>(h, h->nrhs, launches[j])
                                                   : solver_epilogue<double>(h, h->nrhs, launches[j]);
+        if (!rc && h->opt.precision == IOBM_MIXED) rc = escalate_fp64(h);
         if (!rc) rc = launch_projections(h);
         if (!rc) h->solved = true;
         if (rc && !first_rc) first_rc = rc;
@@ -1101,6 +1224,7 @@ void iobm_default_options(iobm_options* o) {
     o->precision = IOBM_MIXED;
     o->refine_delta = 0.01;
     o->chunk = 32;
+    o->max_iter_mixed = 1000;
 }
 
 const char* iobm_status_string(int s) {
@@ -1147,7 +1271,8 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
         !(g.hx > 0) || !(g.hy > 0) || !(g.hz > 0))
         return bad(IOBM_E_ARG, "grid sizes or spacings out of range (need nf in 1..4, nz >= 2 nf + 1)");
     if (!(rs > 0)) return bad(IOBM_E_ARG, "rs must be positive");
-    if (!(h->opt.tol > 0) || h->opt.max_iter < 1 || !(h->opt.refine_delta > 0 && h->opt.refine_delta < 1) ||
+    if (!(h->opt.tol > 0) || h->opt.max_iter < 1 || h->opt.max_iter_mixed < 1 ||
+        !(h->opt.refine_delta > 0 && h->opt.refine_delta < 1) ||
         (h->opt.precision != IOBM_FP64 && h->opt.precision != IOBM_MIXED) || !(h->opt.alpha > 0) ||
         h->opt.use_precond < IOBM_PRECOND_NONE || h->opt.use_precond > IOBM_PRECOND_EQ10_FOURIER)
         return bad(IOBM_E_ARG, "invalid solver options");

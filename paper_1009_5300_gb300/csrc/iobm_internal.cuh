@@ -235,6 +235,7 @@ cudaError_t launch_residual(const double2* y, double2* r64, typename Cplx<T>::ty
                             int nx, int ny, int nz, int nf, const RhsState* st, int mask,
                             double* rr_part, int slot_stride, int nrhs, cudaStream_t s,
                             int* nslots_out);
+cudaError_t launch_set_status(RhsState* st, int nrhs, int from, int to, cudaStream_t s);
 cudaError_t launch_batch_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
                               int* counter, int max_chunks, cudaStream_t s);
 cudaError_t launch_check(RhsState* st, const double* rr_part, int nslots, int slot_stride,

@@ -291,6 +291,18 @@ __global__ void k_check(RhsState* st, const double* rr_part, int nslots, int str
     st[i] = S;
 }
 
+// status `from` -> `to` for every RHS (a warm start turns its freshly
+// initialised RESTART RHS into PENDING ones for an FP64 residual replacement)
+__global__ void k_set_status(RhsState* st, int nrhs, int from, int to) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nrhs && st[i].status == from) st[i].status = to;
+}
+
+cudaError_t launch_set_status(RhsState* st, int nrhs, int from, int to, cudaStream_t s) {
+    k_set_status<<<(nrhs + 127) / 128, 128, 0, s>>>(st, nrhs, from, to);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check(RhsState* st, const double* rr_part, int nslots, int slot_stride,
                          int nrhs, double tol2, int init, cudaStream_t s) {
     k_check<<<(nrhs + 127) / 128, 128, 0, s>>>(st, rr_part, nslots, slot_stride, nrhs, tol2, init);

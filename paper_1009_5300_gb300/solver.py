@@ -194,6 +194,12 @@ class IOBMSolver:
                                       0 if ch is None else len(ch), int(side)), self.h)
         return self.transmission(E)
 
+    def release_workspace(self):
+        """Detach and free the torch-allocated workspace; the results of the last solve
+        are no longer readable afterwards (read them first)."""
+        check(self.lib.iobm_set_workspace(self.h, None, 0), self.h)
+        self._ws = None
+
     def autotune(self, nrhs: int):
         """Pick the stencil tiling for nrhs RHS on this grid (iobm_autotune); (zchunk, variant)."""
         self._ensure_workspace(max(int(nrhs), 1))

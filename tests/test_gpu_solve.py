@@ -91,6 +91,27 @@ def test_eq10_fourier_form_solve():
     assert np.max(np.abs(its[0] - its[1])) <= 0.05 * np.max(its[0])
 
 
+def test_precision_escalation():
+    # with a tiny FP32 iteration limit every RHS stops unconverged in the mixed phase
+    # and is finished by FP64 COCG from its FP64 iterate: same exact solution
+    from paper_1009_5300_gb300 import IOBMSolver, solve_batch
+    jn = kb_junction(4)
+    E = jn.e_fermi
+    ref = transport.solve(jn, E)
+    sol = IOBMSolver.from_junction(jn, precision="mixed", max_iter_mixed=4)
+    res = sol.solve([E])
+    compare(res, ref)
+    assert np.all(res.iterations > 4)
+    sol.close()
+    # the batched path escalates the same way
+    sols = [IOBMSolver.from_junction(jn, precision="mixed", max_iter_mixed=4) for _ in range(2)]
+    out = solve_batch(sols, [[E], [E - 0.02]])
+    compare(out[0], ref)
+    assert abs(out[1].G[0] - transport.conductance(jn, E - 0.02)) < G_TOL
+    for s in sols:
+        s.close()
+
+
 def test_right_incidence_and_reciprocity():
     from paper_1009_5300_gb300 import IOBMSolver
     jn = kb_junction(4)
