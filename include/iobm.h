@@ -67,6 +67,9 @@ extern "C" {
 /* element type of vectors passed to iobm_apply / iobm_apply_precond */
 #define IOBM_ELEM_C64   0  /* complex double, interleaved */
 #define IOBM_ELEM_C32   1  /* complex float, interleaved  */
+#define IOBM_ELEM_C64_DF 2 /* complex double data, stencil in double-float arithmetic (FP32
+                              pairs, about 47 significant bits): what the mixed solver's FP64
+                              residual uses; iobm_apply only */
 
 typedef struct iobm_handle iobm_handle;
 
@@ -260,8 +263,9 @@ int iobm_grad_V(iobm_handle* h, double E, double* dGdV, int dst_is_device, doubl
 
 /* y = (E - H_T - H~) x for nrhs vectors (Eqs. 1-4, 7-2, 8 via FFT),
  * x and y device buffers [nrhs][nz][ny][nx] of element type `elem`
- * (IOBM_ELEM_C64 computes in FP64, IOBM_ELEM_C32 in FP32).  Uses the
- * workspace for the projector scratch. */
+ * (IOBM_ELEM_C64 computes in FP64, IOBM_ELEM_C32 in FP32, IOBM_ELEM_C64_DF
+ * the stencil in double-float arithmetic on FP64 data, the self-energy and KB
+ * terms in FP64).  Uses the workspace for the projector scratch. */
 int iobm_apply(iobm_handle* h, double E, int elem, const void* x, void* y, int nrhs);
 
 /* y = P x with the handle's preconditioner at energy E: Eq. 10 (six face

@@ -31,6 +31,7 @@ IOBM_PRECOND_FOURIER = 2
 IOBM_PRECOND_EQ10_FOURIER = 3
 IOBM_ELEM_C64 = 0
 IOBM_ELEM_C32 = 1
+IOBM_ELEM_C64_DF = 2
 
 
 class Grid(C.Structure):

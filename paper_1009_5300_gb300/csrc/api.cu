@@ -251,10 +251,17 @@ StencilArgs<T> op_args(const iobm_handle* h) {
     a.nf = h->nf;
     const double ihx = 1.0 / (h->g.hx * h->g.hx), ihy = 1.0 / (h->g.hy * h->g.hy),
                  ihz = 1.0 / (h->g.hz * h->g.hz);
+    auto pair = [](double c) {   // c as an FP32 pair hi + lo
+        const float hi = (float)c;
+        return make_float2(hi, (float)(c - (double)hi));
+    };
     for (int n = 1; n <= h->nf; ++n) {
         a.cx[n] = (T)(0.5 * h->w[n] * ihx);
         a.cy[n] = (T)(0.5 * h->w[n] * ihy);
         a.cz[n] = (T)(0.5 * h->w[n] * ihz);
+        a.dfx[n] = pair(0.5 * h->w[n] * ihx);
+        a.dfy[n] = pair(0.5 * h->w[n] * ihy);
+        a.dfz[n] = pair(0.5 * h->w[n] * ihz);
     }
     a.iso = 1;
     for (int n = 1; n <= h->nf; ++n) a.iso &= (a.cx[n] == a.cy[n] && a.cy[n] == a.cz[n]) ? 1 : 0;
@@ -360,9 +367,10 @@ KbArgs<T> kb_args(const iobm_handle* h) {
 template <typename T>
 int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void* sig,
                    const double* ediag, const int* rhs_energy, const RhsState* st, int mask,
-                   long long& launches) {
+                   long long& launches, bool df = false) {
     using C = typename Cplx<T>::type;
     StencilArgs<T> a = op_args<T>(h);
+    if (df) a.variant = 2;   // FP64 data, double-float stencil arithmetic
     a.x = (const C*)x;
     a.y = (C*)y;
     a.ediag = ediag;
@@ -433,7 +441,7 @@ int residual_replacement(iobm_handle* h, int nrhs, int mask, bool mixed, long lo
         launches += 1;
     }
     int rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
-                                    h->rhs_energy.as<int>(), h->st, mask, launches);
+                                    h->rhs_energy.as<int>(), h->st, mask, launches, mixed);
     if (rc) return rc;
     int nslots = 0;
     CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
@@ -633,7 +641,7 @@ int solver_epilogue(iobm_handle* h, int nrhs, long long& launches) {
         CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
     }
     int rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
-                                    h->rhs_energy.as<int>(), h->st, mask, launches);
+                                    h->rhs_energy.as<int>(), h->st, mask, launches, mixed);
     if (rc) return rc;
     int nslots = 0;
     CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
@@ -1601,7 +1609,8 @@ int iobm_grad_V(iobm_handle* h, double E, double* dGdV, int dst_is_device, doubl
 
 static int apply_common(iobm_handle* h, double E, int elem, const void* x, void* y, int nrhs,
                         bool precond) {
-    if (!h || !x || !y || nrhs < 0 || (elem != IOBM_ELEM_C64 && elem != IOBM_ELEM_C32))
+    if (!h || !x || !y || nrhs < 0 ||
+        (elem != IOBM_ELEM_C64 && elem != IOBM_ELEM_C32 && !(elem == IOBM_ELEM_C64_DF && !precond)))
         return h ? fail(h, IOBM_E_ARG, "invalid apply arguments") : IOBM_E_ARG;
     if (nrhs == 0) return IOBM_OK;
     if (cudaEventRecord(h->ev_sync, h->user_stream) == cudaSuccess)
@@ -1659,9 +1668,9 @@ static int apply_common(iobm_handle* h, double E, int elem, const void* x, void*
         }
     } else {
         int rc2;
-        if (elem == IOBM_ELEM_C64)
+        if (elem == IOBM_ELEM_C64 || elem == IOBM_ELEM_C64_DF)
             rc2 = apply_operator<double>(h, x, y, nrhs, h->apply_sig64.p, h->apply_ediag.as<double>(),
-                                         nullptr, nullptr, M_ALL, launches);
+                                         nullptr, nullptr, M_ALL, launches, elem == IOBM_ELEM_C64_DF);
         else
             rc2 = apply_operator<float>(h, x, y, nrhs, h->apply_sig32.p, h->apply_ediag.as<double>(),
                                         nullptr, nullptr, M_ALL, launches);

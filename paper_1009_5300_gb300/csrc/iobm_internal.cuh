@@ -119,8 +119,16 @@ struct StencilArgs {
     int tiles_x, tiles_y;  // lateral tiling
     long long npts;
     int* err;              // set to a nonzero code when a bounded wait gives up (or nullptr)
-    int variant;           // 0: the fastest kernel for the shape, 1: the register-pipelined row kernel
+    int variant;           // 0: the fastest kernel for the shape, 1: the register-pipelined row
+                           // kernel, 2 (FP64 data): double-float arithmetic
+    float2 dfx[kMaxNf + 1];  // variant 2: cx[n], cy[n], cz[n] as FP32 pairs (hi, lo)
+    float2 dfy[kMaxNf + 1];
+    float2 dfz[kMaxNf + 1];
 };
+
+// the double-float row kernel (FP64 data, operator apply without fused p or dots)
+bool stencil_df_supported(int nx, int nf);
+cudaError_t launch_stencil_df(const StencilArgs<double>& a, int nrhs, cudaStream_t s);
 
 // codes written to StencilArgs::err
 enum { ERR_STAGE_TIMEOUT = 1 };

@@ -664,6 +664,10 @@ static cudaError_t launch_tma_nf(const StencilArgs<float>& a, dim3 grid, cudaStr
 
 template <typename T>
 cudaError_t launch_stencil(const StencilArgs<T>& a0, int nrhs, cudaStream_t s) {
+    if constexpr (sizeof(T) == 8) {
+        if (a0.variant == 2 && !a0.fused_p && !a0.dot_mode && stencil_df_supported(a0.nx, a0.nf))
+            return launch_stencil_df(a0, nrhs, s);
+    }
     if (use_rows(a0.nx, a0.nf)) {
         StencilArgs<T> a = a0;
         if (a.zchunk <= 0) a.zchunk = 32;

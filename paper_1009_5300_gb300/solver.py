@@ -274,10 +274,16 @@ class IOBMSolver:
         return ms.value, n.value
 
     # ---- operator access -------------------------------------------------
-    def apply(self, E: float, x: torch.Tensor) -> torch.Tensor:
-        """y = (E - H_T - H~) x for x [nrhs][nz][ny][nx] complex64/complex128 on the device."""
+    def apply(self, E: float, x: torch.Tensor, double_float: bool = False) -> torch.Tensor:
+        """y = (E - H_T - H~) x for x [nrhs][nz][ny][nx] complex64/complex128 on the device.
+        double_float: complex128 data with the stencil in double-float arithmetic (the
+        arithmetic of the mixed solver's FP64 residual)."""
         x = x.contiguous()
         elem = _lib.IOBM_ELEM_C64 if x.dtype == torch.complex128 else _lib.IOBM_ELEM_C32
+        if double_float:
+            if x.dtype != torch.complex128:
+                raise TypeError("double_float needs complex128 data")
+            elem = _lib.IOBM_ELEM_C64_DF
         if x.dtype not in (torch.complex64, torch.complex128):
             raise TypeError("x must be complex64 or complex128")
         nrhs = x.numel() // int(np.prod(self.shape))

@@ -56,6 +56,29 @@ def test_apply_matches_oracle(nx, ny, nz, nf, kb):
     y32 = sol.apply(E, xd.to(torch.complex64)).cpu().numpy()
     err32 = np.max(np.abs(y32 - ref)) / np.max(np.abs(ref))
     assert err32 < 2e-5, err32
+    # double-float stencil on FP64 data (the mixed solver's FP64 residual)
+    ydf = sol.apply(E, xd, double_float=True).cpu().numpy()
+    errdf = np.max(np.abs(ydf - ref)) / np.max(np.abs(ref))
+    assert errdf < 1e-12, errdf
+    sol.close()
+
+
+@pytest.mark.parametrize("scale", [1e-6, 1.0, 1e6])
+def test_double_float_apply_on_smooth_fields(scale):
+    # smooth fields make the FD taps cancel against the diagonal; the double-float
+    # arithmetic must still match FP64 to 1e-12 of the largest term, at any magnitude
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = make(48, 48, 40, 4, True)
+    E = jn.e_fermi + 0.013
+    sol = IOBMSolver.from_junction(jn, precision="mixed")
+    z, y, x = np.meshgrid(np.arange(jn.nz), np.arange(jn.ny), np.arange(jn.nx), indexing="ij")
+    f = scale * (np.cos(2 * np.pi * x / jn.nx) * np.exp(1j * 2 * np.pi * y / jn.ny)
+                 * np.sin(0.05 * z + 0.3) + 0.5)
+    xd = torch.from_numpy(np.ascontiguousarray(f[None].astype(np.complex128))).cuda()
+    y64 = sol.apply(E, xd).cpu().numpy()
+    ydf = sol.apply(E, xd, double_float=True).cpu().numpy()
+    big = scale * 0.5 * 3 * 1.4 / jn.hx ** 2          # size of the diagonal term
+    assert np.max(np.abs(ydf - y64)) < 1e-12 * big
     sol.close()
 
 
