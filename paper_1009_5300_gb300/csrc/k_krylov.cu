@@ -21,20 +21,34 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
+// Sum of the per-CTA partial slots of one RHS by one warp: lane l takes slots
+// l, l + 32, ..., then a fixed xor-shuffle tree; the order depends only on the
+// slot count, so an RHS gets the same sums alone and in any batch.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __global__ void k_beta(RhsState* st, const double2* rho_part, const double* rr_part, int nslots,
                        int stride, int nrhs, int max_iter, double tol2, double delta2, int mixed) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrhs) return;
-    RhsState S = st[i];
-    if (S.status != ST_ACTIVE) return;
-    double2 rho = make_double2(0.0, 0.0);
-    double rr = 0.0;
-    for (int j = 0; j < nslots; ++j) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= nrhs) return;   // whole warps
+    if (st[i].status != ST_ACTIVE) return;
+    double rx = 0.0, ry = 0.0, rr = 0.0;
+    for (int j = lane; j < nslots; j += 32) {
         const double2 v = rho_part[(long long)i * stride + j];
-        rho.x += v.x;
-        rho.y += v.y;
+        rx += v.x;
+        ry += v.y;
         rr += rr_part[(long long)i * stride + j];
     }
+    rx = warp_sum(rx);
+    ry = warp_sum(ry);
+    rr = warp_sum(rr);
+    if (lane != 0) return;
+    RhsState S = st[i];
+    const double2 rho = make_double2(rx, ry);
     S.rr = rr;
     if (!isfinite(rr)) {
         S.status = ST_BREAKDOWN;
@@ -54,16 +68,21 @@ __global__ void k_beta(RhsState* st, const double2* rho_part, const double* rr_p
 }
 
 __global__ void k_alpha(RhsState* st, const double2* mu_part, int nslots, int stride, int nrhs) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= nrhs) return;
-    RhsState S = st[i];
-    if (S.status != ST_ACTIVE) return;
-    double2 mu = make_double2(0.0, 0.0);
-    for (int j = 0; j < nslots; ++j) {
+    if (st[i].status != ST_ACTIVE) return;
+    double mx = 0.0, my = 0.0;
+    for (int j = lane; j < nslots; j += 32) {
         const double2 v = mu_part[(long long)i * stride + j];
-        mu.x += v.x;
-        mu.y += v.y;
+        mx += v.x;
+        my += v.y;
     }
+    mx = warp_sum(mx);
+    my = warp_sum(my);
+    if (lane != 0) return;
+    RhsState S = st[i];
+    const double2 mu = make_double2(mx, my);
     if (!finite2(mu) || (mu.x == 0.0 && mu.y == 0.0)) {
         S.status = ST_BREAKDOWN;
     } else {
@@ -86,13 +105,13 @@ __global__ void k_restart_scalars(RhsState* st, const double2* rho_part, const d
 cudaError_t launch_beta(RhsState* st, const double2* rho_part, const double* rr_part, int nslots,
                         int slot_stride, int nrhs, int max_iter, double tol2, double delta2,
                         int mixed, cudaStream_t s) {
-    k_beta<<<(nrhs + 127) / 128, 128, 0, s>>>(st, rho_part, rr_part, nslots, slot_stride, nrhs,
-                                              max_iter, tol2, delta2, mixed);
+    k_beta<<<(nrhs + 3) / 4, 128, 0, s>>>(st, rho_part, rr_part, nslots, slot_stride, nrhs,
+                                          max_iter, tol2, delta2, mixed);   // a warp per RHS
     return cudaGetLastError();
 }
 cudaError_t launch_alpha(RhsState* st, const double2* mu_part, int nslots, int slot_stride,
                          int nrhs, cudaStream_t s) {
-    k_alpha<<<(nrhs + 127) / 128, 128, 0, s>>>(st, mu_part, nslots, slot_stride, nrhs);
+    k_alpha<<<(nrhs + 3) / 4, 128, 0, s>>>(st, mu_part, nslots, slot_stride, nrhs);
     return cudaGetLastError();
 }
 cudaError_t launch_restart_scalars(RhsState* st, const double2* rho_part, const double* rr_part,
@@ -194,6 +213,11 @@ __device__ __forceinline__ double2 source_value(const RhsDesc& D, const double2*
     return cmul(D.coef[d], ph);
 }
 
+// r = b - y (or r = b when y is null) and per-CTA partials of ||r||^2.  CTAs
+// take whole planes; the source b is nonzero only on the N_f end planes of the
+// incident side, so interior planes give r = -y without FP64 arithmetic.  The
+// squares are summed per thread in FP32 (an estimate of the norm needs no more)
+// and across the CTA in FP64.
 template <typename T>
 __global__ void k_residual(const double2* __restrict__ y, double2* __restrict__ r64,
                            typename Cplx<T>::type* __restrict__ rT, const RhsDesc* desc,
@@ -203,24 +227,35 @@ __global__ void k_residual(const double2* __restrict__ y, double2* __restrict__ 
     __shared__ double red[3 * 8];
     const int rhs = blockIdx.y;
     if (st && !((1 << st[rhs].status) & mask)) return;
-    const long long plane = (long long)nx * ny;
-    const long long npts = plane * nz;
-    const long long base = (long long)rhs * npts;
+    const int plane = nx * ny;
+    const long long base = (long long)rhs * plane * nz;
     const RhsDesc D = desc[rhs];
-    double acc = 0.0, z1 = 0.0, z2 = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i / plane);
-        const int lat = (int)(i - (long long)k * plane);
-        const int iy = lat / nx, ix = lat - iy * nx;
-        double2 v = source_value(D, phx, phy, nx, ny, nz, nf, k, ix, iy);
-        if (y) v = csub(v, y[base + i]);
-        if (r64) r64[base + i] = v;
-        if (rT) rT[base + i] = from_d2<C>(v);
-        acc += v.x * v.x + v.y * v.y;
+    float acc = 0.f;
+    for (int k = blockIdx.x; k < nz; k += gridDim.x) {
+        const bool src = (D.side == 0) ? (k < nf) : (k >= nz - nf);
+        const long long off = base + (long long)k * plane;
+        for (int lat = threadIdx.x; lat < plane; lat += blockDim.x) {
+            double2 v;
+            if (src) {
+                const int iy = lat / nx, ix = lat - iy * nx;
+                v = source_value(D, phx, phy, nx, ny, nz, nf, k, ix, iy);
+                if (y) v = csub(v, y[off + lat]);
+            } else if (y) {
+                const double2 w = y[off + lat];
+                v = make_double2(-w.x, -w.y);
+            } else {
+                v = make_double2(0.0, 0.0);
+            }
+            if (r64) r64[off + lat] = v;
+            const C c = from_d2<C>(v);
+            if (rT) rT[off + lat] = c;
+            const float fx = (float)c.x, fy = (float)c.y;
+            acc = fmaf(fx, fx, fmaf(fy, fy, acc));
+        }
     }
-    block_reduce_3(acc, z1, z2, red);
-    if (threadIdx.x == 0) rr_part[(long long)rhs * stride + blockIdx.x] = acc;
+    double a0 = acc, z1 = 0.0, z2 = 0.0;
+    block_reduce_3(a0, z1, z2, red);
+    if (threadIdx.x == 0) rr_part[(long long)rhs * stride + blockIdx.x] = a0;
 }
 
 constexpr int kResidualBlocks = 64;

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_plane_fft_fwd(const PrecondArgs<T> a) {
 // multipliers over planes 0 .. nz-nf-1, a dense nf x nf solve on the last nf
 // planes, backward substitution with the constant band rows.  In place on the
 // spectrum; one thread per (RHS, mode), loads issued kZPrefetch planes ahead.
-constexpr int kZPrefetch = 4;
+constexpr int kZPrefetch = 8;
 constexpr int kZThreads = 128;
 
 template <typename T, int NF>
@@ -153,13 +153,11 @@ __global__ void __launch_bounds__(kZThreads) k_zsolve(const PrecondArgs<T> a) {
     if (mode >= nxy) return;
     const int e = a.rhs_energy ? a.rhs_energy[rhs] : 0;
     const C* __restrict__ pc = a.pc + ((size_t)e * nxy + mode) * kPcStrideDev;
-    C l[NF + 1], u[NF + 1], S2[NF * NF];
+    C l[NF + 1], u[NF + 1];
 #pragma unroll
     for (int j = 1; j <= NF; ++j) l[j] = pc[j - 1];
 #pragma unroll
     for (int j = 0; j <= NF; ++j) u[j] = pc[NF + j];
-#pragma unroll
-    for (int i = 0; i < NF * NF; ++i) S2[i] = pc[2 * NF + 1 + i];
     const C uinv = cdivc(make_one<C>(), u[0]);
     const int nz = a.nz, m = nz - NF;
     C* __restrict__ s = a.spec + (long long)rhs * a.npts + mode;
@@ -208,8 +206,9 @@ __global__ void __launch_bounds__(kZThreads) k_zsolve(const PrecondArgs<T> a) {
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
         C v = czero<C>();
+        // the end block's inverse is read here, where it is used
 #pragma unroll
-        for (int j = 0; j < NF; ++j) v = cfma(S2[i * NF + j], g[j], v);
+        for (int j = 0; j < NF; ++j) v = cfma(pc[2 * NF + 1 + i * NF + j], g[j], v);
         s[(long long)(m + i) * nxy] = v;
         nxt[i] = v;
     }
