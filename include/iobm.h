@@ -162,6 +162,16 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
 
 void iobm_destroy(iobm_handle* h);
 
+/* Create n junction handles in one call, as iobm_create for each j with
+ * grids[j], V[j], projs[j] (projs may be NULL: no projectors anywhere; an entry
+ * with nproj = 0 means none for that junction), rs[j] and the shared options
+ * and stream; out[0..n) receives the handles (destroy each with iobm_destroy).
+ * On an error no handle is left: those created are destroyed, out[] is NULL,
+ * and the return value is the failing junction's status. */
+int iobm_create_batch(int n, const iobm_grid* grids, const double* const* V,
+                      const iobm_projectors* projs, const double* rs, const iobm_options* opts,
+                      void* cuda_stream, iobm_handle** out);
+
 const char* iobm_status_string(int status);
 const char* iobm_last_error(const iobm_handle* h);
 

@@ -73,6 +73,9 @@ SIGNATURES = {
     "iobm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "iobm_num_rhs": (C.c_int, [C.c_void_p]),
     "iobm_max_open": (C.c_int, [C.c_void_p]),
+    "iobm_create_batch": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p,
+                                    C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
+                                    C.POINTER(C.c_void_p)]),
     "iobm_solve_batch": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_int), C.c_int]),
     "iobm_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),

@@ -1359,6 +1359,26 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     return IOBM_OK;
 }
 
+int iobm_create_batch(int n, const iobm_grid* grids, const double* const* V,
+                      const iobm_projectors* projs, const double* rs, const iobm_options* opts,
+                      void* cuda_stream, iobm_handle** out) {
+    if (n < 1 || !grids || !V || !rs || !out) return IOBM_E_ARG;
+    for (int j = 0; j < n; ++j) out[j] = nullptr;
+    for (int j = 0; j < n; ++j) {
+        const iobm_projectors* pj = (projs && projs[j].nproj > 0) ? &projs[j] : nullptr;
+        const int rc = iobm_create(&grids[j], V[j], pj, rs[j], opts, cuda_stream, &out[j]);
+        if (rc) {
+            for (int i = 0; i < j; ++i) {
+                iobm_destroy(out[i]);
+                out[i] = nullptr;
+            }
+            out[j] = nullptr;
+            return rc;
+        }
+    }
+    return IOBM_OK;
+}
+
 void iobm_destroy(iobm_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);

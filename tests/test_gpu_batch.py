@@ -126,3 +126,30 @@ def test_batch_rejects_duplicate_handles():
     with pytest.raises(IOBMError):
         solve_batch([s, s], [energies_of(jn), energies_of(jn)])
     s.close()
+
+
+def test_create_batch_abi():
+    # iobm_create_batch makes independent handles; an invalid junction leaves none behind
+    import ctypes as C
+    from paper_1009_5300_gb300 import _lib
+    lib = _lib.load()
+    jns = small_junctions()[1:]
+    n = len(jns)
+    grids = (_lib.Grid * n)(*[_lib.Grid(j.nx, j.ny, j.nz, j.hx, j.hy, j.hz, j.nf) for j in jns])
+    Vs = [np.ascontiguousarray(j.V, np.float64) for j in jns]
+    vptr = (C.c_void_p * n)(*[v.ctypes.data for v in Vs])
+    rs = (C.c_double * n)(*[j.rs for j in jns])
+    opts = _lib.Options()
+    lib.iobm_default_options(C.byref(opts))
+    out = (C.c_void_p * n)()
+    assert lib.iobm_create_batch(n, grids, vptr, None, rs, C.byref(opts), None, out) == 0
+    for j, h in zip(jns, out):
+        assert h
+        k = C.c_int(0)
+        assert lib.iobm_open_channels(h, float(j.e_fermi), C.byref(k), 0, None, None) == 0
+        assert k.value >= 1
+        lib.iobm_destroy(h)
+    grids[1].nz = 2            # too few planes for N_f: rejected before any allocation
+    out2 = (C.c_void_p * n)()
+    assert lib.iobm_create_batch(n, grids, vptr, None, rs, C.byref(opts), None, out2) == _lib.IOBM_E_ARG
+    assert not out2[0] and not out2[1]
