@@ -99,6 +99,10 @@ struct iobm_handle {
     int stencil_variant = 0;             // StencilArgs::variant (autotuned)
     DevBuf batch_ctr;                    // chunk counter of this junction in a batched solve
     DevBuf esc_ws, esc_descs, esc_rhs_energy;   // FP64 continuation of stalled mixed RHS
+    cudaGraphExec_t chunk_exec = nullptr;        // the last solve's chunk graph, updated in place
+    void* pin = nullptr;                         // pinned staging buffer for table uploads
+    size_t pin_bytes = 0;
+    bool pc64_valid = false;                     // FP64 preconditioner tables of this solve uploaded
 
     // workspace
     void* ws = nullptr;
@@ -690,7 +694,25 @@ int run_solver(iobm_handle* h, int nrhs, bool warm = false) {
         return rc;
     }
     CK(cudaStreamEndCapture(h->stream, &graph));
-    CK(cudaGraphInstantiate(&exec, graph, 0));
+    // the chunk of the previous solve usually has the same shape: update its
+    // executable graph in place (new kernel arguments) instead of instantiating anew
+    if (h->chunk_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(h->chunk_exec, graph, &info) == cudaSuccess) {
+            exec = h->chunk_exec;
+        } else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(h->chunk_exec);
+        }
+        h->chunk_exec = nullptr;
+    }
+    if (!exec) {
+        const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return cuda_fail(h, e, "cudaGraphInstantiate");
+        }
+    }
     cudaGraphDestroy(graph);
 
     h->hstate.resize(nrhs);
@@ -726,7 +748,7 @@ int run_solver(iobm_handle* h, int nrhs, bool warm = false) {
             live += (S.status == ST_ACTIVE || S.status == ST_RESTART || S.status == ST_PENDING);
         if (!live) break;
     }
-    cudaGraphExecDestroy(exec);
+    h->chunk_exec = exec;   // kept for the next solve
     return solver_epilogue<T>(h, nrhs, launches);
 }
 
@@ -743,7 +765,6 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
     h->users.clear();
     h->side = side;
     const int nf = h->nf;
-    std::vector<std::complex<double>> sig_all, pc_all;
     auto add_desc = [&](int e, const ModeTables& mt, int q, int side_, int profile,
                         const std::complex<double>* coef, double scale) {
         RhsDesc d{};
@@ -775,10 +796,6 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
     h->memo_tables.clear();
     for (int e = 0; e < nE; ++e) {
         ModeTables& mt = tables[e];
-        if (upload_tables) {
-            sig_all.insert(sig_all.end(), mt.sigma.begin(), mt.sigma.end());
-            pc_all.insert(pc_all.end(), mt.pc.begin(), mt.pc.end());
-        }
         std::vector<int> list;
         if (kind == 1 || !channels) {
             for (int c = 0; c < mt.nopen; ++c) list.push_back(c);
@@ -833,17 +850,55 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
         h->energies.clear();
         return IOBM_OK;
     }
-    // device tables
-    std::vector<double2> s64(sig_all.size()), p64(pc_all.size());
-    std::vector<float2> s32(sig_all.size()), p32(pc_all.size());
-    for (size_t i = 0; i < sig_all.size(); ++i) {
-        s64[i] = make_double2(sig_all[i].real(), sig_all[i].imag());
-        s32[i] = make_float2((float)sig_all[i].real(), (float)sig_all[i].imag());
+    // device tables, staged through pinned memory: Sigma~ in FP32 and FP64, the
+    // free-propagator factors in FP32 (FP64 only for an FP64 solve; the FP64
+    // continuation of a mixed solve uploads them when it needs them)
+    size_t nsig = 0, npc = 0;
+    for (const ModeTables& mt : h->energies) {
+        nsig += mt.sigma.size();
+        npc += mt.pc.size();
     }
-    for (size_t i = 0; i < pc_all.size(); ++i) {
-        p64[i] = make_double2(pc_all[i].real(), pc_all[i].imag());
-        p32[i] = make_float2((float)pc_all[i].real(), (float)pc_all[i].imag());
+    const bool pc64_now = h->opt.precision == IOBM_FP64;
+    const size_t pin_need = nsig * (sizeof(double2) + sizeof(float2)) +
+                            npc * (sizeof(float2) + (pc64_now ? sizeof(double2) : 0)) + 64;
+    if (h->pin_bytes < pin_need) {
+        if (h->pin) cudaFreeHost(h->pin);
+        h->pin = nullptr;
+        h->pin_bytes = 0;
+        CK(cudaMallocHost(&h->pin, pin_need));
+        h->pin_bytes = pin_need;
     }
+    CK(cudaStreamSynchronize(h->stream));   // the previous uploads from the staging buffer are done
+    double2* s64 = reinterpret_cast<double2*>(h->pin);
+    float2* s32 = reinterpret_cast<float2*>(s64 + nsig);
+    float2* p32 = s32 + nsig;
+    double2* p64 = reinterpret_cast<double2*>(p32 + npc);
+    {
+        size_t is = 0, ip = 0;
+        for (const ModeTables& mt : h->energies) {
+            for (const auto& v : mt.sigma) {
+                s64[is] = make_double2(v.real(), v.imag());
+                s32[is] = make_float2((float)v.real(), (float)v.imag());
+                ++is;
+            }
+            for (const auto& v : mt.pc) {
+                p32[ip] = make_float2((float)v.real(), (float)v.imag());
+                if (pc64_now) p64[ip] = make_double2(v.real(), v.imag());
+                ++ip;
+            }
+        }
+    }
+    auto put = [&](DevBuf& b, const void* src, size_t bytes) -> cudaError_t {
+        cudaError_t e = b.ensure(std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess && bytes)
+            e = cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, h->stream);
+        return e;
+    };
+    CK(put(h->sig64, s64, sizeof(double2) * nsig));
+    CK(put(h->sig32, s32, sizeof(float2) * nsig));
+    CK(put(h->pc32, p32, sizeof(float2) * npc));
+    if (pc64_now) CK(put(h->pc64, p64, sizeof(double2) * npc));
+    h->pc64_valid = pc64_now;
     std::vector<double> ed(nE);
     std::vector<int> optr(nE + 1, 0);
     std::vector<int2> obins;
@@ -855,10 +910,6 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
         h->max_open = std::max(h->max_open, mt.nopen);
         for (int c = 0; c < mt.nopen; ++c) obins.push_back(make_int2(mt.open_kx[c], mt.open_ky[c]));
     }
-    CK(upload(h->sig64, s64, h->stream));
-    CK(upload(h->sig32, s32, h->stream));
-    CK(upload(h->pc64, p64, h->stream));
-    CK(upload(h->pc32, p32, h->stream));
     CK(upload(h->ediag, ed, h->stream));
     CK(upload(h->rhs_energy, h->hrhs_energy, h->stream));
     CK(upload(h->descs, h->hdesc, h->stream));
@@ -880,6 +931,13 @@ int escalate_fp64(iobm_handle* h) {
     }
     if (idx.empty()) return IOBM_OK;
     const int m = (int)idx.size();
+    if (!h->pc64_valid) {   // FP64 free-propagator factors for the FP64 iterations
+        std::vector<double2> p64;
+        for (const ModeTables& mt : h->energies)
+            for (const auto& v : mt.pc) p64.push_back(make_double2(v.real(), v.imag()));
+        CK(upload(h->pc64, p64, h->stream));
+        h->pc64_valid = true;
+    }
     std::vector<RhsDesc> sd(m);
     std::vector<int> se(m);
     for (int k = 0; k < m; ++k) {
@@ -1382,6 +1440,8 @@ int iobm_create_batch(int n, const iobm_grid* grids, const double* const* V,
 void iobm_destroy(iobm_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->chunk_exec) cudaGraphExecDestroy(h->chunk_exec);
+    if (h->pin) cudaFreeHost(h->pin);
     DevBuf* bufs[] = {&h->V32, &h->V64, &h->twx32, &h->twy32, &h->twx64, &h->twy64, &h->phx,
                       &h->phy, &h->pptr, &h->pidx, &h->pval32, &h->pval64, &h->pcoup, &h->uidx,
                       &h->uptr, &h->uproj, &h->uval32, &h->uval64, &h->sig32, &h->sig64, &h->pc32,
