@@ -31,9 +31,11 @@ struct CtPlan {
     }
 };
 
+// one R-point butterfly j of a pass: reads src[(j + r N/R) ss], returns the R
+// outputs and the index of the first (output r goes to base + r NS)
 template <typename C, int N, int NS, int R>
-__device__ __forceinline__ void ct_bfly(const C* src, int ss, C* dst, int ds, int j,
-                                        const C* tw, bool inv) {
+__device__ __forceinline__ int ct_bfly_out(const C* src, int ss, int j, const C* tw, bool inv,
+                                           C (&o)[R]) {
     constexpr int NR = N / R;
     constexpr int TS = N / (NS * R);
     const int k = j % NS;
@@ -48,7 +50,6 @@ __device__ __forceinline__ void ct_bfly(const C* src, int ss, C* dst, int ds, in
         }
         v[r] = u;
     }
-    C o[R];
     if constexpr (R == 2) {
         o[0] = cadd(v[0], v[1]);
         o[1] = csub(v[0], v[1]);
@@ -74,7 +75,14 @@ __device__ __forceinline__ void ct_bfly(const C* src, int ss, C* dst, int ds, in
             o[aa] = acc;
         }
     }
-    const int base = (j / NS) * NS * R + k;
+    return (j / NS) * NS * R + k;
+}
+
+template <typename C, int N, int NS, int R>
+__device__ __forceinline__ void ct_bfly(const C* src, int ss, C* dst, int ds, int j,
+                                        const C* tw, bool inv) {
+    C o[R];
+    const int base = ct_bfly_out<C, N, NS, R>(src, ss, j, tw, inv, o);
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[(base + r * NS) * ds] = o[r];
 }
@@ -85,13 +93,67 @@ __device__ __forceinline__ void ct_passes(C*& cur, C*& oth, int ls, int es, cons
     if constexpr (P < CtPlan<N>::npass) {
         constexpr int R = CtPlan<N>::radix(P);
         constexpr int PER = N / R;
+        // line index fastest: a row pass then touches elements line * (N + 1) + c,
+        // an odd stride that spreads 16 consecutive lines over 16 different 8-byte
+        // bank pairs, and a column pass touches consecutive elements
         for (int t = threadIdx.x; t < N * PER; t += blockDim.x) {
-            const int line = t / PER, j = t - line * PER;
+            const int line = t % N, j = t / N;
             ct_bfly<C, N, NS, R>(cur + line * ls, es, oth + line * ls, es, j, tw, inv);
         }
         __syncthreads();
         C* s = cur; cur = oth; oth = s;
         ct_passes<C, N, P + 1, NS * R>(cur, oth, ls, es, tw, inv);
+    }
+}
+
+// Output positions of the last column pass for a CTA of NT threads: thread tid
+// handles butterflies t = tid + k NT (k < K) of column t % N and index
+// j = t / N < N / R, whose R outputs are rows j + r N / R; output "slot" k R + r.
+template <int N, int NT>
+struct CtLastPass {
+    static constexpr int R = CtPlan<N>::radix(CtPlan<N>::npass - 1);
+    static constexpr int NS = N / R;                  // sub-transform size before the pass
+    static constexpr int K = (N * NS + NT - 1) / NT;  // butterflies per thread
+    static constexpr int SLOTS = K * R;
+    __device__ static bool pos(int tid, int k, int r, int& row, int& col) {
+        const int t = tid + k * NT;
+        if (t >= N * NS) return false;
+        col = t % N;
+        row = t / N + r * NS;
+        return true;
+    }
+};
+
+// Column passes of a 2D transform whose last pass hands every output to
+// store(row, col, value, slot) (slot as in CtLastPass, a compile-time constant
+// after unrolling) instead of writing it back to shared memory; consecutive
+// threads store consecutive columns of a row.  The CTA has NT threads.
+template <typename C, int N, int P, int NS, int NT, typename Store>
+__device__ __forceinline__ void ct_col_passes_store(C*& cur, C*& oth, int pitch, const C* tw,
+                                                    bool inv, Store& store) {
+    constexpr int R = CtPlan<N>::radix(P);
+    constexpr int PER = N / R;
+    if constexpr (P + 1 < CtPlan<N>::npass) {
+        for (int t = threadIdx.x; t < N * PER; t += NT) {
+            const int line = t % N, j = t / N;
+            ct_bfly<C, N, NS, R>(cur + line, pitch, oth + line, pitch, j, tw, inv);
+        }
+        __syncthreads();
+        C* s = cur; cur = oth; oth = s;
+        ct_col_passes_store<C, N, P + 1, NS * R, NT>(cur, oth, pitch, tw, inv, store);
+    } else {
+        constexpr int K = (N * PER + NT - 1) / NT;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int t = threadIdx.x + k * NT;
+            if (t < N * PER) {
+                const int line = t % N, j = t / N;
+                C o[R];
+                const int base = ct_bfly_out<C, N, NS, R>(cur + line, pitch, j, tw, inv, o);
+#pragma unroll
+                for (int r = 0; r < R; ++r) store(base + r * NS, line, o[r], k * R + r);
+            }
+        }
     }
 }
 
@@ -109,6 +171,17 @@ __device__ __forceinline__ C* ct_fft2(C* a, C* b, const C* tw, bool inv) {
     ct_passes<C, N, 0, 1>(cur, oth, P, 1, tw, inv);   // rows
     ct_passes<C, N, 0, 1>(cur, oth, 1, P, tw, inv);   // columns
     return cur;
+}
+
+// The same transform with the outputs delivered to store(row, col, value) by the
+// last column pass (no trailing shared-memory round trip and barrier).
+template <typename C, int N, int NT, typename Store>
+__device__ __forceinline__ void ct_fft2_store(C* a, C* b, const C* tw, bool inv, Store store) {
+    constexpr int P = CtPitch<N>::P;
+    C* cur = a;
+    C* oth = b;
+    ct_passes<C, N, 0, 1>(cur, oth, P, 1, tw, inv);   // rows
+    ct_col_passes_store<C, N, 0, 1, NT>(cur, oth, P, tw, inv, store);
 }
 
 }  // namespace iobm

@@ -357,8 +357,9 @@ __global__ void __launch_bounds__(256, 4) k_update_fft_ct(const PrecondArgs<T> a
         for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[(i / N) * PT + (i % N)] = a.r[off + i];
     }
     __syncthreads();
-    C* res = ct_fft2<C, N>(A, B, tw, false);
-    for (int i = threadIdx.x; i < NXY; i += blockDim.x) a.spec[off + i] = res[(i / N) * PT + (i % N)];
+    C* __restrict__ spec = a.spec + off;
+    ct_fft2_store<C, N, 256>(A, B, tw, false,
+                             [&](int row, int col, C v, int) { spec[row * N + col] = v; });
 }
 
 template <typename T, int N>
@@ -376,32 +377,32 @@ __global__ void __launch_bounds__(256, 4) k_ifft_dots_ct(const PrecondArgs<T> a)
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.twx[i];
     const long long off = (long long)rhs * a.npts + (long long)plane * NXY;
     for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[(i / N) * PT + (i % N)] = a.spec[off + i];
-    // r is needed only after the transform: load it now so the loads overlap the FFT
-    constexpr int PER = (NXY + 255) / 256;
-    C rv[PER];
-    if (a.dot_part) {
+    // r at the positions this thread's last column pass produces, loaded now so
+    // the loads overlap the transform
+    using L = CtLastPass<N, 256>;
+    C* __restrict__ zo = a.z + off;
+    const C* __restrict__ rin = a.r + off;
+    const bool dots = a.dot_part != nullptr;
+    C rv[L::SLOTS];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int i = threadIdx.x + j * 256;
-            rv[j] = (i < NXY) ? a.r[off + i] : czero<C>();
+    for (int k = 0; k < L::K; ++k)
+#pragma unroll
+        for (int r = 0; r < L::R; ++r) {
+            int row, col;
+            rv[k * L::R + r] = (dots && L::pos(threadIdx.x, k, r, row, col)) ? rin[row * N + col] : czero<C>();
         }
-    }
     __syncthreads();
-    C* res = ct_fft2<C, N>(A, B, tw, true);
+    // the last column pass stores z and forms r^T z and |r|^2 on the way
     T dre = 0, dim = 0, nrm = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int i = threadIdx.x + j * 256;
-        if (i >= NXY) continue;
-        const C z = res[(i / N) * PT + (i % N)];
-        a.z[off + i] = z;
-        if (a.dot_part) {
-            const C r = rv[j];
+    ct_fft2_store<C, N, 256>(A, B, tw, true, [&](int row, int col, C z, int slot) {
+        zo[row * N + col] = z;
+        if (dots) {
+            const C r = rv[slot];
             dre += r.x * z.x - r.y * z.y;
             dim += r.x * z.y + r.y * z.x;
             nrm += r.x * r.x + r.y * r.y;
         }
-    }
+    });
     if (a.dot_part) {
         double d0 = dre, d1 = dim, d2 = nrm;
         block_reduce_3(d0, d1, d2, red);
