@@ -243,6 +243,16 @@ int iobm_autotune(iobm_handle* h, int nrhs, int* zchunk, int* variant);
  * the fastest kernel for the shape, 1 = the register-pipelined row kernel. */
 int iobm_set_tiling(iobm_handle* h, int zchunk, int variant);
 
+/* Eigenchannel transmissions of energy index e of the last solve (Sec. IV,
+ * Table II: the eigenvalues of T^dagger T, T the transmission matrix): with
+ * t~_oc = t_oc sqrt(v_o / v_c) the flux-normalised amplitudes (out o, in c) of
+ * the FP64 solutions, tau[0..n) are the eigenvalues of t~^dagger t~ in
+ * descending order; they lie in [0, 1] and sum to G of that energy.  Needs
+ * every open incident channel of the energy in the last solve (IOBM_E_STATE
+ * otherwise).  *n_out = number of open channels; tau may be NULL to query it,
+ * else it holds max_out >= n values.  Host computation (cyclic Jacobi). */
+int iobm_eigenchannels(iobm_handle* h, int e, double* tau, int max_out, int* n_out);
+
 /* Number of incident channels (user-visible RHS) of the last solve. */
 int iobm_num_rhs(const iobm_handle* h);
 

@@ -18,6 +18,8 @@ Paper passages followed:
 * Landauer-Buttiker (Sec. III): G = G_0 sum_{o,i} T_oi with
   T_oi = |t_oi|^2 v_o / v_i (flux normalisation by the discrete group velocity)
   and R_oi = |r_oi|^2 v_o / v_i.
+* Eigenchannels (Sec. IV, Table II): eigenvalues of T^dagger T for the
+  flux-normalised transmission matrix.
 * dG/dV(r) (not in the paper; follows from Eq. 7 with dA/dV(r) = -e_r e_r^T and
   A = A^T): with A lambda_o = w_o, where w_o is the linear functional that
   returns t_o from a solved wave,
@@ -158,6 +160,18 @@ def solve(jn, E: float, side: str = "L", channels: Optional[Sequence[int]] = Non
 
 def conductance(jn, E: float) -> float:
     return solve(jn, E).G
+
+
+def eigenchannels(sol: Solution) -> np.ndarray:
+    """Eigenchannel transmissions (Sec. IV, Table II: eigenvalues of T^dagger T, T the
+    transmission matrix) of a solve over every open incident channel: with the
+    flux-normalised amplitudes t~_oi = t_oi sqrt(v_o / v_i), the eigenvalues of
+    t~^H t~ in descending order."""
+    if sol.t.shape[1] != sol.n_open:
+        raise ValueError("eigenchannels need every open incident channel")
+    v = sol.vel
+    tt = sol.t * np.sqrt(v[:, None] / v[None, :])
+    return np.sort(np.linalg.eigvalsh(tt.conj().T @ tt))[::-1]
 
 
 def exit_functional(jn, md: ModeData, m_out: int, side: str = "L") -> np.ndarray:

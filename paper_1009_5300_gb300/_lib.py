@@ -73,6 +73,7 @@ SIGNATURES = {
     "iobm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "iobm_num_rhs": (C.c_int, [C.c_void_p]),
     "iobm_max_open": (C.c_int, [C.c_void_p]),
+    "iobm_eigenchannels": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "iobm_create_batch": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p,
                                     C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
                                     C.POINTER(C.c_void_p)]),

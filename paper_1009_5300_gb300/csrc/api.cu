@@ -1533,6 +1533,46 @@ int iobm_solve_batch(int n, iobm_handle* const* handles, const double* const* E,
     return solve_batch(n, handles, E, nE, side);
 }
 
+int iobm_eigenchannels(iobm_handle* h, int e, double* tau, int max_out, int* n_out) {
+    if (!h || !n_out) return IOBM_E_ARG;
+    if (!h->solved) return fail(h, IOBM_E_STATE, "no solve to report on");
+    if (e < 0 || e >= (int)h->energies.size()) return fail(h, IOBM_E_ARG, "energy index out of range");
+    const ModeTables& mt = h->energies[e];
+    const int n = mt.nopen;
+    *n_out = n;
+    if (!tau) return IOBM_OK;
+    if (max_out < n) return fail(h, IOBM_E_ARG, "max_out is smaller than the open-channel count");
+    if (n == 0) return IOBM_OK;
+    // the flux-normalised transmission matrix tt[o][c] = t_oc sqrt(v_o / v_c) needs
+    // every open incident channel of this energy from one side
+    std::vector<int> user_of(n, -1);
+    for (size_t i = 0; i < h->users.size(); ++i)
+        if (h->users[i].energy == e) user_of[h->users[i].chan] = (int)i;
+    for (int c = 0; c < n; ++c)
+        if (user_of[c] < 0) return fail(h, IOBM_E_STATE, "eigenchannels need every open incident channel");
+    std::vector<std::complex<double>> t, r;
+    const int rc = compute_tr(h, t, r);
+    if (rc) return rc;
+    const int mo = std::max(h->max_open, 1);
+    std::vector<std::complex<double>> tt((size_t)n * n);
+    for (int c = 0; c < n; ++c)
+        for (int o = 0; o < n; ++o)
+            tt[(size_t)o * n + c] = t[(size_t)user_of[c] * mo + o] * std::sqrt(mt.vel[o] / mt.vel[c]);
+    // T^dagger T (Hermitian, positive semidefinite)
+    std::vector<std::complex<double>> m((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            std::complex<double> acc = 0.0;
+            for (int o = 0; o < n; ++o) acc += std::conj(tt[(size_t)o * n + i]) * tt[(size_t)o * n + j];
+            m[(size_t)i * n + j] = acc;
+            m[(size_t)j * n + i] = std::conj(acc);
+        }
+    std::vector<double> w;
+    hermitian_eigenvalues(m, n, w);
+    for (int i = 0; i < n; ++i) tau[i] = w[i];
+    return IOBM_OK;
+}
+
 int iobm_num_rhs(const iobm_handle* h) { return h ? (int)h->users.size() : 0; }
 
 int iobm_max_open(const iobm_handle* h) { return (h && h->solved) ? h->max_open : 0; }

@@ -403,6 +403,55 @@ int build_mode_tables_many(int nx, int ny, double hx, double hy, double hz, int 
     return 0;
 }
 
+void hermitian_eigenvalues(const std::vector<std::complex<double>>& m, int n, std::vector<double>& w) {
+    const int N = 2 * n;
+    std::vector<double> a((size_t)N * N, 0.0);
+    auto at = [&](int i, int j) -> double& { return a[(size_t)i * N + j]; };
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            const std::complex<double> v = (i == j) ? std::complex<double>(m[(size_t)i * n + i].real(), 0.0)
+                                                    : m[(size_t)i * n + j];
+            // [[X, -Y], [Y, X]] with m = X + iY, X symmetric, Y antisymmetric
+            at(i, j) = at(j, i) = v.real();
+            at(n + i, n + j) = at(n + j, n + i) = v.real();
+            at(n + i, j) = v.imag();
+            at(j, n + i) = v.imag();
+            at(i, n + j) = -v.imag();
+            at(n + j, i) = -v.imag();
+        }
+    double scale = 0.0;
+    for (double v : a) scale += v * v;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j) off += at(i, j) * at(i, j);
+        if (off <= 1e-30 * scale || off == 0.0) break;
+        for (int p = 0; p < N; ++p)
+            for (int q = p + 1; q < N; ++q) {
+                const double apq = at(p, q);
+                if (apq == 0.0) continue;
+                const double theta = (at(q, q) - at(p, p)) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < N; ++k) {   // rotate columns p, q
+                    const double akp = at(k, p), akq = at(k, q);
+                    at(k, p) = c * akp - s * akq;
+                    at(k, q) = s * akp + c * akq;
+                }
+                for (int k = 0; k < N; ++k) {   // and rows p, q
+                    const double apk = at(p, k), aqk = at(q, k);
+                    at(p, k) = c * apk - s * aqk;
+                    at(q, k) = s * apk + c * aqk;
+                }
+            }
+    }
+    std::vector<double> d(N);
+    for (int i = 0; i < N; ++i) d[i] = at(i, i);
+    std::sort(d.begin(), d.end(), [](double x, double y) { return x > y; });
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = 0.5 * (d[2 * i] + d[2 * i + 1]);   // each value appears twice
+}
+
 bool fft_plan(int n, std::vector<int>& radices) {
     radices.clear();
     if (n < 1) return false;

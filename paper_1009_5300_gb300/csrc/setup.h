@@ -57,6 +57,12 @@ struct ProjTables {
     std::vector<double> uval;
 };
 
+// Eigenvalues (descending) of the n x n complex Hermitian matrix m (row-major,
+// only the upper triangle is read): cyclic Jacobi rotations on its real
+// symmetric 2n x 2n embedding [[Re m, -Im m], [Im m, Re m]], whose spectrum is
+// that of m with every eigenvalue twice.
+void hermitian_eigenvalues(const std::vector<std::complex<double>>& m, int n, std::vector<double>& w);
+
 // Validates and converts the CSR projectors.  Returns 0, 1 (IOBM_E_ARG) or
 // 3 (IOBM_E_PROJ_BOUNDARY).
 int build_projectors(int nproj, const int64_t* row_ptr, const int32_t* idx, const double* val,

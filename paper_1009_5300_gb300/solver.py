@@ -238,6 +238,15 @@ class IOBMSolver:
             residual=np.array([r.residual for r in rep]),
             device_ms=ms.value, launches=la.value, iterations_total=it.value)
 
+    def eigenchannels(self, e: int = 0) -> np.ndarray:
+        """Eigenchannel transmissions (eigenvalues of T^dagger T, descending) of energy
+        index e of the last solve, which must have solved every open channel."""
+        n = C.c_int(0)
+        check(self.lib.iobm_eigenchannels(self.h, int(e), None, 0, C.byref(n)), self.h)
+        tau = np.zeros(max(n.value, 1))
+        check(self.lib.iobm_eigenchannels(self.h, int(e), _ptr(tau), n.value, C.byref(n)), self.h)
+        return tau[: n.value]
+
     def solution(self, rhs: int) -> torch.Tensor:
         out = torch.empty(self.shape, dtype=torch.complex128, device=self.device)
         check(self.lib.iobm_solution(self.h, int(rhs), C.c_void_p(out.data_ptr()), 1), self.h)

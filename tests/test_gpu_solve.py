@@ -112,6 +112,33 @@ def test_precision_escalation():
         s.close()
 
 
+def test_eigenchannels():
+    # eigenvalues of T^dagger T from the library's FP64 amplitudes against the oracle's
+    from paper_1009_5300_gb300 import IOBMSolver
+    from paper_1009_5300_gb300._lib import IOBMError
+    jn = kb_junction(4)
+    E = jn.e_fermi
+    ref = transport.solve(jn, E)
+    tau_ref = transport.eigenchannels(ref)
+    sol = IOBMSolver.from_junction(jn, precision="mixed")
+    res = sol.solve([E])
+    tau = sol.eigenchannels(0)
+    assert len(tau) == ref.n_open
+    assert np.max(np.abs(tau - tau_ref)) < 1e-6
+    assert abs(tau.sum() - res.G[0]) < 1e-9
+    # a solve over a channel subset cannot give the transmission matrix
+    sol.solve([E], channels=[0])
+    with pytest.raises(IOBMError):
+        sol.eigenchannels(0)
+    sol.close()
+    flat = S.small_wire(nx=12, ny=10, nz=20, h=0.6, natom=1, depth=0.0, rs=1.5, nf=4)
+    flat = flat.copy_with(V=np.zeros_like(flat.V))
+    sf = IOBMSolver.from_junction(flat, precision="mixed")
+    sf.solve([flat.e_fermi])
+    assert np.max(np.abs(sf.eigenchannels(0) - 1.0)) < 1e-6
+    sf.close()
+
+
 def test_right_incidence_and_reciprocity():
     from paper_1009_5300_gb300 import IOBMSolver
     jn = kb_junction(4)

@@ -144,3 +144,33 @@ def test_gradient_zero_for_flat_potential():
     jn = flat_junction(4)
     g = transport.grad_V(jn, jn.e_fermi)
     assert np.max(np.abs(g)) < 1e-9
+
+
+def test_eigenchannels_flat_and_uniform():
+    # flat potential: every eigenchannel transmits fully
+    jn = flat_junction(4)
+    tau = transport.eigenchannels(transport.solve(jn, jn.e_fermi))
+    assert np.max(np.abs(tau - 1.0)) < 1e-10
+    # laterally uniform V(z): the channels decouple, T is diagonal, and the
+    # eigenchannel transmissions are its diagonal (each from the 1D transfer matrix)
+    nx, ny, nz, h = 10, 9, 30, 0.5
+    jn = S.small_wire(nx=nx, ny=ny, nz=nz, h=h, natom=1, depth=0.0, rs=1.2, nf=1)
+    z = np.arange(nz) * h
+    Vz = 0.35 * np.exp(-((z - 7.0) / 1.3) ** 2) - 0.2 * np.exp(-((z - 9.5) / 0.8) ** 2)
+    jn = jn.copy_with(V=np.broadcast_to(Vz[:, None, None], (nz, ny, nx)).copy())
+    sol = transport.solve(jn, jn.e_fermi)
+    tau = transport.eigenchannels(sol)
+    ref = np.sort([transfer_T_nf1(Vz, jn.e_fermi - sol.md.eps_perp[m], h)[0] for m in sol.open_modes])[::-1]
+    assert np.max(np.abs(tau - ref)) < 1e-10
+
+
+def test_eigenchannels_bounds_and_sum():
+    # unitarity (T + R = 1 per channel, t~^H t~ + r~^H r~ = 1) puts every eigenvalue
+    # in [0, 1]; the trace of t~^H t~ is G
+    jn = kb_junction(4)
+    sol = transport.solve(jn, jn.e_fermi)
+    tau = transport.eigenchannels(sol)
+    assert len(tau) == sol.n_open
+    assert np.all(tau > -1e-12) and np.all(tau < 1 + 1e-10)
+    assert abs(tau.sum() - sol.G) < 1e-10
+    assert np.all(np.diff(tau) <= 1e-15)
