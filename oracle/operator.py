@@ -148,13 +148,37 @@ def assemble_augmented(jn, E: float, md: ModeData) -> sp.csc_matrix:
     return sp.vstack([top, bot]).tocsc().astype(np.complex128)
 
 
+# lateral planes above this many points use numpy's FFT for the sums of Eq. 19
+# (the explicit phase matrix would hold N_xy^2 entries)
+EXPLICIT_DFT_LIMIT = 4096
+
+
 def _sigma_apply_end(jn, md: ModeData, planes_vals: np.ndarray) -> np.ndarray:
-    """Sigma applied to the N_f end planes [d][l] through Eqs. 19, 18-2 (explicit DFT)."""
+    """Sigma applied to the N_f end planes [d][l] through Eqs. 19, 18-2 (explicit DFT;
+    for planes above EXPLICIT_DFT_LIMIT points the same sums by FFT)."""
     nxy = jn.nx * jn.ny
+    if nxy > EXPLICIT_DFT_LIMIT:
+        return _sigma_apply_end_fft(jn, md, planes_vals)
     F = lateral_phase(jn.nx, jn.ny, jn.hx, jn.hy, md)
     ft = (F @ planes_vals.T) / nxy                    # [nu, d]  (Eq. 19)
     y = np.einsum("mde,me->md", md.sigma, ft)          # Sigma~ psi~
     return (F.conj().T @ y).T                          # back to real space [d][l]
+
+
+def _sigma_apply_end_fft(jn, md: ModeData, planes_vals: np.ndarray) -> np.ndarray:
+    """The sums of Eq. 19 by numpy's FFT: exp(-i G_nu . r_l) with G = 2 pi nu / L is the
+    DFT kernel at frequency index nu mod N, so psi~_nu = fft2(plane)[nu_y mod N_y,
+    nu_x mod N_x] / N_xy and the back sum is N_xy ifft2."""
+    nf, nxy = planes_vals.shape
+    ny, nx = jn.ny, jn.nx
+    kx = md.nu[:, 0] % nx
+    ky = md.nu[:, 1] % ny
+    spec = np.fft.fft2(planes_vals.reshape(nf, ny, nx), axes=(1, 2)) / nxy
+    ft = spec[:, ky, kx].T                              # [nu, d]
+    y = np.einsum("mde,me->md", md.sigma, ft)
+    Y = np.zeros((nf, ny, nx), dtype=np.complex128)
+    Y[:, ky, kx] = y.T
+    return (np.fft.ifft2(Y, axes=(1, 2)) * nxy).reshape(nf, nxy)
 
 
 def apply_A(jn, E: float, md: ModeData, psi: np.ndarray) -> np.ndarray:

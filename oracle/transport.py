@@ -69,8 +69,12 @@ def incident_wave_planes(jn, md: ModeData, m: int, depths: np.ndarray) -> np.nda
     """Unit incident wave of mode m at depth index d (negative = electrode plane -d):
     f(l) lambda_in^d with f(l) = exp(i G_m . r_l); returned as [len(depths)][N_xy]."""
     lam = md.lam[m, md.prop[m]]
-    F = lateral_phase(jn.nx, jn.ny, jn.hx, jn.hy, md)
-    f = F[m].conj()
+    # the row of mode m of the Eq. 19 phase matrix, conjugated: exp(+i G_m . r_l)
+    x = np.arange(jn.nx) * jn.hx
+    y = np.arange(jn.ny) * jn.hy
+    Gx = 2.0 * np.pi * md.nu[m, 0] / (jn.nx * jn.hx)
+    Gy = 2.0 * np.pi * md.nu[m, 1] / (jn.ny * jn.hy)
+    f = np.exp(1j * (Gy * y[:, None] + Gx * x[None, :])).reshape(-1)
     return (lam ** depths)[:, None] * f[None, :]
 
 

@@ -98,6 +98,7 @@ struct iobm_handle {
     int zchunk = kZChunkDefault;         // stencil z-planes per CTA (autotuned)
     int stencil_variant = 0;             // StencilArgs::variant (autotuned)
     DevBuf batch_ctr;                    // chunk counter of this junction in a batched solve
+    DevBuf sig_scratch;                  // large-plane self-energy spectra
     DevBuf esc_ws, esc_descs, esc_rhs_energy;   // FP64 continuation of stalled mixed RHS
     cudaGraphExec_t chunk_exec = nullptr;        // the last solve's chunk graph, updated in place
     void* pin = nullptr;                         // pinned staging buffer for table uploads
@@ -176,17 +177,33 @@ bool fourier_precond(const iobm_handle* h) {
     return h->opt.use_precond == IOBM_PRECOND_FOURIER || h->opt.use_precond == IOBM_PRECOND_EQ10_FOURIER;
 }
 
+bool large_plane(const iobm_handle* h) { return h->nxy > kSmemPlaneLimit; }
+
+// partial slots per plane written by a plane transform (one per row block for
+// the two-pass transforms of large planes)
+int plane_slots(const iobm_handle* h) { return large_plane(h) ? large_row_blocks(h->g.ny) : 1; }
+
+// mu partial slots of the self-energy
+int sigma_slots(const iobm_handle* h) { return 2 * h->nf * plane_slots(h); }
+
 int slots_for(const iobm_handle* h) {
     const int ns_op = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, h->nf);
     const int ns_pc = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, 1);
-    return std::max(std::max(ns_op + 2 * h->nf + 1, 64), std::max(h->g.nz, ns_pc));
+    return std::max(std::max(ns_op + sigma_slots(h) + 1, 64),
+                    std::max(h->g.nz * plane_slots(h), ns_pc));
 }
 
 // number of rho / |r|^2 partial slots the preconditioner pass writes
 int rho_slots(const iobm_handle* h) {
     return fourier_precond(h)
-               ? h->g.nz
+               ? h->g.nz * plane_slots(h)
                : stencil_slots(h->g.nx, h->g.ny, h->g.nz, h->zchunk, 1);
+}
+
+// scratch of the large-plane self-energy (compact end-plane spectra, in and out)
+cudaError_t ensure_sigma_scratch(iobm_handle* h, int nrhs) {
+    if (!large_plane(h)) return cudaSuccess;
+    return h->sig_scratch.ensure(2 * (size_t)std::max(nrhs, 1) * 2 * h->nf * h->nxy * sizeof(double2));
 }
 
 size_t workspace_bytes(const iobm_handle* h, int nrhs, int prec) {
@@ -241,6 +258,8 @@ int bind_workspace(iobm_handle* h, int nrhs) {
     h->x64 = (prec == IOBM_MIXED) ? (double2*)take(sizeof(double2) * n) : (double2*)h->vx;
     h->ws_nrhs = nrhs;
     h->ws_prec = prec;
+    const cudaError_t e = ensure_sigma_scratch(h, nrhs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "self-energy scratch");
     return IOBM_OK;
 }
 
@@ -329,6 +348,7 @@ PrecondArgs<T> fourier_args(const iobm_handle* h, const void* pc) {
 template <typename T>
 SigmaArgs<T> sigma_args(const iobm_handle* h, const void* sig) {
     SigmaArgs<T> a{};
+    a.scratch = (typename Cplx<T>::type*)h->sig_scratch.p;
     a.nx = h->g.nx;
     a.ny = h->g.ny;
     a.nz = h->g.nz;
@@ -507,7 +527,7 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     s.slot_stride = h->slot_stride;
     s.slot_base = ns;
     CK(launch_sigma<T>(s, nrhs, h->stream));
-    int nslots_mu = ns + 2 * h->nf;
+    int nslots_mu = ns + sigma_slots(h);
     launches += 3;
     if (h->pt.nproj > 0) {
         KbArgs<T> k = kb_args<T>(h);
@@ -1345,9 +1365,8 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     h->nxy = g.nx * g.ny;
     h->npts = (long long)h->nxy * g.nz;
     if (h->npts > (1LL << 31) - 1) return bad(IOBM_E_UNSUPPORTED, "grid larger than 2^31 points");
-    if (h->nxy > 4096)
-        return bad(IOBM_E_UNSUPPORTED, "lateral planes above 4096 points are not supported by the "
-                                       "shared-memory FFT of this build");
+    if (h->nxy > kSmemPlaneLimit && !large_plane_supported(g.nx, g.ny))
+        return bad(IOBM_E_UNSUPPORTED, "lateral sizes above 256 are not supported");
     if (g.nz < 2 * g.nf + 2)
         return bad(IOBM_E_ARG, "need at least 2 nf + 2 planes");
     std::vector<int> rx, ry;
@@ -1378,6 +1397,7 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     if (e == cudaSuccess) e = sigma_prepare();
     if (e == cudaSuccess) e = precond_prepare();
     if (e == cudaSuccess) e = stencil_prepare();
+    if (e == cudaSuccess) e = fft_large_prepare();
     if (e != cudaSuccess) return bad(IOBM_E_CUDA, std::string("stream/event setup: ") + cudaGetErrorString(e));
 
     std::vector<float> v32(h->npts);
@@ -1735,6 +1755,7 @@ static int apply_common(iobm_handle* h, double E, int elem, const void* x, void*
     if (nrhs == 0) return IOBM_OK;
     if (cudaEventRecord(h->ev_sync, h->user_stream) == cudaSuccess)
         cudaStreamWaitEvent(h->stream, h->ev_sync, 0);
+    CK(ensure_sigma_scratch(h, nrhs));
     long long launches = 0;
     const bool need_tables = !precond || h->opt.use_precond == IOBM_PRECOND_FOURIER;
     if (need_tables) {

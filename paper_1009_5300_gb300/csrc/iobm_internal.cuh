@@ -148,9 +148,10 @@ struct SigmaArgs {
     FftAxis ax, ay;
     const C* twx;           // [nx] exp(-2 pi i k / nx)
     const C* twy;           // [ny]
-    double2* dot_part;      // slot_base + end*nf + d
+    double2* dot_part;      // slot_base + end*nf + d (planes > 4096 points: see k_fft_large.cu)
     int slot_stride, slot_base;
     long long npts;
+    C* scratch;             // planes > 4096 points: 2 * nrhs * 2 nf * nxy elements
 };
 
 template <typename T>
@@ -210,6 +211,16 @@ cudaError_t launch_update_precond_fourier(const PrecondArgs<T>& a, int nrhs, cud
 template <typename T> size_t precond_smem_bytes(int nx, int ny);
 cudaError_t precond_prepare();
 cudaError_t stencil_prepare();
+
+// lateral planes above 4096 points (up to 256 x 256): two-pass global-memory FFTs
+constexpr int kSmemPlaneLimit = 4096;
+cudaError_t fft_large_prepare();
+int large_row_blocks(int ny);
+bool large_plane_supported(int nx, int ny);
+template <typename T>
+cudaError_t launch_precond_large(const PrecondArgs<T>& a, int nrhs, cudaStream_t s,
+                                 cudaError_t (*zsweeps)(const PrecondArgs<T>&, int, cudaStream_t));
+template <typename T> cudaError_t launch_sigma_large(const SigmaArgs<T>& a, int nrhs, cudaStream_t s);
 
 // ---- launchers (defined in the .cu files) ----------------------------------
 

@@ -503,6 +503,7 @@ static cudaError_t launch_inv_ct(const PrecondArgs<T>& a, int nrhs, cudaStream_t
 
 template <typename T>
 cudaError_t launch_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s) {
+    if (a.nx * a.ny > kSmemPlaneLimit) return launch_precond_large<T>(a, nrhs, s, launch_zsolve<T>);
     const size_t smem = precond_smem_bytes<T>(a.nx, a.ny);
     if (smem > (size_t)kPrecondSmemLimit) return cudaErrorInvalidValue;
     cudaError_t e;

@@ -36,6 +36,8 @@ CASES = [
     (3, 20, 12, 1, False),     # narrower than the full-row stencil tiles: 2-D tiled kernel
     (16, 16, 14, 1, True),     # compile-time-FFT self-energy with N_f = 1 (cluster of one CTA)
     (32, 32, 18, 2, False),    # compile-time-FFT self-energy, radix 4 and 2 passes, N_f = 2
+    (72, 72, 14, 4, True),     # planes above 4096 points: two-pass global-memory FFTs
+    (96, 48, 16, 2, True),     # a large non-square plane, 2-D tiled stencil (nx > 64)
 ]
 
 

@@ -117,3 +117,17 @@ def test_preconditioner_positive_for_paper_alphas():
     # and just below ln 6 the face-neighbour P loses definiteness on a periodic grid
     c1 = math.exp(-(math.log(6.0) - 0.05))
     assert 1 - 6 * c1 < 0
+
+
+@pytest.mark.parametrize("nx,ny,nf", [(12, 10, 4), (9, 8, 1), (16, 16, 2)])
+def test_sigma_fft_route_matches_explicit_sums(nx, ny, nf):
+    # the FFT route used for large planes gives the explicit Eq. 19 sums
+    from oracle.operator import _sigma_apply_end_fft, lateral_phase
+    jn = S.small_wire(nx=nx, ny=ny, nz=2 * nf + 3, h=0.5, natom=1, depth=0.0, rs=1.5, nf=nf)
+    md = modes.mode_data(nx, ny, jn.hx, jn.hy, jn.hz, nf, jn.e_fermi)
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal((nf, nx * ny)) + 1j * rng.standard_normal((nf, nx * ny))
+    F = lateral_phase(nx, ny, jn.hx, jn.hy, md)
+    ft = (F @ v.T) / (nx * ny)
+    ref = (F.conj().T @ np.einsum("mde,me->md", md.sigma, ft)).T
+    assert np.max(np.abs(_sigma_apply_end_fft(jn, md, v) - ref)) < 1e-12 * np.max(np.abs(ref))
