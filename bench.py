@@ -464,6 +464,63 @@ def batch_arm(args, rank, world, local_rank):
     return 0
 
 
+WIRE128_WORKLOAD = ("wire128: 7-atom wire at 4.3 bohr spacing, Gaussian wells (2.0 Ha, width 1.5 bohr) "
+                    "+ s/p/d KB projectors, 128x128x256 grid, h=0.3 bohr, 9-point FD, r_s=2.0 jellium "
+                    "(109 open channels at E_F), {e} energies, every open channel in batches of {b} "
+                    "channels, mixed precision, Fourier preconditioner (two-pass plane FFTs)")
+
+
+def wire128_arm(args, rank, world, local_rank):
+    """The large cross-section workload: every open channel of each energy, solved in
+    batches of --batch channels (one solve per batch), energies dealt to the ranks."""
+    import numpy as np
+    import torch
+
+    import iobm_synth as S
+    from paper_1009_5300_gb300 import IOBMSolver, build_library
+
+    build_library()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    jn = S.wire128()
+    Es = jn.energies[: args.wire128_energies][rank::world]
+    sol = IOBMSolver.from_junction(jn, precision="mixed", device=dev)
+    sol.solve(Es[:1], channels=list(range(min(args.batch, 4))))   # warm-up
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    stream = torch.cuda.current_stream(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    solves, iters, converged = 0, 0, True
+    ev0.record(stream)
+    for E in Es:
+        n_open = sol.open_channels(float(E))[0].shape[0]
+        for c0 in range(0, n_open, args.batch):
+            res = sol.solve([E], channels=list(range(c0, min(c0 + args.batch, n_open))))
+            solves += res.nrhs
+            iters += res.iterations_total
+            converged &= bool(res.converged)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if rank == 0:
+        line = {"metric": METRIC, "value": solves * world / (ms / 1000.0), "unit": UNIT,
+                "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "c64+f64", "data": "synthetic",
+                "config": {"workload": WIRE128_WORKLOAD.format(e=len(Es), b=args.batch),
+                           "channel_solves": solves, "grid_points": jn.npts,
+                           "l2": "inputs larger than L2",
+                           "parallelism": f"energies dealt to {world} replica(s)"},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clocks,
+                "iterations_mean": iters / max(1, solves), "converged": converged}
+        print(json.dumps(line), flush=True)
+    sol.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,9 +535,12 @@ def main():
                     help="FP64 residual replacement factor of the mixed solver (library default)")
     ap.add_argument("--chunk", type=int, default=None,
                     help="COCG iterations per captured graph (library default)")
-    ap.add_argument("--workload", choices=["wire48", "batch"], default="wire48",
+    ap.add_argument("--workload", choices=["wire48", "batch", "wire128"], default="wire48",
                     help="wire48: the 48x48x160 wire (default line); batch: the uneven "
-                         "many-junction workload solved in grouped graph launches")
+                         "many-junction workload solved in grouped graph launches; wire128: "
+                         "the 128x128x256 large cross-section wire")
+    ap.add_argument("--wire128-energies", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=32, help="channels per solve (wire128)")
     ap.add_argument("--junctions", type=int, default=256)
     ap.add_argument("--batch-energies", type=int, default=16)
     args = ap.parse_args()
@@ -491,6 +551,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.workload == "batch":
         return batch_arm(args, rank, world, local_rank)
+    if args.workload == "wire128":
+        return wire128_arm(args, rank, world, local_rank)
     return native_arm(args, rank, world, local_rank)
 
 

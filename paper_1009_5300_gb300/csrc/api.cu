@@ -1029,9 +1029,9 @@ int escalate_fp64(iobm_handle* h) {
     CK(cudaMemcpyAsync(h->st, h->hstate.data(), sizeof(RhsState) * h->nrhs, cudaMemcpyHostToDevice,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    h->last_ms += sub_ms;
-    h->last_launches += sub_launches;
-    h->last_iters += sub_iters;
+    h->last_ms = sv.last_ms + sub_ms;
+    h->last_launches = sv.last_launches + sub_launches;
+    h->last_iters = sv.last_iters + sub_iters;
     return IOBM_OK;
 }
 
