@@ -29,9 +29,31 @@ sys.path.insert(0, ROOT)
 
 METRIC = "channel-solves/sec at 1e-6 G0 (mixed vs FP64 GPU); stencil HBM GB/s vs peak"
 UNIT = "channel-solves/s"
-# DRAM bytes (read + write) per RHS-point of one k_stencil_rows_tma<48,4,3> launch, from an
-# ncu capture of the 8-energy wire48 case with all 56 RHS active: 695.0 MB / 20.64 M points
-# (the algorithmic figure is 32.07 B); to be re-taken whenever that kernel changes
+# Roofline kernels: per COCG iteration kernel, the algorithmic HBM bytes per
+# RHS-point (complex FP32 vectors, 8 B per element) and per grid point of a launch,
+# and the measured DRAM bytes per RHS-point (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch with all 56 RHS of the 8-energy wire48 case
+# active), None until captured for the kernel as it stands.
+ROOFLINE_KERNELS = {
+    # p = z + beta p_old, q = (r - V z) + beta q_old: read z r p_old q_old, write p q
+    "operator": {"kernel": "k_pq_update<float> (implicit operator form: direction and "
+                           "operator update + p^T q partials)",
+                 "bytes_rhs_point": 48.0, "bytes_point": 4.0, "dram_rhs_point": None},
+    # x += alpha p, r -= alpha q, forward plane FFTs: read x p r q, write x r spectrum
+    "update_fft": {"kernel": "k_update_fft_ct<float,48> (x, r update + forward plane FFTs)",
+                   "bytes_rhs_point": 56.0, "bytes_point": 0.0, "dram_rhs_point": None},
+    # z-sweeps: read and write the spectrum
+    "zsweep": {"kernel": "k_zsolve<float,4> (free-propagator z-sweeps per lateral mode)",
+               "bytes_rhs_point": 16.0, "bytes_point": 0.0, "dram_rhs_point": None},
+    # inverse plane FFTs + dots: read spectrum and r, write z
+    "ifft": {"kernel": "k_ifft_dots_ct<float,48> (inverse plane FFTs + r^T z, |r|^2 partials)",
+             "bytes_rhs_point": 24.0, "bytes_point": 0.0, "dram_rhs_point": None},
+}
+ROOFLINE_STAGE = "update_fft"
+# The explicit-form stencil k_stencil_rows_tma<48,4,3>: 32 B per RHS-point (read z and
+# p_old, write p and q) + 4 B per point (V); DRAM bytes per RHS-point from an ncu capture
+# of the 8-energy wire48 case with all 56 RHS active: 695.0 MB / 20.64 M points
+STENCIL_BYTES_RHS_POINT = 32.0
 STENCIL_DRAM_BYTES_PER_RHS_POINT = 695.0e6 / (56 * 368640)
 WORKLOAD = ("wire48: 6-atom wire, Gaussian wells (0.5 Ha, width 1.5 bohr, spacing 6.8 bohr) "
             "+ s/p KB projectors (radius 3 bohr), 48x48x160 grid, h=0.35 bohr, 9-point FD, "
@@ -224,7 +246,7 @@ def native_arm(args, rank, world, local_rank):
     barrier()
 
     sampler = ClockSampler(local_rank)
-    solver.profile(True)
+    solver.profile(ROOFLINE_STAGE)
     sampler.start()
     stream = torch.cuda.current_stream(dev)
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -238,7 +260,7 @@ def native_arm(args, rank, world, local_rank):
     barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    stencil_ms, stencil_launches = solver.kernel_stats()
+    kern_ms, kern_launches = solver.kernel_stats()
     solver.profile(False)
 
     solves = sum(r.nrhs for r in results)
@@ -256,29 +278,54 @@ def native_arm(args, rank, world, local_rank):
         ms_max, solves_all = ms, float(solves)
     value = solves_all / (ms_max / 1000.0)
 
-    # roofline of the dominant kernel (fused stencil): algorithmic bytes per
-    # launch = 32 B (read z, read p_old, write p, write q; complex FP32) per grid
-    # point per active RHS + 4 B per grid point (V)
+    # roofline of the dominant kernel: algorithmic bytes of its launches (per
+    # RHS-point for every active RHS-iteration, plus the per-point tables once a
+    # launch) over its CUDA-event time inside the timed region
     npts = jn.npts
-    alg_bytes = 32.0 * npts * iters_total + 4.0 * npts * stencil_launches
+    rk = ROOFLINE_KERNELS[ROOFLINE_STAGE]
+    alg_bytes = rk["bytes_rhs_point"] * npts * iters_total + rk["bytes_point"] * npts * kern_launches
     peak, peak_kind = load_peaks()
     roof = None
-    if stencil_launches > 0 and stencil_ms > 0:
-        achieved = alg_bytes / (stencil_ms / 1000.0) / 1e9
-        rhs_points = npts * iters_total / stencil_launches
+    if kern_launches > 0 and kern_ms > 0:
+        achieved = alg_bytes / (kern_ms / 1000.0) / 1e9
+        rhs_points = npts * iters_total / kern_launches
+        dram = rk["dram_rhs_point"]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": STENCIL_DRAM_BYTES_PER_RHS_POINT * rhs_points,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                  "launch on the 8-energy case (56 RHS), scaled by RHS-points",
-                "kernel": "k_stencil_rows_tma<48,4,3> (fused p update + operator + p^T q)",
-                "launches": stencil_launches,
-                "avg_launch_ms": stencil_ms / stencil_launches,
-                "alg_bytes_per_launch": alg_bytes / stencil_launches,
+                "traffic": dram * rhs_points if dram is not None else None,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                   "launch on the 8-energy case (56 RHS), scaled by RHS-points"
+                                   if dram is not None else "not captured for this kernel"),
+                "kernel": rk["kernel"],
+                "launches": kern_launches,
+                "avg_launch_ms": kern_ms / kern_launches,
+                "alg_bytes_per_launch": alg_bytes / kern_launches,
                 "peak_source": f"{peak_kind} hbm_gbs"}
 
     extra = {}
     if rank == 0 and not args.no_fp64:
+        # the explicit FD stencil kernel (fused p update + operator + p^T q) on the same
+        # workload: one solve with the explicit operator form, its launches timed
+        sx = IOBMSolver.from_junction(jn, precision="mixed", device=dev, op_form="explicit")
+        sx.solve(E[:8])                   # warm
+        sx.profile("operator")
+        rx = sx.solve(E[:8])
+        st_ms, st_launches = sx.kernel_stats()
+        sx.profile(False)
+        sx.close()
+        if st_launches > 0 and st_ms > 0:
+            st_bytes = (STENCIL_BYTES_RHS_POINT * npts * rx.iterations_total
+                        + 4.0 * npts * st_launches)
+            st_ach = st_bytes / (st_ms / 1000.0) / 1e9
+            extra["stencil_roofline"] = {
+                "kernel": "k_stencil_rows_tma<48,4,3> (explicit form: fused p update + "
+                          "FD operator + p^T q)",
+                "bound": "hbm", "achieved": st_ach, "peak": peak, "unit": "GB/s",
+                "frac": st_ach / peak, "launches": st_launches,
+                "avg_launch_ms": st_ms / st_launches,
+                "traffic": STENCIL_DRAM_BYTES_PER_RHS_POINT * npts * rx.iterations_total / st_launches,
+                "sample": "one explicit-form solve of the first 8 energies",
+                "iterations_mean": float(rx.iterations.mean())}
         # plain FP64 GPU solver on a sample of the energies, same accuracy target
         idx = [0, len(E) // 2, len(E) - 1]
         sample = E[idx]

@@ -108,6 +108,18 @@ typedef struct {
                                     FFT, per-mode tridiagonal multiply in z, inverse FFT;
                                     the same operator as IOBM_PRECOND_EQ10 up to rounding  */
 
+/* How each COCG iteration forms q = A p (iobm_options.op_form).  With the
+ * free-propagator preconditioner M = (E - T - H~)^{-1} the operator splits as
+ * A = M^{-1} - W, W = V_loc + V_NL the potential terms of H_T (Eqs. 2-4), and as the
+ * iteration has z = M r in hand, A z = r - W z; the new direction p = z + beta p'
+ * then gives q = A p = (r - W z) + beta q' with no stencil or self-energy
+ * application (the same iterates in exact arithmetic; the FP64 residual checks
+ * still apply the full operator).  IOBM_OP_AUTO takes this form whenever
+ * use_precond is IOBM_PRECOND_FOURIER and the explicit form otherwise;
+ * IOBM_OP_EXPLICIT always applies the stencil, self-energy and projectors. */
+#define IOBM_OP_AUTO      0
+#define IOBM_OP_EXPLICIT  1
+
 /* Solver options.  use_precond: one of IOBM_PRECOND_*.  alpha: parameter of
  * Eq. 10 (C_0 = 1, C_1 = exp(-alpha)) for IOBM_PRECOND_EQ10(_FOURIER).  tol: stop when
  * ||b - A psi||_2 / ||b||_2 <= tol, the residual evaluated in FP64.
@@ -119,7 +131,8 @@ typedef struct {
  * stops there (or breaks down) without converging is continued with FP64
  * iterations from its FP64 iterate, up to max_iter more (precision escalation:
  * once cond(A) times the FP32 rounding unit is no longer small, the FP32 inner
- * iteration stops making progress while FP64 still converges). */
+ * iteration stops making progress while FP64 still converges).
+ * op_form: IOBM_OP_AUTO or IOBM_OP_EXPLICIT (above). */
 typedef struct {
     double alpha;
     int use_precond;
@@ -129,6 +142,7 @@ typedef struct {
     double refine_delta;
     int chunk;
     int max_iter_mixed;
+    int op_form;
 } iobm_options;
 
 /* Per right-hand-side report, in solve order (energy-major, then incident
@@ -145,7 +159,7 @@ typedef struct {
 
 /* Fill opts with the defaults: alpha 1.8, use_precond IOBM_PRECOND_FOURIER, tol 1e-8,
  * max_iter 20000, precision IOBM_MIXED, refine_delta 0.01, chunk 32,
- * max_iter_mixed 1000. */
+ * max_iter_mixed 1000, op_form IOBM_OP_AUTO. */
 void iobm_default_options(iobm_options* opts);
 
 /* Create a solver for one junction.  V_loc: host [nz][ny][nx] local
@@ -310,13 +324,18 @@ int iobm_set_potential(iobm_handle* h, const double* V_loc, int src_is_device);
 int iobm_channels_host(const iobm_grid* grid, double E, int* n_open, int max_out, int* nu,
                        double* vel, double* lam, double* btilde, double* mrow, double* sigma);
 
-/* Enable (1) or disable (0) CUDA-event timing of every fused stencil launch
- * (the dominant kernel: p = z + beta p_old, q = (E - T - V) p and the p^T q
- * partials) inside the captured iteration graphs; resets the counters. */
+/* CUDA-event timing of one kernel of every COCG iteration inside the captured
+ * iteration graphs; resets the counters.  enable: 0 off; 1 the operator kernel
+ * (the fused stencil p = z + beta p_old, q = (E - T - V) p with the p^T q
+ * partials, or in the implicit operator form the pass p = z + beta p_old,
+ * q = (r - V z) + beta q_old); 2 the update x += alpha p, r -= alpha q with the
+ * forward plane FFTs; 3 the z-sweeps; 4 the inverse plane FFTs with the r^T z
+ * and |r|^2 partials (2-4: Fourier preconditioners with planes of at most 4096
+ * points).  IOBM_E_ARG for other values. */
 int iobm_profile(iobm_handle* h, int enable);
 
-/* Accumulated device time (ms) and count of the timed stencil launches
- * since iobm_profile(h, 1). */
+/* Accumulated device time (ms) and count of the timed launches since
+ * iobm_profile(h, enable > 0). */
 int iobm_kernel_stats(const iobm_handle* h, double* stencil_ms, long long* stencil_launches);
 
 /* Allocation-free form of the Eq. 10 preconditioner with its COCG dot

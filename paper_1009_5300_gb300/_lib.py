@@ -29,6 +29,8 @@ IOBM_PRECOND_NONE = 0
 IOBM_PRECOND_EQ10 = 1
 IOBM_PRECOND_FOURIER = 2
 IOBM_PRECOND_EQ10_FOURIER = 3
+IOBM_OP_AUTO = 0
+IOBM_OP_EXPLICIT = 1
 IOBM_ELEM_C64 = 0
 IOBM_ELEM_C32 = 1
 IOBM_ELEM_C64_DF = 2
@@ -48,7 +50,7 @@ class Projectors(C.Structure):
 class Options(C.Structure):
     _fields_ = [("alpha", C.c_double), ("use_precond", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("refine_delta", C.c_double),
-                ("chunk", C.c_int), ("max_iter_mixed", C.c_int)]
+                ("chunk", C.c_int), ("max_iter_mixed", C.c_int), ("op_form", C.c_int)]
 
 
 class Report(C.Structure):

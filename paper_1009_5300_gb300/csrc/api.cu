@@ -8,6 +8,7 @@
 #include <type_traits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -66,6 +67,8 @@ struct iobm_handle {
     iobm_options opt{};
     cudaStream_t user_stream = nullptr;
     cudaStream_t stream = nullptr;      // private stream (capturable)
+    cudaStream_t cond_stream = nullptr; // captures the bodies of conditional graph nodes
+    bool graph_conditionals = true;     // IF nodes around the residual replacements
     cudaEvent_t ev_sync = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
     std::string err;
     long long npts = 0;
@@ -177,6 +180,11 @@ bool fourier_precond(const iobm_handle* h) {
     return h->opt.use_precond == IOBM_PRECOND_FOURIER || h->opt.use_precond == IOBM_PRECOND_EQ10_FOURIER;
 }
 
+// q = A p through the free-propagator identity A z = r - V z - V_NL z (no stencil)
+bool implicit_operator(const iobm_handle* h) {
+    return h->opt.op_form == IOBM_OP_AUTO && h->opt.use_precond == IOBM_PRECOND_FOURIER;
+}
+
 bool large_plane(const iobm_handle* h) { return h->nxy > kSmemPlaneLimit; }
 
 // partial slots per plane written by a plane transform (one per row block for
@@ -190,7 +198,7 @@ int slots_for(const iobm_handle* h) {
     const int ns_op = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, h->nf);
     const int ns_pc = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, 1);
     return std::max(std::max(ns_op + sigma_slots(h) + 1, 64),
-                    std::max(h->g.nz * plane_slots(h), ns_pc));
+                    std::max(std::max(h->g.nz * plane_slots(h), ns_pc), h->g.nz + 1));
 }
 
 // number of rho / |r|^2 partial slots the preconditioner pass writes
@@ -478,6 +486,50 @@ int residual_replacement(iobm_handle* h, int nrhs, int mask, bool mixed, long lo
     return apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
 }
 
+// Runs body() (launches on h->stream).  While h->stream is being captured the
+// launches go into the body of a conditional IF node that executes only when
+// some RHS has a status in `mask` when the graph reaches it (decided on the
+// device), so the masked launches of steps that concern no RHS cost nothing.
+//
+// Kernel profilers cannot see the kernel nodes of graphs that hold conditional
+// nodes: with IOBM_GRAPH_CONDITIONALS=0 in the environment at handle creation
+// the steps are captured as plain masked launches instead (the same kernels on
+// the same RHS, plus the launches that find no RHS to work on).
+template <typename Body>
+int captured_if_any(iobm_handle* h, int nrhs, int mask, Body body) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(h->stream, &cs));
+    if (cs != cudaStreamCaptureStatusActive || !h->graph_conditionals) return body();
+    cudaGraph_t cg = nullptr;
+    CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault));
+    CK(launch_status_cond(cond, h->st, nrhs, mask, h->stream));
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &cg, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &p));
+    CK(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1,
+                                           cudaStreamSetCaptureDependencies));
+    CK(cudaStreamBeginCaptureToGraph(h->cond_stream, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    cudaStream_t main = h->stream;
+    h->stream = h->cond_stream;
+    const int rc = body();
+    h->stream = main;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cond_stream, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(h, e, "conditional body capture");
+    return IOBM_OK;
+}
+
 // One COCG iteration for every ACTIVE RHS.  Each RHS keeps its current
 // direction in one of two buffers (RhsState::pbuf), so RHS that pause for an
 // FP64 residual replacement resume with their own direction.
@@ -494,58 +546,90 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     CK(launch_beta(h->st, h->rho_part, h->rr_part, rho_slots(h), h->slot_stride, nrhs,
                    iter_cap(h), tol2, delta2, mixed ? 1 : 0, h->stream));
     launches += 2;
-    const void* sig = std::is_same<T, float>::value ? h->sig32.p : h->sig64.p;
-    StencilArgs<T> a = op_args<T>(h);
-    a.x = (const C*)h->vz;
-    a.pbufs[0] = (C*)h->vp[0];
-    a.pbufs[1] = (C*)h->vp[1];
-    a.y = (C*)h->vq;
-    a.fused_p = 1;
-    a.ediag = h->ediag.as<double>();
-    a.rhs_energy = h->rhs_energy.as<int>();
-    a.state = h->st;
-    a.mask = M_ACTIVE;
-    a.dot_mode = 1;
-    a.dot_part = h->mu_part;
-    a.nrm_part = nullptr;
-    a.slot_stride = h->slot_stride;
-    a.slot_base = 0;
     // event record nodes inside the captured graph (external records execute with the graph)
     const bool timed = h->profile && slot >= 0;
-    if (timed) CK(cudaEventRecordWithFlags(h->kev[2 * slot], h->stream, cudaEventRecordExternal));
-    CK(launch_stencil<T>(a, nrhs, h->stream));
-    if (timed)
-        CK(cudaEventRecordWithFlags(h->kev[2 * slot + 1], h->stream, cudaEventRecordExternal));
-    SigmaArgs<T> s = sigma_args<T>(h, sig);
-    s.pnew[0] = (const C*)h->vp[0];
-    s.pnew[1] = (const C*)h->vp[1];
-    s.y = (C*)h->vq;
-    s.rhs_energy = h->rhs_energy.as<int>();
-    s.state = h->st;
-    s.mask = M_ACTIVE;
-    s.dot_part = h->mu_part;
-    s.slot_stride = h->slot_stride;
-    s.slot_base = ns;
-    CK(launch_sigma<T>(s, nrhs, h->stream));
-    int nslots_mu = ns + sigma_slots(h);
-    launches += 3;
-    if (h->pt.nproj > 0) {
-        KbArgs<T> k = kb_args<T>(h);
-        k.pnew[0] = (const C*)h->vp[0];
-        k.pnew[1] = (const C*)h->vp[1];
-        k.y = (C*)h->vq;
-        k.state = h->st;
-        k.mask = M_ACTIVE;
-        k.dot_part = h->mu_part;
-        k.slot_stride = h->slot_stride;
-        k.slot_base = nslots_mu;
-        CK(launch_kb<T>(k, nrhs, h->stream));
-        nslots_mu += 1;
+    cudaEvent_t* kev = timed ? &h->kev[2 * slot] : nullptr;
+    C* pb[2] = {(C*)h->vp[0], (C*)h->vp[1]};
+    int nslots_mu = 0;
+    if (implicit_operator(h)) {
+        // p = z + beta p_old, q = (r - V z) + beta q_old, then q -= V_NL z
+        if (timed && h->profile == 1)
+            CK(cudaEventRecordWithFlags(kev[0], h->stream, cudaEventRecordExternal));
+        CK(launch_pq_update<T>((const C*)h->vz, (const C*)h->vr, pb, (C*)h->vq,
+                               std::is_same<T, float>::value ? (const T*)h->V32.p : (const T*)h->V64.p,
+                               h->st, M_ACTIVE, h->g.nx, h->g.ny, h->g.nz, nrhs, h->mu_part,
+                               h->slot_stride, h->stream));
+        if (timed && h->profile == 1)
+            CK(cudaEventRecordWithFlags(kev[1], h->stream, cudaEventRecordExternal));
+        nslots_mu = h->g.nz;   // one p^T q partial per plane
         launches += 1;
+        if (h->pt.nproj > 0) {
+            KbArgs<T> k = kb_args<T>(h);
+            k.pnew[0] = (const C*)h->vp[0];
+            k.pnew[1] = (const C*)h->vp[1];
+            k.zsrc = (const C*)h->vz;
+            k.y = (C*)h->vq;
+            k.state = h->st;
+            k.mask = M_ACTIVE;
+            k.dot_part = h->mu_part;
+            k.slot_stride = h->slot_stride;
+            k.slot_base = nslots_mu;
+            CK(launch_kb<T>(k, nrhs, h->stream));
+            nslots_mu += 1;
+            launches += 1;
+        }
+    } else {
+        const void* sig = std::is_same<T, float>::value ? h->sig32.p : h->sig64.p;
+        StencilArgs<T> a = op_args<T>(h);
+        a.x = (const C*)h->vz;
+        a.pbufs[0] = (C*)h->vp[0];
+        a.pbufs[1] = (C*)h->vp[1];
+        a.y = (C*)h->vq;
+        a.fused_p = 1;
+        a.ediag = h->ediag.as<double>();
+        a.rhs_energy = h->rhs_energy.as<int>();
+        a.state = h->st;
+        a.mask = M_ACTIVE;
+        a.dot_mode = 1;
+        a.dot_part = h->mu_part;
+        a.nrm_part = nullptr;
+        a.slot_stride = h->slot_stride;
+        a.slot_base = 0;
+        if (timed && h->profile == 1)
+            CK(cudaEventRecordWithFlags(kev[0], h->stream, cudaEventRecordExternal));
+        CK(launch_stencil<T>(a, nrhs, h->stream));
+        if (timed && h->profile == 1)
+            CK(cudaEventRecordWithFlags(kev[1], h->stream, cudaEventRecordExternal));
+        SigmaArgs<T> s = sigma_args<T>(h, sig);
+        s.pnew[0] = (const C*)h->vp[0];
+        s.pnew[1] = (const C*)h->vp[1];
+        s.y = (C*)h->vq;
+        s.rhs_energy = h->rhs_energy.as<int>();
+        s.state = h->st;
+        s.mask = M_ACTIVE;
+        s.dot_part = h->mu_part;
+        s.slot_stride = h->slot_stride;
+        s.slot_base = ns;
+        CK(launch_sigma<T>(s, nrhs, h->stream));
+        nslots_mu = ns + sigma_slots(h);
+        launches += 3;
+        if (h->pt.nproj > 0) {
+            KbArgs<T> k = kb_args<T>(h);
+            k.pnew[0] = (const C*)h->vp[0];
+            k.pnew[1] = (const C*)h->vp[1];
+            k.y = (C*)h->vq;
+            k.state = h->st;
+            k.mask = M_ACTIVE;
+            k.dot_part = h->mu_part;
+            k.slot_stride = h->slot_stride;
+            k.slot_base = nslots_mu;
+            CK(launch_kb<T>(k, nrhs, h->stream));
+            nslots_mu += 1;
+            launches += 1;
+        }
     }
     CK(launch_alpha(h->st, h->mu_part, nslots_mu, h->slot_stride, nrhs, h->stream));
     launches += 1;
-    C* pb[2] = {(C*)h->vp[0], (C*)h->vp[1]};
     bool fused = false;
     if (fourier_precond(h)) {
         // x += alpha p, r -= alpha q fused with the forward plane FFTs of the preconditioner
@@ -559,8 +643,9 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
         f.dot_part = h->rho_part;
         f.nrm_part = h->rr_part;
         f.slot_stride = h->slot_stride;
-        const cudaError_t e = launch_update_precond_fourier<T>(f, nrhs, h->stream, (C*)h->vx,
-                                                               (C*)h->vr, pb, (const C*)h->vq);
+        const cudaError_t e = launch_update_precond_fourier<T>(
+            f, nrhs, h->stream, (C*)h->vx, (C*)h->vr, pb, (const C*)h->vq, kev,
+            timed ? h->profile - 1 : 0);
         if (e == cudaSuccess) {
             fused = true;
             launches += 3;
@@ -577,8 +662,12 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     }
     // FP64 residual replacement of the RHS that became PENDING since the last one
     // (masked launches), every kReplaceEvery-th iteration of the captured chunk
-    if (replace_now)
-        return residual_replacement<T>(h, nrhs, M_PENDING, mixed, launches);
+    if (replace_now) {
+        launches += 1;   // the condition kernel
+        return captured_if_any(h, nrhs, M_PENDING, [&]() {
+            return residual_replacement<T>(h, nrhs, M_PENDING, mixed, launches);
+        });
+    }
     return IOBM_OK;
 }
 
@@ -1311,6 +1400,7 @@ void iobm_default_options(iobm_options* o) {
     o->refine_delta = 0.01;
     o->chunk = 32;
     o->max_iter_mixed = 1000;
+    o->op_form = IOBM_OP_AUTO;
 }
 
 const char* iobm_status_string(int s) {
@@ -1360,7 +1450,8 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     if (!(h->opt.tol > 0) || h->opt.max_iter < 1 || h->opt.max_iter_mixed < 1 ||
         !(h->opt.refine_delta > 0 && h->opt.refine_delta < 1) ||
         (h->opt.precision != IOBM_FP64 && h->opt.precision != IOBM_MIXED) || !(h->opt.alpha > 0) ||
-        h->opt.use_precond < IOBM_PRECOND_NONE || h->opt.use_precond > IOBM_PRECOND_EQ10_FOURIER)
+        h->opt.use_precond < IOBM_PRECOND_NONE || h->opt.use_precond > IOBM_PRECOND_EQ10_FOURIER ||
+        (h->opt.op_form != IOBM_OP_AUTO && h->opt.op_form != IOBM_OP_EXPLICIT))
         return bad(IOBM_E_ARG, "invalid solver options");
     h->nxy = g.nx * g.ny;
     h->npts = (long long)h->nxy * g.nz;
@@ -1390,7 +1481,10 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     h->w = fd_weights(g.nf);
 
     h->user_stream = (cudaStream_t)cuda_stream;
+    if (const char* env = std::getenv("IOBM_GRAPH_CONDITIONALS"))
+        h->graph_conditionals = std::strcmp(env, "0") != 0;
     cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cond_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sync, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t1);
@@ -1474,6 +1568,7 @@ void iobm_destroy(iobm_handle* h) {
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
     for (cudaEvent_t ev : h->kev) cudaEventDestroy(ev);
     if (h->stream) cudaStreamDestroy(h->stream);
+    if (h->cond_stream) cudaStreamDestroy(h->cond_stream);
     delete h;
 }
 
@@ -1891,7 +1986,8 @@ int iobm_channels_host(const iobm_grid* g, double E, int* n_open, int max_out, i
 
 int iobm_profile(iobm_handle* h, int enable) {
     if (!h) return IOBM_E_ARG;
-    h->profile = enable ? 1 : 0;
+    if (enable < 0 || enable > 4) return IOBM_E_ARG;
+    h->profile = enable;
     h->prof_ms = 0.0;
     h->prof_launches = 0;
     return IOBM_OK;

@@ -43,7 +43,7 @@ __device__ __forceinline__ int ct_bfly_out(const C* src, int ss, int j, const C*
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         C u = src[(j + r * NR) * ss];
-        if (r) {
+        if (r && NS > 1) {   // the first pass has k = 0: every twiddle is 1
             C w = tw[(r * k * TS) % N];
             if (inv) w.y = -w.y;
             u = cmul(u, w);
@@ -62,6 +62,19 @@ __device__ __forceinline__ int ct_bfly_out(const C* src, int ss, int j, const C*
         o[2] = csub(a0, a2);
         o[1] = cadd(a1, a3);
         o[3] = csub(a1, a3);
+    } else if constexpr (R == 3) {
+        // w = exp(-+2 pi i / 3) = -1/2 -+ i sqrt(3)/2
+        using T = decltype(v[0].x);
+        const T c = (T)-0.5, sn = (T)0.86602540378443864676;
+        const C t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+        o[0] = cadd(v[0], t1);
+        C m;
+        m.x = v[0].x + c * t1.x;
+        m.y = v[0].y + c * t1.y;
+        C js;   // -i sn t2 (forward) or +i sn t2 (inverse)
+        if (inv) { js.x = -sn * t2.y; js.y = sn * t2.x; } else { js.x = sn * t2.y; js.y = -sn * t2.x; }
+        o[1] = cadd(m, js);
+        o[2] = csub(m, js);
     } else {
 #pragma unroll
         for (int aa = 0; aa < R; ++aa) {

@@ -159,6 +159,8 @@ struct KbArgs {
     using C = typename Cplx<T>::type;
     const C* x;
     const C* pnew[2];        // if set: operand = pnew[1 - pbuf] of the RHS (COCG direction)
+    const C* zsrc;           // if set: y -= V_NL zsrc, the dot partial still pairs the operand
+                             // above with the added term (the implicit operator form)
     C* y;                    // y[support] -= V_NL x
     int nproj;
     const int* pptr;         // [nproj+1] projector CSR
@@ -203,11 +205,14 @@ struct PrecondArgs {
 };
 
 template <typename T> cudaError_t launch_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s);
+// ev (optional): a pair of events recorded around stage `timed` (1 the update +
+// forward FFT, 2 the z-sweeps, 3 the inverse FFT + dots)
 template <typename T>
 cudaError_t launch_update_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s,
                                           typename Cplx<T>::type* x, typename Cplx<T>::type* r,
                                           typename Cplx<T>::type* const* pbufs,
-                                          const typename Cplx<T>::type* q);
+                                          const typename Cplx<T>::type* q,
+                                          const cudaEvent_t* ev = nullptr, int timed = 0);
 template <typename T> size_t precond_smem_bytes(int nx, int ny);
 cudaError_t precond_prepare();
 cudaError_t stencil_prepare();
@@ -243,6 +248,14 @@ cudaError_t launch_axpy_update(typename Cplx<T>::type* x, typename Cplx<T>::type
                                typename Cplx<T>::type* const* pbufs,
                                const typename Cplx<T>::type* q, const RhsState* st, int mask,
                                long long npts, int nrhs, cudaStream_t s);
+// The implicit operator form (free-propagator preconditioner M, A = M^{-1} - V - V_NL,
+// z = M r): p = z + beta p_old into pbufs[1 - pbuf], q = (r - V z) + beta q in place, and
+// the p^T q partials in slots [0, nz), one per plane (V_NL z is added by launch_kb with zsrc)
+template <typename T>
+cudaError_t launch_pq_update(const typename Cplx<T>::type* z, const typename Cplx<T>::type* r,
+                             typename Cplx<T>::type* const* pbufs, typename Cplx<T>::type* q,
+                             const T* V, const RhsState* st, int mask, int nx, int ny, int nz,
+                             int nrhs, double2* mu_part, int slot_stride, cudaStream_t s);
 // x64 += x32; x32 = 0 (mixed-precision fold before the FP64 residual)
 cudaError_t launch_fold(double2* x64, float2* x32, const RhsState* st, int mask, long long npts,
                         int nrhs, cudaStream_t s);
@@ -255,6 +268,8 @@ cudaError_t launch_residual(const double2* y, double2* r64, typename Cplx<T>::ty
                             double* rr_part, int slot_stride, int nrhs, cudaStream_t s,
                             int* nslots_out);
 cudaError_t launch_set_status(RhsState* st, int nrhs, int from, int to, cudaStream_t s);
+cudaError_t launch_status_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
+                               int mask, cudaStream_t s);
 cudaError_t launch_batch_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
                               int* counter, int max_chunks, cudaStream_t s);
 cudaError_t launch_check(RhsState* st, const double* rr_part, int nslots, int slot_stride,

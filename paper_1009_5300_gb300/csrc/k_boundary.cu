@@ -280,6 +280,8 @@ cudaError_t launch_sigma(const SigmaArgs<T>& a, int nrhs, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // KB nonlocal term.
+constexpr int kKbBatch = 8;    // support points per lane in flight (projections)
+constexpr int kKbBatch2 = 4;   // union points per thread in flight (application)
 template <typename T>
 __global__ void __launch_bounds__(1024) k_kb(const KbArgs<T> a) {
     using C = typename Cplx<T>::type;
@@ -292,18 +294,34 @@ __global__ void __launch_bounds__(1024) k_kb(const KbArgs<T> a) {
     if (!((1 << st) & a.mask)) return;
     const long long base = (long long)rhs * a.npts;
     const C* xb = a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x;
-    const C* __restrict__ X = xb + base;
+    const C* __restrict__ D = xb + base;                        // dot operand
+    const C* __restrict__ X = (a.zsrc ? a.zsrc : xb) + base;    // projected operand
     C* __restrict__ Y = a.y + base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
-    // phase 1: s_p = E_p * dvol * sum_r p(r) x(r), one warp per projector
+    // phase 1: s_p = E_p * dvol * sum_r p(r) x(r), one warp per projector; each
+    // lane gathers kKbBatch support points at a time (index loads, then the
+    // operand loads, all in flight together)
     for (int p = warp; p < a.nproj; p += nw) {
         T tre = 0, tim = 0;
-        for (int i = a.pptr[p] + lane; i < a.pptr[p + 1]; i += 32) {
-            const C xv = X[a.pidx[i]];
-            const T v = a.pval[i];
-            tre += v * xv.x;
-            tim += v * xv.y;
+        const int e0 = a.pptr[p], e1 = a.pptr[p + 1];
+        for (int i0 = e0 + lane; i0 < e1; i0 += 32 * kKbBatch) {
+            int idx[kKbBatch];
+            T v[kKbBatch];
+#pragma unroll
+            for (int u = 0; u < kKbBatch; ++u) {
+                const int i = i0 + 32 * u;
+                idx[u] = (i < e1) ? a.pidx[i] : -1;
+                v[u] = (i < e1) ? a.pval[i] : (T)0;
+            }
+            C xv[kKbBatch];
+#pragma unroll
+            for (int u = 0; u < kKbBatch; ++u) xv[u] = (idx[u] >= 0) ? X[idx[u]] : czero<C>();
+#pragma unroll
+            for (int u = 0; u < kKbBatch; ++u) {
+                tre += v[u] * xv[u].x;
+                tim += v[u] * xv[u].y;
+            }
         }
         double re = tre, im = tim;
 #pragma unroll
@@ -318,16 +336,34 @@ __global__ void __launch_bounds__(1024) k_kb(const KbArgs<T> a) {
     }
     __syncthreads();
 
-    // phase 2: y(r) -= sum_p p(r) s_p over the union of supports
+    // phase 2: y(r) -= sum_p p(r) s_p over the union of supports, kKbBatch2 union
+    // points per thread at a time
     T tre = 0, tim = 0;
-    for (int u = threadIdx.x; u < a.nunion; u += blockDim.x) {
-        C acc = czero<C>();
-        for (int e = a.uptr[u]; e < a.uptr[u + 1]; ++e) acc = caxpy(a.uval[e], s[a.uproj[e]], acc);
-        const int g = a.uidx[u];
-        Y[g] = csub(Y[g], acc);
-        const C xv = X[g];
-        tre -= xv.x * acc.x - xv.y * acc.y;
-        tim -= xv.x * acc.y + xv.y * acc.x;
+    for (int u0 = threadIdx.x; u0 < a.nunion; u0 += blockDim.x * kKbBatch2) {
+        int g[kKbBatch2], eb[kKbBatch2], ee[kKbBatch2];
+#pragma unroll
+        for (int k = 0; k < kKbBatch2; ++k) {
+            const int u = u0 + k * blockDim.x;
+            const bool ok = u < a.nunion;
+            g[k] = ok ? a.uidx[u] : -1;
+            eb[k] = ok ? a.uptr[u] : 0;
+            ee[k] = ok ? a.uptr[u + 1] : 0;
+        }
+        C yv[kKbBatch2], dv[kKbBatch2];
+#pragma unroll
+        for (int k = 0; k < kKbBatch2; ++k) {
+            yv[k] = (g[k] >= 0) ? Y[g[k]] : czero<C>();
+            dv[k] = (g[k] >= 0) ? D[g[k]] : czero<C>();
+        }
+#pragma unroll
+        for (int k = 0; k < kKbBatch2; ++k) {
+            if (g[k] < 0) continue;
+            C acc = czero<C>();
+            for (int e = eb[k]; e < ee[k]; ++e) acc = caxpy(a.uval[e], s[a.uproj[e]], acc);
+            Y[g[k]] = csub(yv[k], acc);
+            tre -= dv[k].x * acc.x - dv[k].y * acc.y;
+            tim -= dv[k].x * acc.y + dv[k].y * acc.x;
+        }
     }
     double dre = tre, dim = tim, dummy = 0.0;
     if (a.dot_part) {

@@ -166,6 +166,107 @@ template cudaError_t launch_axpy_update<float>(float2*, float2*, float2* const*,
 template cudaError_t launch_axpy_update<double>(double2*, double2*, double2* const*, const double2*,
                                                 const RhsState*, int, long long, int, cudaStream_t);
 
+// Direction and operator update of the implicit operator form.  With the
+// free-propagator preconditioner M = (E - T - Sigma)^{-1} the operator of Eq. 7 is
+// A = M^{-1} - V - V_NL, and z = M r gives A z = r - V z - V_NL z, hence for
+// p = z + beta p_old:  q = A p = (r - V z) + beta q_old - V_NL z  (the last term
+// from k_kb).  One CTA per (plane, RHS); mu = p^T q partial per plane.
+template <typename C, typename T>
+__device__ __forceinline__ void pq_point(const C zv, const C rv, const T v, const C* pold,
+                                         const C* qold, bool first, C be, C& pv, C& qv) {
+    qv.x = rv.x - v * zv.x;
+    qv.y = rv.y - v * zv.y;
+    if (first) {
+        pv = zv;
+    } else {
+        pv = cfma(be, *pold, zv);
+        qv = cfma(be, *qold, qv);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pq_update(const typename Cplx<T>::type* __restrict__ z,
+                                                   const typename Cplx<T>::type* __restrict__ r,
+                                                   typename Cplx<T>::type* p0,
+                                                   typename Cplx<T>::type* p1,
+                                                   typename Cplx<T>::type* __restrict__ q,
+                                                   const T* __restrict__ V, const RhsState* st,
+                                                   int mask, int nxy, long long npts,
+                                                   double2* mu_part, int slot_stride) {
+    using C = typename Cplx<T>::type;
+    __shared__ double red[3 * 8];
+    const int rhs = blockIdx.y;
+    const RhsState& S = st[rhs];
+    if (!((1 << S.status) & mask)) return;
+    const bool first = S.first != 0;
+    const C be = from_d2<C>(S.beta);
+    const long long off = (long long)rhs * npts + (long long)blockIdx.x * nxy;
+    const C* __restrict__ pold = ((S.pbuf & 1) ? p1 : p0) + off;
+    C* __restrict__ pnew = ((S.pbuf & 1) ? p0 : p1) + off;
+    const C* __restrict__ zp = z + off;
+    const C* __restrict__ rp = r + off;
+    C* __restrict__ qp = q + off;
+    const T* __restrict__ Vp = V + (long long)blockIdx.x * nxy;
+    T mre = 0, mim = 0;
+    if (sizeof(T) == 4 && (nxy & 1) == 0) {
+        // two complex FP32 values per 16-byte access (every plane starts 16-byte aligned)
+        const int n2 = nxy >> 1;
+        for (int j = threadIdx.x; j < n2; j += blockDim.x) {
+            const float4 z4 = reinterpret_cast<const float4*>(zp)[j];
+            const float4 r4 = reinterpret_cast<const float4*>(rp)[j];
+            const float2 v2 = reinterpret_cast<const float2*>(Vp)[j];
+            float4 po4 = make_float4(0.f, 0.f, 0.f, 0.f), qo4 = po4;
+            if (!first) {
+                po4 = reinterpret_cast<const float4*>(pold)[j];
+                qo4 = reinterpret_cast<const float4*>(qp)[j];
+            }
+            C pa, qa, pb, qb;
+            const C poa = {po4.x, po4.y}, pob = {po4.z, po4.w};
+            const C qoa = {qo4.x, qo4.y}, qob = {qo4.z, qo4.w};
+            pq_point<C, T>(C{z4.x, z4.y}, C{r4.x, r4.y}, (T)v2.x, &poa, &qoa, first, be, pa, qa);
+            pq_point<C, T>(C{z4.z, z4.w}, C{r4.z, r4.w}, (T)v2.y, &pob, &qob, first, be, pb, qb);
+            reinterpret_cast<float4*>(pnew)[j] = make_float4(pa.x, pa.y, pb.x, pb.y);
+            reinterpret_cast<float4*>(qp)[j] = make_float4(qa.x, qa.y, qb.x, qb.y);
+            mre += pa.x * qa.x - pa.y * qa.y;
+            mim += pa.x * qa.y + pa.y * qa.x;
+            mre += pb.x * qb.x - pb.y * qb.y;
+            mim += pb.x * qb.y + pb.y * qb.x;
+        }
+    } else {
+        for (int j = threadIdx.x; j < nxy; j += blockDim.x) {
+            C pv, qv;
+            pq_point<C, T>(zp[j], rp[j], Vp[j], pold + j, qp + j, first, be, pv, qv);
+            pnew[j] = pv;
+            qp[j] = qv;
+            mre += pv.x * qv.x - pv.y * qv.y;
+            mim += pv.x * qv.y + pv.y * qv.x;
+        }
+    }
+    double a0 = mre, a1 = mim, a2 = 0.0;
+    block_reduce_3(a0, a1, a2, red);
+    if (threadIdx.x == 0) mu_part[(long long)rhs * slot_stride + blockIdx.x] = make_double2(a0, a1);
+}
+
+template <typename T>
+cudaError_t launch_pq_update(const typename Cplx<T>::type* z, const typename Cplx<T>::type* r,
+                             typename Cplx<T>::type* const* pbufs, typename Cplx<T>::type* q,
+                             const T* V, const RhsState* st, int mask, int nx, int ny, int nz,
+                             int nrhs, double2* mu_part, int slot_stride, cudaStream_t s) {
+    const int nxy = nx * ny;
+    const long long npts = (long long)nxy * nz;
+    const int threads = nxy >= 4096 ? 256 : 128;
+    dim3 grid(nz, nrhs);
+    k_pq_update<T><<<grid, threads, 0, s>>>(z, r, pbufs[0], pbufs[1], q, V, st, mask, nxy, npts,
+                                            mu_part, slot_stride);
+    return cudaGetLastError();
+}
+template cudaError_t launch_pq_update<float>(const float2*, const float2*, float2* const*, float2*,
+                                             const float*, const RhsState*, int, int, int, int,
+                                             int, double2*, int, cudaStream_t);
+template cudaError_t launch_pq_update<double>(const double2*, const double2*, double2* const*,
+                                              double2*, const double*, const RhsState*, int, int,
+                                              int, int, int, double2*, int, cudaStream_t);
+
 __global__ void k_fold(double2* __restrict__ x64, float2* __restrict__ x32, const RhsState* st,
                        int mask, long long npts) {
     const int rhs = blockIdx.y;
@@ -485,6 +586,21 @@ __global__ void k_batch_cond(cudaGraphConditionalHandle cond, const RhsState* st
         *counter = c;
         cudaGraphSetConditional(cond, (live && c < max_chunks) ? 1u : 0u);
     }
+}
+
+// IF-node condition: 1 when some RHS has a status bit in `mask`
+__global__ void k_status_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
+                              int mask) {
+    int any = 0;
+    for (int i = threadIdx.x; i < nrhs; i += blockDim.x) any |= (1 << st[i].status) & mask;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
+}
+
+cudaError_t launch_status_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
+                               int mask, cudaStream_t s) {
+    k_status_cond<<<1, 256, 0, s>>>(cond, st, nrhs, mask);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,

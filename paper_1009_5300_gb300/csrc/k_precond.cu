@@ -531,21 +531,33 @@ template <typename T>
 cudaError_t launch_update_precond_fourier(const PrecondArgs<T>& a, int nrhs, cudaStream_t s,
                                           typename Cplx<T>::type* x, typename Cplx<T>::type* r,
                                           typename Cplx<T>::type* const* pbufs,
-                                          const typename Cplx<T>::type* q) {
+                                          const typename Cplx<T>::type* q,
+                                          const cudaEvent_t* ev, int timed) {
     if (!ct_size(a.nx, a.ny)) return cudaErrorNotSupported;
-    cudaError_t e = launch_fwd_ct<T>(a, nrhs, s, x, r, pbufs[0], pbufs[1], q, 1);
-    if (e != cudaSuccess) return e;
-    e = launch_zsolve<T>(a, nrhs, s);
-    if (e != cudaSuccess) return e;
-    return launch_inv_ct<T>(a, nrhs, s);
+    // event record nodes when captured into a graph
+    auto mark = [&](int stage, int k) {
+        return (ev && timed == stage) ? cudaEventRecordWithFlags(ev[k], s, cudaEventRecordExternal)
+                                      : cudaSuccess;
+    };
+    cudaError_t e = mark(1, 0);
+    if (e == cudaSuccess) e = launch_fwd_ct<T>(a, nrhs, s, x, r, pbufs[0], pbufs[1], q, 1);
+    if (e == cudaSuccess) e = mark(1, 1);
+    if (e == cudaSuccess) e = mark(2, 0);
+    if (e == cudaSuccess) e = launch_zsolve<T>(a, nrhs, s);
+    if (e == cudaSuccess) e = mark(2, 1);
+    if (e == cudaSuccess) e = mark(3, 0);
+    if (e == cudaSuccess) e = launch_inv_ct<T>(a, nrhs, s);
+    if (e == cudaSuccess) e = mark(3, 1);
+    return e;
 }
 
 template cudaError_t launch_update_precond_fourier<float>(const PrecondArgs<float>&, int, cudaStream_t,
                                                           float2*, float2*, float2* const*,
-                                                          const float2*);
+                                                          const float2*, const cudaEvent_t*, int);
 template cudaError_t launch_update_precond_fourier<double>(const PrecondArgs<double>&, int,
                                                            cudaStream_t, double2*, double2*,
-                                                           double2* const*, const double2*);
+                                                           double2* const*, const double2*,
+                                                           const cudaEvent_t*, int);
 
 template size_t precond_smem_bytes<float>(int, int);
 template size_t precond_smem_bytes<double>(int, int);

@@ -57,6 +57,8 @@ def default_options(**kw) -> _lib.Options:
             v = {"none": _lib.IOBM_PRECOND_NONE, "eq10": _lib.IOBM_PRECOND_EQ10,
                  "fourier": _lib.IOBM_PRECOND_FOURIER,
                  "eq10_fourier": _lib.IOBM_PRECOND_EQ10_FOURIER}[v]
+        if k == "op_form" and isinstance(v, str):
+            v = {"auto": _lib.IOBM_OP_AUTO, "explicit": _lib.IOBM_OP_EXPLICIT}[v]
         setattr(o, k, v)
     return o
 
@@ -272,11 +274,18 @@ class IOBMSolver:
             Vn = np.ascontiguousarray(np.asarray(V, np.float64).reshape(self.shape))
             check(self.lib.iobm_set_potential(self.h, _ptr(Vn), 0), self.h)
 
-    def profile(self, enable: bool = True):
-        check(self.lib.iobm_profile(self.h, 1 if enable else 0), self.h)
+    PROFILE_STAGES = {"operator": 1, "update_fft": 2, "zsweep": 3, "ifft": 4}
+
+    def profile(self, enable=True):
+        """Time one kernel of every captured COCG iteration with CUDA events: True or
+        "operator" (the fused stencil, or the direction/operator update of the implicit
+        form), "update_fft" (x, r update + forward plane FFTs), "zsweep", "ifft"
+        (inverse FFTs + dot partials); False stops."""
+        stage = self.PROFILE_STAGES[enable] if isinstance(enable, str) else (1 if enable else 0)
+        check(self.lib.iobm_profile(self.h, stage), self.h)
 
     def kernel_stats(self):
-        """(total ms, launches) of the timed fused-stencil launches since profile(True)."""
+        """(total ms, launches) of the kernel timed since profile(...)."""
         ms = C.c_double(0)
         n = C.c_longlong(0)
         check(self.lib.iobm_kernel_stats(self.h, C.byref(ms), C.byref(n)), self.h)

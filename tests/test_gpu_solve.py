@@ -59,13 +59,16 @@ def test_wire16(wire16_oracle, precision):
 
 @pytest.mark.parametrize("nf", [1, 4])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("precond", ["fourier", "eq10"])
+@pytest.mark.parametrize("precond", ["fourier", "fourier_explicit", "eq10"])
 def test_multichannel_kb(nf, precision, precond):
     from paper_1009_5300_gb300 import IOBMSolver
     jn = kb_junction(nf)
     E = jn.e_fermi
     ref = transport.solve(jn, E)
-    sol = IOBMSolver.from_junction(jn, precision=precision, use_precond=precond)
+    kw = {"use_precond": precond}
+    if precond == "fourier_explicit":   # stencil + self-energy + projectors every iteration
+        kw = {"use_precond": "fourier", "op_form": "explicit"}
+    sol = IOBMSolver.from_junction(jn, precision=precision, **kw)
     res = sol.solve([E])
     assert ref.n_open >= 3
     compare(res, ref)
@@ -89,6 +92,46 @@ def test_eq10_fourier_form_solve():
         sol.close()
     # different rounding over ~200 Krylov steps moves the counts by a few per cent
     assert np.max(np.abs(its[0] - its[1])) <= 0.05 * np.max(its[0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_implicit_operator_form(precision):
+    # with the free-propagator preconditioner, q = A p formed as (r - V z) + beta q_old
+    # - V_NL z drives the same Krylov iteration as the explicit operator: both reach
+    # the oracle's solution, with iteration counts a rounding-level apart
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = kb_junction(4)
+    Es = [jn.e_fermi - 0.02, jn.e_fermi]
+    its, stage_ms = {}, {}
+    for form in ("auto", "explicit"):
+        sol = IOBMSolver.from_junction(jn, precision=precision, op_form=form)
+        sol.profile("operator")
+        res = sol.solve(Es)
+        stage_ms[form] = sol.kernel_stats()
+        sol.profile(False)
+        assert res.converged, res.status
+        assert np.all(res.residual <= 1e-8)
+        for e, E in enumerate(Es):
+            assert abs(res.G[e] - transport.conductance(jn, E)) < G_TOL
+        its[form] = res.iterations.astype(float)
+        sol.close()
+    for form in its:
+        assert stage_ms[form][1] > 0 and stage_ms[form][0] > 0
+    assert its["auto"].mean() <= 1.2 * its["explicit"].mean() + 2
+
+
+def test_profile_stages():
+    # every timed stage of the fused Fourier preconditioner reports launches
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = kb_junction(4)
+    sol = IOBMSolver.from_junction(jn, precision="mixed")
+    for stage in ("operator", "update_fft", "zsweep", "ifft"):
+        sol.profile(stage)
+        sol.solve([jn.e_fermi])
+        ms, n = sol.kernel_stats()
+        assert n > 0 and ms > 0, stage
+    sol.profile(False)
+    sol.close()
 
 
 def test_precision_escalation():
