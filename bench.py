@@ -32,8 +32,8 @@ UNIT = "channel-solves/s"
 # Roofline kernels: per COCG iteration kernel, the algorithmic HBM bytes per
 # RHS-point (complex FP32 vectors, 8 B per element) and per grid point of a launch,
 # and the measured DRAM bytes per RHS-point (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch with all 56 RHS of the 8-energy wire48 case
-# active), None until captured for the kernel as it stands.
+# dram__bytes_write.sum of one launch of the first COCG iteration with all 56 RHS of
+# the 8-energy wire48 case active), None until captured for the kernel as it stands.
 ROOFLINE_KERNELS = {
     # p = z + beta p_old, q = (r - V z) + beta q_old: read z r p_old q_old, write p q
     "operator": {"kernel": "k_pq_update<float> (implicit operator form: direction and "
@@ -41,10 +41,11 @@ ROOFLINE_KERNELS = {
                  "bytes_rhs_point": 48.0, "bytes_point": 4.0, "dram_rhs_point": None},
     # x += alpha p, r -= alpha q, forward plane FFTs: read x p r q, write x r spectrum
     "update_fft": {"kernel": "k_update_fft_ct<float,48> (x, r update + forward plane FFTs)",
-                   "bytes_rhs_point": 56.0, "bytes_point": 0.0, "dram_rhs_point": None},
-    # z-sweeps: read and write the spectrum
+                   "bytes_rhs_point": 56.0, "bytes_point": 0.0,
+                   "dram_rhs_point": (660657920 + 435025664) / (56 * 368640)},
+    # z-sweeps in place: read the spectrum, write the forward sweep, read it back, write z
     "zsweep": {"kernel": "k_zsolve<float,4> (free-propagator z-sweeps per lateral mode)",
-               "bytes_rhs_point": 16.0, "bytes_point": 0.0, "dram_rhs_point": None},
+               "bytes_rhs_point": 32.0, "bytes_point": 0.0, "dram_rhs_point": None},
     # inverse plane FFTs + dots: read spectrum and r, write z
     "ifft": {"kernel": "k_ifft_dots_ct<float,48> (inverse plane FFTs + r^T z, |r|^2 partials)",
              "bytes_rhs_point": 24.0, "bytes_point": 0.0, "dram_rhs_point": None},

@@ -102,6 +102,7 @@ struct iobm_handle {
     int stencil_variant = 0;             // StencilArgs::variant (autotuned)
     DevBuf batch_ctr;                    // chunk counter of this junction in a batched solve
     DevBuf sig_scratch;                  // large-plane self-energy spectra
+    DevBuf kb_scratch;                  // KB projections [rhs][projector]
     DevBuf esc_ws, esc_descs, esc_rhs_energy;   // FP64 continuation of stalled mixed RHS
     cudaGraphExec_t chunk_exec = nullptr;        // the last solve's chunk graph, updated in place
     void* pin = nullptr;                         // pinned staging buffer for table uploads
@@ -197,8 +198,9 @@ int sigma_slots(const iobm_handle* h) { return 2 * h->nf * plane_slots(h); }
 int slots_for(const iobm_handle* h) {
     const int ns_op = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, h->nf);
     const int ns_pc = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, 1);
-    return std::max(std::max(ns_op + sigma_slots(h) + 1, 64),
-                    std::max(std::max(h->g.nz * plane_slots(h), ns_pc), h->g.nz + 1));
+    const int kb = h->pt.nproj > 0 ? kb_slots((int)h->pt.uidx.size()) : 0;
+    return std::max(std::max(ns_op + sigma_slots(h) + kb, 64),
+                    std::max(std::max(h->g.nz * plane_slots(h), ns_pc), h->g.nz + kb));
 }
 
 // number of rho / |r|^2 partial slots the preconditioner pass writes
@@ -210,6 +212,10 @@ int rho_slots(const iobm_handle* h) {
 
 // scratch of the large-plane self-energy (compact end-plane spectra, in and out)
 cudaError_t ensure_sigma_scratch(iobm_handle* h, int nrhs) {
+    if (h->pt.nproj > 0) {   // KB projections per (RHS, projector)
+        const cudaError_t e = h->kb_scratch.ensure((size_t)std::max(nrhs, 1) * h->pt.nproj * sizeof(double2));
+        if (e != cudaSuccess) return e;
+    }
     if (!large_plane(h)) return cudaSuccess;
     return h->sig_scratch.ensure(2 * (size_t)std::max(nrhs, 1) * 2 * h->nf * h->nxy * sizeof(double2));
 }
@@ -392,6 +398,7 @@ KbArgs<T> kb_args(const iobm_handle* h) {
     a.uval = std::is_same<T, float>::value ? (const T*)h->uval32.p : (const T*)h->uval64.p;
     a.npts = h->npts;
     a.mask = M_ALL;
+    a.sp = (typename Cplx<T>::type*)h->kb_scratch.p;
     return a;
 }
 
@@ -425,7 +432,7 @@ int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void*
         k.state = st;
         k.mask = mask;
         CK(launch_kb<T>(k, nrhs, h->stream));
-        launches += 1;
+        launches += 2;
     }
     return IOBM_OK;
 }
@@ -575,8 +582,8 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
             k.slot_stride = h->slot_stride;
             k.slot_base = nslots_mu;
             CK(launch_kb<T>(k, nrhs, h->stream));
-            nslots_mu += 1;
-            launches += 1;
+            nslots_mu += kb_slots(k.nunion);
+            launches += 2;
         }
     } else {
         const void* sig = std::is_same<T, float>::value ? h->sig32.p : h->sig64.p;
@@ -624,8 +631,8 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
             k.slot_stride = h->slot_stride;
             k.slot_base = nslots_mu;
             CK(launch_kb<T>(k, nrhs, h->stream));
-            nslots_mu += 1;
-            launches += 1;
+            nslots_mu += kb_slots(k.nunion);
+            launches += 2;
         }
     }
     CK(launch_alpha(h->st, h->mu_part, nslots_mu, h->slot_stride, nrhs, h->stream));
@@ -1561,7 +1568,9 @@ void iobm_destroy(iobm_handle* h) {
                       &h->uptr, &h->uproj, &h->uval32, &h->uval64, &h->sig32, &h->sig64, &h->pc32,
                       &h->pc64, &h->ediag, &h->rhs_energy, &h->descs, &h->open_ptr, &h->open_bins,
                       &h->proj_out, &h->apply_sig32, &h->apply_sig64, &h->apply_pc32,
-                      &h->apply_pc64, &h->apply_ediag, &h->ws_owned};
+                      &h->apply_pc64, &h->apply_ediag, &h->ws_owned, &h->errflag,
+                      &h->batch_ctr, &h->sig_scratch, &h->kb_scratch, &h->esc_ws,
+                      &h->esc_descs, &h->esc_rhs_energy};
     for (DevBuf* b : bufs) b->release();
     if (h->ev_sync) cudaEventDestroy(h->ev_sync);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);

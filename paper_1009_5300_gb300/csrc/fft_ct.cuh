@@ -10,6 +10,9 @@
 #include "iobm_internal.cuh"
 #include "complex_ops.cuh"
 
+#include <type_traits>
+#include <utility>
+
 namespace iobm {
 
 // Radix sequence of an N-point transform.  Twiddles (tw[t] = exp(-2 pi i t / N))
@@ -44,7 +47,8 @@ __device__ __forceinline__ int ct_bfly_out(const C* src, int ss, int j, const C*
     for (int r = 0; r < R; ++r) {
         C u = src[(j + r * NR) * ss];
         if (r && NS > 1) {   // the first pass has k = 0: every twiddle is 1
-            C w = tw[(r * k * TS) % N];
+            // r k TS <= (R - 1)(NS - 1) N / (NS R) < N: no reduction mod N needed
+            C w = tw[r * k * TS];
             if (inv) w.y = -w.y;
             u = cmul(u, w);
         }
@@ -100,23 +104,49 @@ __device__ __forceinline__ void ct_bfly(const C* src, int ss, C* dst, int ds, in
     for (int r = 0; r < R; ++r) dst[(base + r * NS) * ds] = o[r];
 }
 
-// all passes of N-point transforms along `lines` lines (line stride ls, element stride es)
-template <typename C, int N, int P, int NS>
+// all passes of N-point transforms along N lines (line stride ls, element stride es)
+// by a CTA of NT threads
+template <typename C, int N, int P, int NS, int NT>
 __device__ __forceinline__ void ct_passes(C*& cur, C*& oth, int ls, int es, const C* tw, bool inv) {
     if constexpr (P < CtPlan<N>::npass) {
         constexpr int R = CtPlan<N>::radix(P);
-        constexpr int PER = N / R;
+        constexpr int NB = N * (N / R);   // butterflies of the pass
         // line index fastest: a row pass then touches elements line * (N + 1) + c,
         // an odd stride that spreads 16 consecutive lines over 16 different 8-byte
         // bank pairs, and a column pass touches consecutive elements
-        for (int t = threadIdx.x; t < N * PER; t += blockDim.x) {
-            const int line = t % N, j = t / N;
-            ct_bfly<C, N, NS, R>(cur + line * ls, es, oth + line * ls, es, j, tw, inv);
+#pragma unroll
+        for (int k = 0; k < (NB + NT - 1) / NT; ++k) {
+            const int t = threadIdx.x + k * NT;
+            if (NB % NT == 0 || t < NB) {
+                const int line = t % N, j = t / N;
+                ct_bfly<C, N, NS, R>(cur + line * ls, es, oth + line * ls, es, j, tw, inv);
+            }
         }
         __syncthreads();
         C* s = cur; cur = oth; oth = s;
-        ct_passes<C, N, P + 1, NS * R>(cur, oth, ls, es, tw, inv);
+        ct_passes<C, N, P + 1, NS * R, NT>(cur, oth, ls, es, tw, inv);
     }
+}
+
+// f(std::integral_constant<int, k>) for k = 0 .. K-1 (compile-time loop index)
+template <int K, typename F, int... I>
+__device__ __forceinline__ void ct_for_impl(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int K, typename F>
+__device__ __forceinline__ void ct_for(F&& f) {
+    ct_for_impl<K>(f, std::make_integer_sequence<int, K>{});
+}
+
+// Row-major element i = tid + K NT of an N x N plane, as its index in the padded
+// shared-memory layout (rows of pitch PT), from the thread's first row and column
+// (row0, col0) = (tid / N, tid % N): the step K NT is a compile-time constant, so
+// only a compare and adds remain.
+template <int N, int NT, int PT, int K>
+__device__ __forceinline__ int ct_padded_index(int row0, int col0) {
+    constexpr int dr = (K * NT) / N, dc = (K * NT) % N;
+    const int c = col0 + dc;
+    return (c >= N) ? (row0 + dr + 1) * PT + (c - N) : (row0 + dr) * PT + c;
 }
 
 // Output positions of the last column pass for a CTA of NT threads: thread tid
@@ -147,9 +177,13 @@ __device__ __forceinline__ void ct_col_passes_store(C*& cur, C*& oth, int pitch,
     constexpr int R = CtPlan<N>::radix(P);
     constexpr int PER = N / R;
     if constexpr (P + 1 < CtPlan<N>::npass) {
-        for (int t = threadIdx.x; t < N * PER; t += NT) {
-            const int line = t % N, j = t / N;
-            ct_bfly<C, N, NS, R>(cur + line, pitch, oth + line, pitch, j, tw, inv);
+#pragma unroll
+        for (int k = 0; k < (N * PER + NT - 1) / NT; ++k) {
+            const int t = threadIdx.x + k * NT;
+            if ((N * PER) % NT == 0 || t < N * PER) {
+                const int line = t % N, j = t / N;
+                ct_bfly<C, N, NS, R>(cur + line, pitch, oth + line, pitch, j, tw, inv);
+            }
         }
         __syncthreads();
         C* s = cur; cur = oth; oth = s;
@@ -176,13 +210,13 @@ template <int N> struct CtPitch { static constexpr int P = N + 1; };
 
 // 2D FFT of an N x N plane in shared memory (a, rows of pitch N+1), b scratch of
 // the same shape; returns the buffer that holds the result
-template <typename C, int N>
+template <typename C, int N, int NT>
 __device__ __forceinline__ C* ct_fft2(C* a, C* b, const C* tw, bool inv) {
     constexpr int P = CtPitch<N>::P;
     C* cur = a;
     C* oth = b;
-    ct_passes<C, N, 0, 1>(cur, oth, P, 1, tw, inv);   // rows
-    ct_passes<C, N, 0, 1>(cur, oth, 1, P, tw, inv);   // columns
+    ct_passes<C, N, 0, 1, NT>(cur, oth, P, 1, tw, inv);   // rows
+    ct_passes<C, N, 0, 1, NT>(cur, oth, 1, P, tw, inv);   // columns
     return cur;
 }
 
@@ -193,7 +227,7 @@ __device__ __forceinline__ void ct_fft2_store(C* a, C* b, const C* tw, bool inv,
     constexpr int P = CtPitch<N>::P;
     C* cur = a;
     C* oth = b;
-    ct_passes<C, N, 0, 1>(cur, oth, P, 1, tw, inv);   // rows
+    ct_passes<C, N, 0, 1, NT>(cur, oth, P, 1, tw, inv);   // rows
     ct_col_passes_store<C, N, 0, 1, NT>(cur, oth, P, tw, inv, store);
 }
 

@@ -175,10 +175,14 @@ struct KbArgs {
     const T* uval;           // value of each entry
     const RhsState* state;
     int mask;
-    double2* dot_part;
+    double2* dot_part;       // one partial per application CTA: slots slot_base + [0, kb_slots)
     int slot_stride, slot_base;
     long long npts;
+    C* sp;                   // scratch [rhs][nproj]: E_p dvol <p|x>
 };
+
+// dot-product partial slots the KB application writes per RHS
+int kb_slots(int nunion);
 
 constexpr int kPcStrideDev = 25;   // per-mode preconditioner table stride (nf = 4)
 

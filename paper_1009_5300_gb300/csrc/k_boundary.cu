@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kSigmaCtThreads) k_sigma_ct(const SigmaArgs<T>
         }
     }
     __syncthreads();
-    ct_fft2<C, N>(A, B, tw, false);   // an even number of passes: the spectrum is in A
+    ct_fft2<C, N, kSigmaCtThreads>(A, B, tw, false);   // an even number of passes: the spectrum is in A
 
     cluster.sync();   // every spectrum of the cluster is complete
 
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kSigmaCtThreads) k_sigma_ct(const SigmaArgs<T>
         if (m < NXY) A[(m / N) * PT + (m % N)] = out[j];
     }
     __syncthreads();
-    ct_fft2<C, N>(A, B, tw, true);
+    ct_fft2<C, N, kSigmaCtThreads>(A, B, tw, true);
 
     T tre = 0, tim = 0;
 #pragma unroll
@@ -279,111 +279,165 @@ cudaError_t launch_sigma(const SigmaArgs<T>& a, int nrhs, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// KB nonlocal term.
-constexpr int kKbBatch = 8;    // support points per lane in flight (projections)
-constexpr int kKbBatch2 = 4;   // union points per thread in flight (application)
+// KB nonlocal term, y -= sum_p |p> E_p dvol <p|x>, in two kernels: the
+// projections (one CTA per (projector, group of kKbRhs RHS), the support split
+// over the CTA's threads and reduced in a fixed order) into a [rhs][projector]
+// scratch, then the application over the union of supports (one thread per
+// union point and RHS group) with the partials of the dot product x'^T (-V_NL x)
+// per CTA.  The index tables are loaded once per RHS group and the operand
+// gathers of the group's RHS are in flight together.
+constexpr int kKbProjThreads = 128;
+constexpr int kKbBatch = 4;            // support points per thread and RHS in flight
+constexpr int kKbApplyThreads = 256;
+constexpr int kKbRhs = 4;              // RHS per CTA
+
+int kb_slots(int nunion) { return (nunion + kKbApplyThreads - 1) / kKbApplyThreads; }
+
 template <typename T>
-__global__ void __launch_bounds__(1024) k_kb(const KbArgs<T> a) {
-    using C = typename Cplx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);                   // [nproj] E_p-weighted projections
-    double* red = reinterpret_cast<double*>(s + a.nproj);   // block reduction scratch
-
-    const int rhs = blockIdx.x;
+__device__ __forceinline__ bool kb_rhs_live(const KbArgs<T>& a, int rhs, int nrhs) {
+    if (rhs >= nrhs) return false;
     const int st = a.state ? a.state[rhs].status : ST_ACTIVE;
-    if (!((1 << st) & a.mask)) return;
-    const long long base = (long long)rhs * a.npts;
-    const C* xb = a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x;
-    const C* __restrict__ D = xb + base;                        // dot operand
-    const C* __restrict__ X = (a.zsrc ? a.zsrc : xb) + base;    // projected operand
-    C* __restrict__ Y = a.y + base;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    return ((1 << st) & a.mask) != 0;
+}
 
-    // phase 1: s_p = E_p * dvol * sum_r p(r) x(r), one warp per projector; each
-    // lane gathers kKbBatch support points at a time (index loads, then the
-    // operand loads, all in flight together)
-    for (int p = warp; p < a.nproj; p += nw) {
-        T tre = 0, tim = 0;
-        const int e0 = a.pptr[p], e1 = a.pptr[p + 1];
-        for (int i0 = e0 + lane; i0 < e1; i0 += 32 * kKbBatch) {
-            int idx[kKbBatch];
-            T v[kKbBatch];
+template <typename T>
+__global__ void __launch_bounds__(kKbProjThreads) k_kb_proj(const KbArgs<T> a, int nrhs) {
+    using C = typename Cplx<T>::type;
+    __shared__ double red[2 * kKbRhs][kKbProjThreads / 32];
+    const int p = blockIdx.x, r0 = blockIdx.y * kKbRhs;
+    bool live[kKbRhs];
+    const C* X[kKbRhs];
+    bool any = false;
 #pragma unroll
-            for (int u = 0; u < kKbBatch; ++u) {
-                const int i = i0 + 32 * u;
-                idx[u] = (i < e1) ? a.pidx[i] : -1;
-                v[u] = (i < e1) ? a.pval[i] : (T)0;
-            }
-            C xv[kKbBatch];
-#pragma unroll
-            for (int u = 0; u < kKbBatch; ++u) xv[u] = (idx[u] >= 0) ? X[idx[u]] : czero<C>();
-#pragma unroll
-            for (int u = 0; u < kKbBatch; ++u) {
-                tre += v[u] * xv[u].x;
-                tim += v[u] * xv[u].y;
-            }
+    for (int j = 0; j < kKbRhs; ++j) {
+        live[j] = kb_rhs_live(a, r0 + j, nrhs);
+        any |= live[j];
+        X[j] = nullptr;
+        if (live[j]) {
+            const int rhs = r0 + j;
+            const C* xb = a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x;
+            X[j] = (a.zsrc ? a.zsrc : xb) + (long long)rhs * a.npts;   // projected operand
         }
-        double re = tre, im = tim;
+    }
+    if (!any) return;
+    const int e0 = a.pptr[p], e1 = a.pptr[p + 1];
+    T tre[kKbRhs], tim[kKbRhs];
+#pragma unroll
+    for (int j = 0; j < kKbRhs; ++j) tre[j] = tim[j] = 0;
+    for (int i0 = e0 + threadIdx.x; i0 < e1; i0 += kKbProjThreads * kKbBatch) {
+        int idx[kKbBatch];
+        T v[kKbBatch];
+#pragma unroll
+        for (int u = 0; u < kKbBatch; ++u) {
+            const int i = i0 + kKbProjThreads * u;
+            idx[u] = (i < e1) ? a.pidx[i] : -1;
+            v[u] = (i < e1) ? a.pval[i] : (T)0;
+        }
+        C xv[kKbRhs][kKbBatch];
+#pragma unroll
+        for (int j = 0; j < kKbRhs; ++j)
+#pragma unroll
+            for (int u = 0; u < kKbBatch; ++u)
+                xv[j][u] = (live[j] && idx[u] >= 0) ? X[j][idx[u]] : czero<C>();
+#pragma unroll
+        for (int j = 0; j < kKbRhs; ++j)
+#pragma unroll
+            for (int u = 0; u < kKbBatch; ++u) {
+                tre[j] += v[u] * xv[j][u].x;
+                tim[j] += v[u] * xv[j][u].y;
+            }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kKbRhs; ++j) {
+        double re = tre[j], im = tim[j];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             re += __shfl_down_sync(0xffffffffu, re, o);
             im += __shfl_down_sync(0xffffffffu, im, o);
         }
         if (lane == 0) {
-            const double f = a.coupling[p] * a.dvol;
-            s[p] = from_d2<C>(make_double2(re * f, im * f));
+            red[2 * j][warp] = re;
+            red[2 * j + 1][warp] = im;
         }
     }
     __syncthreads();
+    if (threadIdx.x < kKbRhs && live[threadIdx.x]) {
+        const int j = threadIdx.x;
+        double sr = 0.0, si = 0.0;
+        for (int w = 0; w < kKbProjThreads / 32; ++w) {
+            sr += red[2 * j][w];
+            si += red[2 * j + 1][w];
+        }
+        const double f = a.coupling[p] * a.dvol;
+        a.sp[(long long)(r0 + j) * a.nproj + p] = from_d2<C>(make_double2(sr * f, si * f));
+    }
+}
 
-    // phase 2: y(r) -= sum_p p(r) s_p over the union of supports, kKbBatch2 union
-    // points per thread at a time
-    T tre = 0, tim = 0;
-    for (int u0 = threadIdx.x; u0 < a.nunion; u0 += blockDim.x * kKbBatch2) {
-        int g[kKbBatch2], eb[kKbBatch2], ee[kKbBatch2];
+template <typename T>
+__global__ void __launch_bounds__(kKbApplyThreads) k_kb_apply(const KbArgs<T> a, int nrhs) {
+    using C = typename Cplx<T>::type;
+    __shared__ double red[3 * (kKbApplyThreads / 32)];
+    const int r0 = blockIdx.y * kKbRhs;
+    bool live[kKbRhs];
+    bool any = false;
 #pragma unroll
-        for (int k = 0; k < kKbBatch2; ++k) {
-            const int u = u0 + k * blockDim.x;
-            const bool ok = u < a.nunion;
-            g[k] = ok ? a.uidx[u] : -1;
-            eb[k] = ok ? a.uptr[u] : 0;
-            ee[k] = ok ? a.uptr[u + 1] : 0;
-        }
-        C yv[kKbBatch2], dv[kKbBatch2];
+    for (int j = 0; j < kKbRhs; ++j) {
+        live[j] = kb_rhs_live(a, r0 + j, nrhs);
+        any |= live[j];
+    }
+    if (!any) return;
+    const int u = blockIdx.x * kKbApplyThreads + threadIdx.x;
+    const bool in = u < a.nunion;
+    const int g = in ? a.uidx[u] : 0;
+    const int eb = in ? a.uptr[u] : 0, ee = in ? a.uptr[u + 1] : 0;
+    C yv[kKbRhs], dv[kKbRhs], acc[kKbRhs];
 #pragma unroll
-        for (int k = 0; k < kKbBatch2; ++k) {
-            yv[k] = (g[k] >= 0) ? Y[g[k]] : czero<C>();
-            dv[k] = (g[k] >= 0) ? D[g[k]] : czero<C>();
-        }
-#pragma unroll
-        for (int k = 0; k < kKbBatch2; ++k) {
-            if (g[k] < 0) continue;
-            C acc = czero<C>();
-            for (int e = eb[k]; e < ee[k]; ++e) acc = caxpy(a.uval[e], s[a.uproj[e]], acc);
-            Y[g[k]] = csub(yv[k], acc);
-            tre -= dv[k].x * acc.x - dv[k].y * acc.y;
-            tim -= dv[k].x * acc.y + dv[k].y * acc.x;
+    for (int j = 0; j < kKbRhs; ++j) {
+        yv[j] = dv[j] = acc[j] = czero<C>();
+        if (in && live[j]) {
+            const int rhs = r0 + j;
+            const long long base = (long long)rhs * a.npts;
+            yv[j] = a.y[base + g];
+            if (a.dot_part) {
+                const C* xb = a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x;
+                dv[j] = xb[base + g];   // dot operand
+            }
         }
     }
-    double dre = tre, dim = tim, dummy = 0.0;
-    if (a.dot_part) {
-        block_reduce_3(dre, dim, dummy, red);
-        if (threadIdx.x == 0)
-            a.dot_part[(long long)rhs * a.slot_stride + a.slot_base] = make_double2(dre, dim);
+    for (int e = eb; e < ee; ++e) {
+        const T v = a.uval[e];
+        const int pj = a.uproj[e];
+#pragma unroll
+        for (int j = 0; j < kKbRhs; ++j)
+            if (live[j]) acc[j] = caxpy(v, a.sp[(long long)(r0 + j) * a.nproj + pj], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kKbRhs; ++j) {
+        if (in && live[j]) a.y[(long long)(r0 + j) * a.npts + g] = csub(yv[j], acc[j]);
+        if (a.dot_part && live[j]) {   // uniform over the CTA
+            double dre = -(double)(dv[j].x * acc[j].x - dv[j].y * acc[j].y);
+            double dim = -(double)(dv[j].x * acc[j].y + dv[j].y * acc[j].x);
+            double dummy = 0.0;
+            block_reduce_3(dre, dim, dummy, red);
+            if (threadIdx.x == 0)
+                a.dot_part[(long long)(r0 + j) * a.slot_stride + a.slot_base + blockIdx.x] =
+                    make_double2(dre, dim);
+            __syncthreads();   // red is reused by the next RHS
+        }
     }
 }
 
 template <typename T>
 cudaError_t launch_kb(const KbArgs<T>& a, int nrhs, cudaStream_t s) {
-    using C = typename Cplx<T>::type;
     if (a.nproj == 0) return cudaSuccess;
-    const size_t smem = sizeof(C) * a.nproj + 3 * 32 * sizeof(double) + 16;
-    if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(k_kb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-        if (err != cudaSuccess) return err;
-    }
-    k_kb<T><<<nrhs, 1024, smem, s>>>(a);
+    if (!a.sp) return cudaErrorInvalidValue;
+    const int groups = (nrhs + kKbRhs - 1) / kKbRhs;
+    k_kb_proj<T><<<dim3(a.nproj, groups), kKbProjThreads, 0, s>>>(a, nrhs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.nunion == 0) return cudaSuccess;
+    k_kb_apply<T><<<dim3(kb_slots(a.nunion), groups), kKbApplyThreads, 0, s>>>(a, nrhs);
     return cudaGetLastError();
 }
 

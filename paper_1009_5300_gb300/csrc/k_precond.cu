@@ -343,16 +343,17 @@ __global__ void __launch_bounds__(256, 4) k_update_fft_ct(const PrecondArgs<T> a
                 pv[j] = P[i];
             }
         }
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
+        const int row0 = threadIdx.x / N, col0 = threadIdx.x % N;
+        ct_for<PER>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
             const int i = threadIdx.x + j * 256;
-            if (i < NXY) {
+            if (NXY % 256 == 0 || i < NXY) {
                 const C rn = csub(rv[j], cmul(al, qv[j]));
                 R[i] = rn;
-                A[(i / N) * PT + (i % N)] = rn;
+                A[ct_padded_index<N, 256, PT, j>(row0, col0)] = rn;
                 Xv[i] = cfma(al, pv[j], xv[j]);
             }
-        }
+        });
     } else {
         for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[(i / N) * PT + (i % N)] = a.r[off + i];
     }
@@ -362,8 +363,17 @@ __global__ void __launch_bounds__(256, 4) k_update_fft_ct(const PrecondArgs<T> a
                              [&](int row, int col, C v, int) { spec[row * N + col] = v; });
 }
 
+// CTAs of 256 threads per SM that the shared memory of a plane transform
+// (two padded N x N planes and the twiddles) allows, at most 5
 template <typename T, int N>
-__global__ void __launch_bounds__(256, 4) k_ifft_dots_ct(const PrecondArgs<T> a) {
+struct CtOccupancy {
+    static constexpr int kSmem = (int)sizeof(typename Cplx<T>::type) * (2 * N * (N + 1) + N) + 1024;
+    static constexpr int kFit = (227 * 1024) / kSmem;
+    static constexpr int value = kFit < 1 ? 1 : (kFit > 5 ? 5 : kFit);
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256, (CtOccupancy<T, N>::value)) k_ifft_dots_ct(const PrecondArgs<T> a) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[3 * 8];
@@ -376,7 +386,15 @@ __global__ void __launch_bounds__(256, 4) k_ifft_dots_ct(const PrecondArgs<T> a)
     C* tw = B + N * PT;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.twx[i];
     const long long off = (long long)rhs * a.npts + (long long)plane * NXY;
-    for (int i = threadIdx.x; i < NXY; i += blockDim.x) A[(i / N) * PT + (i % N)] = a.spec[off + i];
+    {
+        constexpr int PER = (NXY + 255) / 256;
+        const int row0 = threadIdx.x / N, col0 = threadIdx.x % N;
+        ct_for<PER>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            const int i = threadIdx.x + j * 256;
+            if (NXY % 256 == 0 || i < NXY) A[ct_padded_index<N, 256, PT, j>(row0, col0)] = a.spec[off + i];
+        });
+    }
     // r at the positions this thread's last column pass produces, loaded now so
     // the loads overlap the transform
     using L = CtLastPass<N, 256>;
