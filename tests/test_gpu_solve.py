@@ -120,6 +120,30 @@ def test_implicit_operator_form(precision):
     assert its["auto"].mean() <= 1.2 * its["explicit"].mean() + 2
 
 
+def test_replacement_steps_with_and_without_conditional_nodes(monkeypatch):
+    # the FP64 residual replacements captured as IF nodes (default) and as plain masked
+    # launches (IOBM_GRAPH_CONDITIONALS=0, read when a handle is created) run the same
+    # kernels on the same RHS: bit-identical results
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = kb_junction(4)
+    Es = [jn.e_fermi - 0.02, jn.e_fermi]
+    out = []
+    for flag in (None, "0"):
+        if flag is None:
+            monkeypatch.delenv("IOBM_GRAPH_CONDITIONALS", raising=False)
+        else:
+            monkeypatch.setenv("IOBM_GRAPH_CONDITIONALS", flag)
+        sol = IOBMSolver.from_junction(jn, precision="mixed")
+        res = sol.solve(Es)
+        assert res.converged
+        out.append(res)
+        sol.close()
+    assert np.array_equal(out[0].T, out[1].T)
+    assert np.array_equal(out[0].R, out[1].R)
+    assert np.array_equal(out[0].iterations, out[1].iterations)
+    assert np.array_equal(out[0].replacements, out[1].replacements)
+
+
 def test_profile_stages():
     # every timed stage of the fused Fourier preconditioner reports launches
     from paper_1009_5300_gb300 import IOBMSolver
