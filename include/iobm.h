@@ -336,7 +336,7 @@ int iobm_profile(iobm_handle* h, int enable);
 
 /* Accumulated device time (ms) and count of the timed launches since
  * iobm_profile(h, enable > 0). */
-int iobm_kernel_stats(const iobm_handle* h, double* stencil_ms, long long* stencil_launches);
+int iobm_kernel_stats(const iobm_handle* h, double* kernel_ms, long long* kernel_launches);
 
 /* Allocation-free form of the Eq. 10 preconditioner with its COCG dot
  * products, for callers that cannot allocate device memory: for instance an

@@ -2002,10 +2002,10 @@ int iobm_profile(iobm_handle* h, int enable) {
     return IOBM_OK;
 }
 
-int iobm_kernel_stats(const iobm_handle* h, double* stencil_ms, long long* stencil_launches) {
+int iobm_kernel_stats(const iobm_handle* h, double* kernel_ms, long long* kernel_launches) {
     if (!h) return IOBM_E_ARG;
-    if (stencil_ms) *stencil_ms = h->prof_ms;
-    if (stencil_launches) *stencil_launches = h->prof_launches;
+    if (kernel_ms) *kernel_ms = h->prof_ms;
+    if (kernel_launches) *kernel_launches = h->prof_launches;
     return IOBM_OK;
 }
 
