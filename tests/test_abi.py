@@ -37,3 +37,19 @@ def test_every_declared_symbol_is_exported(lib):
 def test_status_strings(lib):
     for code in range(0, 10):
         assert lib.iobm_status_string(code)
+
+
+def test_default_options_and_binding_layout(lib):
+    # the ctypes mirror of iobm_options matches the header's field list, and the
+    # defaults documented beside iobm_default_options are what the library fills in
+    import ctypes as C
+    from paper_1009_5300_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "iobm.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\} iobm_options;", src).group(1)
+    fields = re.findall(r"\b(?:double|int)\s+([A-Za-z_0-9]+)\s*;", body)
+    assert fields == [f for f, _ in _lib.Options._fields_]
+    o = _lib.Options()
+    lib.iobm_default_options(C.byref(o))
+    assert (o.alpha, o.use_precond, o.tol, o.max_iter) == (1.8, _lib.IOBM_PRECOND_FOURIER, 1e-8, 20000)
+    assert (o.precision, o.refine_delta, o.chunk) == (_lib.IOBM_MIXED, 0.01, 32)
+    assert (o.max_iter_mixed, o.op_form) == (1000, _lib.IOBM_OP_AUTO)
