@@ -103,6 +103,7 @@ struct iobm_handle {
     DevBuf batch_ctr;                    // chunk counter of this junction in a batched solve
     DevBuf sig_scratch;                  // large-plane self-energy spectra
     DevBuf kb_scratch;                  // KB projections [rhs][projector]
+    DevBuf uplane;                      // [nz+1] first union-of-supports entry of each plane
     DevBuf esc_ws, esc_descs, esc_rhs_energy;   // FP64 continuation of stalled mixed RHS
     cudaGraphExec_t chunk_exec = nullptr;        // the last solve's chunk graph, updated in place
     void* pin = nullptr;                         // pinned staging buffer for table uploads
@@ -399,6 +400,7 @@ KbArgs<T> kb_args(const iobm_handle* h) {
     a.npts = h->npts;
     a.mask = M_ALL;
     a.sp = (typename Cplx<T>::type*)h->kb_scratch.p;
+    a.uplane = h->uplane.as<int>();
     return a;
 }
 
@@ -559,32 +561,25 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     C* pb[2] = {(C*)h->vp[0], (C*)h->vp[1]};
     int nslots_mu = 0;
     if (implicit_operator(h)) {
-        // p = z + beta p_old, q = (r - V z) + beta q_old, then q -= V_NL z
+        // projections of z, then p = z + beta p_old, q = (r - V z) + beta q_old - V_NL z
+        KbArgs<T> k = kb_args<T>(h);   // nproj = 0: no KB term
+        if (h->pt.nproj > 0) {
+            k.zsrc = (const C*)h->vz;
+            k.state = h->st;
+            k.mask = M_ACTIVE;
+            CK(launch_kb_proj<T>(k, nrhs, h->stream));
+            launches += 1;
+        }
         if (timed && h->profile == 1)
             CK(cudaEventRecordWithFlags(kev[0], h->stream, cudaEventRecordExternal));
         CK(launch_pq_update<T>((const C*)h->vz, (const C*)h->vr, pb, (C*)h->vq,
                                std::is_same<T, float>::value ? (const T*)h->V32.p : (const T*)h->V64.p,
                                h->st, M_ACTIVE, h->g.nx, h->g.ny, h->g.nz, nrhs, h->mu_part,
-                               h->slot_stride, h->stream));
+                               h->slot_stride, k, h->stream));
         if (timed && h->profile == 1)
             CK(cudaEventRecordWithFlags(kev[1], h->stream, cudaEventRecordExternal));
         nslots_mu = h->g.nz;   // one p^T q partial per plane
         launches += 1;
-        if (h->pt.nproj > 0) {
-            KbArgs<T> k = kb_args<T>(h);
-            k.pnew[0] = (const C*)h->vp[0];
-            k.pnew[1] = (const C*)h->vp[1];
-            k.zsrc = (const C*)h->vz;
-            k.y = (C*)h->vq;
-            k.state = h->st;
-            k.mask = M_ACTIVE;
-            k.dot_part = h->mu_part;
-            k.slot_stride = h->slot_stride;
-            k.slot_base = nslots_mu;
-            CK(launch_kb<T>(k, nrhs, h->stream));
-            nslots_mu += kb_slots(k.nunion);
-            launches += 2;
-        }
     } else {
         const void* sig = std::is_same<T, float>::value ? h->sig32.p : h->sig64.p;
         StencilArgs<T> a = op_args<T>(h);
@@ -1521,6 +1516,11 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     tw(g.ny, +1.0, py64, py32);
     std::vector<float> pv32(h->pt.pval.begin(), h->pt.pval.end());
     std::vector<float> uv32(h->pt.uval.begin(), h->pt.uval.end());
+    // union-of-supports points of plane k: uidx[uplane[k] .. uplane[k+1]) (uidx is sorted)
+    std::vector<int> uplane(g.nz + 1);
+    for (int k = 0; k <= g.nz; ++k)
+        uplane[k] = (int)(std::lower_bound(h->pt.uidx.begin(), h->pt.uidx.end(),
+                                           (long long)k * h->nxy) - h->pt.uidx.begin());
     cudaStream_t s = h->stream;
     if ((e = upload(h->V32, v32, s)) || (e = upload(h->V64, v64, s)) || (e = upload(h->twx32, tx32, s)) ||
         (e = upload(h->twy32, ty32, s)) || (e = upload(h->twx64, tx64, s)) ||
@@ -1530,6 +1530,7 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
         (e = upload(h->pcoup, h->pt.coupling, s)) || (e = upload(h->uidx, h->pt.uidx, s)) ||
         (e = upload(h->uptr, h->pt.uptr, s)) || (e = upload(h->uproj, h->pt.uproj, s)) ||
         (e = upload(h->uval32, uv32, s)) || (e = upload(h->uval64, h->pt.uval, s)) ||
+        (e = upload(h->uplane, uplane, s)) ||
         (e = h->errflag.ensure(sizeof(int))) || (e = cudaMemsetAsync(h->errflag.p, 0, sizeof(int), s)))
         return bad(IOBM_E_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
     e = cudaStreamSynchronize(s);
@@ -1569,7 +1570,7 @@ void iobm_destroy(iobm_handle* h) {
                       &h->pc64, &h->ediag, &h->rhs_energy, &h->descs, &h->open_ptr, &h->open_bins,
                       &h->proj_out, &h->apply_sig32, &h->apply_sig64, &h->apply_pc32,
                       &h->apply_pc64, &h->apply_ediag, &h->ws_owned, &h->errflag,
-                      &h->batch_ctr, &h->sig_scratch, &h->kb_scratch, &h->esc_ws,
+                      &h->batch_ctr, &h->sig_scratch, &h->kb_scratch, &h->uplane, &h->esc_ws,
                       &h->esc_descs, &h->esc_rhs_energy};
     for (DevBuf* b : bufs) b->release();
     if (h->ev_sync) cudaEventDestroy(h->ev_sync);

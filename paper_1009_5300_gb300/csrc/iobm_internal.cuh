@@ -179,6 +179,7 @@ struct KbArgs {
     int slot_stride, slot_base;
     long long npts;
     C* sp;                   // scratch [rhs][nproj]: E_p dvol <p|x>
+    const int* uplane;       // [nz+1]: union points of plane k are uidx[uplane[k] .. uplane[k+1])
 };
 
 // dot-product partial slots the KB application writes per RHS
@@ -255,11 +256,16 @@ cudaError_t launch_axpy_update(typename Cplx<T>::type* x, typename Cplx<T>::type
 // The implicit operator form (free-propagator preconditioner M, A = M^{-1} - V - V_NL,
 // z = M r): p = z + beta p_old into pbufs[1 - pbuf], q = (r - V z) + beta q in place, and
 // the p^T q partials in slots [0, nz), one per plane (V_NL z is added by launch_kb with zsrc)
+// With kb.nproj > 0 the pass also applies q -= V_NL z at the union points of each plane
+// from the projections kb.sp that launch_kb_proj wrote before it.
 template <typename T>
 cudaError_t launch_pq_update(const typename Cplx<T>::type* z, const typename Cplx<T>::type* r,
                              typename Cplx<T>::type* const* pbufs, typename Cplx<T>::type* q,
                              const T* V, const RhsState* st, int mask, int nx, int ny, int nz,
-                             int nrhs, double2* mu_part, int slot_stride, cudaStream_t s);
+                             int nrhs, double2* mu_part, int slot_stride, const KbArgs<T>& kb,
+                             cudaStream_t s);
+// the projections kb.sp[rhs][p] = E_p dvol <p|x> alone (x = kb.zsrc, or the operand of launch_kb)
+template <typename T> cudaError_t launch_kb_proj(const KbArgs<T>& a, int nrhs, cudaStream_t s);
 // x64 += x32; x32 = 0 (mixed-precision fold before the FP64 residual)
 cudaError_t launch_fold(double2* x64, float2* x32, const RhsState* st, int mask, long long npts,
                         int nrhs, cudaStream_t s);

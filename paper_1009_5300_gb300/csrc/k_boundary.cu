@@ -315,8 +315,9 @@ __global__ void __launch_bounds__(kKbProjThreads) k_kb_proj(const KbArgs<T> a, i
         X[j] = nullptr;
         if (live[j]) {
             const int rhs = r0 + j;
-            const C* xb = a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x;
-            X[j] = (a.zsrc ? a.zsrc : xb) + (long long)rhs * a.npts;   // projected operand
+            const C* xb = a.zsrc ? a.zsrc
+                                 : (a.pnew[0] ? a.pnew[1 - (a.state[rhs].pbuf & 1)] : a.x);
+            X[j] = xb + (long long)rhs * a.npts;   // projected operand
         }
     }
     if (!any) return;
@@ -429,6 +430,15 @@ __global__ void __launch_bounds__(kKbApplyThreads) k_kb_apply(const KbArgs<T> a,
 }
 
 template <typename T>
+cudaError_t launch_kb_proj(const KbArgs<T>& a, int nrhs, cudaStream_t s) {
+    if (a.nproj == 0) return cudaSuccess;
+    if (!a.sp) return cudaErrorInvalidValue;
+    const int groups = (nrhs + kKbRhs - 1) / kKbRhs;
+    k_kb_proj<T><<<dim3(a.nproj, groups), kKbProjThreads, 0, s>>>(a, nrhs);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_kb(const KbArgs<T>& a, int nrhs, cudaStream_t s) {
     if (a.nproj == 0) return cudaSuccess;
     if (!a.sp) return cudaErrorInvalidValue;
@@ -465,6 +475,8 @@ template size_t sigma_smem_bytes<float>(int, int, int);
 template size_t sigma_smem_bytes<double>(int, int, int);
 template cudaError_t launch_sigma<float>(const SigmaArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_sigma<double>(const SigmaArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_kb_proj<float>(const KbArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_kb_proj<double>(const KbArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_kb<float>(const KbArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_kb<double>(const KbArgs<double>&, int, cudaStream_t);
 

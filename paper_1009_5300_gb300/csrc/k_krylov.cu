@@ -169,8 +169,10 @@ template cudaError_t launch_axpy_update<double>(double2*, double2*, double2* con
 // Direction and operator update of the implicit operator form.  With the
 // free-propagator preconditioner M = (E - T - Sigma)^{-1} the operator of Eq. 7 is
 // A = M^{-1} - V - V_NL, and z = M r gives A z = r - V z - V_NL z, hence for
-// p = z + beta p_old:  q = A p = (r - V z) + beta q_old - V_NL z  (the last term
-// from k_kb).  One CTA per (plane, RHS); mu = p^T q partial per plane.
+// p = z + beta p_old:  q = A p = (r - V z) + beta q_old - V_NL z.  One CTA per
+// (plane, RHS); mu = p^T q partial per plane.  The V_NL z term is applied by the
+// same CTA at the union-of-supports points of its plane, from the projections
+// kb.sp computed before the launch, once the streaming part has stored p and q.
 template <typename C, typename T>
 __device__ __forceinline__ void pq_point(const C zv, const C rv, const T v, const C* pold,
                                          const C* qold, bool first, C be, C& pv, C& qv) {
@@ -192,7 +194,8 @@ __global__ void __launch_bounds__(256) k_pq_update(const typename Cplx<T>::type*
                                                    typename Cplx<T>::type* __restrict__ q,
                                                    const T* __restrict__ V, const RhsState* st,
                                                    int mask, int nxy, long long npts,
-                                                   double2* mu_part, int slot_stride) {
+                                                   double2* mu_part, int slot_stride,
+                                                   const KbArgs<T> kb) {
     using C = typename Cplx<T>::type;
     __shared__ double red[3 * 8];
     const int rhs = blockIdx.y;
@@ -242,6 +245,24 @@ __global__ void __launch_bounds__(256) k_pq_update(const typename Cplx<T>::type*
             mim += pv.x * qv.y + pv.y * qv.x;
         }
     }
+    if (kb.nproj > 0) {
+        const int u0 = kb.uplane[blockIdx.x], u1 = kb.uplane[blockIdx.x + 1];
+        if (u0 < u1) {   // uniform over the CTA
+            __syncthreads();   // this CTA's p and q stores are visible to all its threads
+            const C* __restrict__ S = kb.sp + (long long)rhs * kb.nproj;
+            const int gbase = blockIdx.x * nxy;
+            for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+                const int g = kb.uidx[u] - gbase;
+                C acc = czero<C>();
+                for (int e = kb.uptr[u]; e < kb.uptr[u + 1]; ++e)
+                    acc = caxpy(kb.uval[e], S[kb.uproj[e]], acc);
+                qp[g] = csub(qp[g], acc);
+                const C pv = pnew[g];
+                mre -= pv.x * acc.x - pv.y * acc.y;
+                mim -= pv.x * acc.y + pv.y * acc.x;
+            }
+        }
+    }
     double a0 = mre, a1 = mim, a2 = 0.0;
     block_reduce_3(a0, a1, a2, red);
     if (threadIdx.x == 0) mu_part[(long long)rhs * slot_stride + blockIdx.x] = make_double2(a0, a1);
@@ -251,21 +272,24 @@ template <typename T>
 cudaError_t launch_pq_update(const typename Cplx<T>::type* z, const typename Cplx<T>::type* r,
                              typename Cplx<T>::type* const* pbufs, typename Cplx<T>::type* q,
                              const T* V, const RhsState* st, int mask, int nx, int ny, int nz,
-                             int nrhs, double2* mu_part, int slot_stride, cudaStream_t s) {
+                             int nrhs, double2* mu_part, int slot_stride, const KbArgs<T>& kb,
+                             cudaStream_t s) {
     const int nxy = nx * ny;
     const long long npts = (long long)nxy * nz;
+    if (kb.nproj > 0 && (!kb.sp || !kb.uplane)) return cudaErrorInvalidValue;
     const int threads = nxy >= 4096 ? 256 : 128;
     dim3 grid(nz, nrhs);
     k_pq_update<T><<<grid, threads, 0, s>>>(z, r, pbufs[0], pbufs[1], q, V, st, mask, nxy, npts,
-                                            mu_part, slot_stride);
+                                            mu_part, slot_stride, kb);
     return cudaGetLastError();
 }
 template cudaError_t launch_pq_update<float>(const float2*, const float2*, float2* const*, float2*,
                                              const float*, const RhsState*, int, int, int, int,
-                                             int, double2*, int, cudaStream_t);
+                                             int, double2*, int, const KbArgs<float>&, cudaStream_t);
 template cudaError_t launch_pq_update<double>(const double2*, const double2*, double2* const*,
                                               double2*, const double*, const RhsState*, int, int,
-                                              int, int, int, double2*, int, cudaStream_t);
+                                              int, int, int, double2*, int, const KbArgs<double>&,
+                                              cudaStream_t);
 
 __global__ void k_fold(double2* __restrict__ x64, float2* __restrict__ x32, const RhsState* st,
                        int mask, long long npts) {
