@@ -4,7 +4,9 @@ Paper passages followed:
 
 * Lateral modes: G_nu = 2 pi nu / L with nu = -N/2 .. N/2-1 (Eq. 8 and the
   Appendix), and the lateral Fourier transform with the 1/N_xy on the forward
-  side (Eq. 19).  kappa = 0 throughout (the Appendix sets it to zero).
+  side (Eq. 19).  The lateral Bloch vector kappa of Eq. 8 shifts every mode to
+  G_nu + kappa (the wave picks up exp(i kappa L) across a lateral period); it is
+  a parameter here, zero by default (the examples of Sec. III).
 * The electrode recurrence: in a flat (zero-potential) jellium electrode
   Eq. 2 decouples per lateral mode nu into the 1D recurrence
 
@@ -98,6 +100,7 @@ class ModeData:
     vel: np.ndarray               # [Nmodes] group velocity of propagating root (0 if closed)
     sigma: np.ndarray             # [Nmodes, nf, nf] Sigma~ in depth coordinates
     K: np.ndarray                 # [nf, nf] coupling to the electrode planes
+    kappa: Tuple[float, float] = (0.0, 0.0)   # lateral Bloch vector (Eq. 8)
 
     @property
     def open_modes(self) -> np.ndarray:
@@ -167,10 +170,11 @@ def sigma_mode(lam: np.ndarray, K: np.ndarray) -> np.ndarray:
 
 
 def mode_data(nx: int, ny: int, hx: float, hy: float, hz: float, nf: int, E: float,
-              check_threshold: bool = True) -> ModeData:
+              check_threshold: bool = True, kappa=(0.0, 0.0)) -> ModeData:
     w = second_derivative_weights(nf)
-    Gx = lateral_G(nx, hx)
-    Gy = lateral_G(ny, hy)
+    kappa = (float(kappa[0]), float(kappa[1]))
+    Gx = lateral_G(nx, hx) + kappa[0]     # G_nu + kappa (Eq. 8)
+    Gy = lateral_G(ny, hy) + kappa[1]
     ex = lateral_energy_1d(Gx, hx, w)
     ey = lateral_energy_1d(Gy, hy, w)
     nux, nuy = lateral_indices(nx), lateral_indices(ny)
@@ -201,7 +205,7 @@ def mode_data(nx: int, ny: int, hx: float, hy: float, hz: float, nf: int, E: flo
             sigma[m] = sigma_mode(sel, K)
             m += 1
     return ModeData(E=E, nf=nf, hz=hz, w=w, nu=nu, eps_perp=eps, lam=lam, prop=prop,
-                    vel=vel, sigma=sigma, K=K)
+                    vel=vel, sigma=sigma, K=K, kappa=kappa)
 
 
 def incident_source_mode(md: ModeData, m: int) -> np.ndarray:
@@ -213,24 +217,25 @@ def incident_source_mode(md: ModeData, m: int) -> np.ndarray:
     return -md.K @ (lam_in ** (-e)) - md.sigma[m] @ (lam_in ** d)
 
 
-def count_open_channels(nx, ny, hx, hy, hz, nf, E) -> int:
+def count_open_channels(nx, ny, hx, hy, hz, nf, E, kappa=(0.0, 0.0)) -> int:
     """Number of propagating right-going channels at energy E."""
-    md = mode_data(nx, ny, hx, hy, hz, nf, E, check_threshold=False)
+    md = mode_data(nx, ny, hx, hy, hz, nf, E, check_threshold=False, kappa=kappa)
     return int(np.sum(md.prop >= 0))
 
 
 def lateral_phase(nx: int, ny: int, hx: float, hy: float, md: ModeData) -> np.ndarray:
-    """F[m, l] = exp(-i G_m . r_l) for all modes m and lateral points l = y*nx + x."""
+    """F[m, l] = exp(-i (G_m + kappa) . r_l) for all modes m and lateral points l = y*nx + x."""
     x = np.arange(nx) * hx
     y = np.arange(ny) * hy
-    Gx = 2.0 * np.pi * md.nu[:, 0] / (nx * hx)
-    Gy = 2.0 * np.pi * md.nu[:, 1] / (ny * hy)
+    Gx = 2.0 * np.pi * md.nu[:, 0] / (nx * hx) + md.kappa[0]
+    Gy = 2.0 * np.pi * md.nu[:, 1] / (ny * hy) + md.kappa[1]
     ph = np.exp(-1j * (Gy[:, None, None] * y[None, :, None] + Gx[:, None, None] * x[None, None, :]))
     return ph.reshape(len(md.nu), nx * ny)
 
 
 def eq19_forward(nx, ny, hx, hy, md: ModeData, plane: np.ndarray) -> np.ndarray:
-    """psi~_nu = (1/N_xy) sum_l exp(-i G_nu . r_l) psi(r_l)  (Eq. 19), as an explicit sum."""
+    """psi~_nu = (1/N_xy) sum_l exp(-i (G_nu + kappa) . r_l) psi(r_l)  (Eq. 19), as an
+    explicit sum."""
     F = lateral_phase(nx, ny, hx, hy, md)
     return F @ plane.reshape(-1) / (nx * ny)
 

@@ -3,7 +3,9 @@
 Paper passages followed:
 
 * Eq. 1: the kinetic operator -1/2 d^2/dr^2 with FD weights on each axis;
-  x and y periodic (Sec. II: "periodic in the x and y directions").
+  x and y periodic (Sec. II: "periodic in the x and y directions"), or Bloch
+  periodic psi(r + L) = exp(i kappa L) psi(r) for a lateral Bloch vector kappa
+  (Eq. 8): a coupling that wraps across the lateral period carries that phase.
 * Eqs. 2-4: H_T is the Hamiltonian of planes z_0 .. z_{N_z+1}; couplings that
   would reach beyond those planes are dropped from H_T (they are accounted for
   by the self-energy and the source).  H_T contains the local potential V(r)
@@ -42,15 +44,20 @@ from .fd import second_derivative_weights
 from .modes import ModeData, lateral_phase
 
 
-def _fd_matrix_periodic(n: int, w: np.ndarray) -> sp.csr_matrix:
-    """n x n circulant matrix of the FD second-derivative weights (dimensionless)."""
+def _fd_matrix_periodic(n: int, w: np.ndarray, phase=None) -> sp.csr_matrix:
+    """n x n circulant matrix of the FD second-derivative weights (dimensionless).
+    With phase = exp(i kappa L): Bloch-periodic, a coupling to i + s >= n carries
+    phase and one to i + s < 0 its conjugate."""
     nf = len(w) - 1
     rows, cols, vals = [], [], []
     for i in range(n):
         for s in range(-nf, nf + 1):
             rows.append(i)
             cols.append((i + s) % n)
-            vals.append(w[abs(s)])
+            v = w[abs(s)]
+            if phase is not None:
+                v = v * (phase if i + s >= n else (np.conj(phase) if i + s < 0 else 1.0))
+            vals.append(v)
     return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))  # duplicates summed
 
 
@@ -68,12 +75,21 @@ def _fd_matrix_truncated(n: int, w: np.ndarray) -> sp.csr_matrix:
     return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
 
 
-def h_local(jn) -> sp.csr_matrix:
-    """H_T without the KB term: -1/2 (D_xx + D_yy + D_zz) + V (Eqs. 1-4)."""
+def _bloch_phases(jn, kappa):
+    """(exp(i kappa_x L_x), exp(i kappa_y L_y)), or (None, None) at kappa = 0."""
+    if kappa[0] == 0.0 and kappa[1] == 0.0:
+        return None, None
+    return (np.exp(1j * kappa[0] * jn.nx * jn.hx), np.exp(1j * kappa[1] * jn.ny * jn.hy))
+
+
+def h_local(jn, kappa=(0.0, 0.0)) -> sp.csr_matrix:
+    """H_T without the KB term: -1/2 (D_xx + D_yy + D_zz) + V (Eqs. 1-4), laterally
+    Bloch periodic with vector kappa."""
     w = second_derivative_weights(jn.nf)
     Ix, Iy, Iz = sp.identity(jn.nx), sp.identity(jn.ny), sp.identity(jn.nz)
-    Dx = _fd_matrix_periodic(jn.nx, w) / jn.hx ** 2
-    Dy = _fd_matrix_periodic(jn.ny, w) / jn.hy ** 2
+    px, py = _bloch_phases(jn, kappa)
+    Dx = _fd_matrix_periodic(jn.nx, w, px) / jn.hx ** 2
+    Dy = _fd_matrix_periodic(jn.ny, w, py) / jn.hy ** 2
     Dz = _fd_matrix_truncated(jn.nz, w) / jn.hz ** 2
     lap = (sp.kron(sp.kron(Iz, Iy), Dx) + sp.kron(sp.kron(Iz, Dy), Ix)
            + sp.kron(sp.kron(Dz, Iy), Ix))
@@ -121,7 +137,7 @@ def assemble_A_local(jn, E: float, md: ModeData) -> sp.csc_matrix:
     """E - H_T(local) - H~ as a sparse matrix with the two dense end blocks (Eqs. 7, 7-2, 8)."""
     nxy = jn.nx * jn.ny
     npts = jn.npts
-    A = (E * sp.identity(npts) - h_local(jn)).tocoo()
+    A = (E * sp.identity(npts) - h_local(jn, md.kappa)).tocoo()
     S = sigma_dense(jn, md)
     rows, cols, vals = [A.row], [A.col], [A.data.astype(np.complex128)]
     for side in ("L", "R"):
@@ -173,12 +189,23 @@ def _sigma_apply_end_fft(jn, md: ModeData, planes_vals: np.ndarray) -> np.ndarra
     ny, nx = jn.ny, jn.nx
     kx = md.nu[:, 0] % nx
     ky = md.nu[:, 1] % ny
-    spec = np.fft.fft2(planes_vals.reshape(nf, ny, nx), axes=(1, 2)) / nxy
+    vals = planes_vals.reshape(nf, ny, nx)
+    gauge = None
+    if md.kappa[0] != 0.0 or md.kappa[1] != 0.0:
+        # exp(-i (G + kappa).r) = exp(-i G.r) exp(-i kappa.r): the FFT of the gauged plane
+        x = np.arange(nx) * jn.hx
+        y = np.arange(ny) * jn.hy
+        gauge = np.exp(-1j * (md.kappa[1] * y[:, None] + md.kappa[0] * x[None, :]))
+        vals = vals * gauge[None]
+    spec = np.fft.fft2(vals, axes=(1, 2)) / nxy
     ft = spec[:, ky, kx].T                              # [nu, d]
-    y = np.einsum("mde,me->md", md.sigma, ft)
+    yv = np.einsum("mde,me->md", md.sigma, ft)
     Y = np.zeros((nf, ny, nx), dtype=np.complex128)
-    Y[:, ky, kx] = y.T
-    return (np.fft.ifft2(Y, axes=(1, 2)) * nxy).reshape(nf, nxy)
+    Y[:, ky, kx] = yv.T
+    out = np.fft.ifft2(Y, axes=(1, 2)) * nxy
+    if gauge is not None:
+        out = out * np.conj(gauge)[None]
+    return out.reshape(nf, nxy)
 
 
 def apply_A(jn, E: float, md: ModeData, psi: np.ndarray) -> np.ndarray:
@@ -187,10 +214,22 @@ def apply_A(jn, E: float, md: ModeData, psi: np.ndarray) -> np.ndarray:
     nf = jn.nf
     psi = np.asarray(psi, dtype=np.complex128)
     lap = np.zeros_like(psi)
+    px, py = _bloch_phases(jn, md.kappa)
+
+    def wrap(n, size, phase):
+        # Bloch factor of psi(i + n) read from the stored period: phase past the end
+        i = np.arange(size)
+        return np.where(i + n >= size, phase, np.where(i + n < 0, np.conj(phase), 1.0))
+
     for n in range(-nf, nf + 1):
         c = w[abs(n)]
-        lap += c / jn.hx ** 2 * np.roll(psi, -n, axis=2)
-        lap += c / jn.hy ** 2 * np.roll(psi, -n, axis=1)
+        sx = np.roll(psi, -n, axis=2)
+        sy = np.roll(psi, -n, axis=1)
+        if px is not None:
+            sx = sx * wrap(n, jn.nx, px)[None, None, :]
+            sy = sy * wrap(n, jn.ny, py)[None, :, None]
+        lap += c / jn.hx ** 2 * sx
+        lap += c / jn.hy ** 2 * sy
         sh = np.zeros_like(psi)
         if n >= 0:
             sh[: jn.nz - n] = psi[n:]

@@ -61,19 +61,19 @@ class Solution:
         return len(self.open_modes)
 
 
-def modes_for(jn, E: float) -> ModeData:
-    return mode_data(jn.nx, jn.ny, jn.hx, jn.hy, jn.hz, jn.nf, E)
+def modes_for(jn, E: float, kappa=(0.0, 0.0)) -> ModeData:
+    return mode_data(jn.nx, jn.ny, jn.hx, jn.hy, jn.hz, jn.nf, E, kappa=kappa)
 
 
 def incident_wave_planes(jn, md: ModeData, m: int, depths: np.ndarray) -> np.ndarray:
     """Unit incident wave of mode m at depth index d (negative = electrode plane -d):
-    f(l) lambda_in^d with f(l) = exp(i G_m . r_l); returned as [len(depths)][N_xy]."""
+    f(l) lambda_in^d with f(l) = exp(i (G_m + kappa) . r_l); returned as [len(depths)][N_xy]."""
     lam = md.lam[m, md.prop[m]]
-    # the row of mode m of the Eq. 19 phase matrix, conjugated: exp(+i G_m . r_l)
+    # the row of mode m of the Eq. 19 phase matrix, conjugated: exp(+i (G_m + kappa) . r_l)
     x = np.arange(jn.nx) * jn.hx
     y = np.arange(jn.ny) * jn.hy
-    Gx = 2.0 * np.pi * md.nu[m, 0] / (jn.nx * jn.hx)
-    Gy = 2.0 * np.pi * md.nu[m, 1] / (jn.ny * jn.hy)
+    Gx = 2.0 * np.pi * md.nu[m, 0] / (jn.nx * jn.hx) + md.kappa[0]
+    Gy = 2.0 * np.pi * md.nu[m, 1] / (jn.ny * jn.hy) + md.kappa[1]
     f = np.exp(1j * (Gy * y[:, None] + Gx * x[None, :])).reshape(-1)
     return (lam ** depths)[:, None] * f[None, :]
 
@@ -131,10 +131,11 @@ def project(jn, md: ModeData, psi: np.ndarray, m_in: int, side: str):
     return t, r
 
 
-def solve(jn, E: float, side: str = "L", channels: Optional[Sequence[int]] = None) -> Solution:
+def solve(jn, E: float, side: str = "L", channels: Optional[Sequence[int]] = None,
+          kappa=(0.0, 0.0)) -> Solution:
     """Exact solve of Eq. 7 for every open incident channel (or the given subset,
-    indices into the open-channel list)."""
-    md = modes_for(jn, E)
+    indices into the open-channel list), at lateral Bloch vector kappa."""
+    md = modes_for(jn, E, kappa)
     opens = md.open_modes
     chan = list(range(len(opens))) if channels is None else list(channels)
     M = assemble_augmented(jn, E, md)
@@ -162,8 +163,8 @@ def solve(jn, E: float, side: str = "L", channels: Optional[Sequence[int]] = Non
                     t=t, r=r, T=T, R=R, G=float(T.sum()), vel=vel)
 
 
-def conductance(jn, E: float) -> float:
-    return solve(jn, E).G
+def conductance(jn, E: float, kappa=(0.0, 0.0)) -> float:
+    return solve(jn, E, kappa=kappa).G
 
 
 def eigenchannels(sol: Solution) -> np.ndarray:
@@ -191,19 +192,21 @@ def exit_functional(jn, md: ModeData, m_out: int, side: str = "L") -> np.ndarray
     return wv.reshape(jn.nz, jn.ny, jn.nx)
 
 
-def grad_V(jn, E: float, sol: Optional[Solution] = None) -> np.ndarray:
-    """dG/dV(r) in G_0 per Ha for left-incident waves (adjoint, same operator)."""
+def grad_V(jn, E: float, sol: Optional[Solution] = None, kappa=(0.0, 0.0)) -> np.ndarray:
+    """dG/dV(r) in G_0 per Ha for left-incident waves: lambda_o = A^{-T} w_o (the
+    same operator at kappa = 0, where A = A^T; the transposed solve otherwise)."""
     if sol is None:
-        sol = solve(jn, E)
+        sol = solve(jn, E, kappa=kappa)
     md = sol.md
     M = assemble_augmented(jn, E, md)
     lu = spla.splu(M)
+    trans = "N" if (md.kappa[0] == 0.0 and md.kappa[1] == 0.0) else "T"
     nproj = len(jn.projectors)
     opens = sol.open_modes
     g = np.zeros((jn.nz, jn.ny, jn.nx))
     for o, m_out in enumerate(opens):
         wv = exit_functional(jn, md, m_out, sol.side).reshape(-1)
-        lam_o = lu.solve(np.concatenate([wv, np.zeros(nproj, np.complex128)]))[: jn.npts]
+        lam_o = lu.solve(np.concatenate([wv, np.zeros(nproj, np.complex128)]), trans=trans)[: jn.npts]
         lam_o = lam_o.reshape(jn.nz, jn.ny, jn.nx)
         for i in range(sol.psi.shape[0]):
             coef = 2.0 * sol.vel[o] / sol.vel[i] * np.conj(sol.t[o, i])
