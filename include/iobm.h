@@ -324,6 +324,14 @@ int iobm_set_potential(iobm_handle* h, const double* V_loc, int src_is_device);
 int iobm_channels_host(const iobm_grid* grid, double E, int* n_open, int max_out, int* nu,
                        double* vel, double* lam, double* btilde, double* mrow, double* sigma);
 
+/* The same tables at a lateral Bloch vector (kappa_x, kappa_y) (1/bohr): every lateral
+ * mode becomes G_nu + kappa (Eq. 8), the wave picking up exp(i kappa L) across a lateral
+ * period.  iobm_channels_host is this call at kappa = 0.  Host-only set-up: the solver
+ * itself runs at kappa = 0.  IOBM_E_ARG for a non-finite kappa. */
+int iobm_channels_host_bloch(const iobm_grid* grid, double kappa_x, double kappa_y, double E,
+                             int* n_open, int max_out, int* nu, double* vel, double* lam,
+                             double* btilde, double* mrow, double* sigma);
+
 /* CUDA-event timing of one kernel of every COCG iteration inside the captured
  * iteration graphs; resets the counters.  enable: 0 off; 1 the operator kernel
  * (the fused stencil p = z + beta p_old, q = (E - T - V) p with the p^T q

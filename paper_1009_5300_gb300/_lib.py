@@ -96,6 +96,9 @@ SIGNATURES = {
     "iobm_channels_host": (C.c_int, [C.POINTER(Grid), C.c_double, C.POINTER(C.c_int), C.c_int,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "iobm_channels_host_bloch": (C.c_int, [C.POINTER(Grid), C.c_double, C.c_double, C.c_double,
+                                           C.POINTER(C.c_int), C.c_int, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "iobm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "iobm_precond_dots_noalloc": (C.c_int, [C.POINTER(Grid), C.c_double, C.c_void_p, C.c_void_p,
                                             C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -1957,11 +1957,19 @@ int iobm_set_potential(iobm_handle* h, const double* V_loc, int src_is_device) {
 
 int iobm_channels_host(const iobm_grid* g, double E, int* n_open, int max_out, int* nu,
                        double* vel, double* lam, double* btilde, double* mrow, double* sigma) {
+    return iobm_channels_host_bloch(g, 0.0, 0.0, E, n_open, max_out, nu, vel, lam, btilde, mrow,
+                                    sigma);
+}
+
+int iobm_channels_host_bloch(const iobm_grid* g, double kappa_x, double kappa_y, double E,
+                             int* n_open, int max_out, int* nu, double* vel, double* lam,
+                             double* btilde, double* mrow, double* sigma) {
     if (!g || !n_open || g->nx < 1 || g->ny < 1 || g->nf < 1 || g->nf > kMaxNf) return IOBM_E_ARG;
+    if (!std::isfinite(kappa_x) || !std::isfinite(kappa_y)) return IOBM_E_ARG;
     ModeTables mt;
     std::string msg;
     const int rc = build_mode_tables(g->nx, g->ny, g->hx, g->hy, g->hz, g->nf, E, sigma != nullptr,
-                                     mt, msg);
+                                     mt, msg, kappa_x, kappa_y);
     if (rc) return rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED;
     const int nf = g->nf;
     *n_open = mt.nopen;

@@ -283,11 +283,13 @@ int solve_mode(double dE, int nf, double hz, const std::vector<double>& w,
 }  // namespace
 
 int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, double E,
-                      bool want_sigma, ModeTables& out, std::string& msg) {
+                      bool want_sigma, ModeTables& out, std::string& msg, double kappa_x,
+                      double kappa_y) {
     const std::vector<double> w = fd_weights(nf);
     const double two_pi = 2.0 * M_PI;
-    auto eps1d = [&](int nu, int n, double h) {
-        const double G = two_pi * nu / (n * h);
+    // lateral dispersion at G_nu + kappa (Eq. 8 with the lateral Bloch vector)
+    auto eps1d = [&](int nu, int n, double h, double kappa) {
+        const double G = two_pi * nu / (n * h) + kappa;
         double s = w[0];
         for (int k = 1; k <= nf; ++k) s += 2.0 * w[k] * std::cos(k * G * h);
         return -0.5 * s / (h * h);
@@ -316,8 +318,8 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
         out.pc.assign((size_t)nx * ny * kPcStride, cd(0.0, 0.0));
     }
     std::vector<double> ex(nx), ey(ny);
-    for (int ix = 0; ix < nx; ++ix) ex[ix] = eps1d(nu_of_index(ix, nx), nx, hx);
-    for (int iy = 0; iy < ny; ++iy) ey[iy] = eps1d(nu_of_index(iy, ny), ny, hy);
+    for (int ix = 0; ix < nx; ++ix) ex[ix] = eps1d(nu_of_index(ix, nx), nx, hx, kappa_x);
+    for (int iy = 0; iy < ny; ++iy) ey[iy] = eps1d(nu_of_index(iy, ny), ny, hy, kappa_y);
     // distinct lateral energies (the dispersion is even in nu, and symmetric in
     // x <-> y on square cells), each solved once
     std::vector<double> eperp((size_t)nx * ny);
@@ -366,8 +368,10 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
         }
     }
     out.nopen = (int)out.open_canon.size();
-    // partner channel (-nu) of every open channel; the lateral dispersion is even in nu
+    // partner channel (-nu) of every open channel; at kappa = 0 the lateral dispersion
+    // is even in nu (at kappa != 0 the partner is a channel of -kappa: none is recorded)
     out.open_partner.assign(out.nopen, -1);
+    if (kappa_x != 0.0 || kappa_y != 0.0) return 0;
     for (int c = 0; c < out.nopen; ++c) {
         const int bx = bin_of_nu(-out.open_nux[c], nx), by = bin_of_nu(-out.open_nuy[c], ny);
         for (int d = 0; d < out.nopen; ++d)

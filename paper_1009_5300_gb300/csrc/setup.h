@@ -35,11 +35,14 @@ struct ModeTables {
 
 constexpr int kPcStride = 25;   // nf + (nf + 1) + nf * nf for nf = 4
 
-// Builds the tables of energy E.  Returns 0, or 2 (IOBM_E_THRESHOLD) when E is
-// within 1e-9 Ha of a channel edge, or 9 when a mode has more than one
-// propagating right-going root.  `msg` receives a one-line reason.
+// Builds the tables of energy E at lateral Bloch vector (kappa_x, kappa_y) (modes
+// G_nu + kappa).  Returns 0, or 2 (IOBM_E_THRESHOLD) when E is within 1e-9 Ha of a
+// channel edge, or 9 when a mode has more than one propagating right-going root.
+// `msg` receives a one-line reason.  open_partner (the -nu channel) is filled at
+// kappa = 0 only.
 int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, double E,
-                      bool want_sigma, ModeTables& out, std::string& msg);
+                      bool want_sigma, ModeTables& out, std::string& msg, double kappa_x = 0.0,
+                      double kappa_y = 0.0);
 
 // The tables of several energies, built in parallel host threads.
 int build_mode_tables_many(int nx, int ny, double hx, double hy, double hz, int nf, const double* E,

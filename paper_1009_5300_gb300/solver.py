@@ -63,14 +63,16 @@ def default_options(**kw) -> _lib.Options:
     return o
 
 
-def channels_host(nx, ny, hx, hy, hz, nf, E, max_out=None, want_sigma=False):
-    """Host-side channel tables of the library (no GPU needed): iobm_channels_host."""
+def channels_host(nx, ny, hx, hy, hz, nf, E, max_out=None, want_sigma=False, kappa=(0.0, 0.0)):
+    """Host-side channel tables of the library (no GPU needed): iobm_channels_host_bloch
+    (at lateral Bloch vector kappa; iobm_channels_host at kappa = 0)."""
     lib = _lib.load()
     g = _lib.Grid(nx, ny, 2 * nf + 1, hx, hy, hz, nf)
     n = C.c_int(0)
+    kx, ky = float(kappa[0]), float(kappa[1])
     if max_out is None:
-        check(lib.iobm_channels_host(C.byref(g), E, C.byref(n), 0, None, None, None, None, None,
-                                     None))
+        check(lib.iobm_channels_host_bloch(C.byref(g), kx, ky, E, C.byref(n), 0, None, None, None,
+                                           None, None, None))
         max_out = n.value
     nu = np.zeros((max(max_out, 1), 2), np.int32)
     vel = np.zeros(max(max_out, 1))
@@ -78,9 +80,9 @@ def channels_host(nx, ny, hx, hy, hz, nf, E, max_out=None, want_sigma=False):
     bt = np.zeros((max(max_out, 1), nf, 2))
     mrow = np.zeros((max(max_out, 1), nf, 2))
     sig = np.zeros((ny, nx, nf, nf, 2)) if want_sigma else None
-    check(lib.iobm_channels_host(C.byref(g), E, C.byref(n), max_out, _ptr(nu), _ptr(vel),
-                                 _ptr(lam), _ptr(bt), _ptr(mrow),
-                                 _ptr(sig) if want_sigma else None))
+    check(lib.iobm_channels_host_bloch(C.byref(g), kx, ky, E, C.byref(n), max_out, _ptr(nu),
+                                       _ptr(vel), _ptr(lam), _ptr(bt), _ptr(mrow),
+                                       _ptr(sig) if want_sigma else None))
     k = n.value
     out = dict(n_open=k, nu=nu[:k], vel=vel[:k], lam=lam[:k, 0] + 1j * lam[:k, 1],
                btilde=bt[:k, :, 0] + 1j * bt[:k, :, 1], mrow=mrow[:k, :, 0] + 1j * mrow[:k, :, 1])

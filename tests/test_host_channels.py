@@ -27,8 +27,20 @@ CASES = [(16, 16, 0.4, 0.4, 0.4, 4, S.fermi_energy(3.28)),
 
 @pytest.mark.parametrize("nx,ny,hx,hy,hz,nf,E", CASES)
 def test_channels_match_oracle(host, nx, ny, hx, hy, hz, nf, E):
-    lib = host(nx, ny, hx, hy, hz, nf, E, want_sigma=True)
-    md = modes.mode_data(nx, ny, hx, hy, hz, nf, E)
+    check_against_oracle(host, nx, ny, hx, hy, hz, nf, E, (0.0, 0.0))
+
+
+# lateral Bloch vectors as fractions of pi / L per axis
+@pytest.mark.parametrize("case,fx,fy", [(0, 0.31, -0.57), (2, -0.8, 0.45), (3, 0.5, 0.0)])
+def test_channels_match_oracle_at_kappa(host, case, fx, fy):
+    nx, ny, hx, hy, hz, nf, E = CASES[case]
+    kappa = (fx * np.pi / (nx * hx), fy * np.pi / (ny * hy))
+    check_against_oracle(host, nx, ny, hx, hy, hz, nf, E, kappa)
+
+
+def check_against_oracle(host, nx, ny, hx, hy, hz, nf, E, kappa):
+    lib = host(nx, ny, hx, hy, hz, nf, E, want_sigma=True, kappa=kappa)
+    md = modes.mode_data(nx, ny, hx, hy, hz, nf, E, kappa=kappa)
     opens = md.open_modes
     assert lib["n_open"] == len(opens)
     assert np.array_equal(lib["nu"], md.nu[opens])
