@@ -339,7 +339,10 @@ int iobm_channels_host_bloch(const iobm_grid* grid, double kappa_x, double kappa
  * q = (r - V z) + beta q_old); 2 the update x += alpha p, r -= alpha q with the
  * forward plane FFTs; 3 the z-sweeps; 4 the inverse plane FFTs with the r^T z
  * and |r|^2 partials (2-4: Fourier preconditioners with planes of at most 4096
- * points).  IOBM_E_ARG for other values. */
+ * points).  IOBM_E_ARG for other values.  The FP64 residual replacements run as
+ * conditional graph nodes, whose kernels kernel profilers cannot list; with
+ * IOBM_GRAPH_CONDITIONALS=0 in the environment when a handle is created they are
+ * captured as plain masked launches instead (bit-identical results). */
 int iobm_profile(iobm_handle* h, int enable);
 
 /* Accumulated device time (ms) and count of the timed launches since
