@@ -23,7 +23,7 @@
  *
  * Layouts: grid functions are [z][y][x] with x fastest (z = plane index
  * 0 .. N_z+1).  Complex vectors are interleaved (re, im) pairs of double
- * (IOBM_FP64) or float (IOBM_FP32).  A batch of vectors is [rhs][z][y][x].
+ * (IOBM_ELEM_C64) or float (IOBM_ELEM_C32).  A batch of vectors is [rhs][z][y][x].
  *
  * Ownership: the caller owns every input buffer; the library copies what it
  * keeps during iobm_create.  The handle owns its persistent device tables
@@ -54,7 +54,9 @@ extern "C" {
 #define IOBM_E_PROJ_BOUNDARY  3  /* a projector touches the N_f outermost planes          */
 #define IOBM_E_NOCONV         4  /* per-RHS: iteration limit reached                      */
 #define IOBM_E_BREAKDOWN      5  /* per-RHS: COCG breakdown (r^T z or p^T A p vanished)   */
-#define IOBM_E_TIMEOUT        6  /* a bounded device wait gave up                         */
+#define IOBM_E_TIMEOUT        6  /* a bounded device wait gave up (see iobm_set_wait_limit):
+                                    the kernel drained its own copies and returned, the
+                                    call's results are invalid, the context stays usable   */
 #define IOBM_E_CUDA           7  /* CUDA runtime error                                    */
 #define IOBM_E_STATE          8  /* call out of order (e.g. transmission before solve)    */
 #define IOBM_E_UNSUPPORTED    9  /* size outside what this build supports (see message)   */
@@ -77,7 +79,9 @@ typedef struct iobm_handle iobm_handle;
  * (nz = N_z + 2).  nf is the FD half-width N_f of Eq. 1 (1 .. 4); the
  * self-energy then acts on the nf outermost planes at each end.  x and y
  * are periodic with period nx*hx and ny*hy.  nx and ny may only contain
- * the prime factors 2, 3 and 5 (lateral FFT radices), and nx*ny <= 4096. */
+ * the prime factors 2, 3 and 5 (lateral FFT radices).  Planes of at most
+ * 4096 points are transformed in one CTA's shared memory; larger planes
+ * (nx <= 256 and ny <= 256) by two passes through global memory. */
 typedef struct {
     int nx, ny, nz;
     double hx, hy, hz;
@@ -162,8 +166,11 @@ typedef struct {
  * max_iter_mixed 1000, op_form IOBM_OP_AUTO. */
 void iobm_default_options(iobm_options* opts);
 
-/* Create a solver for one junction.  V_loc: host [nz][ny][nx] local
- * potential (Ha), copied.  proj: KB projectors (host arrays, copied; NULL
+/* Create a solver for one junction: the truncated Hamiltonian H_T of the
+ * transition region (Eqs. 1-4: FD kinetic operator, local potential V_loc and
+ * the nonlocal Kleinman-Bylander term of the norm-conserving pseudopotentials
+ * of Sec. III) between two jellium electrodes (Sec. II).  V_loc: host
+ * [nz][ny][nx] local potential (Ha), copied.  proj: KB projectors (host arrays, copied; NULL
  * for none).  rs: Wigner-Seitz radius of the jellium electrodes (bohr); it
  * only sets iobm_fermi_energy.  opts: NULL for defaults.  cuda_stream: a
  * cudaStream_t (NULL = legacy default stream).  Errors: IOBM_E_ARG for bad
@@ -287,7 +294,11 @@ int iobm_transmission(iobm_handle* h, double* T, double* R, int max_open, double
  * double) to dst (host or device). */
 int iobm_solution(iobm_handle* h, int rhs, void* dst, int dst_is_device);
 
-/* dG/dV(r) (G_0 per Ha) at energy E for left-incident waves: solves the
+/* dG/dV(r) (G_0 per Ha) at energy E for left-incident waves.  Not in the
+ * paper: it differentiates the Landauer sum of Sec. III through Eq. 7 with
+ * dA/dV(r) = -e_r e_r^T, using A = A^T (Eq. 8 is symmetric in l <-> l' at a
+ * zero lateral Bloch vector).  Takes the energy itself rather than an index
+ * into an earlier solve, so it needs no prior iobm_solve.  It solves the
  * n_open forward waves and the n_open adjoint waves A lambda_o = w_o (same
  * operator, A = A^T) in one batch, then accumulates
  * dG/dV(r) = sum_{o,i} 2 (v_o/v_i) Re[conj(t_oi) lambda_o(r) psi_i(r)] in FP64.
@@ -345,6 +356,17 @@ int iobm_channels_host_bloch(const iobm_grid* grid, double kappa_x, double kappa
  * captured as plain masked launches instead (bit-identical results). */
 int iobm_profile(iobm_handle* h, int enable);
 
+/* Limit of the bounded device waits of this handle's kernels (the bulk-copy
+ * stencil waits on its staged copies): cycles = 0 restores the default of
+ * about one second of SM clock.  A wait that reaches the limit gives up: its
+ * CTA waits (with the default limit) for its own copies still in flight and
+ * returns, and the call reports IOBM_E_TIMEOUT.  inject_stall = 1 makes every
+ * CTA of that kernel also wait once on a barrier that no copy completes, so
+ * that the give-up path runs (for tests of the error path; 0 = off).  Applies
+ * to later calls; the bulk-copy kernel serves FP32 operators and the Eq. 10
+ * preconditioner on rows of 12, 16, 24, 32, 48 or 64 points. */
+int iobm_set_wait_limit(iobm_handle* h, long long cycles, int inject_stall);
+
 /* Accumulated device time (ms) and count of the timed launches since
  * iobm_profile(h, enable > 0). */
 int iobm_kernel_stats(const iobm_handle* h, double* kernel_ms, long long* kernel_launches);
@@ -364,17 +386,23 @@ int iobm_kernel_stats(const iobm_handle* h, double* kernel_ms, long long* kernel
  * Everything is enqueued on cuda_stream (a cudaStream_t, NULL = legacy
  * default stream); the call does not synchronise.
  *
+ * r and z must not overlap (z = P r reads neighbours of r that other blocks
+ * may already have written to z): overlapping ranges return IOBM_E_ARG.
+ *
  * The per-block partial sums live in a fixed device array compiled into the
  * library (1.5 MiB per GPU, held by every GPU that loads the library until the
  * process exits): at most 65536 partial slots, where one RHS uses at most
- * ceil(nx/32) * ceil(ny/8) * ceil(nz/32) slots; larger requests return
- * IOBM_E_UNSUPPORTED.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current, so make the first
- * call before capturing a stream.  Every call shares the array and overwrites
- * every slot it reads, so calls need no clearing, but calls that overlap on
- * the GPU (other streams, other threads) race and must be serialised by the
- * caller.  Calls no cudaMalloc, cudaFree or allocating library routine.
- * Errors: IOBM_E_ARG, IOBM_E_UNSUPPORTED, IOBM_E_CUDA. */
+ * ceil(nx/32) * ceil(ny/8) * ceil(nz/32) slots, and nrhs <= 65535 (the RHS
+ * index is a grid dimension); larger requests return IOBM_E_UNSUPPORTED.
+ * A call made while cuda_stream is not being captured looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; a call during
+ * stream capture uses the address found by the last such call, so make at
+ * least one call on the device before capturing a stream (and again after a
+ * cudaDeviceReset, which invalidates it).  Every call shares the array and
+ * overwrites every slot it reads, so calls need no clearing, but calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Errors: IOBM_E_ARG, IOBM_E_UNSUPPORTED, IOBM_E_CUDA. */
 int iobm_precond_dots_noalloc(const iobm_grid* grid, double alpha, const void* r, void* z,
                               int nrhs, double* rho, double* rr, void* cuda_stream);
 

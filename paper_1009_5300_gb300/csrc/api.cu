@@ -98,6 +98,8 @@ struct iobm_handle {
     int side = 0;
     int nrhs = 0;                        // internal RHS
     int max_open = 0;
+    long long wait_cycles = 0;           // bounded-wait limit of the bulk-copy kernels (0: default)
+    int wait_inject = 0;                 // 1: their CTAs also wait on a barrier no copy completes
     int zchunk = kZChunkDefault;         // stencil z-planes per CTA (autotuned)
     int stencil_variant = 0;             // StencilArgs::variant (autotuned)
     DevBuf batch_ctr;                    // chunk counter of this junction in a batched solve
@@ -312,6 +314,8 @@ StencilArgs<T> op_args(const iobm_handle* h) {
     a.variant = h->stencil_variant;
     a.mask = M_ALL;
     a.err = h->errflag.as<int>();
+    a.wait_cycles = h->wait_cycles;
+    a.wait_inject = h->wait_inject;
     return a;
 }
 
@@ -333,6 +337,8 @@ StencilArgs<T> precond_args(const iobm_handle* h) {
     a.variant = h->stencil_variant;
     a.mask = M_ALL;
     a.err = h->errflag.as<int>();
+    a.wait_cycles = h->wait_cycles;
+    a.wait_inject = h->wait_inject;
     return a;
 }
 
@@ -681,7 +687,9 @@ int check_err_flag(iobm_handle* h) {
     if (v == 0) return IOBM_OK;
     CK(cudaMemsetAsync(h->errflag.p, 0, sizeof(int), h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    return fail(h, IOBM_E_CUDA, "a kernel's bounded wait on its staged copies timed out");
+    return fail(h, IOBM_E_TIMEOUT,
+                "a kernel's bounded wait on its staged copies gave up (its CTA drained its own "
+                "copies and returned; the results of this call are invalid)");
 }
 
 // Solver start for every RHS: zero x and the directions, r = b, ||b||^2, z = P r.
@@ -1464,7 +1472,7 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
         return bad(IOBM_E_ARG, "need at least 2 nf + 2 planes");
     std::vector<int> rx, ry;
     if (!fft_plan(g.nx, rx) || !fft_plan(g.ny, ry))
-        return bad(IOBM_E_UNSUPPORTED, "lateral sizes must have prime factors <= 13");
+        return bad(IOBM_E_UNSUPPORTED, "lateral sizes may only have the prime factors 2, 3 and 5");
     if ((int)rx.size() > kMaxRadixPasses || (int)ry.size() > kMaxRadixPasses)
         return bad(IOBM_E_UNSUPPORTED, "too many FFT passes");
     h->ax.n = g.nx;
@@ -1999,6 +2007,15 @@ int iobm_channels_host_bloch(const iobm_grid* g, double kappa_x, double kappa_y,
             sigma[2 * i] = mt.sigma[i].real();
             sigma[2 * i + 1] = mt.sigma[i].imag();
         }
+    return IOBM_OK;
+}
+
+int iobm_set_wait_limit(iobm_handle* h, long long cycles, int inject_stall) {
+    if (!h) return IOBM_E_ARG;
+    if (cycles < 0 || (inject_stall != 0 && inject_stall != 1))
+        return fail(h, IOBM_E_ARG, "wait limit must be >= 0 and inject_stall 0 or 1");
+    h->wait_cycles = cycles;
+    h->wait_inject = inject_stall;
     return IOBM_OK;
 }
 

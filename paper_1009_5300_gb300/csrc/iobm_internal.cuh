@@ -124,6 +124,9 @@ struct StencilArgs {
     float2 dfx[kMaxNf + 1];  // variant 2: cx[n], cy[n], cz[n] as FP32 pairs (hi, lo)
     float2 dfy[kMaxNf + 1];
     float2 dfz[kMaxNf + 1];
+    long long wait_cycles;   // limit of the bounded copy waits (0: about one second)
+    int wait_inject;         // 1: each CTA of the bulk-copy kernel also waits once on a
+                             // barrier that no copy completes (tests the give-up path)
 };
 
 // the double-float row kernel (FP64 data, operator apply without fused p or dots)

@@ -416,10 +416,11 @@ __global__ void __launch_bounds__(NX * kRowTY, MINB) k_stencil_rows_tma(const St
     C* tiles = reinterpret_cast<C*>(smem_tma + 128);   // [2][SR][TP] combined operand rows
     C* stages = tiles + 2 * TILE;                      // stage s: z at 2 s SLAB, p_old at (2 s + 1) SLAB
     if (tid == 0) {
-        for (int s = 0; s < D; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s <= D; ++s) mbar_init(&bar[s], 1);   // bar[D]: no copy completes it
         mbar_init_fence();
     }
     __syncthreads();
+    const long long wlim = a.wait_cycles > 0 ? a.wait_cycles : kWaitCycles;
 
     // copy assignment of warp 0.  A halo side (NF rows above or below the own
     // rows) whose source rows do not wrap around in y is one copy of NF rows,
@@ -506,7 +507,8 @@ __global__ void __launch_bounds__(NX * kRowTY, MINB) k_stencil_rows_tma(const St
         C* tile = tiles + (kk & 1) * TILE;
         const T vk = vnext;
         if (Vk && own && k + 1 < k1) vnext = Vk[plane];
-        const bool ok = mbar_wait_bounded(&bar[s], (kk / D) & 1);
+        bool ok = mbar_wait_bounded(&bar[s], (kk / D) & 1, wlim);
+        if (a.wait_inject && kk == 0 && tid == 0) ok = ok && mbar_wait_bounded(&bar[D], 0, wlim);
         const C* sz = stages + 2 * s * SLAB;
         const C* sp = sz + SLAB;
         C qn = czero<C>();

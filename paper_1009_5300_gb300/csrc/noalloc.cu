@@ -22,6 +22,7 @@ namespace {
 constexpr int kNoAllocSlots = 1 << 16;
 constexpr int kNoAllocZChunk = 32;
 constexpr int kMaxDevices = 64;
+constexpr int kMaxGridZ = 65535;
 
 static __device__ __align__(256) double2 g_dot_partials[kNoAllocSlots];
 static __device__ __align__(256) double g_nrm_partials[kNoAllocSlots];
@@ -33,16 +34,22 @@ struct DeviceScratch {
 DeviceScratch g_scratch[kMaxDevices];
 std::mutex g_scratch_mutex;
 
-// Device addresses of the two arrays on the current device (looked up once per
-// device; in host code the array names are only host-side stand-ins).
-cudaError_t scratch_for_current_device(DeviceScratch& out) {
+// Device addresses of the two arrays on the current device (in host code the
+// array names are only host-side stand-ins).  Looked up afresh on every call made
+// while the stream is not being captured (cheap, and it follows a context that
+// was destroyed and re-created, e.g. after cudaDeviceReset); during stream capture
+// the address cached by the last such call is used.
+cudaError_t scratch_for_current_device(cudaStream_t stream, DeviceScratch& out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     DeviceScratch& s = g_scratch[dev];
-    if (!s.dot) {
+    if (cs == cudaStreamCaptureStatusNone || !s.dot) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_dot_partials);
         if (e != cudaSuccess) return e;
@@ -84,12 +91,21 @@ extern "C" int iobm_precond_dots_noalloc(const iobm_grid* grid, double alpha, co
     const iobm_grid& g = *grid;
     if (g.nx < 1 || g.ny < 1 || g.nz < 1) return IOBM_E_ARG;
     if (nrhs == 0) return IOBM_OK;
-    if (nrhs > kNoAllocSlots) return IOBM_E_UNSUPPORTED;   // at least one slot per RHS
+    // the RHS index is the grid's z dimension (at most 65535), and every RHS needs at
+    // least one partial slot
+    if (nrhs > kMaxGridZ || nrhs > kNoAllocSlots) return IOBM_E_UNSUPPORTED;
     const int per_rhs = stencil_slots(g.nx, g.ny, g.nz, kNoAllocZChunk, 1);
     if ((long long)per_rhs * nrhs > kNoAllocSlots) return IOBM_E_UNSUPPORTED;
-    DeviceScratch s;
-    if (scratch_for_current_device(s) != cudaSuccess) return IOBM_E_CUDA;
+    // z = P r reads neighbours of r that other CTAs may already have overwritten
+    // in z, so the two ranges must not overlap
+    const unsigned long long bytes =
+        (unsigned long long)nrhs * g.nx * g.ny * g.nz * sizeof(double2);
+    const unsigned long long rb = reinterpret_cast<unsigned long long>(r);
+    const unsigned long long zb = reinterpret_cast<unsigned long long>(z);
+    if (rb < zb + bytes && zb < rb + bytes) return IOBM_E_ARG;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    DeviceScratch s;
+    if (scratch_for_current_device(stream, s) != cudaSuccess) return IOBM_E_CUDA;
 
     StencilArgs<double> a{};
     a.x = static_cast<const double2*>(r);

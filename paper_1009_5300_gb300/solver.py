@@ -276,6 +276,11 @@ class IOBMSolver:
             Vn = np.ascontiguousarray(np.asarray(V, np.float64).reshape(self.shape))
             check(self.lib.iobm_set_potential(self.h, _ptr(Vn), 0), self.h)
 
+    def set_wait_limit(self, cycles: int = 0, inject_stall: bool = False):
+        """Bounded-wait limit of the bulk-copy kernels (0: default, about one second), and
+        optionally an extra wait on a barrier no copy completes (iobm_set_wait_limit)."""
+        check(self.lib.iobm_set_wait_limit(self.h, int(cycles), 1 if inject_stall else 0), self.h)
+
     PROFILE_STAGES = {"operator": 1, "update_fft": 2, "zsweep": 3, "ifft": 4}
 
     def profile(self, enable=True):

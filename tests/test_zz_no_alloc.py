@@ -63,3 +63,22 @@ def test_noalloc_rejects_oversized_requests():
     rc = lib.iobm_precond_dots_noalloc(C.byref(grid), 1.8, C.c_void_p(16), C.c_void_p(16),
                                        (1 << 16) + 1, C.c_void_p(16), C.c_void_p(16), None)
     assert rc == _lib.IOBM_E_UNSUPPORTED
+
+
+def test_noalloc_rejects_grid_z_overflow_and_aliasing():
+    # 65536 RHS of a small grid fit the slot array (one slot each) but not the launch's
+    # grid z dimension; and an in-place call (r == z, or overlapping ranges) would let
+    # blocks read halo values of r that others already overwrote.  Both are refused
+    # on the host before any device access (the pointers are never dereferenced).
+    from paper_1009_5300_gb300 import _lib
+    lib = _lib.load()
+    grid = _lib.Grid(8, 8, 8, 0.3, 0.3, 0.3, 1)
+    rc = lib.iobm_precond_dots_noalloc(C.byref(grid), 1.8, C.c_void_p(16), C.c_void_p(1 << 40),
+                                       1 << 16, C.c_void_p(16), C.c_void_p(16), None)
+    assert rc == _lib.IOBM_E_UNSUPPORTED
+    nbytes = 8 * 8 * 8 * 16
+    for zoff in (0, 16, nbytes - 16):
+        rc = lib.iobm_precond_dots_noalloc(C.byref(grid), 1.8, C.c_void_p(1 << 20),
+                                           C.c_void_p((1 << 20) + zoff), 1, C.c_void_p(16),
+                                           C.c_void_p(16), None)
+        assert rc == _lib.IOBM_E_ARG
