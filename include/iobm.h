@@ -18,7 +18,8 @@
  * give transmission, reflection and the Landauer conductance (Sec. III).
  *
  * Units: Hartree atomic units (energies in Ha, lengths in bohr); the
- * electrode potential is the zero of energy; the lateral Bloch vector is 0.
+ * electrode potential is the zero of energy; the lateral Bloch vector is 0
+ * unless iobm_set_bloch sets another.
  * Conductance is returned in units of G_0 = 2 e^2 / h.
  *
  * Layouts: grid functions are [z][y][x] with x fastest (z = plane index
@@ -324,6 +325,32 @@ int iobm_apply_precond(iobm_handle* h, double E, int elem, const void* x, void* 
  * gradient-based optimisation.  Eqs. 2-4: V enters H_T on every plane. */
 int iobm_set_potential(iobm_handle* h, const double* V_loc, int src_is_device);
 
+/* Lateral Bloch vector kappa = (kappa_x, kappa_y) (1/bohr) of the later solves,
+ * gradients and operator applications of this handle (Eq. 8: every lateral mode
+ * becomes G_nu + kappa and the wave picks up exp(i kappa L) across a lateral
+ * period); (0, 0), the default, is the periodic problem.
+ *
+ * At kappa != 0 the matrix of Eq. 7 is no longer complex symmetric: A(kappa)^T =
+ * A(-kappa).  The library then solves in the gauge phi = exp(-i kappa.r) psi (where
+ * the lateral FFTs, the self-energy and preconditioner tables at G_nu + kappa and
+ * the channel projections keep their periodic form; the FD couplings and the
+ * projectors carry the phases) by preconditioned Bi-CG, whose shadow sequence
+ * solves the transposed system: iobm_solve pairs every incident channel nu at kappa
+ * with the channel -nu at -kappa incident from the same side (the time-reversed
+ * partner) and returns both.  After such a solve, energy slot e in [0, nE) of
+ * iobm_transmission (G, nopen, iobm_report.energy_index) is E[e] at +kappa and slot
+ * nE + e is E[e] at -kappa; iobm_num_rhs counts the channels of both, the -kappa
+ * ones after the +kappa ones in the same order, each with its channel index in the
+ * open list at -kappa.  iobm_grad_V pairs each forward wave with the adjoint wave
+ * of the same channel (lambda_o = A(kappa)^{-T} w_o).  iobm_solution returns psi
+ * (the gauge undone).  iobm_apply applies the operator at +kappa to phi (the
+ * gauge representation) in FP64 only (IOBM_ELEM_C64; IOBM_ELEM_C64_DF is computed
+ * as IOBM_ELEM_C64); iobm_apply_precond applies (E - T - H~)^{-1} at +kappa.
+ * Requires use_precond = IOBM_PRECOND_FOURIER and op_form = IOBM_OP_AUTO
+ * (IOBM_E_UNSUPPORTED otherwise); iobm_solve_batch refuses handles with kappa != 0.
+ * IOBM_E_ARG for a non-finite kappa. */
+int iobm_set_bloch(iobm_handle* h, double kappa_x, double kappa_y);
+
 /* Host-only set-up (needs no GPU and no handle): the electrode channel data
  * at energy E for a lateral grid, as used by the solver.  n_open: number of
  * open channels.  nu [max_out][2], vel [max_out], lam [max_out][2] (the
@@ -337,8 +364,8 @@ int iobm_channels_host(const iobm_grid* grid, double E, int* n_open, int max_out
 
 /* The same tables at a lateral Bloch vector (kappa_x, kappa_y) (1/bohr): every lateral
  * mode becomes G_nu + kappa (Eq. 8), the wave picking up exp(i kappa L) across a lateral
- * period.  iobm_channels_host is this call at kappa = 0.  Host-only set-up: the solver
- * itself runs at kappa = 0.  IOBM_E_ARG for a non-finite kappa. */
+ * period.  iobm_channels_host is this call at kappa = 0 (the solver takes kappa from
+ * iobm_set_bloch).  IOBM_E_ARG for a non-finite kappa. */
 int iobm_channels_host_bloch(const iobm_grid* grid, double kappa_x, double kappa_y, double E,
                              int* n_open, int max_out, int* nu, double* vel, double* lam,
                              double* btilde, double* mrow, double* sigma);

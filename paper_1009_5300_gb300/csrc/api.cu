@@ -98,6 +98,15 @@ struct iobm_handle {
     int side = 0;
     int nrhs = 0;                        // internal RHS
     int max_open = 0;
+    // lateral Bloch vector (Eq. 8); nonzero: the solve runs in the gauge
+    // phi = exp(-i kappa.r) psi as preconditioned Bi-CG on (kappa, -kappa) pairs
+    double kappa[2] = {0.0, 0.0};
+    int pairs = 0;                       // Bi-CG pairs of the current solve (0: COCG)
+    DevBuf rhs_sign;                     // [nrhs] +1 / -1: the operator of each RHS is at s kappa
+    DevBuf apply_sign;                   // [nrhs] +1 for iobm_apply
+    DevBuf gph32, gph64;                 // [nxy] exp(i kappa.r_l) for the KB projectors
+    DevBuf gpx, gpy;                     // [nx], [ny] exp(i kappa_x x h_x), exp(i kappa_y y h_y)
+    DevBuf esc_rhs_sign;                 // the FP64 continuation's signs
     long long wait_cycles = 0;           // bounded-wait limit of the bulk-copy kernels (0: default)
     int wait_inject = 0;                 // 1: their CTAs also wait on a barrier no copy completes
     int zchunk = kZChunkDefault;         // stencil z-planes per CTA (autotuned)
@@ -167,10 +176,15 @@ int cuda_fail(iobm_handle* h, cudaError_t e, const char* where) {
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
+bool bloch(const iobm_handle* h) { return h->kappa[0] != 0.0 || h->kappa[1] != 0.0; }
+
 // Internal (real-profile) RHS are solved to tol / sqrt(2): an incident channel
 // psi = x_c +- i x_s then has ||b - A psi|| <= ||r_c|| + ||r_s|| <= tol ||b||
 // because ||b||^2 = ||b_c||^2 + ||b_s||^2 (cos and sin profiles are orthogonal).
-double internal_tol2(const iobm_handle* h) { return 0.5 * h->opt.tol * h->opt.tol; }
+// At a lateral Bloch vector every channel is one internal RHS, solved to tol.
+double internal_tol2(const iobm_handle* h) {
+    return (bloch(h) ? 1.0 : 0.5) * h->opt.tol * h->opt.tol;
+}
 
 // per-RHS iteration limit of the current solve (the FP32 phase of a mixed solve
 // stops at max_iter_mixed; the FP64 continuation gets max_iter)
@@ -316,6 +330,18 @@ StencilArgs<T> op_args(const iobm_handle* h) {
     a.err = h->errflag.as<int>();
     a.wait_cycles = h->wait_cycles;
     a.wait_inject = h->wait_inject;
+    if (std::is_same<T, double>::value && bloch(h)) {
+        // lateral taps at the Bloch vector (FP64 kernels; per RHS the sign of kappa)
+        a.rhs_sign = h->rhs_sign.as<int>();
+        for (int n = 1; n <= h->nf; ++n) {
+            const double tx = n * h->kappa[0] * h->g.hx, ty = n * h->kappa[1] * h->g.hy;
+            const double cx = 0.5 * h->w[n] * ihx, cy = 0.5 * h->w[n] * ihy;
+            a.bxc[n] = (T)(cx * std::cos(tx));
+            a.bxs[n] = (T)(cx * std::sin(tx));
+            a.byc[n] = (T)(cy * std::cos(ty));
+            a.bys[n] = (T)(cy * std::sin(ty));
+        }
+    }
     return a;
 }
 
@@ -407,6 +433,12 @@ KbArgs<T> kb_args(const iobm_handle* h) {
     a.mask = M_ALL;
     a.sp = (typename Cplx<T>::type*)h->kb_scratch.p;
     a.uplane = h->uplane.as<int>();
+    a.nxy = h->nxy;
+    if (bloch(h)) {
+        a.rhs_sign = h->rhs_sign.as<int>();
+        a.gph = std::is_same<T, float>::value ? (const typename Cplx<T>::type*)h->gph32.p
+                                              : (const typename Cplx<T>::type*)h->gph64.p;
+    }
     return a;
 }
 
@@ -414,10 +446,13 @@ KbArgs<T> kb_args(const iobm_handle* h) {
 template <typename T>
 int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void* sig,
                    const double* ediag, const int* rhs_energy, const RhsState* st, int mask,
-                   long long& launches, bool df = false) {
+                   long long& launches, bool df = false, const int* signs = nullptr) {
     using C = typename Cplx<T>::type;
     StencilArgs<T> a = op_args<T>(h);
-    if (df) a.variant = 2;   // FP64 data, double-float stencil arithmetic
+    // FP64 data, double-float stencil arithmetic (the double-float kernel has no
+    // Bloch phases: at a lateral Bloch vector the FP64 stencil runs instead)
+    if (df && !bloch(h)) a.variant = 2;
+    if (signs && std::is_same<T, double>::value && bloch(h)) a.rhs_sign = signs;
     a.x = (const C*)x;
     a.y = (C*)y;
     a.ediag = ediag;
@@ -439,9 +474,23 @@ int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void*
         k.y = (C*)y;
         k.state = st;
         k.mask = mask;
+        if (signs && bloch(h)) k.rhs_sign = signs;
         CK(launch_kb<T>(k, nrhs, h->stream));
         launches += 2;
     }
+    return IOBM_OK;
+}
+
+// Bi-CG: rho = r~^T z of every pair (primary partials) once z = P r is formed for
+// the RHS in mask; the own r^T z partials of the preconditioner pass are replaced.
+template <typename T>
+int pair_rho(iobm_handle* h, int nrhs, int mask, long long& launches) {
+    using C = typename Cplx<T>::type;
+    if (!h->pairs) return IOBM_OK;
+    (void)nrhs;
+    CK(launch_pair_dot<T>((const C*)h->vr, nullptr, (const C*)h->vz, h->st, mask, h->npts, h->pairs,
+                          h->rho_part, rho_slots(h), h->slot_stride, h->stream));
+    launches += 1;
     return IOBM_OK;
 }
 
@@ -462,7 +511,7 @@ int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) 
         f.slot_stride = h->slot_stride;
         CK(launch_precond_fourier<T>(f, nrhs, h->stream));
         launches += 3;
-        return IOBM_OK;
+        return pair_rho<T>(h, nrhs, mask, launches);
     }
     StencilArgs<T> a = precond_args<T>(h);
     a.x = (const C*)h->vr;
@@ -476,7 +525,7 @@ int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) 
     a.slot_base = 0;
     CK(launch_stencil<T>(a, nrhs, h->stream));
     launches += 1;
-    return IOBM_OK;
+    return pair_rho<T>(h, nrhs, mask, launches);
 }
 
 // FP64 residual replacement for RHS in `mask` (PENDING): x64 (+)= x, r = b - A x64.
@@ -494,7 +543,8 @@ int residual_replacement(iobm_handle* h, int nrhs, int mask, bool mixed, long lo
     CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
                           h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, h->st, mask,
                           h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
-    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, internal_tol2(h), 0, h->stream));
+    CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, internal_tol2(h), 0, h->stream,
+                    h->pairs));
     launches += 2;
     // RESTART RHS get z = P r and the rho / |r|^2 partials of the replaced residual;
     // the next iteration returns them to ACTIVE and forms beta from these partials
@@ -559,7 +609,7 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     CK(launch_restart_scalars(h->st, h->rho_part, h->rr_part, h->ns_stencil, h->slot_stride, nrhs,
                               h->stream));
     CK(launch_beta(h->st, h->rho_part, h->rr_part, rho_slots(h), h->slot_stride, nrhs,
-                   iter_cap(h), tol2, delta2, mixed ? 1 : 0, h->stream));
+                   iter_cap(h), tol2, delta2, mixed ? 1 : 0, h->stream, h->pairs));
     launches += 2;
     // event record nodes inside the captured graph (external records execute with the graph)
     const bool timed = h->profile && slot >= 0;
@@ -586,6 +636,11 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
             CK(cudaEventRecordWithFlags(kev[1], h->stream, cudaEventRecordExternal));
         nslots_mu = h->g.nz;   // one p^T q partial per plane
         launches += 1;
+        if (h->pairs) {   // Bi-CG: mu = p~^T q with the shadow's new direction
+            CK(launch_pair_dot<T>(nullptr, pb, (const C*)h->vq, h->st, M_ACTIVE, h->npts, h->pairs,
+                                  h->mu_part, nslots_mu, h->slot_stride, h->stream));
+            launches += 1;
+        }
     } else {
         const void* sig = std::is_same<T, float>::value ? h->sig32.p : h->sig64.p;
         StencilArgs<T> a = op_args<T>(h);
@@ -636,7 +691,7 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
             launches += 2;
         }
     }
-    CK(launch_alpha(h->st, h->mu_part, nslots_mu, h->slot_stride, nrhs, h->stream));
+    CK(launch_alpha(h->st, h->mu_part, nslots_mu, h->slot_stride, nrhs, h->stream, h->pairs));
     launches += 1;
     bool fused = false;
     if (fourier_precond(h)) {
@@ -657,6 +712,8 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
         if (e == cudaSuccess) {
             fused = true;
             launches += 3;
+            const int rc = pair_rho<T>(h, nrhs, M_ACTIVE, launches);
+            if (rc) return rc;
         } else if (e != cudaErrorNotSupported) {
             return cuda_fail(h, e, "launch_update_precond_fourier");
         }
@@ -876,8 +933,14 @@ int run_solver(iobm_handle* h, int nrhs, bool warm = false) {
 // channels at one energy followed by the adjoint functionals of every channel.
 // An incident channel exp(i G.r) is run as the real profiles cos(G.r) and
 // sin(G.r) of its +-G pair (one profile for a self-conjugate G).
+int upload_solve_tables(iobm_handle* h);
+int prepare_rhs_bloch(iobm_handle* h, const double* E, int nE, const int* channels, int nch,
+                      int side, int kind, bool upload_tables);
+
 int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, int nch, int side,
                 int kind, bool upload_tables = true) {
+    if (bloch(h)) return prepare_rhs_bloch(h, E, nE, channels, nch, side, kind, upload_tables);
+    h->pairs = 0;
     h->energies.clear();
     h->hdesc.clear();
     h->hrhs_energy.clear();
@@ -969,6 +1032,13 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
         h->energies.clear();
         return IOBM_OK;
     }
+    return upload_solve_tables(h);
+}
+
+// Device copies of the per-energy-slot tables, energies, RHS descriptors and
+// open-channel lists of the RHS list just built (h->energies, h->hdesc, ...).
+int upload_solve_tables(iobm_handle* h) {
+    const int nE = (int)h->energies.size();
     // device tables, staged through pinned memory: Sigma~ in FP32 and FP64, the
     // free-propagator factors in FP32 (FP64 only for an FP64 solve; the FP64
     // continuation of a mixed solve uploads them when it needs them)
@@ -1023,7 +1093,7 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
     std::vector<int2> obins;
     h->max_open = 0;
     for (int e = 0; e < nE; ++e) {
-        ed[e] = E[e];
+        ed[e] = h->energies[e].E;
         const ModeTables& mt = h->energies[e];
         optr[e + 1] = optr[e] + mt.nopen;
         h->max_open = std::max(h->max_open, mt.nopen);
@@ -1034,7 +1104,130 @@ int prepare_rhs(iobm_handle* h, const double* E, int nE, const int* channels, in
     CK(upload(h->descs, h->hdesc, h->stream));
     CK(upload(h->open_ptr, optr, h->stream));
     CK(upload(h->open_bins, obins, h->stream));
+    if (h->pairs) {
+        std::vector<int> sg(h->nrhs);
+        for (int i = 0; i < h->nrhs; ++i) sg[i] = i < h->pairs ? 1 : -1;
+        CK(upload(h->rhs_sign, sg, h->stream));
+    }
     return IOBM_OK;
+}
+
+
+// The RHS list at a lateral Bloch vector kappa (Eq. 8), solved in the gauge
+// phi = exp(-i kappa.r) psi, where the operator A(kappa) has A(kappa)^T = A(-kappa):
+// energy slots [0, nE) hold the tables at +kappa (modes G_nu + kappa), slots
+// [nE, 2 nE) those at -kappa.  Every internal RHS is one incident channel (source
+// exp(i G_nu.r) b~ in the gauge, no real-profile pairing) and RHS i + pairs is the
+// Bi-CG shadow of RHS i: kind 0, the channel -nu of -kappa incident from the same
+// side (time-reversed partner; its solution is the -kappa problem's wave); kind 1
+// (gradient, one energy), the adjoint functional w_o of the same channel o, whose
+// shadow solution is lambda_o = A(kappa)^{-T} w_o in the gauge of -kappa.
+int prepare_rhs_bloch(iobm_handle* h, const double* E, int nE, const int* channels, int nch,
+                      int side, int kind, bool upload_tables) {
+    h->energies.clear();
+    h->hdesc.clear();
+    h->hrhs_energy.clear();
+    h->users.clear();
+    h->side = side;
+    const int nf = h->nf;
+    for (int e = 0; e < nE; ++e)
+        if (!std::isfinite(E[e])) return fail(h, IOBM_E_ARG, "non-finite energy");
+    std::vector<ModeTables> tables;
+    const bool memo_hit = upload_tables && (int)h->memo_E.size() == nE &&
+                          (int)h->memo_tables.size() == 2 * nE &&
+                          std::equal(h->memo_E.begin(), h->memo_E.end(), E);
+    if (memo_hit) {
+        tables = std::move(h->memo_tables);
+    } else {
+        std::string msg;
+        std::vector<ModeTables> minus;
+        int rc = build_mode_tables_many(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, nf, E, nE, true,
+                                        tables, msg, h->kappa[0], h->kappa[1]);
+        if (!rc)
+            rc = build_mode_tables_many(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, nf, E, nE, true,
+                                        minus, msg, -h->kappa[0], -h->kappa[1]);
+        if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
+        for (ModeTables& mt : minus) tables.push_back(std::move(mt));
+    }
+    h->memo_E.clear();
+    h->memo_tables.clear();
+    auto add_desc = [&](int slot, int kx, int ky, int side_, const std::complex<double>* coef,
+                        double scale) {
+        RhsDesc d{};
+        d.energy = slot;
+        d.kx = kx;
+        d.ky = ky;
+        d.side = side_;
+        d.profile = PROF_EXP_PLUS;
+        for (int k = 0; k < nf; ++k) d.coef[k] = make_double2(scale * coef[k].real(), scale * coef[k].imag());
+        h->hdesc.push_back(d);
+        h->hrhs_energy.push_back(slot);
+    };
+    // index, in the open list of a -kappa slot, of the channel with lateral index -nu
+    auto partner = [&](const ModeTables& mm, const ModeTables& mp, int c) {
+        const int bx = (h->g.nx - mp.open_kx[c]) % h->g.nx, by = (h->g.ny - mp.open_ky[c]) % h->g.ny;
+        for (int d = 0; d < mm.nopen; ++d)
+            if (mm.open_kx[d] == bx && mm.open_ky[d] == by) return d;
+        return -1;
+    };
+    struct Item { int e, c, cm; };
+    std::vector<Item> items;
+    for (int e = 0; e < nE; ++e) {
+        const ModeTables& mp = tables[e];
+        const ModeTables& mm = tables[nE + e];
+        if (mm.nopen != mp.nopen)
+            return fail(h, IOBM_E_UNSUPPORTED, "open channels of +kappa and -kappa differ");
+        std::vector<int> list;
+        if (kind == 1 || !channels) {
+            for (int c = 0; c < mp.nopen; ++c) list.push_back(c);
+        } else {
+            for (int c = 0; c < nch; ++c)
+                if (channels[c] >= 0 && channels[c] < mp.nopen &&
+                    std::find(list.begin(), list.end(), channels[c]) == list.end())
+                    list.push_back(channels[c]);
+            std::sort(list.begin(), list.end());
+        }
+        for (int c : list) {
+            const int cm = partner(mm, mp, c);
+            if (cm < 0) return fail(h, IOBM_E_UNSUPPORTED, "open channel without a -nu partner at -kappa");
+            items.push_back({e, c, cm});
+        }
+    }
+    const int fside = (kind == 1) ? 0 : side;
+    const int n = (int)items.size();
+    h->pairs = n;
+    for (int i = 0; i < n; ++i) {   // primaries: the channels at +kappa
+        const ModeTables& mp = tables[items[i].e];
+        const int c = items[i].c;
+        add_desc(items[i].e, mp.open_kx[c], mp.open_ky[c], fside, &mp.btilde[(size_t)c * nf], 1.0);
+        h->users.push_back({items[i].e, c, fside, i, -1, 1});
+    }
+    for (int i = 0; i < n; ++i) {   // shadows
+        const ModeTables& mp = tables[items[i].e];
+        const ModeTables& mm = tables[nE + items[i].e];
+        if (kind == 1) {
+            // w_o = mrow_o exp(-i (G_o + kappa).r) / N_xy on the exit planes; in the
+            // gauge of -kappa this is exp(i G_{-nu}.r) mrow_o / N_xy
+            const int c = items[i].c;
+            add_desc(nE + items[i].e, (h->g.nx - mp.open_kx[c]) % h->g.nx,
+                     (h->g.ny - mp.open_ky[c]) % h->g.ny, 1 - fside, &mp.mrow[(size_t)c * nf],
+                     1.0 / h->nxy);
+        } else {
+            const int cm = items[i].cm;
+            add_desc(nE + items[i].e, mm.open_kx[cm], mm.open_ky[cm], fside,
+                     &mm.btilde[(size_t)cm * nf], 1.0);
+            h->users.push_back({nE + items[i].e, cm, fside, n + i, -1, 1});
+        }
+    }
+    h->energies = std::move(tables);
+    h->nrhs = (int)h->hdesc.size();
+    if (!upload_tables) {
+        h->memo_E.assign(E, E + nE);
+        h->memo_tables = std::move(h->energies);
+        h->energies.clear();
+        return IOBM_OK;
+    }
+    return upload_solve_tables(h);
 }
 
 // Precision escalation after a mixed solve: the RHS that stopped without
@@ -1057,14 +1250,19 @@ int escalate_fp64(iobm_handle* h) {
         CK(upload(h->pc64, p64, h->stream));
         h->pc64_valid = true;
     }
+    // Bi-CG pairs stop together, so the stalled set holds whole pairs: its primaries
+    // (indices below pairs) come first, their shadows after in the same order
+    const int sub_pairs = h->pairs ? m / 2 : 0;
     std::vector<RhsDesc> sd(m);
-    std::vector<int> se(m);
+    std::vector<int> se(m), ss(m);
     for (int k = 0; k < m; ++k) {
         sd[k] = h->hdesc[idx[k]];
         se[k] = h->hrhs_energy[idx[k]];
+        ss[k] = k < sub_pairs ? 1 : -1;
     }
     CK(upload(h->esc_descs, sd, h->stream));
     CK(upload(h->esc_rhs_energy, se, h->stream));
+    if (h->pairs) CK(upload(h->esc_rhs_sign, ss, h->stream));
     const size_t need = workspace_bytes(h, m, IOBM_FP64);
     CK(h->esc_ws.ensure(need));
 
@@ -1072,11 +1270,11 @@ int escalate_fp64(iobm_handle* h) {
         void* ws; size_t ws_bytes; int ws_nrhs, ws_prec, slot_stride, ns_stencil, nrhs, precision;
         RhsState* st; double2 *mu_part, *rho_part; double* rr_part;
         void *vx, *vr, *vp0, *vp1, *vq, *vz; double2 *x64, *y64;
-        double last_ms; long long last_launches, last_iters; int profile;
+        double last_ms; long long last_launches, last_iters; int profile, pairs;
     } sv{h->ws, h->ws_bytes, h->ws_nrhs, h->ws_prec, h->slot_stride, h->ns_stencil, h->nrhs,
          h->opt.precision, h->st, h->mu_part, h->rho_part, h->rr_part, h->vx, h->vr, h->vp[0],
          h->vp[1], h->vq, h->vz, h->x64, h->y64, h->last_ms, h->last_launches, h->last_iters,
-         h->profile};
+         h->profile, h->pairs};
     std::vector<RhsState> main_state = h->hstate;
     auto restore = [&]() {
         h->ws = sv.ws; h->ws_bytes = sv.ws_bytes; h->ws_nrhs = sv.ws_nrhs; h->ws_prec = sv.ws_prec;
@@ -1084,12 +1282,15 @@ int escalate_fp64(iobm_handle* h) {
         h->opt.precision = sv.precision; h->st = sv.st; h->mu_part = sv.mu_part;
         h->rho_part = sv.rho_part; h->rr_part = sv.rr_part; h->vx = sv.vx; h->vr = sv.vr;
         h->vp[0] = sv.vp0; h->vp[1] = sv.vp1; h->vq = sv.vq; h->vz = sv.vz; h->x64 = sv.x64;
-        h->y64 = sv.y64; h->profile = sv.profile;
+        h->y64 = sv.y64; h->profile = sv.profile; h->pairs = sv.pairs;
         std::swap(h->descs, h->esc_descs);
         std::swap(h->rhs_energy, h->esc_rhs_energy);
+        if (sv.pairs) std::swap(h->rhs_sign, h->esc_rhs_sign);
     };
     std::swap(h->descs, h->esc_descs);
     std::swap(h->rhs_energy, h->esc_rhs_energy);
+    if (h->pairs) std::swap(h->rhs_sign, h->esc_rhs_sign);
+    h->pairs = sub_pairs;
     h->ws = h->esc_ws.p;
     h->ws_bytes = need;
     h->opt.precision = IOBM_FP64;
@@ -1579,7 +1780,8 @@ void iobm_destroy(iobm_handle* h) {
                       &h->proj_out, &h->apply_sig32, &h->apply_sig64, &h->apply_pc32,
                       &h->apply_pc64, &h->apply_ediag, &h->ws_owned, &h->errflag,
                       &h->batch_ctr, &h->sig_scratch, &h->kb_scratch, &h->uplane, &h->esc_ws,
-                      &h->esc_descs, &h->esc_rhs_energy};
+                      &h->esc_descs, &h->esc_rhs_energy, &h->rhs_sign, &h->apply_sign,
+                      &h->gph32, &h->gph64, &h->gpx, &h->gpy, &h->esc_rhs_sign};
     for (DevBuf* b : bufs) b->release();
     if (h->ev_sync) cudaEventDestroy(h->ev_sync);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
@@ -1595,7 +1797,7 @@ int iobm_open_channels(iobm_handle* h, double E, int* n_open, int max_out, int* 
     ModeTables mt;
     std::string msg;
     const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, h->nf, E, false, mt,
-                                     msg);
+                                     msg, h->kappa[0], h->kappa[1]);
     if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
     *n_open = mt.nopen;
     for (int c = 0; c < mt.nopen && c < max_out; ++c) {
@@ -1660,6 +1862,8 @@ int iobm_solve_batch(int n, iobm_handle* const* handles, const double* const* E,
     if (n < 1 || !handles || !E || !nE || (side != 0 && side != 1)) return IOBM_E_ARG;
     for (int j = 0; j < n; ++j) {
         if (!handles[j] || !E[j] || nE[j] < 1) return IOBM_E_ARG;
+        if (bloch(handles[j]))
+            return fail(handles[j], IOBM_E_UNSUPPORTED, "batched solves run at a zero Bloch vector");
         for (int i = 0; i < j; ++i)
             if (handles[i] == handles[j]) return fail(handles[j], IOBM_E_ARG, "a handle appears twice in the batch");
     }
@@ -1781,9 +1985,16 @@ int iobm_solution(iobm_handle* h, int rhs, void* dst, int dst_is_device) {
     const iobm_handle::User& U = h->users[rhs];
     const size_t bytes = sizeof(double2) * h->npts;
     double2* tmp = h->y64;   // scratch of the last solve
-    CK(launch_combine(tmp, h->x64 + (size_t)U.ic * h->npts, make_double2(1.0, 0.0),
-                      U.is >= 0 ? h->x64 + (size_t)U.is * h->npts : nullptr,
-                      make_double2(0.0, (double)U.sign), h->npts, h->stream));
+    if (bloch(h)) {
+        // psi = exp(i s kappa.r) phi, s = -1 for the -kappa channels (the upper slots)
+        const int sgn = U.energy < (int)h->energies.size() / 2 ? 1 : -1;
+        CK(launch_gauge(tmp, h->x64 + (size_t)U.ic * h->npts, h->gpx.as<double2>(),
+                        h->gpy.as<double2>(), sgn, h->g.nx, h->g.ny, h->g.nz, h->stream));
+    } else {
+        CK(launch_combine(tmp, h->x64 + (size_t)U.ic * h->npts, make_double2(1.0, 0.0),
+                          U.is >= 0 ? h->x64 + (size_t)U.is * h->npts : nullptr,
+                          make_double2(0.0, (double)U.sign), h->npts, h->stream));
+    }
     CK(cudaMemcpyAsync(dst, tmp, bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1866,16 +2077,22 @@ static int apply_common(iobm_handle* h, double E, int elem, const void* x, void*
         (elem != IOBM_ELEM_C64 && elem != IOBM_ELEM_C32 && !(elem == IOBM_ELEM_C64_DF && !precond)))
         return h ? fail(h, IOBM_E_ARG, "invalid apply arguments") : IOBM_E_ARG;
     if (nrhs == 0) return IOBM_OK;
+    if (bloch(h) && !precond && elem == IOBM_ELEM_C32)
+        return fail(h, IOBM_E_UNSUPPORTED, "the FP32 operator has no lateral Bloch phases");
     if (cudaEventRecord(h->ev_sync, h->user_stream) == cudaSuccess)
         cudaStreamWaitEvent(h->stream, h->ev_sync, 0);
     CK(ensure_sigma_scratch(h, nrhs));
+    if (bloch(h)) {   // every vector at +kappa
+        std::vector<int> ones(nrhs, 1);
+        CK(upload(h->apply_sign, ones, h->stream));
+    }
     long long launches = 0;
     const bool need_tables = !precond || h->opt.use_precond == IOBM_PRECOND_FOURIER;
     if (need_tables) {
         ModeTables mt;
         std::string msg;
         const int rc = build_mode_tables(h->g.nx, h->g.ny, h->g.hx, h->g.hy, h->g.hz, h->nf, E, true,
-                                         mt, msg);
+                                         mt, msg, h->kappa[0], h->kappa[1]);
         if (rc) return fail(h, rc == 2 ? IOBM_E_THRESHOLD : IOBM_E_UNSUPPORTED, msg);
         std::vector<double2> s64(mt.sigma.size()), p64(mt.pc.size());
         std::vector<float2> s32(mt.sigma.size()), p32(mt.pc.size());
@@ -1924,7 +2141,8 @@ static int apply_common(iobm_handle* h, double E, int elem, const void* x, void*
         int rc2;
         if (elem == IOBM_ELEM_C64 || elem == IOBM_ELEM_C64_DF)
             rc2 = apply_operator<double>(h, x, y, nrhs, h->apply_sig64.p, h->apply_ediag.as<double>(),
-                                         nullptr, nullptr, M_ALL, launches, elem == IOBM_ELEM_C64_DF);
+                                         nullptr, nullptr, M_ALL, launches, elem == IOBM_ELEM_C64_DF,
+                                         h->apply_sign.as<int>());
         else
             rc2 = apply_operator<float>(h, x, y, nrhs, h->apply_sig32.p, h->apply_ediag.as<double>(),
                                         nullptr, nullptr, M_ALL, launches);
@@ -2007,6 +2225,42 @@ int iobm_channels_host_bloch(const iobm_grid* g, double kappa_x, double kappa_y,
             sigma[2 * i] = mt.sigma[i].real();
             sigma[2 * i + 1] = mt.sigma[i].imag();
         }
+    return IOBM_OK;
+}
+
+int iobm_set_bloch(iobm_handle* h, double kappa_x, double kappa_y) {
+    if (!h) return IOBM_E_ARG;
+    if (!std::isfinite(kappa_x) || !std::isfinite(kappa_y))
+        return fail(h, IOBM_E_ARG, "non-finite Bloch vector");
+    if ((kappa_x != 0.0 || kappa_y != 0.0) &&
+        (h->opt.use_precond != IOBM_PRECOND_FOURIER || h->opt.op_form != IOBM_OP_AUTO))
+        return fail(h, IOBM_E_UNSUPPORTED,
+                    "a nonzero Bloch vector needs the free-propagator preconditioner and the "
+                    "implicit operator form");
+    h->kappa[0] = kappa_x;
+    h->kappa[1] = kappa_y;
+    h->solved = false;
+    h->memo_E.clear();
+    h->memo_tables.clear();
+    if (!bloch(h)) return IOBM_OK;
+    // exp(i kappa.r) on the lateral plane (KB gauge phases) and per axis (read-back)
+    std::vector<double2> px(h->g.nx), py(h->g.ny), g64((size_t)h->nxy);
+    std::vector<float2> g32((size_t)h->nxy);
+    for (int x = 0; x < h->g.nx; ++x)
+        px[x] = make_double2(std::cos(kappa_x * x * h->g.hx), std::sin(kappa_x * x * h->g.hx));
+    for (int y = 0; y < h->g.ny; ++y)
+        py[y] = make_double2(std::cos(kappa_y * y * h->g.hy), std::sin(kappa_y * y * h->g.hy));
+    for (int y = 0; y < h->g.ny; ++y)
+        for (int x = 0; x < h->g.nx; ++x) {
+            const double a = kappa_x * x * h->g.hx + kappa_y * y * h->g.hy;
+            g64[(size_t)y * h->g.nx + x] = make_double2(std::cos(a), std::sin(a));
+            g32[(size_t)y * h->g.nx + x] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    CK(upload(h->gpx, px, h->stream));
+    CK(upload(h->gpy, py, h->stream));
+    CK(upload(h->gph64, g64, h->stream));
+    CK(upload(h->gph32, g32, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return IOBM_OK;
 }
 

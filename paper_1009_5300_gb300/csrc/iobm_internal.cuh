@@ -127,6 +127,13 @@ struct StencilArgs {
     long long wait_cycles;   // limit of the bounded copy waits (0: about one second)
     int wait_inject;         // 1: each CTA of the bulk-copy kernel also waits once on a
                              // barrier that no copy completes (tests the give-up path)
+    // Lateral Bloch vector kappa in the gauge phi = exp(-i kappa.r) psi (FP64 kernels
+    // only): with rhs_sign set, RHS i applies the operator at s kappa, s = rhs_sign[i]
+    // = +1 or -1, whose lateral taps are c_n (exp(i s n theta) x_{+n} + exp(-i s n theta)
+    // x_{-n}) = bc[n] (x_{+n} + x_{-n}) + i s bs[n] (x_{+n} - x_{-n}), theta = kappa h.
+    const int* rhs_sign;
+    T bxc[kMaxNf + 1], bxs[kMaxNf + 1];   // c_x,n cos(n kappa_x h_x), c_x,n sin(n kappa_x h_x)
+    T byc[kMaxNf + 1], bys[kMaxNf + 1];
 };
 
 // the double-float row kernel (FP64 data, operator apply without fused p or dots)
@@ -183,6 +190,12 @@ struct KbArgs {
     long long npts;
     C* sp;                   // scratch [rhs][nproj]: E_p dvol <p|x>
     const int* uplane;       // [nz+1]: union points of plane k are uidx[uplane[k] .. uplane[k+1])
+    // Lateral Bloch vector (gauge phi = exp(-i kappa.r) psi): with rhs_sign set, the
+    // projector of RHS i is p(r) exp(i s kappa.r) on the right and p(r) exp(-i s kappa.r)
+    // on the left, s = rhs_sign[i]; gph[l] = exp(i kappa.r_l) on the lateral plane.
+    const int* rhs_sign;
+    const C* gph;
+    int nxy;
 };
 
 // dot-product partial slots the KB application writes per RHS
@@ -243,11 +256,27 @@ template <typename T> size_t sigma_smem_bytes(int nx, int ny, int threads);
 template <typename T> cudaError_t launch_kb(const KbArgs<T>& a, int nrhs, cudaStream_t s);
 
 // Krylov scalar and vector kernels
+// pairs > 0: preconditioned Bi-CG on RHS pairs (i, i + pairs), i < pairs, the primary
+// solving A x = b and its shadow A^T x~ = b~ (nrhs = 2 pairs).  rho = r~^T z and
+// mu = p~^T q are the primary's partials (launch_pair_dot); both members share
+// alpha, beta and their status (a pair stops, is replaced or breaks down together).
 cudaError_t launch_beta(RhsState* st, const double2* rho_part, const double* rr_part, int nslots,
                         int slot_stride, int nrhs, int max_iter, double tol2, double delta2,
-                        int mixed, cudaStream_t s);
+                        int mixed, cudaStream_t s, int pairs = 0);
 cudaError_t launch_alpha(RhsState* st, const double2* mu_part, int nslots, int slot_stride,
-                         int nrhs, cudaStream_t s);
+                         int nrhs, cudaStream_t s, int pairs = 0);
+// Bi-CG cross products: part[i][slot] = partials of a_{i+pairs}^T b_i for every pair i
+// whose primary has a status in mask; a is the shadow's vector (or, with a_dir, a
+// host array of the two direction buffers: the shadow's new direction
+// a_dir[1 - pbuf]), b the primary's.  nslots equal chunks of the RHS.
+template <typename T>
+cudaError_t launch_pair_dot(const typename Cplx<T>::type* a, typename Cplx<T>::type* const* a_dir,
+                            const typename Cplx<T>::type* b, const RhsState* st, int mask,
+                            long long npts, int pairs, double2* part, int nslots, int slot_stride,
+                            cudaStream_t s);
+// dst[i] = src[i] * exp(i s kappa.r) for one vector (s = +1 or -1; phx[x] = exp(i kappa_x x h_x))
+cudaError_t launch_gauge(double2* dst, const double2* src, const double2* phx, const double2* phy,
+                         int sign, int nx, int ny, int nz, cudaStream_t s);
 cudaError_t launch_restart_scalars(RhsState* st, const double2* rho_part, const double* rr_part,
                                    int nslots, int slot_stride, int nrhs, cudaStream_t s);
 // x += alpha p, r -= alpha q with p = pbufs[pbuf] of each RHS
@@ -286,7 +315,7 @@ cudaError_t launch_status_cond(cudaGraphConditionalHandle cond, const RhsState* 
 cudaError_t launch_batch_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
                               int* counter, int max_chunks, cudaStream_t s);
 cudaError_t launch_check(RhsState* st, const double* rr_part, int nslots, int slot_stride,
-                         int nrhs, double tol2, int init, cudaStream_t s);
+                         int nrhs, double tol2, int init, cudaStream_t s, int pairs = 0);
 cudaError_t launch_projection(const double2* psi, const RhsDesc* desc, const int* open_ptr,
                               const int2* open_bins, const double2* phx, const double2* phy,
                               int nx, int ny, int nz, int nf, int max_open, double2* out,

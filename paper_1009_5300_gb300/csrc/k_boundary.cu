@@ -293,6 +293,14 @@ constexpr int kKbRhs = 4;              // RHS per CTA
 
 int kb_slots(int nunion) { return (nunion + kKbApplyThreads - 1) / kKbApplyThreads; }
 
+// exp(i s kappa.r_l) from gph[l] = exp(i kappa.r_l), s = +1 or -1
+template <typename C>
+__device__ __forceinline__ C bloch_phase(const C* gph, int l, int s) {
+    C g = gph[l];
+    if (s < 0) g.y = -g.y;
+    return g;
+}
+
 template <typename T>
 __device__ __forceinline__ bool kb_rhs_live(const KbArgs<T>& a, int rhs, int nrhs) {
     if (rhs >= nrhs) return false;
@@ -340,6 +348,16 @@ __global__ void __launch_bounds__(kKbProjThreads) k_kb_proj(const KbArgs<T> a, i
 #pragma unroll
             for (int u = 0; u < kKbBatch; ++u)
                 xv[j][u] = (live[j] && idx[u] >= 0) ? X[j][idx[u]] : czero<C>();
+        if (a.rhs_sign) {   // right projector p(r) exp(i s kappa.r) (gauge of a Bloch vector)
+#pragma unroll
+            for (int j = 0; j < kKbRhs; ++j) {
+                const int sj = live[j] ? a.rhs_sign[r0 + j] : 1;
+#pragma unroll
+                for (int u = 0; u < kKbBatch; ++u)
+                    if (live[j] && idx[u] >= 0)
+                        xv[j][u] = cmul(bloch_phase(a.gph, idx[u] % a.nxy, sj), xv[j][u]);
+            }
+        }
 #pragma unroll
         for (int j = 0; j < kKbRhs; ++j)
 #pragma unroll
@@ -412,6 +430,11 @@ __global__ void __launch_bounds__(kKbApplyThreads) k_kb_apply(const KbArgs<T> a,
 #pragma unroll
         for (int j = 0; j < kKbRhs; ++j)
             if (live[j]) acc[j] = caxpy(v, a.sp[(long long)(r0 + j) * a.nproj + pj], acc[j]);
+    }
+    if (a.rhs_sign && in) {   // left projector p(r) exp(-i s kappa.r)
+#pragma unroll
+        for (int j = 0; j < kKbRhs; ++j)
+            if (live[j]) acc[j] = cmul(bloch_phase(a.gph, g % a.nxy, -a.rhs_sign[r0 + j]), acc[j]);
     }
 #pragma unroll
     for (int j = 0; j < kKbRhs; ++j) {

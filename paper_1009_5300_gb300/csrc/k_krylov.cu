@@ -30,10 +30,67 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Bi-CG pairs (primary i, shadow i + pairs): rho = r~^T z from the primary's
+// partials, each member's |r|^2 from its own; the pair moves through the states
+// together (it is replaced when either member's residual fell by delta, it stops
+// when both are below tol).
+__device__ void beta_pair(RhsState* st, const double2* rho_part, const double* rr_part, int nslots,
+                          int stride, int i, int pairs, int max_iter, double tol2, double delta2,
+                          int mixed, int lane) {
+    const int j = i + pairs;
+    if (st[i].status != ST_ACTIVE) return;
+    double rx = 0.0, ry = 0.0, ri = 0.0, rj = 0.0;
+    for (int k = lane; k < nslots; k += 32) {
+        const double2 v = rho_part[(long long)i * stride + k];
+        rx += v.x;
+        ry += v.y;
+        ri += rr_part[(long long)i * stride + k];
+        rj += rr_part[(long long)j * stride + k];
+    }
+    rx = warp_sum(rx);
+    ry = warp_sum(ry);
+    ri = warp_sum(ri);
+    rj = warp_sum(rj);
+    if (lane != 0) return;
+    RhsState A = st[i], B = st[j];
+    const double2 rho = make_double2(rx, ry);
+    A.rr = ri;
+    B.rr = rj;
+    int to = ST_ACTIVE;
+    if (!isfinite(ri) || !isfinite(rj)) {
+        to = ST_BREAKDOWN;
+    } else if ((ri <= tol2 * A.bb && rj <= tol2 * B.bb) ||
+               (mixed && (ri <= delta2 * A.rr_ref || rj <= delta2 * B.rr_ref))) {
+        to = ST_PENDING;
+    } else if (A.iters >= max_iter) {
+        to = ST_NOCONV;
+    } else if (!finite2(rho) || (rho.x == 0.0 && rho.y == 0.0)) {
+        to = ST_BREAKDOWN;
+    }
+    if (to == ST_ACTIVE) {
+        const double2 be = A.first ? make_double2(0.0, 0.0) : cdiv(rho, A.rho);
+        A.beta = B.beta = be;
+        A.rho_prev = B.rho_prev = A.rho;
+        A.rho = B.rho = rho;
+        A.iters += 1;
+        B.iters += 1;
+    }
+    A.status = B.status = to;
+    st[i] = A;
+    st[j] = B;
+}
+
 __global__ void k_beta(RhsState* st, const double2* rho_part, const double* rr_part, int nslots,
-                       int stride, int nrhs, int max_iter, double tol2, double delta2, int mixed) {
+                       int stride, int nrhs, int max_iter, double tol2, double delta2, int mixed,
+                       int pairs) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    if (pairs > 0) {
+        if (i < pairs)
+            beta_pair(st, rho_part, rr_part, nslots, stride, i, pairs, max_iter, tol2, delta2, mixed,
+                      lane);
+        return;
+    }
     if (i >= nrhs) return;   // whole warps
     if (st[i].status != ST_ACTIVE) return;
     double rx = 0.0, ry = 0.0, rr = 0.0;
@@ -67,10 +124,11 @@ __global__ void k_beta(RhsState* st, const double2* rho_part, const double* rr_p
     st[i] = S;
 }
 
-__global__ void k_alpha(RhsState* st, const double2* mu_part, int nslots, int stride, int nrhs) {
+__global__ void k_alpha(RhsState* st, const double2* mu_part, int nslots, int stride, int nrhs,
+                        int pairs) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (i >= nrhs) return;
+    if (i >= (pairs > 0 ? pairs : nrhs)) return;
     if (st[i].status != ST_ACTIVE) return;
     double mx = 0.0, my = 0.0;
     for (int j = lane; j < nslots; j += 32) {
@@ -82,7 +140,7 @@ __global__ void k_alpha(RhsState* st, const double2* mu_part, int nslots, int st
     my = warp_sum(my);
     if (lane != 0) return;
     RhsState S = st[i];
-    const double2 mu = make_double2(mx, my);
+    const double2 mu = make_double2(mx, my);   // pairs: mu = p~^T q, the shadow's p~
     if (!finite2(mu) || (mu.x == 0.0 && mu.y == 0.0)) {
         S.status = ST_BREAKDOWN;
     } else {
@@ -91,6 +149,14 @@ __global__ void k_alpha(RhsState* st, const double2* mu_part, int nslots, int st
     }
     S.first = 0;
     st[i] = S;
+    if (pairs > 0) {   // the shadow takes the same alpha and status
+        RhsState B = st[i + pairs];
+        B.status = S.status;
+        B.alpha = S.alpha;
+        if (S.status != ST_BREAKDOWN) B.pbuf ^= 1;
+        B.first = 0;
+        st[i + pairs] = B;
+    }
 }
 
 __global__ void k_restart_scalars(RhsState* st, const double2* rho_part, const double* rr_part,
@@ -104,15 +170,72 @@ __global__ void k_restart_scalars(RhsState* st, const double2* rho_part, const d
 
 cudaError_t launch_beta(RhsState* st, const double2* rho_part, const double* rr_part, int nslots,
                         int slot_stride, int nrhs, int max_iter, double tol2, double delta2,
-                        int mixed, cudaStream_t s) {
+                        int mixed, cudaStream_t s, int pairs) {
     k_beta<<<(nrhs + 3) / 4, 128, 0, s>>>(st, rho_part, rr_part, nslots, slot_stride, nrhs,
-                                          max_iter, tol2, delta2, mixed);   // a warp per RHS
+                                          max_iter, tol2, delta2, mixed, pairs);   // a warp per RHS
     return cudaGetLastError();
 }
 cudaError_t launch_alpha(RhsState* st, const double2* mu_part, int nslots, int slot_stride,
-                         int nrhs, cudaStream_t s) {
-    k_alpha<<<(nrhs + 3) / 4, 128, 0, s>>>(st, mu_part, nslots, slot_stride, nrhs);
+                         int nrhs, cudaStream_t s, int pairs) {
+    k_alpha<<<(nrhs + 3) / 4, 128, 0, s>>>(st, mu_part, nslots, slot_stride, nrhs, pairs);
     return cudaGetLastError();
+}
+
+// Bi-CG cross products a_{i+pairs}^T b_i: block x of pair i sums the points of
+// chunk x (equal chunks of the RHS, fixed order) into part[i][x].
+template <typename T>
+__global__ void k_pair_dot(const typename Cplx<T>::type* __restrict__ a,
+                           const typename Cplx<T>::type* dir0, const typename Cplx<T>::type* dir1,
+                           const typename Cplx<T>::type* __restrict__ b, const RhsState* st,
+                           int mask, long long npts, int pairs, double2* part, int slot_stride) {
+    using C = typename Cplx<T>::type;
+    __shared__ double red[3 * 8];
+    const int i = blockIdx.y, j = i + pairs;
+    if (!((1 << st[i].status) & mask)) return;
+    const C* __restrict__ av = (dir0 ? ((st[j].pbuf & 1) ? dir0 : dir1) : a) + (long long)j * npts;
+    const C* __restrict__ bv = b + (long long)i * npts;
+    const long long chunk = (npts + gridDim.x - 1) / gridDim.x;
+    const long long k0 = blockIdx.x * chunk, k1 = min(npts, k0 + chunk);
+    double re = 0.0, im = 0.0;
+    for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const C u = av[k], v = bv[k];
+        re += (double)u.x * v.x - (double)u.y * v.y;
+        im += (double)u.x * v.y + (double)u.y * v.x;
+    }
+    double z = 0.0;
+    block_reduce_3(re, im, z, red);
+    if (threadIdx.x == 0) part[(long long)i * slot_stride + blockIdx.x] = make_double2(re, im);
+}
+
+template <typename T>
+cudaError_t launch_pair_dot(const typename Cplx<T>::type* a, typename Cplx<T>::type* const* a_dir,
+                            const typename Cplx<T>::type* b, const RhsState* st, int mask,
+                            long long npts, int pairs, double2* part, int nslots, int slot_stride,
+                            cudaStream_t s) {
+    if (pairs <= 0 || nslots <= 0) return cudaSuccess;
+    k_pair_dot<T><<<dim3(nslots, pairs), 256, 0, s>>>(a, a_dir ? a_dir[0] : nullptr,
+                                                        a_dir ? a_dir[1] : nullptr, b, st, mask,
+                                                        npts, pairs, part, slot_stride);
+    return cudaGetLastError();
+}
+template cudaError_t launch_pair_dot<float>(const float2*, float2* const*, const float2*,
+                                            const RhsState*, int, long long, int, double2*, int,
+                                            int, cudaStream_t);
+template cudaError_t launch_pair_dot<double>(const double2*, double2* const*, const double2*,
+                                             const RhsState*, int, long long, int, double2*, int,
+                                             int, cudaStream_t);
+
+__global__ void k_gauge(double2* __restrict__ dst, const double2* __restrict__ src,
+                        const double2* phx, const double2* phy, int sign, int nx, int ny,
+                        long long npts) {
+    const long long nxy = (long long)nx * ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(i % nxy);
+        double2 ph = cmul(phx[l % nx], phy[l / nx]);
+        if (sign < 0) ph.y = -ph.y;
+        dst[i] = cmul(ph, src[i]);
+    }
 }
 cudaError_t launch_restart_scalars(RhsState* st, const double2* rho_part, const double* rr_part,
                                    int nslots, int slot_stride, int nrhs, cudaStream_t s) {
@@ -256,6 +379,11 @@ __global__ void __launch_bounds__(256) k_pq_update(const typename Cplx<T>::type*
                 C acc = czero<C>();
                 for (int e = kb.uptr[u]; e < kb.uptr[u + 1]; ++e)
                     acc = caxpy(kb.uval[e], S[kb.uproj[e]], acc);
+                if (kb.rhs_sign) {   // left projector p(r) exp(-i s kappa.r)
+                    C ph = kb.gph[g];
+                    if (kb.rhs_sign[rhs] > 0) ph.y = -ph.y;
+                    acc = cmul(ph, acc);
+                }
                 qp[g] = csub(qp[g], acc);
                 const C pv = pnew[g];
                 mre -= pv.x * acc.x - pv.y * acc.y;
@@ -408,9 +536,43 @@ template cudaError_t launch_residual<double>(const double2*, double2*, double2*,
 
 // init = 1: record ||b||^2 and start every RHS; init = 0: judge the FP64
 // residual of the PENDING RHS; init = 2: record the residual of RHS that stopped.
+// pairs > 0, init = 0: the FP64 check of a Bi-CG pair, both members together
+__device__ void check_pair(RhsState* st, const double* rr_part, int nslots, int stride, int i,
+                           int pairs, double tol2) {
+    const int j = i + pairs;
+    RhsState A = st[i], B = st[j];
+    if (A.status != ST_PENDING) return;
+    double ri = 0.0, rj = 0.0;
+    for (int k = 0; k < nslots; ++k) {
+        ri += rr_part[(long long)i * stride + k];
+        rj += rr_part[(long long)j * stride + k];
+    }
+    A.res64 = sqrt(ri / A.bb);
+    B.res64 = sqrt(rj / B.bb);
+    A.replacements += 1;
+    B.replacements += 1;
+    int to;
+    if (ri <= tol2 * A.bb && rj <= tol2 * B.bb) {
+        to = ST_CONVERGED;
+    } else if (!isfinite(ri) || !isfinite(rj)) {
+        to = ST_BREAKDOWN;
+    } else {
+        A.rr_ref = ri;
+        B.rr_ref = rj;
+        to = ST_RESTART;
+    }
+    A.status = B.status = to;
+    st[i] = A;
+    st[j] = B;
+}
+
 __global__ void k_check(RhsState* st, const double* rr_part, int nslots, int stride, int nrhs,
-                        double tol2, int init) {
+                        double tol2, int init, int pairs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pairs > 0 && init == 0) {
+        if (i < pairs) check_pair(st, rr_part, nslots, stride, i, pairs, tol2);
+        return;
+    }
     if (i >= nrhs) return;
     RhsState S = st[i];
     double rr = 0.0;
@@ -464,8 +626,9 @@ cudaError_t launch_set_status(RhsState* st, int nrhs, int from, int to, cudaStre
 }
 
 cudaError_t launch_check(RhsState* st, const double* rr_part, int nslots, int slot_stride,
-                         int nrhs, double tol2, int init, cudaStream_t s) {
-    k_check<<<(nrhs + 127) / 128, 128, 0, s>>>(st, rr_part, nslots, slot_stride, nrhs, tol2, init);
+                         int nrhs, double tol2, int init, cudaStream_t s, int pairs) {
+    k_check<<<(nrhs + 127) / 128, 128, 0, s>>>(st, rr_part, nslots, slot_stride, nrhs, tol2, init,
+                                               pairs);
     return cudaGetLastError();
 }
 
@@ -582,6 +745,13 @@ __global__ void k_combine(double2* __restrict__ dst, const double2* __restrict__
         if (x2) v = cfma(c2, x2[i], v);
         dst[i] = v;
     }
+}
+
+cudaError_t launch_gauge(double2* dst, const double2* src, const double2* phx, const double2* phy,
+                         int sign, int nx, int ny, int nz, cudaStream_t s) {
+    const long long npts = (long long)nx * ny * nz;
+    k_gauge<<<vec_blocks(npts), 256, 0, s>>>(dst, src, phx, phy, sign, nx, ny, npts);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_combine(double2* dst, const double2* x1, double2 c1, const double2* x2,

@@ -29,6 +29,18 @@ namespace iobm {
 constexpr int kTX = 32;
 constexpr int kTY = 8;
 
+// One lateral tap pair at a lateral Bloch vector (gauge exp(-i kappa.r)):
+// acc + c (x_m + x_p) + i s (x_p - x_m), with c = c_n cos(n theta) and s the signed
+// c_n sin(n theta): the taps c_n exp(-+ i n theta) on x_{-+n}.
+template <typename C, typename T>
+__device__ __forceinline__ C bloch_taps(C acc, C xm, C xp, T c, T s) {
+    acc = caxpy(c, cadd(xm, xp), acc);
+    const C d = csub(xp, xm);
+    acc.x -= s * d.y;
+    acc.y += s * d.x;
+    return acc;
+}
+
 template <typename T, int NF>
 __global__ void __launch_bounds__(kTX* kTY) k_stencil(const StencilArgs<T> a) {
     using C = typename Cplx<T>::type;
@@ -67,6 +79,7 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(const StencilArgs<T> a) {
     C* __restrict__ PN = a.fused_p ? a.pbufs[1 - pb] + base : nullptr;
     const T ed = a.ediag ? (T)a.ediag[a.rhs_energy ? a.rhs_energy[rhs] : 0] : (T)0;
     const T cen = a.c0 + ed;
+    const int sg = (sizeof(T) == 8 && a.rhs_sign) ? a.rhs_sign[rhs] : 0;   // Bloch phase sign
     T tapsum2 = 0;   // 2 sum_n (c_x,n + c_y,n + c_z,n): moves the taps' diagonal into the direct form
 #pragma unroll
     for (int n = 1; n <= NF; ++n) tapsum2 += 2 * (a.cx[n] + a.cy[n] + a.cz[n]);
@@ -115,11 +128,22 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(const StencilArgs<T> a) {
             if constexpr (sizeof(T) == 8) {
                 // FP64: direct form, the diagonal carries -2 sum c_n
                 acc = cscale(x0, d - tapsum2);
+                if (sg == 0) {
 #pragma unroll
-                for (int n = 1; n <= NF; ++n) {
-                    acc = caxpy(a.cz[n], cadd(q[NF - n], q[NF + n]), acc);
-                    acc = caxpy(a.cx[n], cadd(tile[ly + NF][lx + NF - n], tile[ly + NF][lx + NF + n]), acc);
-                    acc = caxpy(a.cy[n], cadd(tile[ly + NF - n][lx + NF], tile[ly + NF + n][lx + NF]), acc);
+                    for (int n = 1; n <= NF; ++n) {
+                        acc = caxpy(a.cz[n], cadd(q[NF - n], q[NF + n]), acc);
+                        acc = caxpy(a.cx[n], cadd(tile[ly + NF][lx + NF - n], tile[ly + NF][lx + NF + n]), acc);
+                        acc = caxpy(a.cy[n], cadd(tile[ly + NF - n][lx + NF], tile[ly + NF + n][lx + NF]), acc);
+                    }
+                } else {
+#pragma unroll
+                    for (int n = 1; n <= NF; ++n) {
+                        acc = caxpy(a.cz[n], cadd(q[NF - n], q[NF + n]), acc);
+                        acc = bloch_taps(acc, tile[ly + NF][lx + NF - n], tile[ly + NF][lx + NF + n],
+                                         a.bxc[n], sg * a.bxs[n]);
+                        acc = bloch_taps(acc, tile[ly + NF - n][lx + NF], tile[ly + NF + n][lx + NF],
+                                         a.byc[n], sg * a.bys[n]);
+                    }
                 }
             } else {
                 const C x2 = cadd(x0, x0);
@@ -209,6 +233,7 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
     C* __restrict__ PN = a.fused_p ? a.pbufs[1 - pb] + base : nullptr;
     const T ed = a.ediag ? (T)a.ediag[a.rhs_energy ? a.rhs_energy[rhs] : 0] : (T)0;
     const T cen = a.c0 + ed;
+    const int sg = (sizeof(T) == 8 && a.rhs_sign) ? a.rhs_sign[rhs] : 0;   // Bloch phase sign
     T tapsum2 = 0;   // 2 sum_n (c_x,n + c_y,n + c_z,n): moves the taps' diagonal into the direct form
 #pragma unroll
     for (int n = 1; n <= NF; ++n) tapsum2 += 2 * (a.cx[n] + a.cy[n] + a.cz[n]);
@@ -298,13 +323,24 @@ __global__ void __launch_bounds__(512) k_stencil_rows(const StencilArgs<T> a) {
                 // FP64: direct form, the diagonal carries -2 sum c_n (2 instead of 3
                 // FP64 operations per tap pair and component; the FP64 ALU is the limit)
                 acc = cscale(x0, d - tapsum2);
+                if (sg == 0) {
 #pragma unroll
-                for (int n = 1; n <= NF; ++n) {
-                    const int xm = (x - n < 0) ? x - n + nx : x - n;
-                    const int xp = (x + n >= nx) ? x + n - nx : x + n;
-                    acc = caxpy(a.cz[n], cadd(q[NF - n], q[NF + n]), acc);
-                    acc = caxpy(a.cx[n], cadd(row[xm], row[xp]), acc);
-                    acc = caxpy(a.cy[n], cadd(row[x - n * nx], row[x + n * nx]), acc);
+                    for (int n = 1; n <= NF; ++n) {
+                        const int xm = (x - n < 0) ? x - n + nx : x - n;
+                        const int xp = (x + n >= nx) ? x + n - nx : x + n;
+                        acc = caxpy(a.cz[n], cadd(q[NF - n], q[NF + n]), acc);
+                        acc = caxpy(a.cx[n], cadd(row[xm], row[xp]), acc);
+                        acc = caxpy(a.cy[n], cadd(row[x - n * nx], row[x + n * nx]), acc);
+                    }
+                } else {
+#pragma unroll
+                    for (int n = 1; n <= NF; ++n) {
+                        const int xm = (x - n < 0) ? x - n + nx : x - n;
+                        const int xp = (x + n >= nx) ? x + n - nx : x + n;
+                        acc = caxpy(a.cz[n], cadd(q[NF - n], q[NF + n]), acc);
+                        acc = bloch_taps(acc, row[xm], row[xp], a.bxc[n], sg * a.bxs[n]);
+                        acc = bloch_taps(acc, row[x - n * nx], row[x + n * nx], a.byc[n], sg * a.bys[n]);
+                    }
                 }
             } else {
                 const C x2 = cadd(x0, x0);
@@ -667,7 +703,8 @@ static cudaError_t launch_tma_nf(const StencilArgs<float>& a, dim3 grid, cudaStr
 template <typename T>
 cudaError_t launch_stencil(const StencilArgs<T>& a0, int nrhs, cudaStream_t s) {
     if constexpr (sizeof(T) == 8) {
-        if (a0.variant == 2 && !a0.fused_p && !a0.dot_mode && stencil_df_supported(a0.nx, a0.nf))
+        if (a0.variant == 2 && !a0.fused_p && !a0.dot_mode && !a0.rhs_sign &&
+            stencil_df_supported(a0.nx, a0.nf))
             return launch_stencil_df(a0, nrhs, s);
     }
     if (use_rows(a0.nx, a0.nf)) {

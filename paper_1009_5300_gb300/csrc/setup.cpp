@@ -385,7 +385,8 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
 }
 
 int build_mode_tables_many(int nx, int ny, double hx, double hy, double hz, int nf, const double* E,
-                           int nE, bool want_sigma, std::vector<ModeTables>& out, std::string& msg) {
+                           int nE, bool want_sigma, std::vector<ModeTables>& out, std::string& msg,
+                           double kappa_x, double kappa_y) {
     out.assign(nE, ModeTables());
     std::vector<int> rc(nE, 0);
     std::vector<std::string> msgs(nE);
@@ -393,7 +394,8 @@ int build_mode_tables_many(int nx, int ny, double hx, double hy, double hz, int 
     std::atomic<int> next(0);
     auto work = [&]() {
         for (int e = next++; e < nE; e = next++)
-            rc[e] = build_mode_tables(nx, ny, hx, hy, hz, nf, E[e], want_sigma, out[e], msgs[e]);
+            rc[e] = build_mode_tables(nx, ny, hx, hy, hz, nf, E[e], want_sigma, out[e], msgs[e],
+                                      kappa_x, kappa_y);
     };
     std::vector<std::thread> pool;
     for (int t = 1; t < nth; ++t) pool.emplace_back(work);

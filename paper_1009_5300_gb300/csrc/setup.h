@@ -46,7 +46,8 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
 
 // The tables of several energies, built in parallel host threads.
 int build_mode_tables_many(int nx, int ny, double hx, double hy, double hz, int nf, const double* E,
-                           int nE, bool want_sigma, std::vector<ModeTables>& out, std::string& msg);
+                           int nE, bool want_sigma, std::vector<ModeTables>& out, std::string& msg,
+                           double kappa_x = 0.0, double kappa_y = 0.0);
 
 // Radix plan of a lateral FFT length (radices 4, 2, 3, 5); false if n has
 // another prime factor.

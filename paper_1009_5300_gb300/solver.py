@@ -132,6 +132,7 @@ class IOBMSolver:
             raise _lib.IOBMError(rc, self.lib.iobm_status_string(rc).decode() + ": " + msg)
         self.h = h
         self._ws = None
+        self.kappa = (0.0, 0.0)
 
     @classmethod
     def from_junction(cls, jn, **kw):
@@ -216,8 +217,17 @@ class IOBMSolver:
     def set_tiling(self, zchunk: int, variant: int = 0):
         check(self.lib.iobm_set_tiling(self.h, int(zchunk), int(variant)), self.h)
 
+    def set_bloch(self, kappa):
+        """Lateral Bloch vector (kappa_x, kappa_y) of the later solves (iobm_set_bloch).
+        At kappa != 0 a solve also returns the -kappa problem: energy slots nE + e."""
+        kx, ky = float(kappa[0]), float(kappa[1])
+        check(self.lib.iobm_set_bloch(self.h, kx, ky), self.h)
+        self.kappa = (kx, ky)
+
     def transmission(self, E) -> SolveResult:
         nrhs = self.lib.iobm_num_rhs(self.h)
+        if self.kappa != (0.0, 0.0):
+            E = np.concatenate([np.asarray(E), np.asarray(E)])   # +kappa slots, then -kappa
         nE = len(E)
         n_open = np.zeros(nE, np.int32)
         G = np.zeros(nE)
@@ -259,7 +269,8 @@ class IOBMSolver:
     def grad_V(self, E: float):
         """(dG/dV as a [nz][ny][nx] float64 CUDA tensor, G) at energy E."""
         n = self.open_channels(E)[0].shape[0]
-        self._ensure_workspace(max(2 * n, 1))   # forward and adjoint real-profile RHS
+        # forward and adjoint RHS (real profiles; at kappa != 0 one Bi-CG pair per channel)
+        self._ensure_workspace(max(2 * n, 1))
         g = torch.empty(self.shape, dtype=torch.float64, device=self.device)
         G = C.c_double(0)
         with torch.cuda.device(self.device):
