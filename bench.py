@@ -51,11 +51,13 @@ ROOFLINE_KERNELS = {
              "bytes_rhs_point": 24.0, "bytes_point": 0.0, "dram_rhs_point": None},
 }
 ROOFLINE_STAGE = "update_fft"   # the kernel with the largest share of the bench step
-# The explicit-form stencil k_stencil_rows_tma<48,4,3>: 32 B per RHS-point (read z and
-# p_old, write p and q) + 4 B per point (V); DRAM bytes per RHS-point from an ncu capture
-# of the 8-energy wire48 case with all 56 RHS active: 695.0 MB / 20.64 M points
+# The explicit-form stencil (fused p = z + beta p_old, FD operator + V, p^T q): 32 B per
+# RHS-point (read z and p_old, write p and q) + 4 B per point (V) per launch; DRAM bytes
+# per RHS-point from an ncu capture, None until captured for the kernel as it stands.
+STENCIL_KERNEL = ("k_stencil_blk<48,4,4,4> (explicit form: fused p update + FD operator + "
+                  "p^T q; 4 rows per thread, bulk-copy staged)")
 STENCIL_BYTES_RHS_POINT = 32.0
-STENCIL_DRAM_BYTES_PER_RHS_POINT = 695.0e6 / (56 * 368640)
+STENCIL_DRAM_BYTES_PER_RHS_POINT = None
 WORKLOAD = ("wire48: 6-atom wire, Gaussian wells (0.5 Ha, width 1.5 bohr, spacing 6.8 bohr) "
             "+ s/p KB projectors (radius 3 bohr), 48x48x160 grid, h=0.35 bohr, 9-point FD, "
             "r_s=3.28 jellium, 32 energies in [E_F-2eV, E_F+0.5eV], all open channels, "
@@ -371,15 +373,28 @@ def native_arm(args, rank, world, local_rank):
             st_bytes = (STENCIL_BYTES_RHS_POINT * npts * rx.iterations_total
                         + 4.0 * npts * st_launches)
             st_ach = st_bytes / (st_ms / 1000.0) / 1e9
+            # the same kernel at full load: every internal RHS of the bench step active
+            # (workspace 6.7 GB, larger than L2), tiling picked by the autotuner
+            sx2 = IOBMSolver.from_junction(jn, precision="mixed", device=dev, op_form="explicit")
+            zc, var = sx2.autotune(nrhs_int)
+            fl_ms = sx2.time_operator(nrhs_int, reps=20)
+            sx2.close()
+            fl_ach = (STENCIL_BYTES_RHS_POINT * npts * nrhs_int + 4.0 * npts) / (fl_ms / 1e3) / 1e9
             extra["stencil_roofline"] = {
-                "kernel": "k_stencil_rows_tma<48,4,3> (explicit form: fused p update + "
-                          "FD operator + p^T q)",
-                "bound": "hbm", "achieved": st_ach, "peak": peak, "unit": "GB/s",
-                "frac": st_ach / peak, "launches": st_launches,
-                "avg_launch_ms": st_ms / st_launches,
-                "traffic": STENCIL_DRAM_BYTES_PER_RHS_POINT * npts * rx.iterations_total / st_launches,
-                "sample": "one explicit-form solve of the first 8 energies",
-                "iterations_mean": float(rx.iterations.mean())}
+                "kernel": STENCIL_KERNEL,
+                "bound": "hbm", "achieved": fl_ach, "peak": peak, "unit": "GB/s",
+                "frac": fl_ach / peak, "avg_launch_ms": fl_ms,
+                "alg_bytes_per_launch": STENCIL_BYTES_RHS_POINT * npts * nrhs_int + 4.0 * npts,
+                "traffic": STENCIL_DRAM_BYTES_PER_RHS_POINT * npts * nrhs_int
+                           if STENCIL_DRAM_BYTES_PER_RHS_POINT else None,
+                "sample": f"full load: {nrhs_int} RHS of the bench wire all active, 20 timed "
+                          f"launches (iobm_time_operator), autotuned tiling z-chunk {zc}, "
+                          f"variant {var}",
+                "in_solve": {"achieved": st_ach, "frac": st_ach / peak,
+                             "launches": st_launches, "avg_launch_ms": st_ms / st_launches,
+                             "sample": "one explicit-form solve of the first 8 energies (its "
+                                       "late launches run few RHS)",
+                             "iterations_mean": float(rx.iterations.mean())}}
         # plain FP64 GPU solver on the same work: every energy of the step in one batch,
         # same tolerance, timed the same way as the mixed step
         s64 = IOBMSolver.from_junction(jn, precision="fp64", device=dev)

@@ -262,8 +262,19 @@ int iobm_solve_batch(int n, iobm_handle* const* handles, const double* const* E,
 int iobm_autotune(iobm_handle* h, int nrhs, int* zchunk, int* variant);
 
 /* Set the stencil tiling explicitly: zchunk >= 16 z-planes per CTA; variant 0 =
- * the fastest kernel for the shape, 1 = the register-pipelined row kernel. */
+ * the fastest kernel for the shape, 1 = the register-pipelined row kernel, 3 = the
+ * bulk-copy row kernel with one row per thread (FP32 rows of 12 .. 64 points; 0 takes
+ * the bulk-copy kernel with several rows per thread where the shape allows). */
 int iobm_set_tiling(iobm_handle* h, int zchunk, int variant);
+
+/* Average device time (ms, CUDA events on the handle's stream) of one launch of the
+ * fused COCG operator kernel of the explicit operator form -- p = z + beta p_old,
+ * q = (E - T - V) p with the FD stencil of Eqs. 1-4, and the p^T q partials -- on
+ * nrhs RHS of this grid with every RHS active and the handle's tiling, after one
+ * warm-up launch; reps timed launches.  Binds the workspace for nrhs RHS (an attached
+ * one must be large enough) and overwrites it: the last solve's results are gone.
+ * A kernel-timing aid (the roofline of the stencil at full load). */
+int iobm_time_operator(iobm_handle* h, int nrhs, int reps, double* ms_per_launch);
 
 /* Eigenchannel transmissions of energy index e of the last solve (Sec. IV,
  * Table II: the eigenvalues of T^dagger T, T the transmission matrix): with

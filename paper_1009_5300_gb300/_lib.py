@@ -102,6 +102,7 @@ SIGNATURES = {
     "iobm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "iobm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int]),
     "iobm_set_bloch": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+    "iobm_time_operator": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "iobm_precond_dots_noalloc": (C.c_int, [C.POINTER(Grid), C.c_double, C.c_void_p, C.c_void_p,
                                             C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "iobm_kernel_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),

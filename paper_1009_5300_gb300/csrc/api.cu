@@ -1565,13 +1565,17 @@ int autotune_stencil(iobm_handle* h, int nrhs, int* zchunk_out, int* variant_out
     a.dot_part = h->mu_part;
     a.slot_stride = h->slot_stride;
     const int zcands[3] = {kZChunkMin, 32, 64};
-    const int nvar = std::is_same<T, float>::value ? 2 : 1;
+    // FP32: the fastest kernel for the shape, the register-pipelined rows, the one-row
+    // bulk-copy rows; FP64: one kernel
+    const int vcands[3] = {0, 1, 3};
+    const int nvar = std::is_same<T, float>::value ? 3 : 1;
     float best = -1.f;
     int best_z = h->zchunk, best_v = h->stencil_variant;
     for (int zi = 0; zi < 3; ++zi) {
         const int zc = zcands[zi];
         if (zi > 0 && zcands[zi - 1] >= h->g.nz) break;   // larger chunks are all the same launch
-        for (int v = 0; v < nvar; ++v) {
+        for (int vi = 0; vi < nvar; ++vi) {
+            const int v = vcands[vi];
             a.zchunk = zc;
             a.variant = v;
             CK(launch_stencil<T>(a, nrhs, h->stream));   // warm-up
@@ -1599,7 +1603,51 @@ int autotune_stencil(iobm_handle* h, int nrhs, int* zchunk_out, int* variant_out
     return IOBM_OK;
 }
 
+// Average CUDA-event time of the fused COCG operator launch (p = z + beta p_old,
+// q = (E - T - V) p, p^T q partials) on nrhs RHS with every RHS active, with the
+// handle's tiling: one warm-up launch, then reps timed launches.
+template <typename T>
+int time_operator(iobm_handle* h, int nrhs, int reps, double* ms_out) {
+    using C = typename Cplx<T>::type;
+    int rc = bind_workspace(h, nrhs);
+    if (rc) return rc;
+    const size_t bytes = sizeof(C) * (size_t)nrhs * h->npts;
+    // nonzero operands (every float 0x3c3c3c3c, about 0.0115)
+    CK(cudaMemsetAsync(h->vz, 0x3c, bytes, h->stream));
+    CK(cudaMemsetAsync(h->vp[0], 0x3c, bytes, h->stream));
+    StencilArgs<T> a = op_args<T>(h);
+    a.x = (const C*)h->vz;
+    a.pbufs[0] = (C*)h->vp[0];
+    a.pbufs[1] = (C*)h->vp[1];
+    a.y = (C*)h->vq;
+    a.fused_p = 1;
+    a.state = nullptr;   // every RHS active
+    a.dot_mode = 1;
+    a.dot_part = h->mu_part;
+    a.slot_stride = h->slot_stride;
+    CK(launch_stencil<T>(a, nrhs, h->stream));   // warm-up
+    CK(cudaEventRecord(h->ev_t0, h->stream));
+    for (int r = 0; r < reps; ++r) CK(launch_stencil<T>(a, nrhs, h->stream));
+    CK(cudaEventRecord(h->ev_t1, h->stream));
+    CK(cudaEventSynchronize(h->ev_t1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
+    *ms_out = ms / reps;
+    return check_err_flag(h);
+}
+
 extern "C" {
+
+int iobm_time_operator(iobm_handle* h, int nrhs, int reps, double* ms_per_launch) {
+    if (!h || nrhs < 1 || reps < 1 || !ms_per_launch)
+        return h ? fail(h, IOBM_E_ARG, "time_operator needs nrhs >= 1, reps >= 1") : IOBM_E_ARG;
+    if (cudaEventRecord(h->ev_sync, h->user_stream) == cudaSuccess)
+        cudaStreamWaitEvent(h->stream, h->ev_sync, 0);
+    const int rc = (h->opt.precision == IOBM_MIXED) ? time_operator<float>(h, nrhs, reps, ms_per_launch)
+                                                    : time_operator<double>(h, nrhs, reps, ms_per_launch);
+    h->solved = false;
+    return rc;
+}
 
 void iobm_default_options(iobm_options* o) {
     if (!o) return;
@@ -1850,7 +1898,7 @@ int iobm_autotune(iobm_handle* h, int nrhs, int* zchunk, int* variant) {
 
 int iobm_set_tiling(iobm_handle* h, int zchunk, int variant) {
     if (!h) return IOBM_E_ARG;
-    if (zchunk < kZChunkMin || (variant != 0 && variant != 1))
+    if (zchunk < kZChunkMin || (variant != 0 && variant != 1 && variant != 3))
         return fail(h, IOBM_E_ARG, "z-chunk below the minimum or unknown stencil variant");
     h->zchunk = zchunk;
     h->stencil_variant = variant;

@@ -635,6 +635,336 @@ __global__ void __launch_bounds__(NX * kRowTY, MINB) k_stencil_rows_tma(const St
     }
 }
 
+// ---------------------------------------------------------------------------
+// Blocked bulk-copy variant (FP32, row widths of the compile-time FFT plans, ny a
+// multiple of RY): the staging, tile and arithmetic of k_stencil_rows_tma, but each
+// thread owns PT consecutive rows of one x column, so a CTA of NX x TY threads covers
+// RY = TY PT rows.  The per-plane work of a thread (stage wait, CTA barrier, loop and
+// address arithmetic, its share of the halo fill) then serves PT points, and the y
+// taps between a thread's own rows come from its registers: per plane a thread reads
+// 2 N_f tile values for its y taps instead of 2 N_f per point.  The potential of the
+// own rows arrives with the stage (one more bulk copy), and the taps accumulate per
+// axis (three independent chains).
+template <int NX, int NF, int PT, int TY, int D_ = 3>
+struct BlkTma {
+    static constexpr int RY = TY * PT;           // own rows of a CTA
+    static constexpr int SR = RY + 2 * NF;       // tile / stage rows
+    static constexpr int TP = NX + 2 * NF;       // tile pitch (periodic pad columns)
+    static constexpr int TILE = SR * TP;
+    static constexpr int SLAB = SR * NX;
+    static constexpr int VSLAB = RY * NX / 2;    // float2 units holding RY x NX floats
+    static constexpr int D = D_;                 // stages (copies issued D planes ahead)
+    static constexpr int STAGE = 2 * SLAB + VSLAB;
+    static constexpr size_t smem = 128 + sizeof(float2) * (2 * (size_t)TILE + (size_t)D * STAGE);
+};
+
+template <int NX, int NF, int PT, int TY, int MINB, int DS>
+__global__ void __launch_bounds__(NX * TY, MINB) k_stencil_blk(const StencilArgs<float> a) {
+    using T = float;
+    using C = float2;
+    using L = BlkTma<NX, NF, PT, TY, DS>;
+    constexpr int TP = L::TP, TILE = L::TILE, SLAB = L::SLAB, RY = L::RY, D = L::D;
+    constexpr int STAGE = L::STAGE;
+    extern __shared__ __align__(128) unsigned char smem_blk[];
+    __shared__ double red[3 * 16];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_blk);   // [D + 1]
+
+    const int rhs = blockIdx.z;
+    int st = ST_ACTIVE;
+    C beta = czero<C>();
+    bool first_dir = false;
+    if (a.state) {
+        st = a.state[rhs].status;
+        if (a.fused_p && !a.state[rhs].first) beta = from_d2<C>(a.state[rhs].beta);
+        else if (a.fused_p) first_dir = true;
+    }
+    if (!((1 << st) & a.mask)) return;
+
+    const int ny = a.ny, nz = a.nz;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int x = tid % NX;
+    const int ty = tid / NX;                 // 0 .. TY-1
+    const int r0 = ty * PT;                  // this thread's first own row within the tile
+    const int ty0 = blockIdx.x * RY;         // first own row of the tile (full tiles only)
+    const int k0 = blockIdx.y * a.zchunk;
+    const int k1 = min(k0 + a.zchunk, nz);
+    const long long plane = (long long)NX * ny;
+    const long long base = (long long)rhs * a.npts;
+    const C* __restrict__ X = a.x + base;
+    const int pb = (a.fused_p && a.state) ? (a.state[rhs].pbuf & 1) : 0;
+    const C* __restrict__ PO = (a.fused_p && !first_dir) ? a.pbufs[pb] + base : nullptr;
+    const T* __restrict__ Vg = a.V;
+    const T ed = a.ediag ? (T)a.ediag[a.rhs_energy ? a.rhs_energy[rhs] : 0] : (T)0;
+    const T cen = a.c0 + ed;
+
+    C* tiles = reinterpret_cast<C*>(smem_blk + 128);   // [2][SR][TP] combined operand rows
+    C* stages = tiles + 2 * TILE;   // stage s at s STAGE: z [SLAB], p_old [SLAB], V [RY][NX] floats
+    if (tid == 0) {
+        for (int s = 0; s <= D; ++s) mbar_init(&bar[s], 1);   // bar[D]: no copy completes it
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const long long wlim = a.wait_cycles > 0 ? a.wait_cycles : kWaitCycles;
+
+    // copies of warp 0 (as in k_stencil_rows_tma, with RY own rows): lane l < 2 NF a
+    // halo row (a side whose source rows do not wrap in y is one copy by its first
+    // lane), lane 2 NF the own rows of z, lane 2 NF + 1 those of p_old, lane 2 NF + 2
+    // the own rows of V (of plane k itself)
+    constexpr uint32_t row_bytes = NX * sizeof(C);
+    constexpr uint32_t vrow_bytes = NX * sizeof(T);
+    auto issue = [&](int k, int s) {   // all lanes of warp 0
+        const bool own_plane = k + NF < nz;
+        if (lane == 0) {
+            const uint32_t per = (own_plane ? (uint32_t)RY : 0u) * row_bytes + 2u * NF * row_bytes;
+            mbar_arrive_expect_tx(&bar[s], (PO ? 2 * per : per) + (Vg ? RY * vrow_bytes : 0u));
+        }
+        __syncwarp();
+        C* sz = stages + s * STAGE;
+        C* sp = sz + SLAB;
+        if (lane < 2 * NF) {
+            const bool above = lane < NF;
+            const int h = above ? lane : lane - NF;
+            const bool contiguous = above ? (ty0 >= NF) : (ty0 + RY + NF <= ny);
+            const int nrows = contiguous ? (h == 0 ? NF : 0) : 1;
+            if (nrows) {
+                const int srow = above ? lane : NF + RY + h;
+                int gy = (ty0 - NF + srow) % ny;
+                if (gy < 0) gy += ny;
+                fence_proxy_async_smem();
+                const long long src = (long long)k * plane + (long long)gy * NX;
+                bulk_g2s(sz + srow * NX, X + src, nrows * row_bytes, &bar[s]);
+                if (PO) bulk_g2s(sp + srow * NX, PO + src, nrows * row_bytes, &bar[s]);
+            }
+        } else if (own_plane && (lane == 2 * NF || (PO && lane == 2 * NF + 1))) {
+            fence_proxy_async_smem();
+            const long long src = (long long)(k + NF) * plane + (long long)ty0 * NX;
+            if (lane == 2 * NF) bulk_g2s(sz + NF * NX, X + src, RY * row_bytes, &bar[s]);
+            else bulk_g2s(sp + NF * NX, PO + src, RY * row_bytes, &bar[s]);
+        } else if (Vg && lane == 2 * NF + 2) {
+            fence_proxy_async_smem();
+            bulk_g2s(sz + 2 * SLAB, Vg + (long long)k * plane + (long long)ty0 * NX, RY * vrow_bytes,
+                     &bar[s]);
+        }
+    };
+
+    static_assert(NX >= 2 * NF, "pad columns assume NX >= 2 NF");
+    const int tcol = NF + x;
+    const int tpad = (x < NF) ? NF + NX + x : ((x >= NX - NF) ? x - (NX - NF) : -1);
+    const long long own_lat = (long long)(ty0 + r0) * NX + x;   // own row i at + i NX
+
+    auto ld = [&](int k, long long lat) -> C {
+        if (k < 0 || k >= nz) return czero<C>();
+        const long long i = (long long)k * plane + lat;
+        C v = X[i];
+        if (PO) v = cfma(beta, PO[i], v);
+        return v;
+    };
+    if (tid < 32)
+        for (int j = 0; j < D && k0 + j < k1; ++j) issue(k0 + j, j);
+
+    C* PN = a.fused_p ? a.pbufs[1 - pb] + base : nullptr;
+    C q[2 * NF + 1][PT];
+#pragma unroll
+    for (int j = 0; j < 2 * NF; ++j) {
+        const int kk = k0 - NF + j;
+#pragma unroll
+        for (int i = 0; i < PT; ++i) {
+            q[j][i] = ld(kk, own_lat + i * NX);
+            if (PN && kk >= k0 && kk < k1) PN[(long long)kk * plane + own_lat + i * NX] = q[j][i];
+        }
+    }
+    C* __restrict__ Yk = a.y + base + (long long)k0 * plane + own_lat;
+    C* __restrict__ PNk = PN ? PN + (long long)(k0 + NF) * plane + own_lat : nullptr;
+
+    float dre = 0.f, dim = 0.f, nrm = 0.f;
+    constexpr int HF = (2 * NF + TY - 1) / TY;   // halo rows filled per thread
+
+    // Software pipeline, one CTA barrier per plane: the barrier interval of plane k
+    // computes the outputs of plane k from tile buffer k & 1 while it fills buffer
+    // (k + 1) & 1 from the stage of plane k + 1 (its halo rows, the own rows from the
+    // z-queue) and takes the own rows of plane k + 1 + NF into the queue.
+    T vk[PT], vn[PT];
+    C qn[PT];
+    // fill of plane kf into tile buffer (kf - k0) & 1: the stage of kf must have arrived
+    auto fill = [&](int kf, T* vout) {
+        const unsigned kk = (unsigned)(kf - k0);
+        const C* sz = stages + (int)(kk % D) * STAGE;
+        const C* sp = sz + SLAB;
+        const T* sv = reinterpret_cast<const T*>(sz + 2 * SLAB) + r0 * NX + x;
+        C* tile = tiles + (kk & 1) * TILE;
+#pragma unroll
+        for (int i = 0; i < PT; ++i) {
+            qn[i] = czero<C>();
+            if (kf + NF < nz) {
+                const int si = (NF + r0 + i) * NX + x;
+                const C zv = sz[si];
+                qn[i] = PO ? cfma(beta, sp[si], zv) : zv;
+            }
+            vout[i] = Vg ? sv[i * NX] : (T)0;
+        }
+#pragma unroll
+        for (int jj = 0; jj < HF; ++jj) {
+            const int j = ty + jj * TY;
+            if (j < 2 * NF) {
+                const int srow = j < NF ? j : RY + j;
+                const int si = srow * NX + x;
+                const C zv = sz[si];
+                const C v = PO ? cfma(beta, sp[si], zv) : zv;
+                C* trow = tile + srow * TP;
+                trow[tcol] = v;
+                if (tpad >= 0) trow[tpad] = v;
+            }
+        }
+    };
+    // own rows of plane kf (held in the queue) into its tile buffer
+    auto own_rows = [&](int kf, const C* vals) {
+        C* tile = tiles + ((unsigned)(kf - k0) & 1) * TILE;
+#pragma unroll
+        for (int i = 0; i < PT; ++i) {
+            C* row = tile + (NF + r0 + i) * TP;
+            row[tcol] = vals[i];
+            if (tpad >= 0) row[tpad] = vals[i];
+        }
+    };
+    // a CTA barrier that also agrees on a failed wait; on failure the CTA drains the
+    // copies it still has in flight (planes kw .. kw + D - 1) and the kernel returns
+    auto barrier_ok = [&](bool ok, int kw) -> bool {
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                if (a.err) atomicExch(a.err, ERR_STAGE_TIMEOUT);
+                for (int j = kw; j < kw + D && j < k1; ++j)
+                    mbar_wait_bounded(&bar[(j - k0) % D], ((j - k0) / D) & 1);
+            }
+            __syncthreads();
+            return false;
+        }
+        return true;
+    };
+
+    // prologue: plane k0 into tile buffer 0
+    {
+        bool ok = mbar_wait_bounded(&bar[0], 0, wlim);
+        if (a.wait_inject && tid == 0) ok = ok && mbar_wait_bounded(&bar[D], 0, wlim);
+        fill(k0, vk);
+        C own0[PT];
+#pragma unroll
+        for (int i = 0; i < PT; ++i) {
+            own0[i] = q[NF][i];
+            q[2 * NF][i] = qn[i];
+        }
+        own_rows(k0, own0);
+        if (!barrier_ok(ok, k0)) return;
+        if (tid < 32 && k0 + D < k1) issue(k0 + D, 0);
+        if (PNk && k0 + NF < k1) {
+#pragma unroll
+            for (int i = 0; i < PT; ++i) PNk[i * NX] = qn[i];
+        }
+        if (PNk) PNk += plane;
+    }
+
+    for (int k = k0; k < k1; ++k) {
+        const unsigned kk = (unsigned)(k - k0);
+        const C* tile = tiles + (kk & 1) * TILE;
+        const bool next = k + 1 < k1;
+        bool ok = true;
+        if (next) {   // plane k + 1: its stage, tile buffer and queue entry
+            ok = mbar_wait_bounded(&bar[(kk + 1) % D], ((kk + 1) / D) & 1, wlim);
+            fill(k + 1, vn);
+            C own1[PT];
+#pragma unroll
+            for (int i = 0; i < PT; ++i) own1[i] = q[NF + 1][i];
+            own_rows(k + 1, own1);
+        }
+        // y neighbours outside this thread's rows: NF above, NF below
+        C yh[2 * NF];
+#pragma unroll
+        for (int m = 0; m < NF; ++m) {
+            yh[m] = tile[(r0 + m) * TP + tcol];                  // row r0 - NF + m
+            yh[NF + m] = tile[(NF + r0 + PT + m) * TP + tcol];   // row r0 + PT + m
+        }
+#pragma unroll
+        for (int i = 0; i < PT; ++i) {
+            const T d = cen + a.vsign * vk[i];
+            const C x0 = q[NF][i];
+            const C* c = tile + (NF + r0 + i) * TP + tcol;
+            C acc;
+            if (a.iso) {
+                // three independent chains (z, x, y taps), summed at the end
+                const C x2 = p2add(x0, x0);
+                C az = p2mul(x0, make_float2(d, d));
+                C ax = make_float2(0.f, 0.f), ay = ax;
+#pragma unroll
+                for (int n = 1; n <= NF; ++n) {
+                    const int dm = i - n, dp = i + n;   // own-relative rows (compile-time)
+                    const C ym = dm >= 0 ? q[NF][dm < PT ? dm : PT - 1] : yh[dm + NF >= 0 ? dm + NF : 0];
+                    const C yp = dp < PT ? q[NF][dp] : yh[NF + dp - PT < 2 * NF ? NF + dp - PT : 2 * NF - 1];
+                    const C cc = make_float2(a.cz[n], a.cz[n]);
+                    az = p2fma(cc, p2sub(p2add(q[NF - n][i], q[NF + n][i]), x2), az);
+                    ax = p2fma(cc, p2sub(p2add(c[-n], c[n]), x2), ax);
+                    ay = p2fma(cc, p2sub(p2add(ym, yp), x2), ay);
+                }
+                acc = p2add(az, p2add(ax, ay));
+            } else {
+                const C x2 = cadd(x0, x0);
+                C az = cscale(x0, d);
+                C ax = make_float2(0.f, 0.f), ay = ax;
+#pragma unroll
+                for (int n = 1; n <= NF; ++n) {
+                    const int dm = i - n, dp = i + n;
+                    const C ym = dm >= 0 ? q[NF][dm < PT ? dm : PT - 1] : yh[dm + NF >= 0 ? dm + NF : 0];
+                    const C yp = dp < PT ? q[NF][dp] : yh[NF + dp - PT < 2 * NF ? NF + dp - PT : 2 * NF - 1];
+                    az = caxpy(a.cz[n], csub(cadd(q[NF - n][i], q[NF + n][i]), x2), az);
+                    ax = caxpy(a.cx[n], csub(cadd(c[-n], c[n]), x2), ax);
+                    ay = caxpy(a.cy[n], csub(cadd(ym, yp), x2), ay);
+                }
+                acc = cadd(az, cadd(ax, ay));
+            }
+            Yk[i * NX] = acc;
+            if (a.dot_mode) {
+                dre = fmaf(x0.x, acc.x, fmaf(-x0.y, acc.y, dre));
+                dim = fmaf(x0.x, acc.y, fmaf(x0.y, acc.x, dim));
+                nrm = fmaf(x0.x, x0.x, fmaf(x0.y, x0.y, nrm));
+            }
+        }
+        Yk += plane;
+        // tile buffer k & 1 is read, (k + 1) & 1 complete, the stage of plane k + 1 consumed
+        if (next) {
+            if (!barrier_ok(ok, k + 1)) return;
+            if (tid < 32 && k + 1 + D < k1) issue(k + 1 + D, (int)((kk + 1) % D));
+            if (PNk && k + 1 + NF < k1) {
+#pragma unroll
+                for (int i = 0; i < PT; ++i) PNk[i * NX] = qn[i];
+            }
+            if (PNk) PNk += plane;
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * NF; ++j)
+#pragma unroll
+            for (int i = 0; i < PT; ++i) q[j][i] = q[j + 1][i];
+#pragma unroll
+        for (int i = 0; i < PT; ++i) {
+            q[2 * NF][i] = qn[i];
+            vk[i] = vn[i];
+        }
+    }
+
+    if (a.dot_mode) {
+        // partial slots are numbered per kRowTY-row tile (stencil_slots): the CTA's sum
+        // goes to the first of its RY / kRowTY slots, zeros to the others
+        static_assert(RY % kRowTY == 0, "RY spans whole row tiles");
+        double r0d = dre, r1 = dim, r2 = nrm;
+        block_reduce_3(r0d, r1, r2, red);
+        if (tid < RY / kRowTY) {
+            const int tiles_y = ny / kRowTY;
+            const int slot = a.slot_base + blockIdx.x * (RY / kRowTY) + tid + blockIdx.y * tiles_y;
+            a.dot_part[(long long)rhs * a.slot_stride + slot] =
+                tid == 0 ? make_double2(r0d, r1) : make_double2(0.0, 0.0);
+            if (a.nrm_part) a.nrm_part[(long long)rhs * a.slot_stride + slot] = tid == 0 ? r2 : 0.0;
+        }
+    }
+}
+
 static bool use_rows(int nx, int nf) { return nx >= nf && nx >= 4 && nx <= 64; }
 
 // bulk-copy variant: FP32, rows of a multiple of 16 bytes, 16-byte aligned operands
@@ -644,7 +974,9 @@ static bool tma_width(int nx) {
 
 template <typename T>
 static bool use_rows_tma(const StencilArgs<T>& a) {
-    if (sizeof(T) != 4 || a.variant == 1 || !use_rows(a.nx, a.nf) || !tma_width(a.nx)) return false;
+    if (sizeof(T) != 4 || (a.variant != 0 && a.variant != 3) || !use_rows(a.nx, a.nf) ||
+        !tma_width(a.nx))
+        return false;
     uintptr_t al = reinterpret_cast<uintptr_t>(a.x);
     if (a.fused_p) al |= reinterpret_cast<uintptr_t>(a.pbufs[0]) | reinterpret_cast<uintptr_t>(a.pbufs[1]);
     return (al & 15) == 0;
@@ -663,12 +995,61 @@ static cudaError_t prepare_tma() {
     return e;
 }
 
+// row-blocked kernel shape: PT rows per thread, TY thread rows (RY = 16 own rows)
+template <int NX> struct BlkShape {
+    static constexpr int PT = 4;
+    static constexpr int TY = 16 / PT;
+    static constexpr int MINB = 2;
+    static constexpr int D = 3;
+};
+
+template <int NX, int NF>
+static cudaError_t prepare_blk() {
+    using S = BlkShape<NX>;
+    cudaError_t e = cudaFuncSetAttribute(k_stencil_blk<NX, NF, S::PT, S::TY, S::MINB, S::D>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)BlkTma<NX, NF, S::PT, S::TY, S::D>::smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_stencil_blk<NX, NF, S::PT, S::TY, S::MINB, S::D>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+// the blocked kernel: FP32 bulk-copy rows, N_f 1 (Eq. 10) or 4 (the operator), whole
+// 16-row tiles in y, the fastest-kernel variant
+template <typename T>
+static bool use_blk(const StencilArgs<T>& a) {
+    return a.variant == 0 && (a.nf == 1 || a.nf == 4) && a.ny % 16 == 0 && a.nx >= 2 * a.nf;
+}
+
+template <int NX, int NF>
+static void launch_blk(const StencilArgs<float>& a, dim3 grid, cudaStream_t s) {
+    using S = BlkShape<NX>;
+    k_stencil_blk<NX, NF, S::PT, S::TY, S::MINB, S::D>
+        <<<grid, NX * S::TY, BlkTma<NX, NF, S::PT, S::TY, S::D>::smem, s>>>(a);
+}
+
+template <int NX>
+static cudaError_t launch_blk_nf(const StencilArgs<float>& a, int nrhs, cudaStream_t s) {
+    const int nzc = (a.nz + a.zchunk - 1) / a.zchunk;
+    dim3 grid(a.ny / 16, nzc, nrhs);
+    switch (a.nf) {
+        case 1: launch_blk<NX, 1>(a, grid, s); break;
+        case 4: launch_blk<NX, 4>(a, grid, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int NX>
 static cudaError_t prepare_tma_nf() {
     cudaError_t e = prepare_tma<NX, 1>();
     if (e == cudaSuccess) e = prepare_tma<NX, 2>();
     if (e == cudaSuccess) e = prepare_tma<NX, 3>();
     if (e == cudaSuccess) e = prepare_tma<NX, 4>();
+    if (e == cudaSuccess && NX >= 2) e = prepare_blk<NX, 1>();
+    if (e == cudaSuccess && NX >= 8) e = prepare_blk<NX, 4>();
     return e;
 }
 
@@ -717,6 +1098,17 @@ cudaError_t launch_stencil(const StencilArgs<T>& a0, int nrhs, cudaStream_t s) {
         const int threads = a.nx * kRowTY;
         using C = typename Cplx<T>::type;
         if constexpr (sizeof(T) == 4) {
+            if (use_rows_tma(a) && use_blk(a)) {
+                switch (a.nx) {
+                    case 12: return launch_blk_nf<12>(a, nrhs, s);
+                    case 16: return launch_blk_nf<16>(a, nrhs, s);
+                    case 24: return launch_blk_nf<24>(a, nrhs, s);
+                    case 32: return launch_blk_nf<32>(a, nrhs, s);
+                    case 48: return launch_blk_nf<48>(a, nrhs, s);
+                    case 64: return launch_blk_nf<64>(a, nrhs, s);
+                    default: return cudaErrorInvalidValue;
+                }
+            }
             if (use_rows_tma(a)) {
                 switch (a.nx) {
                     case 12: return launch_tma_nf<12>(a, grid, s);

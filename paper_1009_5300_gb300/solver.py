@@ -217,6 +217,15 @@ class IOBMSolver:
     def set_tiling(self, zchunk: int, variant: int = 0):
         check(self.lib.iobm_set_tiling(self.h, int(zchunk), int(variant)), self.h)
 
+    def time_operator(self, nrhs: int, reps: int = 20) -> float:
+        """Average ms of one fused COCG operator launch on nrhs RHS, all active
+        (iobm_time_operator; overwrites the workspace)."""
+        self._ensure_workspace(max(int(nrhs), 1))
+        ms = C.c_double(0)
+        with torch.cuda.device(self.device):
+            check(self.lib.iobm_time_operator(self.h, int(nrhs), int(reps), C.byref(ms)), self.h)
+        return ms.value
+
     def set_bloch(self, kappa):
         """Lateral Bloch vector (kappa_x, kappa_y) of the later solves (iobm_set_bloch).
         At kappa != 0 a solve also returns the -kappa problem: energy slots nE + e."""

@@ -38,6 +38,9 @@ CASES = [
     (32, 32, 18, 2, False),    # compile-time-FFT self-energy, radix 4 and 2 passes, N_f = 2
     (72, 72, 14, 4, True),     # planes above 4096 points: two-pass global-memory FFTs
     (96, 48, 16, 2, True),     # a large non-square plane, 2-D tiled stencil (nx > 64)
+    (24, 32, 37, 4, True),     # row-blocked FP32 kernel: 2 tiles of 16 rows, ragged z-chunk
+    (64, 16, 29, 1, False),    # row-blocked kernel, N_f = 1, widest rows
+    (12, 48, 21, 4, False),    # row-blocked kernel, narrowest rows, 3 tiles in y
 ]
 
 
@@ -84,7 +87,7 @@ def test_double_float_apply_on_smooth_fields(scale):
     sol.close()
 
 
-@pytest.mark.parametrize("nx,ny,nz,nf,kb", CASES[:3])
+@pytest.mark.parametrize("nx,ny,nz,nf,kb", CASES[:3] + CASES[-3:])
 def test_precond_matches_oracle(nx, ny, nz, nf, kb):
     from paper_1009_5300_gb300 import IOBMSolver
     jn = make(nx, ny, nz, nf, kb)
