@@ -137,7 +137,12 @@ typedef struct {
  * iterations from its FP64 iterate, up to max_iter more (precision escalation:
  * once cond(A) times the FP32 rounding unit is no longer small, the FP32 inner
  * iteration stops making progress while FP64 still converges).
- * op_form: IOBM_OP_AUTO or IOBM_OP_EXPLICIT (above). */
+ * op_form: IOBM_OP_AUTO or IOBM_OP_EXPLICIT (above).
+ * fp64_modes: in IOBM_MIXED with IOBM_PRECOND_FOURIER, the number of lateral modes
+ * per energy nearest their channel threshold (smallest |E - eps_perp|) whose
+ * preconditioner z-sweeps run in FP64 with FP64 factors inside the FP32 iterations:
+ * their banded z-systems are the worst conditioned, and FP32 sweeps there cost
+ * iterations; 0 sweeps every mode in FP32. */
 typedef struct {
     double alpha;
     int use_precond;
@@ -148,6 +153,7 @@ typedef struct {
     int chunk;
     int max_iter_mixed;
     int op_form;
+    int fp64_modes;
 } iobm_options;
 
 /* Per right-hand-side report, in solve order (energy-major, then incident
@@ -164,7 +170,7 @@ typedef struct {
 
 /* Fill opts with the defaults: alpha 1.8, use_precond IOBM_PRECOND_FOURIER, tol 1e-8,
  * max_iter 20000, precision IOBM_MIXED, refine_delta 0.01, chunk 32,
- * max_iter_mixed 1000, op_form IOBM_OP_AUTO. */
+ * max_iter_mixed 1000, op_form IOBM_OP_AUTO, fp64_modes 16. */
 void iobm_default_options(iobm_options* opts);
 
 /* Create a solver for one junction: the truncated Hamiltonian H_T of the

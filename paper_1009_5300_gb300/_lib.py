@@ -50,7 +50,8 @@ class Projectors(C.Structure):
 class Options(C.Structure):
     _fields_ = [("alpha", C.c_double), ("use_precond", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("refine_delta", C.c_double),
-                ("chunk", C.c_int), ("max_iter_mixed", C.c_int), ("op_form", C.c_int)]
+                ("chunk", C.c_int), ("max_iter_mixed", C.c_int), ("op_form", C.c_int),
+                ("fp64_modes", C.c_int)]
 
 
 class Report(C.Structure):

@@ -68,6 +68,9 @@ struct iobm_handle {
     cudaStream_t user_stream = nullptr;
     cudaStream_t stream = nullptr;      // private stream (capturable)
     cudaStream_t cond_stream = nullptr; // captures the bodies of conditional graph nodes
+    cudaStream_t side_stream = nullptr; // the double-float z-sweeps beside the FP32 ones
+    cudaEvent_t ev_zfork = nullptr, ev_zjoin = nullptr;
+    bool in_cond_body = false;          // launches go into a conditional node's body graph
     bool graph_conditionals = true;     // IF nodes around the residual replacements
     cudaEvent_t ev_sync = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
     std::string err;
@@ -107,6 +110,8 @@ struct iobm_handle {
     DevBuf gph32, gph64;                 // [nxy] exp(i kappa.r_l) for the KB projectors
     DevBuf gpx, gpy;                     // [nx], [ny] exp(i kappa_x x h_x), exp(i kappa_y y h_y)
     DevBuf esc_rhs_sign;                 // the FP64 continuation's signs
+    DevBuf zflag, zf_bins, zf_pc;        // FP64 z-sweep modes of the solve's energy slots
+    int zf_k = 0;
     long long wait_cycles = 0;           // bounded-wait limit of the bulk-copy kernels (0: default)
     int wait_inject = 0;                 // 1: their CTAs also wait on a barrier no copy completes
     int zchunk = kZChunkDefault;         // stencil z-planes per CTA (autotuned)
@@ -392,6 +397,24 @@ PrecondArgs<T> fourier_args(const iobm_handle* h, const void* pc) {
     return a;
 }
 
+// the solve's FP64 z-sweep modes (FP32 iterations only; the tables follow the
+// solve's energy slots, so single applications do not use them)
+template <typename T>
+void set_fp64_modes(const iobm_handle* h, PrecondArgs<T>& f) {
+    if (!std::is_same<T, float>::value || h->zf_k <= 0) return;
+    f.zflag = h->zflag.as<unsigned char>();
+    f.zf_bins = h->zf_bins.as<int>();
+    f.zf_pc = h->zf_pc.as<double2>();
+    f.zf_k = h->zf_k;
+    // the side stream joins the capture of the main graph when it forks there, so the
+    // body of a conditional node (a capture of its own) takes the single-launch sweeps
+    if (!h->in_cond_body) {
+        f.zf_side = h->side_stream;
+        f.zf_fork = h->ev_zfork;
+        f.zf_join = h->ev_zjoin;
+    }
+}
+
 template <typename T>
 SigmaArgs<T> sigma_args(const iobm_handle* h, const void* sig) {
     SigmaArgs<T> a{};
@@ -500,6 +523,7 @@ int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) 
     using C = typename Cplx<T>::type;
     if (fourier_precond(h)) {
         PrecondArgs<T> f = fourier_args<T>(h, std::is_same<T, float>::value ? h->pc32.p : h->pc64.p);
+        set_fp64_modes<T>(h, f);
         f.r = (const C*)h->vr;
         f.spec = (C*)h->vz;
         f.z = (C*)h->vz;
@@ -586,7 +610,9 @@ int captured_if_any(iobm_handle* h, int nrhs, int mask, Body body) {
                                      cudaStreamCaptureModeThreadLocal));
     cudaStream_t main = h->stream;
     h->stream = h->cond_stream;
+    h->in_cond_body = true;
     const int rc = body();
+    h->in_cond_body = false;
     h->stream = main;
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(h->cond_stream, &g);
@@ -697,6 +723,7 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
     if (fourier_precond(h)) {
         // x += alpha p, r -= alpha q fused with the forward plane FFTs of the preconditioner
         PrecondArgs<T> f = fourier_args<T>(h, std::is_same<T, float>::value ? h->pc32.p : h->pc64.p);
+        set_fp64_modes<T>(h, f);
         f.r = (const C*)h->vr;
         f.spec = (C*)h->vz;
         f.z = (C*)h->vz;
@@ -1108,6 +1135,38 @@ int upload_solve_tables(iobm_handle* h) {
         std::vector<int> sg(h->nrhs);
         for (int i = 0; i < h->nrhs; ++i) sg[i] = i < h->pairs ? 1 : -1;
         CK(upload(h->rhs_sign, sg, h->stream));
+    }
+    // per energy slot the fp64_modes lateral modes nearest their threshold (smallest
+    // |E - eps_perp|, ties by bin): FP64 z-sweeps in the FP32 iterations
+    h->zf_k = (h->opt.precision == IOBM_MIXED && fourier_precond(h) &&
+               h->opt.use_precond == IOBM_PRECOND_FOURIER)
+                  ? std::min(h->opt.fp64_modes, h->nxy) : 0;
+    if (h->zf_k > 0) {
+        const int K = h->zf_k, nxy = h->nxy;
+        std::vector<unsigned char> flag((size_t)nE * nxy, 0);
+        std::vector<int> bins((size_t)nE * K);
+        std::vector<double2> zpc((size_t)nE * K * kPcStrideDev);
+        std::vector<int> order(nxy);
+        for (int e = 0; e < nE; ++e) {
+            const ModeTables& mt = h->energies[e];
+            for (int b = 0; b < nxy; ++b) order[b] = b;
+            std::partial_sort(order.begin(), order.begin() + K, order.end(), [&](int a, int b) {
+                const double da = std::fabs(mt.E - mt.eperp_bin[a]), db = std::fabs(mt.E - mt.eperp_bin[b]);
+                return da < db || (da == db && a < b);
+            });
+            for (int f = 0; f < K; ++f) {
+                const int b = order[f];
+                flag[(size_t)e * nxy + b] = 1;
+                bins[(size_t)e * K + f] = b;
+                for (int j = 0; j < kPcStrideDev; ++j) {
+                    const std::complex<double> v = mt.pc[(size_t)b * kPcStride + j];
+                    zpc[((size_t)e * K + f) * kPcStrideDev + j] = make_double2(v.real(), v.imag());
+                }
+            }
+        }
+        CK(upload(h->zflag, flag, h->stream));
+        CK(upload(h->zf_bins, bins, h->stream));
+        CK(upload(h->zf_pc, zpc, h->stream));
     }
     return IOBM_OK;
 }
@@ -1660,6 +1719,7 @@ void iobm_default_options(iobm_options* o) {
     o->chunk = 32;
     o->max_iter_mixed = 1000;
     o->op_form = IOBM_OP_AUTO;
+    o->fp64_modes = 16;
 }
 
 const char* iobm_status_string(int s) {
@@ -1710,7 +1770,8 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
         !(h->opt.refine_delta > 0 && h->opt.refine_delta < 1) ||
         (h->opt.precision != IOBM_FP64 && h->opt.precision != IOBM_MIXED) || !(h->opt.alpha > 0) ||
         h->opt.use_precond < IOBM_PRECOND_NONE || h->opt.use_precond > IOBM_PRECOND_EQ10_FOURIER ||
-        (h->opt.op_form != IOBM_OP_AUTO && h->opt.op_form != IOBM_OP_EXPLICIT))
+        (h->opt.op_form != IOBM_OP_AUTO && h->opt.op_form != IOBM_OP_EXPLICIT) ||
+        h->opt.fp64_modes < 0)
         return bad(IOBM_E_ARG, "invalid solver options");
     h->nxy = g.nx * g.ny;
     h->npts = (long long)h->nxy * g.nz;
@@ -1744,6 +1805,9 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
         h->graph_conditionals = std::strcmp(env, "0") != 0;
     cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cond_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_zfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_zjoin, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sync, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t1);
@@ -1829,7 +1893,8 @@ void iobm_destroy(iobm_handle* h) {
                       &h->apply_pc64, &h->apply_ediag, &h->ws_owned, &h->errflag,
                       &h->batch_ctr, &h->sig_scratch, &h->kb_scratch, &h->uplane, &h->esc_ws,
                       &h->esc_descs, &h->esc_rhs_energy, &h->rhs_sign, &h->apply_sign,
-                      &h->gph32, &h->gph64, &h->gpx, &h->gpy, &h->esc_rhs_sign};
+                      &h->gph32, &h->gph64, &h->gpx, &h->gpy, &h->esc_rhs_sign,
+                      &h->zflag, &h->zf_bins, &h->zf_pc};
     for (DevBuf* b : bufs) b->release();
     if (h->ev_sync) cudaEventDestroy(h->ev_sync);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
@@ -1837,6 +1902,9 @@ void iobm_destroy(iobm_handle* h) {
     for (cudaEvent_t ev : h->kev) cudaEventDestroy(ev);
     if (h->stream) cudaStreamDestroy(h->stream);
     if (h->cond_stream) cudaStreamDestroy(h->cond_stream);
+    if (h->side_stream) cudaStreamDestroy(h->side_stream);
+    if (h->ev_zfork) cudaEventDestroy(h->ev_zfork);
+    if (h->ev_zjoin) cudaEventDestroy(h->ev_zjoin);
     delete h;
 }
 

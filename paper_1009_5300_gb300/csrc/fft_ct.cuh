@@ -9,6 +9,7 @@
 
 #include "iobm_internal.cuh"
 #include "complex_ops.cuh"
+#include "fft_bfly.cuh"
 
 #include <type_traits>
 #include <utility>
@@ -34,8 +35,9 @@ struct CtPlan {
     }
 };
 
-// one R-point butterfly j of a pass: reads src[(j + r N/R) ss], returns the R
-// outputs and the index of the first (output r goes to base + r NS)
+// one R-point butterfly j of a pass with compile-time sizes: reads
+// src[(j + r N/R) ss], returns the R outputs (small_dft of fft_bfly.cuh) and the
+// index of the first (output r goes to base + r NS)
 template <typename C, int N, int NS, int R>
 __device__ __forceinline__ int ct_bfly_out(const C* src, int ss, int j, const C* tw, bool inv,
                                            C (&o)[R]) {
@@ -54,44 +56,7 @@ __device__ __forceinline__ int ct_bfly_out(const C* src, int ss, int j, const C*
         }
         v[r] = u;
     }
-    if constexpr (R == 2) {
-        o[0] = cadd(v[0], v[1]);
-        o[1] = csub(v[0], v[1]);
-    } else if constexpr (R == 4) {
-        C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-        C a2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
-        C a3;
-        if (inv) { a3.x = -d.y; a3.y = d.x; } else { a3.x = d.y; a3.y = -d.x; }
-        o[0] = cadd(a0, a2);
-        o[2] = csub(a0, a2);
-        o[1] = cadd(a1, a3);
-        o[3] = csub(a1, a3);
-    } else if constexpr (R == 3) {
-        // w = exp(-+2 pi i / 3) = -1/2 -+ i sqrt(3)/2
-        using T = decltype(v[0].x);
-        const T c = (T)-0.5, sn = (T)0.86602540378443864676;
-        const C t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
-        o[0] = cadd(v[0], t1);
-        C m;
-        m.x = v[0].x + c * t1.x;
-        m.y = v[0].y + c * t1.y;
-        C js;   // -i sn t2 (forward) or +i sn t2 (inverse)
-        if (inv) { js.x = -sn * t2.y; js.y = sn * t2.x; } else { js.x = sn * t2.y; js.y = -sn * t2.x; }
-        o[1] = cadd(m, js);
-        o[2] = csub(m, js);
-    } else {
-#pragma unroll
-        for (int aa = 0; aa < R; ++aa) {
-            C acc = v[0];
-#pragma unroll
-            for (int b = 1; b < R; ++b) {
-                C w = tw[((aa * b) % R) * NR];
-                if (inv) w.y = -w.y;
-                acc = cfma(v[b], w, acc);
-            }
-            o[aa] = acc;
-        }
-    }
+    small_dft<C, R>(v, o, tw, NR, inv);
     return (j / NS) * NS * R + k;
 }
 

@@ -222,6 +222,18 @@ struct PrecondArgs {
     double* nrm_part;
     int slot_stride;
     long long npts;
+    // FP32 solves: per energy slot the zf_k lateral modes nearest their channel
+    // threshold take their z-sweeps in FP64, with FP64 factors: zflag[e][bin] = 1 for
+    // them, zf_bins[e][f] their bins, zf_pc[e][f][kPcStrideDev] their factors
+    const unsigned char* zflag;
+    const int* zf_bins;
+    const double2* zf_pc;
+    int zf_k;
+    // host side: with zf_side set, the double-float sweeps run on stream zf_side
+    // (forked from and joined back to the launching stream by the two events)
+    // concurrently with the FP32 sweeps of the other modes
+    cudaStream_t zf_side;
+    cudaEvent_t zf_fork, zf_join;
     int eq10;                // 0: free-propagator z-sweeps (pc tables); 1: Eq. 10 per mode
     double c1;               // Eq. 10 weight exp(-alpha) (eq10 = 1)
 };

@@ -19,70 +19,11 @@
 // per-mode tridiagonal multiply in z).
 #include "iobm_internal.cuh"
 #include "complex_ops.cuh"
+#include "dfloat.cuh"
+#include "fft_bfly.cuh"
 #include "fft_ct.cuh"
 
 namespace iobm {
-
-// one R-point butterfly of a Stockham pass (see the line FFT in k_boundary.cu)
-template <typename C, int R>
-__device__ __forceinline__ void stockham_bfly(const C* src, int ss, C* dst, int ds, int N, int Ns,
-                                              int j, const C* __restrict__ tw, bool inv) {
-    const int NR = N / R;
-    const int k = j % Ns;
-    const int tscale = N / (Ns * R);
-    C v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        C u = src[(j + r * NR) * ss];
-        if (r) {
-            C w = tw[(r * k * tscale) % N];
-            if (inv) w.y = -w.y;
-            u = cmul(u, w);
-        }
-        v[r] = u;
-    }
-    C o[R];
-    if constexpr (R == 2) {
-        o[0] = cadd(v[0], v[1]);
-        o[1] = csub(v[0], v[1]);
-    } else if constexpr (R == 4) {
-        C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-        C a2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
-        C a3;
-        if (inv) { a3.x = -d.y; a3.y = d.x; } else { a3.x = d.y; a3.y = -d.x; }
-        o[0] = cadd(a0, a2);
-        o[2] = csub(a0, a2);
-        o[1] = cadd(a1, a3);
-        o[3] = csub(a1, a3);
-    } else {
-#pragma unroll
-        for (int aa = 0; aa < R; ++aa) {
-            C acc = v[0];
-#pragma unroll
-            for (int b = 1; b < R; ++b) {
-                C w = tw[((aa * b) % R) * NR];
-                if (inv) w.y = -w.y;
-                acc = cfma(v[b], w, acc);
-            }
-            o[aa] = acc;
-        }
-    }
-    const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) dst[(base + r * Ns) * ds] = o[r];
-}
-
-template <typename C>
-__device__ __forceinline__ void bfly_dispatch(int R, const C* src, int ss, C* dst, int ds, int N,
-                                              int Ns, int j, const C* tw, bool inv) {
-    switch (R) {
-        case 2: stockham_bfly<C, 2>(src, ss, dst, ds, N, Ns, j, tw, inv); break;
-        case 3: stockham_bfly<C, 3>(src, ss, dst, ds, N, Ns, j, tw, inv); break;
-        case 4: stockham_bfly<C, 4>(src, ss, dst, ds, N, Ns, j, tw, inv); break;
-        case 5: stockham_bfly<C, 5>(src, ss, dst, ds, N, Ns, j, tw, inv); break;
-        default: break;
-    }
-}
 
 // 2D FFT of an ny x nx plane held in a (x fastest); b is a same-size scratch.
 // Every pass spreads the butterflies of all lines over the whole CTA.
@@ -99,7 +40,7 @@ __device__ C* fft2_block(C* a, C* b, const FftAxis& ax, const FftAxis& ay, const
         const int per = nx / R;
         for (int t = threadIdx.x; t < ny * per; t += blockDim.x) {
             const int row = t / per, j = t - row * per;
-            bfly_dispatch(R, cur + row * nx, 1, oth + row * nx, 1, nx, Ns, j, twx, inv);
+            stockham_bfly_rt(R, cur + row * nx, 1, oth + row * nx, 1, nx, Ns, j, twx, inv);
         }
         __syncthreads();
         C* s = cur; cur = oth; oth = s;
@@ -111,7 +52,7 @@ __device__ C* fft2_block(C* a, C* b, const FftAxis& ax, const FftAxis& ay, const
         const int per = ny / R;
         for (int t = threadIdx.x; t < nx * per; t += blockDim.x) {
             const int col = t / per, j = t - col * per;
-            bfly_dispatch(R, cur + col, nx, oth + col, nx, ny, Ns, j, twy, inv);
+            stockham_bfly_rt(R, cur + col, nx, oth + col, nx, ny, Ns, j, twy, inv);
         }
         __syncthreads();
         C* s = cur; cur = oth; oth = s;
@@ -140,9 +81,223 @@ __global__ void __launch_bounds__(256) k_plane_fft_fwd(const PrecondArgs<T> a) {
 // multipliers over planes 0 .. nz-nf-1, a dense nf x nf solve on the last nf
 // planes, backward substitution with the constant band rows.  In place on the
 // spectrum; one thread per (RHS, mode), loads issued kZPrefetch planes ahead.
+// In FP32 solves the few modes nearest their channel threshold, whose banded
+// z-systems are the worst conditioned, sweep in double-float arithmetic with FP64
+// factors (extra blocks at the front of the grid); the others sweep in FP32.
 constexpr int kZPrefetch = 8;
 constexpr int kZThreads = 128;
 
+template <typename CW, typename CS>
+__device__ __forceinline__ CW zcvt(CS v) {
+    CW r;
+    r.x = v.x;
+    r.y = v.y;
+    return r;
+}
+
+// the sweeps of one mode in working precision CW on storage CS (s: plane 0 of the
+// mode, planes nxy apart; pc: the mode's kPcStrideDev factors)
+template <typename CW, typename CS, int NF>
+__device__ __forceinline__ void zsweep(CS* __restrict__ s, const CW* __restrict__ pc, int nz, int nxy) {
+    using W = decltype(CW{}.x);
+    CW l[NF + 1], u[NF + 1];
+#pragma unroll
+    for (int j = 1; j <= NF; ++j) l[j] = pc[j - 1];
+#pragma unroll
+    for (int j = 0; j <= NF; ++j) u[j] = pc[NF + j];
+    const CW uinv = cdivc(make_one<CW>(), u[0]);
+    const int m = nz - NF;
+    const W scale = (W)1 / (W)nxy;   // the forward FFT carries no 1/N_xy
+    constexpr int PF = kZPrefetch;
+    // forward: y_k = r_k - sum_j l_j y_{k-j}
+    CW hist[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) hist[j] = czero<CW>();   // hist[j] = y_{k-1-j}
+    CW buf[PF];
+#pragma unroll
+    for (int j = 0; j < PF; ++j) buf[j] = (j < m) ? zcvt<CW>(s[(long long)j * nxy]) : czero<CW>();
+    for (int k0 = 0; k0 < m; k0 += PF) {
+        CW cur[PF];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            cur[j] = buf[j];
+            const int kk = k0 + PF + j;
+            buf[j] = (kk < m) ? zcvt<CW>(s[(long long)kk * nxy]) : czero<CW>();
+        }
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int k = k0 + j;
+            if (k < m) {
+                // the newest term last: the older ones do not wait for y_{k-1}
+                CW y = cscale(cur[j], scale);
+#pragma unroll
+                for (int t = NF; t >= 1; --t) y = csub(y, cmul(l[t], hist[t - 1]));
+                s[(long long)k * nxy] = zcvt<CS>(y);
+#pragma unroll
+                for (int t = NF - 1; t > 0; --t) hist[t] = hist[t - 1];
+                hist[0] = y;
+            }
+        }
+    }
+    // last nf planes: g_i = r_i - sum_{j: i-j < m} l_j y_{i-j};  x_2 = S2^{-1} g
+    CW g[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        CW v = cscale(zcvt<CW>(s[(long long)(m + i) * nxy]), scale);
+#pragma unroll
+        for (int j = 1; j <= NF; ++j)
+            if (j > i) v = csub(v, cmul(l[j], hist[j - 1 - i]));
+        g[i] = v;
+    }
+    CW nxt[NF];   // nxt[j] = x_{k+1+j}
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        CW v = czero<CW>();
+        // the end block's inverse is read here, where it is used
+#pragma unroll
+        for (int j = 0; j < NF; ++j) v = cfma(pc[2 * NF + 1 + i * NF + j], g[j], v);
+        s[(long long)(m + i) * nxy] = zcvt<CS>(v);
+        nxt[i] = v;
+    }
+    // backward: x_k = (y_k - sum_j u_j x_{k+j}) / u_0
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+        buf[j] = (m - 1 - j >= 0) ? zcvt<CW>(s[(long long)(m - 1 - j) * nxy]) : czero<CW>();
+    for (int k0 = m - 1; k0 >= 0; k0 -= PF) {
+        CW cur[PF];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            cur[j] = buf[j];
+            const int kk = k0 - PF - j;
+            buf[j] = (kk >= 0) ? zcvt<CW>(s[(long long)kk * nxy]) : czero<CW>();
+        }
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int k = k0 - j;
+            if (k >= 0) {
+                CW v = cur[j];
+#pragma unroll
+                for (int t = NF; t >= 1; --t) v = csub(v, cmul(u[t], nxt[t - 1]));
+                v = cmul(v, uinv);
+                s[(long long)k * nxy] = zcvt<CS>(v);
+#pragma unroll
+                for (int t = NF - 1; t > 0; --t) nxt[t] = nxt[t - 1];
+                nxt[0] = v;
+            }
+        }
+    }
+}
+
+// The same sweeps in double-float arithmetic (about 47 bits) on FP32 storage, with
+// FP64 factors split into FP32 pairs: the forward and backward recurrences carry
+// the double-float values; the spectrum between them is stored in FP32.
+__device__ __forceinline__ Dfc df_neg(Dfc a) {
+    a.hi.x = -a.hi.x; a.hi.y = -a.hi.y; a.lo.x = -a.lo.x; a.lo.y = -a.lo.y;
+    return a;
+}
+
+template <int NF>
+__device__ __forceinline__ void zsweep_df(float2* __restrict__ s, const double2* __restrict__ pc,
+                                          int nz, int nxy) {
+    // forward factors -l_j; backward factors -u_j / u_0 and 1 / u_0 (formed in FP64 once)
+    Dfc nl[NF + 1], nw[NF + 1];
+#pragma unroll
+    for (int j = 1; j <= NF; ++j) nl[j] = df_neg(df_load(pc[j - 1]));
+    const double2 u0 = pc[NF];
+    const double den = u0.x * u0.x + u0.y * u0.y;
+    const double2 ui = make_double2(u0.x / den, -u0.y / den);
+    const Dfc uinv = df_load(ui);
+#pragma unroll
+    for (int j = 1; j <= NF; ++j) {
+        const double2 uj = pc[NF + j];
+        nw[j] = df_load(make_double2(-(uj.x * ui.x - uj.y * ui.y), -(uj.x * ui.y + uj.y * ui.x)));
+    }
+    float sch, scl;
+    df_split(1.0 / (double)nxy, sch, scl);   // the forward FFT carries no 1/N_xy
+    const Dfc zero = df_from(make_float2(0.f, 0.f));
+    const int m = nz - NF;
+    constexpr int PF = kZPrefetch;
+    Dfc hist[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) hist[j] = zero;
+    float2 buf[PF];
+#pragma unroll
+    for (int j = 0; j < PF; ++j) buf[j] = (j < m) ? s[(long long)j * nxy] : make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < m; k0 += PF) {
+        float2 cur[PF];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            cur[j] = buf[j];
+            const int kk = k0 + PF + j;
+            buf[j] = (kk < m) ? s[(long long)kk * nxy] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int k = k0 + j;
+            if (k < m) {
+                // the newest term last: the older ones do not wait for y_{k-1}
+                Dfc y = df_scale(sch, scl, df_from(cur[j]));
+#pragma unroll
+                for (int t = NF; t >= 1; --t) df_cacc(y, nl[t], hist[t - 1]);
+                df_norm(y);
+                s[(long long)k * nxy] = df_round(y);
+#pragma unroll
+                for (int t = NF - 1; t > 0; --t) hist[t] = hist[t - 1];
+                hist[0] = y;
+            }
+        }
+    }
+    Dfc g[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        Dfc v = df_scale(sch, scl, df_from(s[(long long)(m + i) * nxy]));
+#pragma unroll
+        for (int j = 1; j <= NF; ++j)
+            if (j > i) df_cacc(v, nl[j], hist[j - 1 - i]);
+        df_norm(v);
+        g[i] = v;
+    }
+    Dfc nxt[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        Dfc v = zero;
+#pragma unroll
+        for (int j = 0; j < NF; ++j) df_cacc(v, df_load(pc[2 * NF + 1 + i * NF + j]), g[j]);
+        df_norm(v);
+        s[(long long)(m + i) * nxy] = df_round(v);
+        nxt[i] = v;
+    }
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+        buf[j] = (m - 1 - j >= 0) ? s[(long long)(m - 1 - j) * nxy] : make_float2(0.f, 0.f);
+    for (int k0 = m - 1; k0 >= 0; k0 -= PF) {
+        float2 cur[PF];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            cur[j] = buf[j];
+            const int kk = k0 - PF - j;
+            buf[j] = (kk >= 0) ? s[(long long)kk * nxy] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int k = k0 - j;
+            if (k >= 0) {
+                // x_k = y_k / u_0 - sum_t (u_t / u_0) x_{k+t}, the newest term last
+                Dfc x = zero;
+                df_cacc(x, uinv, df_from(cur[j]));
+#pragma unroll
+                for (int t = NF; t >= 1; --t) df_cacc(x, nw[t], nxt[t - 1]);
+                df_norm(x);
+                s[(long long)k * nxy] = df_round(x);
+#pragma unroll
+                for (int t = NF - 1; t > 0; --t) nxt[t] = nxt[t - 1];
+                nxt[0] = x;
+            }
+        }
+    }
+}
+
+// every mode but the double-float ones (flagged in zflag), in the working precision
 template <typename T, int NF>
 __global__ void __launch_bounds__(kZThreads) k_zsolve(const PrecondArgs<T> a) {
     using C = typename Cplx<T>::type;
@@ -152,92 +307,22 @@ __global__ void __launch_bounds__(kZThreads) k_zsolve(const PrecondArgs<T> a) {
     const int mode = blockIdx.x * blockDim.x + threadIdx.x;
     if (mode >= nxy) return;
     const int e = a.rhs_energy ? a.rhs_energy[rhs] : 0;
-    const C* __restrict__ pc = a.pc + ((size_t)e * nxy + mode) * kPcStrideDev;
-    C l[NF + 1], u[NF + 1];
-#pragma unroll
-    for (int j = 1; j <= NF; ++j) l[j] = pc[j - 1];
-#pragma unroll
-    for (int j = 0; j <= NF; ++j) u[j] = pc[NF + j];
-    const C uinv = cdivc(make_one<C>(), u[0]);
-    const int nz = a.nz, m = nz - NF;
-    C* __restrict__ s = a.spec + (long long)rhs * a.npts + mode;
-    const T scale = (T)1 / (T)nxy;   // the forward FFT carries no 1/N_xy
-    constexpr int PF = kZPrefetch;
-    // forward: y_k = r_k - sum_j l_j y_{k-j}
-    C hist[NF];
-#pragma unroll
-    for (int j = 0; j < NF; ++j) hist[j] = czero<C>();   // hist[j] = y_{k-1-j}
-    C buf[PF];
-#pragma unroll
-    for (int j = 0; j < PF; ++j) buf[j] = (j < m) ? s[(long long)j * nxy] : czero<C>();
-    for (int k0 = 0; k0 < m; k0 += PF) {
-        C cur[PF];
-#pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            cur[j] = buf[j];
-            const int kk = k0 + PF + j;
-            buf[j] = (kk < m) ? s[(long long)kk * nxy] : czero<C>();
-        }
-#pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int k = k0 + j;
-            if (k < m) {
-                C y = cscale(cur[j], scale);
-#pragma unroll
-                for (int t = 1; t <= NF; ++t) y = csub(y, cmul(l[t], hist[t - 1]));
-                s[(long long)k * nxy] = y;
-#pragma unroll
-                for (int t = NF - 1; t > 0; --t) hist[t] = hist[t - 1];
-                hist[0] = y;
-            }
-        }
-    }
-    // last nf planes: g_i = r_i - sum_{j: i-j < m} l_j y_{i-j};  x_2 = S2^{-1} g
-    C g[NF];
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-        C v = cscale(s[(long long)(m + i) * nxy], scale);
-#pragma unroll
-        for (int j = 1; j <= NF; ++j)
-            if (j > i) v = csub(v, cmul(l[j], hist[j - 1 - i]));
-        g[i] = v;
-    }
-    C nxt[NF];   // nxt[j] = x_{k+1+j}
-#pragma unroll
-    for (int i = 0; i < NF; ++i) {
-        C v = czero<C>();
-        // the end block's inverse is read here, where it is used
-#pragma unroll
-        for (int j = 0; j < NF; ++j) v = cfma(pc[2 * NF + 1 + i * NF + j], g[j], v);
-        s[(long long)(m + i) * nxy] = v;
-        nxt[i] = v;
-    }
-    // backward: x_k = (y_k - sum_j u_j x_{k+j}) / u_0
-#pragma unroll
-    for (int j = 0; j < PF; ++j) buf[j] = (m - 1 - j >= 0) ? s[(long long)(m - 1 - j) * nxy] : czero<C>();
-    for (int k0 = m - 1; k0 >= 0; k0 -= PF) {
-        C cur[PF];
-#pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            cur[j] = buf[j];
-            const int kk = k0 - PF - j;
-            buf[j] = (kk >= 0) ? s[(long long)kk * nxy] : czero<C>();
-        }
-#pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int k = k0 - j;
-            if (k >= 0) {
-                C v = cur[j];
-#pragma unroll
-                for (int t = 1; t <= NF; ++t) v = csub(v, cmul(u[t], nxt[t - 1]));
-                v = cmul(v, uinv);
-                s[(long long)k * nxy] = v;
-#pragma unroll
-                for (int t = NF - 1; t > 0; --t) nxt[t] = nxt[t - 1];
-                nxt[0] = v;
-            }
-        }
-    }
+    if (sizeof(T) == 4 && a.zf_k > 0 && a.zflag[(size_t)e * nxy + mode]) return;
+    zsweep<C, C, NF>(a.spec + (long long)rhs * a.npts + mode,
+                     a.pc + ((size_t)e * nxy + mode) * kPcStrideDev, a.nz, nxy);
+}
+
+// the double-float sweeps of the flagged modes (FP32 solves; beside or before k_zsolve)
+template <int NF>
+__global__ void __launch_bounds__(kZThreads) k_zsolve_df(const PrecondArgs<float> a) {
+    const int rhs = blockIdx.y;
+    if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= a.zf_k) return;
+    const int e = a.rhs_energy ? a.rhs_energy[rhs] : 0;
+    const int mode = a.zf_bins[(size_t)e * a.zf_k + f];
+    zsweep_df<NF>(a.spec + (long long)rhs * a.npts + mode,
+                  a.zf_pc + ((size_t)e * a.zf_k + f) * kPcStrideDev, a.nz, a.nx * a.ny);
 }
 
 // Eq. 10 in the lateral Fourier basis: with r~ the (unnormalised) plane
@@ -469,19 +554,48 @@ static bool ct_size(int nx, int ny) {
 template <typename T>
 static cudaError_t launch_zsolve(const PrecondArgs<T>& a, int nrhs, cudaStream_t s) {
     const int nxy = a.nx * a.ny;
-    dim3 gz((nxy + kZThreads - 1) / kZThreads, nrhs);
     if (a.eq10) {
+        dim3 gz((nxy + kZThreads - 1) / kZThreads, nrhs);
         k_zmul_eq10<T><<<gz, kZThreads, 0, s>>>(a);
         return cudaGetLastError();
     }
+    const int nzb = (nxy + kZThreads - 1) / kZThreads;
+    if (a.nf < 1 || a.nf > 4) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    const bool fork = sizeof(T) == 4 && a.zf_k > 0 && a.zf_side;
+    if (sizeof(T) == 4 && a.zf_k > 0) {
+        // the double-float sweeps: on the side stream, forked from s and joined back
+        // after the other sweeps, or (no side stream) on s before them
+        cudaStream_t sd = s;
+        if (fork) {
+            e = cudaEventRecord(a.zf_fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(a.zf_side, a.zf_fork, 0);
+            if (e != cudaSuccess) return e;
+            sd = a.zf_side;
+        }
+        if constexpr (sizeof(T) == 4) {
+            dim3 gd((a.zf_k + kZThreads - 1) / kZThreads, nrhs);
+            switch (a.nf) {
+                case 1: k_zsolve_df<1><<<gd, kZThreads, 0, sd>>>(a); break;
+                case 2: k_zsolve_df<2><<<gd, kZThreads, 0, sd>>>(a); break;
+                case 3: k_zsolve_df<3><<<gd, kZThreads, 0, sd>>>(a); break;
+                default: k_zsolve_df<4><<<gd, kZThreads, 0, sd>>>(a); break;
+            }
+        }
+        e = cudaGetLastError();
+        if (e == cudaSuccess && fork) e = cudaEventRecord(a.zf_join, sd);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 gz(nzb, nrhs);
     switch (a.nf) {
         case 1: k_zsolve<T, 1><<<gz, kZThreads, 0, s>>>(a); break;
         case 2: k_zsolve<T, 2><<<gz, kZThreads, 0, s>>>(a); break;
         case 3: k_zsolve<T, 3><<<gz, kZThreads, 0, s>>>(a); break;
-        case 4: k_zsolve<T, 4><<<gz, kZThreads, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;
+        default: k_zsolve<T, 4><<<gz, kZThreads, 0, s>>>(a); break;
     }
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(s, a.zf_join, 0);
+    return e;
 }
 
 // forward transform (optionally fused with the COCG update) for square planes

@@ -317,6 +317,7 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
         out.sigma.assign((size_t)nx * ny * nf * nf, cd(0.0, 0.0));
         out.pc.assign((size_t)nx * ny * kPcStride, cd(0.0, 0.0));
     }
+    out.eperp_bin.assign((size_t)nx * ny, 0.0);
     std::vector<double> ex(nx), ey(ny);
     for (int ix = 0; ix < nx; ++ix) ex[ix] = eps1d(nu_of_index(ix, nx), nx, hx, kappa_x);
     for (int iy = 0; iy < ny; ++iy) ey[iy] = eps1d(nu_of_index(iy, ny), ny, hy, kappa_y);
@@ -348,6 +349,7 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
             const size_t u = std::lower_bound(uniq.begin(), uniq.end(), eperp[canon]) - uniq.begin();
             const ModeSolution& m = sol[u];
             const int kx = bin_of_nu(nux, nx), ky = bin_of_nu(nuy, ny);
+            out.eperp_bin[(size_t)ky * nx + kx] = eperp[canon];
             if (want_sigma) {
                 cd* dst = &out.sigma[((size_t)ky * nx + kx) * nf * nf];
                 for (int i = 0; i < nf * nf; ++i) dst[i] = m.sigma[i];

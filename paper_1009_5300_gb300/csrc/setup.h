@@ -31,6 +31,7 @@ struct ModeTables {
     // mode (constant factors l_1..l_nf, u_0..u_nf and the inverse of the last
     // nf x nf Schur block), [ky][kx][kPcStride]
     std::vector<cd> pc;
+    std::vector<double> eperp_bin;     // [ky][kx] lateral energy eps_perp of each FFT bin
 };
 
 constexpr int kPcStride = 25;   // nf + (nf + 1) + nf * nf for nf = 4
