@@ -38,17 +38,20 @@ ROOFLINE_KERNELS = {
     # p = z + beta p_old, q = (r - V z) + beta q_old: read z r p_old q_old, write p q
     "operator": {"kernel": "k_pq_update<float> (implicit operator form: direction and "
                            "operator update + p^T q partials)",
-                 "bytes_rhs_point": 48.0, "bytes_point": 4.0, "dram_rhs_point": None},
+                 "bytes_rhs_point": 48.0, "bytes_point": 4.0,
+                 "dram_rhs_point": (670682368 + 288807168) / (56 * 368640)},
     # x += alpha p, r -= alpha q, forward plane FFTs: read x p r q, write x r spectrum
     "update_fft": {"kernel": "k_update_fft_ct<float,48> (x, r update + forward plane FFTs)",
                    "bytes_rhs_point": 56.0, "bytes_point": 0.0,
-                   "dram_rhs_point": (660657920 + 435025664) / (56 * 368640)},
+                   "dram_rhs_point": (660668672 + 435869696) / (56 * 368640)},
     # z-sweeps in place: read the spectrum, write the forward sweep, read it back, write z
     "zsweep": {"kernel": "k_zsolve<float,4> (free-propagator z-sweeps per lateral mode)",
-               "bytes_rhs_point": 32.0, "bytes_point": 0.0, "dram_rhs_point": None},
+               "bytes_rhs_point": 32.0, "bytes_point": 0.0,
+               "dram_rhs_point": (229594368 + 196402432) / (56 * 368640)},
     # inverse plane FFTs + dots: read spectrum and r, write z
     "ifft": {"kernel": "k_ifft_dots_ct<float,48> (inverse plane FFTs + r^T z, |r|^2 partials)",
-             "bytes_rhs_point": 24.0, "bytes_point": 0.0, "dram_rhs_point": None},
+             "bytes_rhs_point": 24.0, "bytes_point": 0.0,
+             "dram_rhs_point": (330364672 + 119505152) / (56 * 368640)},
 }
 ROOFLINE_STAGE = "update_fft"   # the kernel with the largest share of the bench step
 # The explicit-form stencil (fused p = z + beta p_old, FD operator + V, p^T q): 32 B per
@@ -57,7 +60,9 @@ ROOFLINE_STAGE = "update_fft"   # the kernel with the largest share of the bench
 STENCIL_KERNEL = ("k_stencil_blk<48,4,4,4> (explicit form: fused p update + FD operator + "
                   "p^T q; 4 rows per thread, bulk-copy staged)")
 STENCIL_BYTES_RHS_POINT = 32.0
-STENCIL_DRAM_BYTES_PER_RHS_POINT = None
+# ncu capture of one full-load launch on 56 RHS (bench.py --workload stencil --stencil-rhs 56):
+# 402.6 MB read + 289.0 MB written
+STENCIL_DRAM_BYTES_PER_RHS_POINT = (402582528 + 289049344) / (56 * 368640)
 WORKLOAD = ("wire48: 6-atom wire, Gaussian wells (0.5 Ha, width 1.5 bohr, spacing 6.8 bohr) "
             "+ s/p KB projectors (radius 3 bohr), 48x48x160 grid, h=0.35 bohr, 9-point FD, "
             "r_s=3.28 jellium, 32 energies in [E_F-2eV, E_F+0.5eV], all open channels, "
@@ -701,6 +706,33 @@ def wire128_arm(args, rank, world, local_rank):
     return 0
 
 
+def stencil_arm(args, rank, world, local_rank):
+    """The explicit-form FD stencil kernel alone at full load: --stencil-rhs RHS of the
+    48x48x160 wire, every RHS active, --steps timed launches after --warmup (iobm_time_operator),
+    the handle's default tiling (z-chunk 32, the fastest kernel for the shape)."""
+    import torch
+    import iobm_synth as S
+    from paper_1009_5300_gb300 import IOBMSolver, build_library
+
+    build_library()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    jn = S.wire48()
+    sol = IOBMSolver.from_junction(jn, precision="mixed", device=dev, op_form="explicit")
+    nrhs = args.stencil_rhs
+    sol.time_operator(nrhs, reps=max(1, args.warmup))
+    ms = sol.time_operator(nrhs, reps=max(1, args.steps))
+    sol.close()
+    npts = jn.npts
+    alg = STENCIL_BYTES_RHS_POINT * npts * nrhs + 4.0 * npts
+    peak, kind = load_peaks()
+    if rank == 0:
+        print(json.dumps({"workload": "stencil", "kernel": STENCIL_KERNEL, "nrhs": nrhs,
+                          "avg_launch_ms": ms, "achieved_gbs": alg / (ms / 1e3) / 1e9,
+                          "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": kind}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -717,10 +749,13 @@ def main():
                     help="FP64 residual replacement factor of the mixed solver (library default)")
     ap.add_argument("--chunk", type=int, default=None,
                     help="COCG iterations per captured graph (library default)")
-    ap.add_argument("--workload", choices=["wire48", "batch", "wire128"], default="wire48",
+    ap.add_argument("--stencil-rhs", type=int, default=228,
+                    help="RHS of the stencil-only measurement (--workload stencil)")
+    ap.add_argument("--workload", choices=["wire48", "batch", "wire128", "stencil"], default="wire48",
                     help="wire48: the 48x48x160 wire (default line); batch: the uneven "
                          "many-junction workload solved in grouped graph launches; wire128: "
-                         "the 128x128x256 large cross-section wire")
+                         "the 128x128x256 large cross-section wire; stencil: the explicit-form "
+                         "FD stencil kernel alone at full load")
     ap.add_argument("--wire128-energies", type=int, default=8)
     ap.add_argument("--batch", type=int, default=32, help="channels per solve (wire128)")
     ap.add_argument("--junctions", type=int, default=256)
@@ -735,6 +770,8 @@ def main():
         return batch_arm(args, rank, world, local_rank)
     if args.workload == "wire128":
         return wire128_arm(args, rank, world, local_rank)
+    if args.workload == "stencil":
+        return stencil_arm(args, rank, world, local_rank)
     return native_arm(args, rank, world, local_rank)
 
 
