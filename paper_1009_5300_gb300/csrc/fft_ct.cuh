@@ -11,9 +11,6 @@
 #include "complex_ops.cuh"
 #include "fft_bfly.cuh"
 
-#include <type_traits>
-#include <utility>
-
 namespace iobm {
 
 // Radix sequence of an N-point transform.  Twiddles (tw[t] = exp(-2 pi i t / N))
@@ -91,16 +88,6 @@ __device__ __forceinline__ void ct_passes(C*& cur, C*& oth, int ls, int es, cons
         C* s = cur; cur = oth; oth = s;
         ct_passes<C, N, P + 1, NS * R, NT>(cur, oth, ls, es, tw, inv);
     }
-}
-
-// f(std::integral_constant<int, k>) for k = 0 .. K-1 (compile-time loop index)
-template <int K, typename F, int... I>
-__device__ __forceinline__ void ct_for_impl(F&& f, std::integer_sequence<int, I...>) {
-    (f(std::integral_constant<int, I>{}), ...);
-}
-template <int K, typename F>
-__device__ __forceinline__ void ct_for(F&& f) {
-    ct_for_impl<K>(f, std::make_integer_sequence<int, K>{});
 }
 
 // Row-major element i = tid + K NT of an N x N plane, as its index in the padded
@@ -194,6 +181,99 @@ __device__ __forceinline__ void ct_fft2_store(C* a, C* b, const C* tw, bool inv,
     C* oth = b;
     ct_passes<C, N, 0, 1, NT>(cur, oth, P, 1, tw, inv);   // rows
     ct_col_passes_store<C, N, 0, 1, NT>(cur, oth, P, tw, inv, store);
+}
+
+// Two-factor plan N = R1 R2 for the sizes whose first radix fits in registers: per
+// axis, one pass of R1-point DFTs in registers (sub-transform size 1: no twiddles)
+// and one pass of R2-point DFTs after the twiddles exp(-+2 pi i r j / N).  A CTA of
+// NT = N R2 threads holds one plane; every thread does one R1-point DFT per first
+// pass and K2 = R1 / R2 R2-point DFTs per second pass.
+template <int N> struct Ct2Plan { static constexpr bool ok = false; };
+template <> struct Ct2Plan<32> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 4; };
+template <> struct Ct2Plan<48> { static constexpr bool ok = true; static constexpr int R1 = 12, R2 = 4; };
+template <> struct Ct2Plan<64> { static constexpr bool ok = true; static constexpr int R1 = 16, R2 = 4; };
+template <int N>
+struct Ct2Shape {
+    static constexpr int R1 = Ct2Plan<N>::R1, R2 = Ct2Plan<N>::R2;
+    static constexpr int NT = N * R2;
+    static constexpr int K2 = R1 / R2;
+    static constexpr int PT = N + 1;   // shared-memory row pitch
+    static_assert(R1 * R2 == N && R1 % R2 == 0, "two-factor plan");
+    // the first pass's inputs of thread tid: row tid / R2, columns tid % R2 + m R2 (m < R1)
+    __device__ static int in_row(int tid) { return tid / R2; }
+    __device__ static int in_col(int tid, int m) { return tid % R2 + m * R2; }
+    // the last pass's outputs of thread tid: column tid % N, rows j + a R1 with
+    // j = tid / N + k R2 (k < K2, a < R2), handed to the store as slot k R2 + a
+    __device__ static int out_row(int tid, int k, int a) { return tid / N + k * R2 + a * R1; }
+    __device__ static int out_col(int tid) { return tid % N; }
+};
+
+// 2D transform of one N x N plane by NT threads.  v holds the thread's inputs of the
+// first row pass (Ct2Shape::in_row / in_col: the caller reads them from global
+// memory), store(row, col, value, slot) takes the output from the last column pass.
+// A and B are two
+// shared-memory planes of pitch N + 1; tw holds exp(-2 pi i t / N), t < N, and must
+// be visible to every thread before the first barrier inside.
+//
+// Pass 1 (rows): thread (row y, j = tid % R2) forms the R1-point DFT of
+// x[y][j + m R2] into A[y][j R1 + a]; pass 2 (rows): butterfly (y, j < R1), y fastest,
+// reads A[y][j + r R1] exp(-+2 pi i r j / N) and writes its R2-point DFT to
+// B[y][j + a R1]; passes 3 and 4 do the same along the columns, B -> A -> store.
+// Every shared-memory access of a warp touches each 8-byte bank pair at most twice.
+template <typename C, int N, bool INV, typename Store>
+__device__ __forceinline__ void ct2_fft2(const C (&v1)[Ct2Plan<N>::R1], C* A, C* B, const C* tw,
+                                         Store store) {
+    using S = Ct2Shape<N>;
+    constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, K2 = S::K2, PT = S::PT;
+    const int tid = threadIdx.x;
+    auto twiddled = [&](C v, int e) {   // v exp(-+2 pi i e / N), 0 <= e < N
+        C w = tw[e];
+        if (INV) w.y = -w.y;
+        return cmul(v, w);
+    };
+    {   // pass 1: rows, R1 points from the input
+        const int j = tid % R2, y = tid / R2;
+        C o[R1];
+        dft_reg<C, R1, INV>(v1, o);
+#pragma unroll
+        for (int a = 0; a < R1; ++a) A[y * PT + j * R1 + a] = o[a];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K2; ++k) {   // pass 2: rows, R2 points
+        const int t = tid + k * NT;
+        const int y = t % N, j = t / N;
+        C v[R2], o[R2];
+        v[0] = A[y * PT + j];
+#pragma unroll
+        for (int r = 1; r < R2; ++r) v[r] = twiddled(A[y * PT + j + r * R1], r * j);
+        dft_reg<C, R2, INV>(v, o);
+#pragma unroll
+        for (int a = 0; a < R2; ++a) B[y * PT + j + a * R1] = o[a];
+    }
+    __syncthreads();
+    {   // pass 3: columns, R1 points
+        const int x = tid % N, j = tid / N;
+        C v[R1], o[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) v[m] = B[(j + m * R2) * PT + x];
+        dft_reg<C, R1, INV>(v, o);
+#pragma unroll
+        for (int a = 0; a < R1; ++a) A[(j * R1 + a) * PT + x] = o[a];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K2; ++k) {   // pass 4: columns, R2 points, to the store
+        const int t = tid + k * NT;
+        const int x = t % N, j = t / N;
+        C v[R2], o[R2];
+        v[0] = A[j * PT + x];
+#pragma unroll
+        for (int r = 1; r < R2; ++r) v[r] = twiddled(A[(j + r * R1) * PT + x], r * j);
+        dft_reg<C, R2, INV>(v, o);
+#pragma unroll
+        for (int a = 0; a < R2; ++a) store(j + a * R1, x, o[a], k * R2 + a);
+    }
 }
 
 }  // namespace iobm

@@ -516,6 +516,68 @@ __global__ void __launch_bounds__(256, (CtOccupancy<T, N>::value)) k_ifft_dots_c
     }
 }
 
+// The same inverse transform and dot products on the two-factor plan (N = 32, 48,
+// 64): the first row pass reads the spectrum from global memory, the last column
+// pass writes z, so a point crosses shared memory twice per axis; r at the outputs
+// of the thread's last pass is loaded with the spectrum, so its latency overlaps
+// the transform.  CTAs of N R2 threads (192 at N = 48), at most four per SM (FP32)
+// or two (FP64), which the registers of the prefetched operands allow without spills.
+template <typename T, int N>
+struct Ct2Occupancy {
+    static constexpr int kSmem = (int)sizeof(typename Cplx<T>::type) * (2 * N * (N + 1) + N) + 1024 + 192;
+    static constexpr int kFit = (228 * 1024) / kSmem;
+    static constexpr int kCap = sizeof(typename Cplx<T>::type) == 8 ? 4 : 2;
+    static constexpr int value = kFit < 1 ? 1 : (kFit > kCap ? kCap : kFit);
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Ct2Shape<N>::NT, (Ct2Occupancy<T, N>::value))
+    k_ifft2_dots(const PrecondArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    using S = Ct2Shape<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[3 * 8];
+    const int plane = blockIdx.x, rhs = blockIdx.y;
+    if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
+    constexpr int PT = S::PT;
+    C* A = reinterpret_cast<C*>(smem_raw);
+    C* B = A + N * PT;
+    C* tw = B + N * PT;
+    for (int i = threadIdx.x; i < N; i += S::NT) tw[i] = a.twx[i];
+    const long long off = (long long)rhs * a.npts + (long long)plane * (N * N);
+    const C* __restrict__ spec = a.spec + off;
+    C* __restrict__ zo = a.z + off;
+    const C* __restrict__ rin = a.r + off;
+    const bool dots = a.dot_part != nullptr;
+    C v[S::R1];
+#pragma unroll
+    for (int m = 0; m < S::R1; ++m) v[m] = spec[S::in_row(threadIdx.x) * N + S::in_col(threadIdx.x, m)];
+    C rv[S::K2 * S::R2];
+#pragma unroll
+    for (int k = 0; k < S::K2; ++k)
+#pragma unroll
+        for (int aa = 0; aa < S::R2; ++aa)
+            rv[k * S::R2 + aa] = dots ? rin[S::out_row(threadIdx.x, k, aa) * N + S::out_col(threadIdx.x)] : czero<C>();
+    T dre = 0, dim = 0, nrm = 0;
+    ct2_fft2<C, N, true>(v, A, B, tw, [&](int row, int col, C z, int slot) {
+        zo[row * N + col] = z;
+        if (dots) {
+            const C r = rv[slot];
+            dre += r.x * z.x - r.y * z.y;
+            dim += r.x * z.y + r.y * z.x;
+            nrm += r.x * r.x + r.y * r.y;
+        }
+    });
+    if (dots) {
+        double d0 = dre, d1 = dim, d2 = nrm;
+        block_reduce_3(d0, d1, d2, red);
+        if (threadIdx.x == 0) {
+            a.dot_part[(long long)rhs * a.slot_stride + plane] = make_double2(d0, d1);
+            a.nrm_part[(long long)rhs * a.slot_stride + plane] = d2;
+        }
+    }
+}
+
 template <typename T>
 size_t precond_smem_bytes(int nx, int ny) {
     using C = typename Cplx<T>::type;
@@ -538,6 +600,9 @@ static cudaError_t prepare_type() {
     set((const void*)k_ifft_dots_ct<T, N>);
     IOBM_CT(12) IOBM_CT(16) IOBM_CT(24) IOBM_CT(32) IOBM_CT(48) IOBM_CT(64)
 #undef IOBM_CT
+    set((const void*)k_ifft2_dots<T, 32>);
+    set((const void*)k_ifft2_dots<T, 48>);
+    set((const void*)k_ifft2_dots<T, 64>);
     return e;
 }
 
@@ -626,8 +691,10 @@ static cudaError_t launch_inv_ct(const PrecondArgs<T>& a, int nrhs, cudaStream_t
     dim3 gp(a.nz, nrhs);
     switch (N) {
 #define IOBM_CT(NN) case NN: k_ifft_dots_ct<T, NN><<<gp, 256, smem, s>>>(a); break;
-        IOBM_CT(12) IOBM_CT(16) IOBM_CT(24) IOBM_CT(32) IOBM_CT(48) IOBM_CT(64)
+#define IOBM_CT2(NN) case NN: k_ifft2_dots<T, NN><<<gp, Ct2Shape<NN>::NT, smem, s>>>(a); break;
+        IOBM_CT(12) IOBM_CT(16) IOBM_CT(24) IOBM_CT2(32) IOBM_CT2(48) IOBM_CT2(64)
 #undef IOBM_CT
+#undef IOBM_CT2
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

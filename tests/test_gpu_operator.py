@@ -145,6 +145,27 @@ def test_fourier_precond_matches_oracle(nx, ny, nz, nf, kb):
     sol.close()
 
 
+@pytest.mark.parametrize("n,nz,nf", [(32, 14, 2), (48, 12, 4), (64, 10, 3)])
+def test_two_factor_inverse_transform_matches_oracle(n, nz, nf):
+    # square planes of 32, 48, 64 points take the two-factor inverse transform
+    # (8 x 4, 12 x 4, 16 x 4); the oracle is its per-mode banded free propagator,
+    # pinned against sparse LU on small grids
+    from oracle import iterative
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = make(n, n, nz, nf, False)
+    E = jn.e_fermi + 0.011
+    md = modes.mode_data(n, n, jn.hx, jn.hy, jn.hz, nf, E)
+    x = np.stack([S.random_field((nz, n, n), 61 + i) for i in range(2)])
+    ref = np.stack([iterative.free_propagator_modes(jn, E, md, xi) for xi in x])
+    scale = np.max(np.abs(ref))
+    sol = IOBMSolver.from_junction(jn, precision="fp64", use_precond="fourier")
+    y = sol.apply_precond(torch.from_numpy(x).cuda(), E).cpu().numpy()
+    assert np.max(np.abs(y - ref)) < 1e-11 * scale
+    y32 = sol.apply_precond(torch.from_numpy(x).cuda().to(torch.complex64), E).cpu().numpy()
+    assert np.max(np.abs(y32 - ref)) < 1e-4 * scale
+    sol.close()
+
+
 def test_projector_on_end_planes_rejected():
     from paper_1009_5300_gb300 import IOBMSolver
     from paper_1009_5300_gb300._lib import IOBMError, IOBM_E_PROJ_BOUNDARY
