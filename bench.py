@@ -706,6 +706,82 @@ def wire128_arm(args, rank, world, local_rank):
     return 0
 
 
+# Sec. III solvers on the synthetic sodium-wire series (iobm_synth.na_wire), every open
+# channel at E_F, FP64 iterations as in the paper: (b) the self-energy as the dense
+# N_f N_xy matrix and (c) through the lateral FFT, both unpreconditioned; (d) with the
+# Eq. 10 preconditioner at alpha = 3.0, 2.4, 1.8; and the default free-propagator
+# preconditioner.  Explicit operator form for (b)-(d) (the dense matrix is what (b)
+# multiplies every iteration).
+ABLATION_SOLVERS = [
+    ("b_dense_sigma", dict(use_precond="none", op_form="explicit", sigma_form="dense")),
+    ("c_fft_sigma", dict(use_precond="none", op_form="explicit", sigma_form="fft")),
+    ("d_eq10_alpha3.0", dict(use_precond="eq10", alpha=3.0, op_form="explicit")),
+    ("d_eq10_alpha2.4", dict(use_precond="eq10", alpha=2.4, op_form="explicit")),
+    ("d_eq10_alpha1.8", dict(use_precond="eq10", alpha=1.8, op_form="explicit")),
+    ("free_propagator", dict()),
+]
+
+
+def ablation_solve(jn, kw, dev, precision):
+    """Solves of every open channel at E_F, CUDA events on the solver's stream: the
+    first (cold: tables, graphs and for (b) the dense matrices built inside), and a
+    second (warm) one when the first took under 20 s; returns the warm time if taken."""
+    import torch
+    from paper_1009_5300_gb300 import IOBMSolver
+
+    sol = IOBMSolver.from_junction(jn, precision=precision, device=dev, max_iter_mixed=100000,
+                                   max_iter=100000, **kw)
+    E = float(jn.energies[0])
+    stream = torch.cuda.current_stream(dev)
+
+    def timed():
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        res = sol.solve([E])
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        return res, ev0.elapsed_time(ev1)
+
+    res, ms = timed()
+    kind = "cold"
+    if ms < 20000.0:
+        res, ms = timed()
+        kind = "warm"
+    out = {"ms": ms, "timed": kind, "iterations_mean": float(res.iterations.mean()),
+           "G": float(res.G[0]), "n_open": int(res.nrhs), "converged": bool(res.converged)}
+    sol.close()
+    return out
+
+
+def ablation_arm(args, rank, world, local_rank):
+    """Solver ablation of Sec. III (Figs. 2-3, Table I) on the synthetic sodium-wire
+    series: per N_atom the time and iterations of each solver, same conductance."""
+    import torch
+    import iobm_synth as S
+    from paper_1009_5300_gb300 import build_library
+
+    build_library()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    rows = []
+    for natom in args.ablation_atoms:
+        jn = S.na_wire(natom)
+        row = {"natom": natom, "grid": [jn.nx, jn.ny, jn.nz]}
+        for name, kw in ABLATION_SOLVERS:
+            row[name] = ablation_solve(jn, kw, dev, args.ablation_precision)
+        Gs = [row[name]["G"] for name, _ in ABLATION_SOLVERS]
+        row["max_dG_G0"] = max(Gs) - min(Gs)
+        rows.append(row)
+        if rank == 0:
+            print(json.dumps(row), flush=True)
+    if rank == 0:
+        print(json.dumps({"workload": "ablation", "precision": args.ablation_precision,
+                          "solvers": [n for n, _ in ABLATION_SOLVERS], "rows": rows}), flush=True)
+    return 0
+
+
 def stencil_arm(args, rank, world, local_rank):
     """The explicit-form FD stencil kernel alone at full load: --stencil-rhs RHS of the
     48x48x160 wire, every RHS active, --steps timed launches after --warmup (iobm_time_operator),
@@ -751,11 +827,15 @@ def main():
                     help="COCG iterations per captured graph (library default)")
     ap.add_argument("--stencil-rhs", type=int, default=228,
                     help="RHS of the stencil-only measurement (--workload stencil)")
-    ap.add_argument("--workload", choices=["wire48", "batch", "wire128", "stencil"], default="wire48",
+    ap.add_argument("--workload", choices=["wire48", "batch", "wire128", "stencil", "ablation"],
+                    default="wire48",
                     help="wire48: the 48x48x160 wire (default line); batch: the uneven "
                          "many-junction workload solved in grouped graph launches; wire128: "
                          "the 128x128x256 large cross-section wire; stencil: the explicit-form "
-                         "FD stencil kernel alone at full load")
+                         "FD stencil kernel alone at full load; ablation: the Sec. III solvers "
+                         "on the synthetic sodium-wire series")
+    ap.add_argument("--ablation-atoms", type=int, nargs="+", default=[3, 4, 5, 6, 7, 8])
+    ap.add_argument("--ablation-precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--wire128-energies", type=int, default=8)
     ap.add_argument("--batch", type=int, default=32, help="channels per solve (wire128)")
     ap.add_argument("--junctions", type=int, default=256)
@@ -772,6 +852,8 @@ def main():
         return wire128_arm(args, rank, world, local_rank)
     if args.workload == "stencil":
         return stencil_arm(args, rank, world, local_rank)
+    if args.workload == "ablation":
+        return ablation_arm(args, rank, world, local_rank)
     return native_arm(args, rank, world, local_rank)
 
 

@@ -125,6 +125,16 @@ typedef struct {
 #define IOBM_OP_AUTO      0
 #define IOBM_OP_EXPLICIT  1
 
+/* How the end-plane self-energy term of Eq. 7 is applied (iobm_options.sigma_form).
+ * IOBM_SIGMA_FFT (default): diagonal per lateral mode after the lateral FFT of
+ * Eq. 19, O(N_xy log N_xy) per plane.  IOBM_SIGMA_DENSE: the dense N_f N_xy square
+ * matrix of each energy, kept in device memory (FP32 and FP64 copies) and multiplied
+ * directly, O((N_f N_xy)^2) per RHS: the solver (b) of Sec. III, an ablation of the
+ * transform (the same operator up to rounding).  Dense matrices above 64 GB per
+ * handle, a nonzero Bloch vector and batched solves return IOBM_E_UNSUPPORTED. */
+#define IOBM_SIGMA_FFT    0
+#define IOBM_SIGMA_DENSE  1
+
 /* Solver options.  use_precond: one of IOBM_PRECOND_*.  alpha: parameter of
  * Eq. 10 (C_0 = 1, C_1 = exp(-alpha)) for IOBM_PRECOND_EQ10(_FOURIER).  tol: stop when
  * ||b - A psi||_2 / ||b||_2 <= tol, the residual evaluated in FP64.
@@ -142,7 +152,8 @@ typedef struct {
  * per energy nearest their channel threshold (smallest |E - eps_perp|) whose
  * preconditioner z-sweeps run in FP64 with FP64 factors inside the FP32 iterations:
  * their banded z-systems are the worst conditioned, and FP32 sweeps there cost
- * iterations; 0 sweeps every mode in FP32. */
+ * iterations; 0 sweeps every mode in FP32.
+ * sigma_form: IOBM_SIGMA_FFT or IOBM_SIGMA_DENSE (above). */
 typedef struct {
     double alpha;
     int use_precond;
@@ -154,6 +165,7 @@ typedef struct {
     int max_iter_mixed;
     int op_form;
     int fp64_modes;
+    int sigma_form;
 } iobm_options;
 
 /* Per right-hand-side report, in solve order (energy-major, then incident
@@ -170,7 +182,7 @@ typedef struct {
 
 /* Fill opts with the defaults: alpha 1.8, use_precond IOBM_PRECOND_FOURIER, tol 1e-8,
  * max_iter 20000, precision IOBM_MIXED, refine_delta 0.01, chunk 32,
- * max_iter_mixed 1000, op_form IOBM_OP_AUTO, fp64_modes 16. */
+ * max_iter_mixed 1000, op_form IOBM_OP_AUTO, fp64_modes 16, sigma_form IOBM_SIGMA_FFT. */
 void iobm_default_options(iobm_options* opts);
 
 /* Create a solver for one junction: the truncated Hamiltonian H_T of the

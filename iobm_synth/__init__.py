@@ -280,6 +280,26 @@ def wire128(junction_id: int = 0, n_energies: int = 8) -> Junction:
                      seed=4 * 1000 + junction_id)
 
 
+def na_wire(natom: int, junction_id: int = 0, nxy: int = 36) -> Junction:
+    """Synthetic stand-in for the Sec. III sodium wires (the paper's DFT potentials are
+    not reproduced): a single row of natom Gaussian wells (0.3 Ha, width 1.8 bohr) at
+    the Na [110] spacing d = (sqrt(3)/2) 8.11 bohr between r_s = 3.99 jellium
+    electrodes; lateral cell 25.66 bohr on nxy x nxy points (36 in Sec. III),
+    N_z = 60 + 10 (natom - 1) planes over L_z = (natom - 1) d + 42.12 bohr; at E_F."""
+    rs = 3.99
+    d = 0.5 * np.sqrt(3.0) * 8.11
+    L = 25.66
+    nz = 60 + 10 * (natom - 1)
+    hz = ((natom - 1) * d + 42.12) / nz
+    h = L / nxy
+    rng = np.random.default_rng(5 * 1000 + 10 * natom + junction_id)
+    atoms = wire_atoms(nxy, nxy, nz, h, h, hz, natom, d, rng)
+    V = gaussian_wells(nxy, nxy, nz, h, h, hz, atoms, 0.3, 1.8)
+    return Junction(name=f"na{natom}", nx=nxy, ny=nxy, nz=nz, hx=h, hy=h, hz=hz, nf=4, V=V,
+                    projectors=[], rs=rs, energies=np.array([fermi_energy(rs)]), atoms=atoms,
+                    seed=5 * 1000 + 10 * natom + junction_id)
+
+
 def small_wire(nx=8, ny=8, nz=24, h=0.5, natom=2, spacing=3.0, depth=0.5, width=1.0,
                rs=3.28, energies=None, kb_kinds=None, seed=12345, nf=4, kb_radius=1.5,
                kb_width=0.6) -> Junction:

@@ -31,6 +31,8 @@ IOBM_PRECOND_FOURIER = 2
 IOBM_PRECOND_EQ10_FOURIER = 3
 IOBM_OP_AUTO = 0
 IOBM_OP_EXPLICIT = 1
+IOBM_SIGMA_FFT = 0
+IOBM_SIGMA_DENSE = 1
 IOBM_ELEM_C64 = 0
 IOBM_ELEM_C32 = 1
 IOBM_ELEM_C64_DF = 2
@@ -51,7 +53,7 @@ class Options(C.Structure):
     _fields_ = [("alpha", C.c_double), ("use_precond", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("refine_delta", C.c_double),
                 ("chunk", C.c_int), ("max_iter_mixed", C.c_int), ("op_form", C.c_int),
-                ("fp64_modes", C.c_int)]
+                ("fp64_modes", C.c_int), ("sigma_form", C.c_int)]
 
 
 class Report(C.Structure):

@@ -125,6 +125,9 @@ struct iobm_handle {
     void* pin = nullptr;                         // pinned staging buffer for table uploads
     size_t pin_bytes = 0;
     bool pc64_valid = false;                     // FP64 preconditioner tables of this solve uploaded
+    // IOBM_SIGMA_DENSE: the dense self-energy matrices of the solve's energies and of
+    // single applications, the FP64 lateral kernels they are filled from, tile partials
+    DevBuf dense32, dense64, apply_dense32, apply_dense64, dense_k, dense_part;
 
     // workspace
     void* ws = nullptr;
@@ -217,6 +220,48 @@ int plane_slots(const iobm_handle* h) { return large_plane(h) ? large_row_blocks
 // mu partial slots of the self-energy
 int sigma_slots(const iobm_handle* h) { return 2 * h->nf * plane_slots(h); }
 
+bool dense_sigma(const iobm_handle* h) { return h->opt.sigma_form == IOBM_SIGMA_DENSE; }
+
+// largest total of dense self-energy matrices (both precisions) a handle builds
+constexpr double kDenseSigmaMaxBytes = 64.0 * (1ull << 30);
+
+// The dense matrices (FP32 and FP64) of ne energies from their FP64 per-mode tables.
+int build_dense_sigma(iobm_handle* h, const void* sig64, int ne, DevBuf& d32, DevBuf& d64) {
+    const double M = (double)h->nf * h->nxy;
+    const double bytes = (double)ne * M * M * (sizeof(float2) + sizeof(double2));
+    if (bytes > kDenseSigmaMaxBytes)
+        return fail(h, IOBM_E_UNSUPPORTED, "dense self-energy matrices above 64 GB");
+    const size_t mm = (size_t)M * (size_t)M * (size_t)ne;
+    CK(h->dense_k.ensure(sizeof(double2) * (size_t)ne * h->nf * h->nf * h->nxy));
+    CK(d32.ensure(sizeof(float2) * mm));
+    CK(d64.ensure(sizeof(double2) * mm));
+    CK(build_sigma_dense((const double2*)sig64, h->twx64.as<double2>(), h->twy64.as<double2>(), h->g.nx,
+                         h->g.ny, h->nf, ne, h->dense_k.as<double2>(), d32.as<float2>(),
+                         d64.as<double2>(), h->stream));
+    return IOBM_OK;
+}
+
+// y_end -= Sigma~ x_end: through the lateral FFT, or (IOBM_SIGMA_DENSE) by the dense
+// matrices that belong to the per-mode tables `sig`
+template <typename T>
+int apply_sigma(iobm_handle* h, const SigmaArgs<T>& s, const void* sig, int nrhs) {
+    if (!dense_sigma(h)) {
+        CK(launch_sigma<T>(s, nrhs, h->stream));
+        return IOBM_OK;
+    }
+    const bool f32 = std::is_same<T, float>::value;
+    const DevBuf* D = nullptr;
+    if (sig == h->sig32.p || sig == h->sig64.p) D = f32 ? &h->dense32 : &h->dense64;
+    else if (sig == h->apply_sig32.p || sig == h->apply_sig64.p) D = f32 ? &h->apply_dense32 : &h->apply_dense64;
+    if (!D || !D->p) return fail(h, IOBM_E_UNSUPPORTED, "dense self-energy matrices not built");
+    if (s.dot_part && h->dense_part.bytes < sizeof(double2) * (size_t)nrhs * 2 *
+                                                   dense_row_tiles(h->nf, h->nxy))
+        return fail(h, IOBM_E_ARG, "dense self-energy partials not allocated for this RHS count");
+    CK(launch_sigma_dense<T>(s, (const typename Cplx<T>::type*)D->p, nrhs, h->dense_part.as<double2>(),
+                             h->nf * plane_slots(h), h->stream));
+    return IOBM_OK;
+}
+
 int slots_for(const iobm_handle* h) {
     const int ns_op = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, h->nf);
     const int ns_pc = stencil_slots(h->g.nx, h->g.ny, h->g.nz, kZChunkMin, 1);
@@ -236,6 +281,11 @@ int rho_slots(const iobm_handle* h) {
 cudaError_t ensure_sigma_scratch(iobm_handle* h, int nrhs) {
     if (h->pt.nproj > 0) {   // KB projections per (RHS, projector)
         const cudaError_t e = h->kb_scratch.ensure((size_t)std::max(nrhs, 1) * h->pt.nproj * sizeof(double2));
+        if (e != cudaSuccess) return e;
+    }
+    if (dense_sigma(h)) {   // tile partials of the dense self-energy (per RHS, end, row tile)
+        const cudaError_t e = h->dense_part.ensure(sizeof(double2) * (size_t)std::max(nrhs, 1) * 2 *
+                                                   dense_row_tiles(h->nf, h->nxy));
         if (e != cudaSuccess) return e;
     }
     if (!large_plane(h)) return cudaSuccess;
@@ -489,7 +539,10 @@ int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void*
     s.rhs_energy = rhs_energy;
     s.state = st;
     s.mask = mask;
-    CK(launch_sigma<T>(s, nrhs, h->stream));
+    {
+        const int rc = apply_sigma<T>(h, s, sig, nrhs);
+        if (rc) return rc;
+    }
     launches += 2;
     if (h->pt.nproj > 0) {
         KbArgs<T> k = kb_args<T>(h);
@@ -699,7 +752,10 @@ int cocg_iteration(iobm_handle* h, int nrhs, bool mixed, long long& launches, in
         s.dot_part = h->mu_part;
         s.slot_stride = h->slot_stride;
         s.slot_base = ns;
-        CK(launch_sigma<T>(s, nrhs, h->stream));
+        {
+            const int rc = apply_sigma<T>(h, s, sig, nrhs);
+            if (rc) return rc;
+        }
         nslots_mu = ns + sigma_slots(h);
         launches += 3;
         if (h->pt.nproj > 0) {
@@ -1112,6 +1168,10 @@ int upload_solve_tables(iobm_handle* h) {
     };
     CK(put(h->sig64, s64, sizeof(double2) * nsig));
     CK(put(h->sig32, s32, sizeof(float2) * nsig));
+    if (dense_sigma(h)) {
+        const int rc = build_dense_sigma(h, h->sig64.p, (int)h->energies.size(), h->dense32, h->dense64);
+        if (rc) return rc;
+    }
     CK(put(h->pc32, p32, sizeof(float2) * npc));
     if (pc64_now) CK(put(h->pc64, p64, sizeof(double2) * npc));
     h->pc64_valid = pc64_now;
@@ -1720,6 +1780,7 @@ void iobm_default_options(iobm_options* o) {
     o->max_iter_mixed = 1000;
     o->op_form = IOBM_OP_AUTO;
     o->fp64_modes = 16;
+    o->sigma_form = IOBM_SIGMA_FFT;
 }
 
 const char* iobm_status_string(int s) {
@@ -1771,7 +1832,8 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
         (h->opt.precision != IOBM_FP64 && h->opt.precision != IOBM_MIXED) || !(h->opt.alpha > 0) ||
         h->opt.use_precond < IOBM_PRECOND_NONE || h->opt.use_precond > IOBM_PRECOND_EQ10_FOURIER ||
         (h->opt.op_form != IOBM_OP_AUTO && h->opt.op_form != IOBM_OP_EXPLICIT) ||
-        h->opt.fp64_modes < 0)
+        h->opt.fp64_modes < 0 ||
+        (h->opt.sigma_form != IOBM_SIGMA_FFT && h->opt.sigma_form != IOBM_SIGMA_DENSE))
         return bad(IOBM_E_ARG, "invalid solver options");
     h->nxy = g.nx * g.ny;
     h->npts = (long long)h->nxy * g.nz;
@@ -1894,7 +1956,8 @@ void iobm_destroy(iobm_handle* h) {
                       &h->batch_ctr, &h->sig_scratch, &h->kb_scratch, &h->uplane, &h->esc_ws,
                       &h->esc_descs, &h->esc_rhs_energy, &h->rhs_sign, &h->apply_sign,
                       &h->gph32, &h->gph64, &h->gpx, &h->gpy, &h->esc_rhs_sign,
-                      &h->zflag, &h->zf_bins, &h->zf_pc};
+                      &h->zflag, &h->zf_bins, &h->zf_pc, &h->dense32, &h->dense64,
+                      &h->apply_dense32, &h->apply_dense64, &h->dense_k, &h->dense_part};
     for (DevBuf* b : bufs) b->release();
     if (h->ev_sync) cudaEventDestroy(h->ev_sync);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
@@ -1980,6 +2043,8 @@ int iobm_solve_batch(int n, iobm_handle* const* handles, const double* const* E,
         if (!handles[j] || !E[j] || nE[j] < 1) return IOBM_E_ARG;
         if (bloch(handles[j]))
             return fail(handles[j], IOBM_E_UNSUPPORTED, "batched solves run at a zero Bloch vector");
+        if (dense_sigma(handles[j]))
+            return fail(handles[j], IOBM_E_UNSUPPORTED, "batched solves use the FFT self-energy");
         for (int i = 0; i < j; ++i)
             if (handles[i] == handles[j]) return fail(handles[j], IOBM_E_ARG, "a handle appears twice in the batch");
     }
@@ -2223,6 +2288,10 @@ static int apply_common(iobm_handle* h, double E, int elem, const void* x, void*
         std::vector<double> ed(1, E);
         CK(upload(h->apply_sig64, s64, h->stream));
         CK(upload(h->apply_sig32, s32, h->stream));
+        if (dense_sigma(h) && !precond) {
+            const int rc = build_dense_sigma(h, h->apply_sig64.p, 1, h->apply_dense32, h->apply_dense64);
+            if (rc) return rc;
+        }
         CK(upload(h->apply_pc64, p64, h->stream));
         CK(upload(h->apply_pc32, p32, h->stream));
         CK(upload(h->apply_ediag, ed, h->stream));
@@ -2349,10 +2418,11 @@ int iobm_set_bloch(iobm_handle* h, double kappa_x, double kappa_y) {
     if (!std::isfinite(kappa_x) || !std::isfinite(kappa_y))
         return fail(h, IOBM_E_ARG, "non-finite Bloch vector");
     if ((kappa_x != 0.0 || kappa_y != 0.0) &&
-        (h->opt.use_precond != IOBM_PRECOND_FOURIER || h->opt.op_form != IOBM_OP_AUTO))
+        (h->opt.use_precond != IOBM_PRECOND_FOURIER || h->opt.op_form != IOBM_OP_AUTO ||
+         dense_sigma(h)))
         return fail(h, IOBM_E_UNSUPPORTED,
-                    "a nonzero Bloch vector needs the free-propagator preconditioner and the "
-                    "implicit operator form");
+                    "a nonzero Bloch vector needs the free-propagator preconditioner, the "
+                    "implicit operator form and the FFT self-energy");
     h->kappa[0] = kappa_x;
     h->kappa[1] = kappa_y;
     h->solved = false;

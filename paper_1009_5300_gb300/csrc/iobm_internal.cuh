@@ -265,6 +265,14 @@ template <typename T> cudaError_t launch_sigma_large(const SigmaArgs<T>& a, int 
 
 template <typename T> cudaError_t launch_stencil(const StencilArgs<T>& a, int nrhs, cudaStream_t s);
 template <typename T> cudaError_t launch_sigma(const SigmaArgs<T>& a, int nrhs, cudaStream_t s);
+// the self-energy as dense matrices (solver (b) of Sec. III; k_sigma_dense.cu)
+int dense_row_tiles(int nf, int nxy);
+cudaError_t build_sigma_dense(const double2* sigma, const double2* twx, const double2* twy, int nx,
+                              int ny, int nf, int ne, double2* kscratch, float2* d32, double2* d64,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_sigma_dense(const SigmaArgs<T>& a, const typename Cplx<T>::type* D, int nrhs,
+                               double2* part, int nslots_end, cudaStream_t s);
 template <typename T> size_t sigma_smem_bytes(int nx, int ny, int threads);
 template <typename T> cudaError_t launch_kb(const KbArgs<T>& a, int nrhs, cudaStream_t s);
 

@@ -59,6 +59,8 @@ def default_options(**kw) -> _lib.Options:
                  "eq10_fourier": _lib.IOBM_PRECOND_EQ10_FOURIER}[v]
         if k == "op_form" and isinstance(v, str):
             v = {"auto": _lib.IOBM_OP_AUTO, "explicit": _lib.IOBM_OP_EXPLICIT}[v]
+        if k == "sigma_form" and isinstance(v, str):
+            v = {"fft": _lib.IOBM_SIGMA_FFT, "dense": _lib.IOBM_SIGMA_DENSE}[v]
         setattr(o, k, v)
     return o
 
