@@ -259,6 +259,11 @@ bool large_plane_supported(int nx, int ny);
 template <typename T>
 cudaError_t launch_precond_large(const PrecondArgs<T>& a, int nrhs, cudaStream_t s,
                                  cudaError_t (*zsweeps)(const PrecondArgs<T>&, int, cudaStream_t));
+// update + forward transform + z-sweeps + inverse transform for 128 x 128 FP32 planes
+// (on-chip CTA-pair transforms; k_fft_large.cu); cudaErrorNotSupported otherwise
+cudaError_t launch_update_precond_128(const PrecondArgs<float>& a, int nrhs, cudaStream_t s, float2* x,
+                                      float2* r, float2* const* pbufs, const float2* q,
+                                      cudaError_t (*zsweeps)(const PrecondArgs<float>&, int, cudaStream_t));
 template <typename T> cudaError_t launch_sigma_large(const SigmaArgs<T>& a, int nrhs, cudaStream_t s);
 
 // ---- launchers (defined in the .cu files) ----------------------------------

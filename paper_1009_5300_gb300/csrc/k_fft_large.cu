@@ -15,9 +15,14 @@
 //    x^T (-Sigma x).
 // Partial sums go to one slot per (plane, row block), so every sum has a
 // fixed order.
+#include <cooperative_groups.h>
+
 #include "iobm_internal.cuh"
 #include "complex_ops.cuh"
+#include "fft_bfly.cuh"
 #include "fft_line.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace iobm {
 
@@ -183,6 +188,158 @@ __global__ void k_sigma_mix_large(const typename Cplx<T>::type* in, typename Cpl
     }
 }
 
+// ---------------------------------------------------------------------------
+// 128 x 128 planes (FP32) transformed on chip by a cluster of two CTAs: CTA
+// rank q holds rows 64 q .. 64 q + 63 (a 66 KB tile, pitch 129).  128 = 16 x 8:
+// pass 1 (rows, 16-point DFTs in registers straight from global memory), pass 2
+// (rows, radix 8 after the twiddles exp(-+2 pi i r j / 128), in place per
+// butterfly), then the columns: pass 3 (16-point DFTs of rows j + 8 m, half of them
+// in the peer CTA's tile, read through distributed shared memory; every input is
+// read before the cluster barrier, the outputs rows 16 j + a are local), pass 4
+// (radix 8 on rows j + 16 r of both tiles, outputs straight to global memory).  The
+// forward transform reads r and writes the spectrum; the inverse reads the spectrum
+// and writes z with the r^T z and |r|^2 partials (slots plane * 16 + rank).
+constexpr int kP128 = 128;
+constexpr int kP128Rows = 64;                  // rows per CTA
+constexpr int kP128Pitch = kP128 + 1;
+constexpr int kP128Threads = 512;
+constexpr size_t kP128Smem = sizeof(float2) * ((size_t)kP128Rows * kP128Pitch + kP128);
+
+// With UPD the forward transform first applies the COCG update x += alpha p,
+// r -= alpha q at the points its first pass reads (r_rw, x, the RHS's direction
+// buffer p0/p1, q), and transforms the updated r.
+struct Fft128Update {
+    float2* x;
+    float2* r;
+    const float2* p[2];
+    const float2* q;
+};
+
+template <bool INV, bool UPD>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kP128Threads, 2)
+    k_fft128_cluster(const PrecondArgs<float> a, int slot_per_plane, const Fft128Update u) {
+    using C = float2;
+    constexpr int N = kP128, R1 = 16, R2 = 8, PT = kP128Pitch;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int plane = blockIdx.x >> 1, rhs = blockIdx.y;
+    if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;   // uniform over the cluster
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[3 * (kP128Threads / 32)];
+    C* A = reinterpret_cast<C*>(smem_raw);             // [64][129]
+    C* tw = A + kP128Rows * PT;                        // [128]
+    const int tid = threadIdx.x;
+    for (int i = tid; i < N; i += kP128Threads) tw[i] = a.twx[i];
+    const long long off = (long long)rhs * a.npts + (long long)plane * (N * N);
+    const C* __restrict__ src = (INV ? a.spec : a.r) + off;
+    auto twiddled = [&](C v, int e) {
+        C w = tw[e];
+        if (INV) w.y = -w.y;
+        return cmul(v, w);
+    };
+    {   // pass 1: row (64 rank + yl), 16-point DFT of columns j + 8 m
+        const int j = tid % R2, yl = tid / R2;
+        C v[R1], o[R1];
+        const long long roff = (long long)(rank * kP128Rows + yl) * N + j;
+        if constexpr (UPD) {
+            const C al = from_d2<C>(a.state[rhs].alpha);
+            C* __restrict__ R = u.r + off + roff;
+            C* __restrict__ X = u.x + off + roff;
+            const C* __restrict__ P = ((a.state[rhs].pbuf & 1) ? u.p[1] : u.p[0]) + off + roff;
+            const C* __restrict__ Q = u.q + off + roff;
+#pragma unroll
+            for (int m = 0; m < R1; ++m) {
+                const int c = m * R2;
+                v[m] = csub(R[c], cmul(al, Q[c]));
+                R[c] = v[m];
+                X[c] = cfma(al, P[c], X[c]);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < R1; ++m) v[m] = src[roff + m * R2];
+        }
+        dft_reg<C, R1, INV>(v, o);
+#pragma unroll
+        for (int q = 0; q < R1; ++q) A[yl * PT + j * R1 + q] = o[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {   // pass 2: rows, radix 8, in place per butterfly
+        const int t = tid + k * kP128Threads;
+        const int yl = t % kP128Rows, j = t / kP128Rows;
+        C v[R2], o[R2];
+        v[0] = A[yl * PT + j];
+#pragma unroll
+        for (int r = 1; r < R2; ++r) v[r] = twiddled(A[yl * PT + j + r * R1], r * j);
+        dft_reg<C, R2, INV>(v, o);
+#pragma unroll
+        for (int q = 0; q < R2; ++q) A[yl * PT + j + q * R1] = o[q];
+    }
+    cluster.sync();   // the row transforms of both tiles are complete
+    C* peer = cluster.map_shared_rank(A, rank ^ 1);
+    const C* t0 = rank == 0 ? A : peer;   // rows 0-63
+    const C* t1 = rank == 0 ? peer : A;   // rows 64-127
+    auto at = [&](int row, int col) -> C {
+        return (row < kP128Rows ? t0 : t1)[(row & (kP128Rows - 1)) * PT + col];
+    };
+    C o3[R1];
+    const int x3 = tid % N, j3 = rank * 4 + tid / N;   // outputs rows 16 j3 .. 16 j3 + 15: local
+    {   // pass 3: columns, 16-point DFT of rows j3 + 8 m (m < 8 in tile 0, m >= 8 in tile 1)
+        C v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            v[m] = at(j3 + m * R2, x3);
+        }
+        dft_reg<C, R1, INV>(v, o3);
+    }
+    cluster.sync();   // every pass-3 read of both tiles is done
+#pragma unroll
+    for (int q = 0; q < R1; ++q) A[(j3 * R1 + q - rank * kP128Rows) * PT + x3] = o3[q];
+    cluster.sync();   // pass-3 outputs of both tiles visible
+    C* __restrict__ dst = (INV ? a.z : a.spec) + off;
+    const C* __restrict__ rin = a.r + off;
+    const bool dots = INV && a.dot_part != nullptr;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {   // pass 4: columns, radix 8 on rows j + 16 r, to global memory
+        const int t = tid + k * kP128Threads;
+        const int x = t % N, j = rank * 8 + t / N;
+        C v[R2], o[R2];
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+            const C u = at(j + r * R1, x);
+            v[r] = r ? twiddled(u, r * j) : u;
+        }
+        dft_reg<C, R2, INV>(v, o);
+#pragma unroll
+        for (int q = 0; q < R2; ++q) {
+            const int i = (j + q * R1) * N + x;
+            dst[i] = o[q];
+            if (dots) {
+                const C rv = rin[i];
+                d0 += rv.x * o[q].x - rv.y * o[q].y;
+                d1 += rv.x * o[q].y + rv.y * o[q].x;
+                d2 += rv.x * rv.x + rv.y * rv.y;
+            }
+        }
+    }
+    if (dots) {
+        double s0 = d0, s1 = d1, s2 = d2;
+        block_reduce_3(s0, s1, s2, red);
+        // the CTA's sum (held by thread 0) in slot `rank` of the plane; rank 0's threads
+        // 2 .. slot_per_plane - 1 write zeros to the plane's other slots
+        const long long plane_slot0 = (long long)rhs * a.slot_stride + (long long)plane * slot_per_plane;
+        if (tid == 0) {
+            a.dot_part[plane_slot0 + rank] = make_double2(s0, s1);
+            if (a.nrm_part) a.nrm_part[plane_slot0 + rank] = s2;
+        } else if (rank == 0 && tid >= 2 && tid < slot_per_plane) {
+            a.dot_part[plane_slot0 + tid] = make_double2(0.0, 0.0);
+            if (a.nrm_part) a.nrm_part[plane_slot0 + tid] = 0.0;
+        }
+    }
+    cluster.sync();   // the peer's tile is not released while this CTA may still read it
+}
+
 template <typename T>
 static size_t rows_smem(int nx) {
     return sizeof(typename Cplx<T>::type) * (size_t)(kLargeRows + kLargeThreads / 32) * nx;
@@ -190,6 +347,11 @@ static size_t rows_smem(int nx) {
 template <typename T>
 static size_t cols_smem(int ny) {
     return sizeof(typename Cplx<T>::type) * (size_t)ny * (kLargeCols + 1 + kLargeThreads / 32);
+}
+
+static void set128(const void* f, cudaError_t& e) {
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP128Smem);
 }
 
 cudaError_t fft_large_prepare() {
@@ -206,6 +368,9 @@ cudaError_t fft_large_prepare() {
     set((const void*)k_fft_rows_large<double, 2>);
     set((const void*)k_fft_cols_large<float>);
     set((const void*)k_fft_cols_large<double>);
+    set128((const void*)k_fft128_cluster<false, false>, e);
+    set128((const void*)k_fft128_cluster<false, true>, e);
+    set128((const void*)k_fft128_cluster<true, false>, e);
     return e;
 }
 
@@ -231,6 +396,18 @@ static cudaError_t launch_cols(typename Cplx<T>::type* data, long long rhs_strid
 template <typename T>
 cudaError_t launch_precond_large(const PrecondArgs<T>& a, int nrhs, cudaStream_t s,
                                  cudaError_t (*zsweeps)(const PrecondArgs<T>&, int, cudaStream_t)) {
+    if constexpr (sizeof(T) == 4) {
+        if (a.nx == kP128 && a.ny == kP128) {   // on-chip transforms by CTA pairs
+            const int sp = large_row_blocks(a.ny);
+            dim3 grid(2 * a.nz, nrhs);
+            k_fft128_cluster<false, false><<<grid, kP128Threads, kP128Smem, s>>>(a, sp, Fft128Update{});
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = zsweeps(a, nrhs, s);
+            if (e != cudaSuccess) return e;
+            k_fft128_cluster<true, false><<<grid, kP128Threads, kP128Smem, s>>>(a, sp, Fft128Update{});
+            return cudaGetLastError();
+        }
+    }
     LargeFftArgs<T> f{};
     f.src = a.r;
     f.dst = a.spec;
@@ -263,6 +440,24 @@ cudaError_t launch_precond_large(const PrecondArgs<T>& a, int nrhs, cudaStream_t
     g.slot_stride = a.slot_stride;
     g.slot_base = 0;
     return launch_rows<T, 1>(g, a.nz, nrhs, s);
+}
+
+// COCG update x += alpha p, r -= alpha q fused with the forward transform of r, the
+// z-sweeps and the inverse transform, for 128 x 128 FP32 planes (the on-chip CTA-pair
+// transforms); cudaErrorNotSupported for other planes
+cudaError_t launch_update_precond_128(const PrecondArgs<float>& a, int nrhs, cudaStream_t s, float2* x,
+                                      float2* r, float2* const* pbufs, const float2* q,
+                                      cudaError_t (*zsweeps)(const PrecondArgs<float>&, int, cudaStream_t)) {
+    if (a.nx != kP128 || a.ny != kP128) return cudaErrorNotSupported;
+    const int sp = large_row_blocks(a.ny);
+    dim3 grid(2 * a.nz, nrhs);
+    Fft128Update u{x, r, {pbufs[0], pbufs[1]}, q};
+    k_fft128_cluster<false, true><<<grid, kP128Threads, kP128Smem, s>>>(a, sp, u);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = zsweeps(a, nrhs, s);
+    if (e != cudaSuccess) return e;
+    k_fft128_cluster<true, false><<<grid, kP128Threads, kP128Smem, s>>>(a, sp, Fft128Update{});
+    return cudaGetLastError();
 }
 
 // self-energy through the two-pass transforms; scratch: 2 * nrhs * 2 nf * nxy

@@ -732,7 +732,11 @@ cudaError_t launch_update_precond_fourier(const PrecondArgs<T>& a, int nrhs, cud
                                           typename Cplx<T>::type* const* pbufs,
                                           const typename Cplx<T>::type* q,
                                           const cudaEvent_t* ev, int timed) {
-    if (!ct_size(a.nx, a.ny)) return cudaErrorNotSupported;
+    if (!ct_size(a.nx, a.ny)) {
+        if constexpr (sizeof(T) == 4)
+            return launch_update_precond_128(a, nrhs, s, x, r, pbufs, q, launch_zsolve<float>);
+        return cudaErrorNotSupported;
+    }
     // event record nodes when captured into a graph
     auto mark = [&](int stage, int k) {
         return (ev && timed == stage) ? cudaEventRecordWithFlags(ev[k], s, cudaEventRecordExternal)

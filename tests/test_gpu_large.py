@@ -45,6 +45,30 @@ def test_large_plane_preconditioner_inverts_free_operator(nx, ny, nz, nf):
     sol.close()
 
 
+@pytest.mark.parametrize("nf", [4, 2])
+def test_cluster_plane_transform_matches_oracle(nf):
+    # 128 x 128 FP32 planes: forward and inverse transforms on chip by CTA pairs (the
+    # column passes read the peer's rows through distributed shared memory); against the
+    # oracle's per-mode banded free propagator, with the FP64 two-pass path beside it
+    from oracle import iterative
+    from paper_1009_5300_gb300 import IOBMSolver
+    n, nz = 128, 11
+    jn = S.small_wire(nx=n, ny=n, nz=nz, h=0.3, natom=1, depth=0.7, width=1.0, rs=2.0, nf=nf,
+                      seed=13)
+    E = jn.e_fermi + 0.004
+    md = modes.mode_data(n, n, jn.hx, jn.hy, jn.hz, nf, E)
+    x = np.stack([S.random_field((nz, n, n), 71 + i) for i in range(3)])
+    ref = np.stack([iterative.free_propagator_modes(jn, E, md, xi) for xi in x])
+    scale = np.max(np.abs(ref))
+    sol = IOBMSolver.from_junction(jn, precision="fp64", use_precond="fourier")
+    xd = torch.from_numpy(x).cuda()
+    y64 = sol.apply_precond(xd, E).cpu().numpy()
+    assert np.max(np.abs(y64 - ref)) < 1e-11 * scale
+    y32 = sol.apply_precond(xd.to(torch.complex64), E).cpu().numpy()
+    assert np.max(np.abs(y32 - ref)) < 1e-4 * scale
+    sol.close()
+
+
 def check_solution(jn, E, sol, res, k):
     e = int(res.energy_index[k])
     c = int(res.channel[k])
