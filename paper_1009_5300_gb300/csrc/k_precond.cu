@@ -520,13 +520,13 @@ __global__ void __launch_bounds__(256, (CtOccupancy<T, N>::value)) k_ifft_dots_c
 // 64): the first row pass reads the spectrum from global memory, the last column
 // pass writes z, so a point crosses shared memory twice per axis; r at the outputs
 // of the thread's last pass is loaded with the spectrum, so its latency overlaps
-// the transform.  CTAs of N R2 threads (192 at N = 48), at most four per SM (FP32)
+// the transform.  CTAs of N R2 threads (192 at N = 48), at most five per SM (FP32)
 // or two (FP64), which the registers of the prefetched operands allow without spills.
 template <typename T, int N>
 struct Ct2Occupancy {
     static constexpr int kSmem = (int)sizeof(typename Cplx<T>::type) * (2 * N * (N + 1) + N) + 1024 + 192;
     static constexpr int kFit = (228 * 1024) / kSmem;
-    static constexpr int kCap = sizeof(typename Cplx<T>::type) == 8 ? 4 : 2;
+    static constexpr int kCap = sizeof(typename Cplx<T>::type) == 8 ? 5 : 2;
     static constexpr int value = kFit < 1 ? 1 : (kFit > kCap ? kCap : kFit);
 };
 
