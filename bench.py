@@ -57,12 +57,19 @@ ROOFLINE_STAGE = "update_fft"   # the kernel with the largest share of the bench
 # The explicit-form stencil (fused p = z + beta p_old, FD operator + V, p^T q): 32 B per
 # RHS-point (read z and p_old, write p and q) + 4 B per point (V) per launch; DRAM bytes
 # per RHS-point from an ncu capture, None until captured for the kernel as it stands.
-STENCIL_KERNEL = ("k_stencil_blk<48,4,4,4> (explicit form: fused p update + FD operator + "
-                  "p^T q; 4 rows per thread, bulk-copy staged)")
+# Kernel per stencil variant (iobm_set_tiling) on the 48-point rows of the bench wire.
+STENCIL_KERNELS = {
+    0: "k_stencil_blk<48,4,4,4> (explicit form: fused p update + FD operator + p^T q; "
+       "4 rows per thread, bulk-copy staged)",
+    1: "k_stencil_rows<float,4> (register-pipelined rows)",
+    3: "k_stencil_rows_tma<48,4> (one row per thread, bulk-copy staged)",
+    4: "k_stencil_ring<48,4> (explicit form: fused p update + FD operator + p^T q; "
+       "operand planes in a shared-memory ring, one thread per point, bulk-copy staged)",
+}
 STENCIL_BYTES_RHS_POINT = 32.0
-# ncu capture of one full-load launch on 56 RHS (bench.py --workload stencil --stencil-rhs 56):
-# 402.6 MB read + 289.0 MB written
-STENCIL_DRAM_BYTES_PER_RHS_POINT = (402582528 + 289049344) / (56 * 368640)
+# ncu captures of one full-load launch on 56 RHS (bench.py --workload stencil
+# --stencil-rhs 56 --stencil-variant V): DRAM bytes read + written per RHS-point
+STENCIL_DRAM_BYTES_PER_RHS_POINT = {0: (402582528 + 289049344) / (56 * 368640)}
 WORKLOAD = ("wire48: 6-atom wire, Gaussian wells (0.5 Ha, width 1.5 bohr, spacing 6.8 bohr) "
             "+ s/p KB projectors (radius 3 bohr), 48x48x160 grid, h=0.35 bohr, 9-point FD, "
             "r_s=3.28 jellium, 32 energies in [E_F-2eV, E_F+0.5eV], all open channels, "
@@ -385,13 +392,13 @@ def native_arm(args, rank, world, local_rank):
             fl_ms = sx2.time_operator(nrhs_int, reps=20)
             sx2.close()
             fl_ach = (STENCIL_BYTES_RHS_POINT * npts * nrhs_int + 4.0 * npts) / (fl_ms / 1e3) / 1e9
+            dram = STENCIL_DRAM_BYTES_PER_RHS_POINT.get(var)
             extra["stencil_roofline"] = {
-                "kernel": STENCIL_KERNEL,
+                "kernel": STENCIL_KERNELS.get(var, f"stencil variant {var}"),
                 "bound": "hbm", "achieved": fl_ach, "peak": peak, "unit": "GB/s",
                 "frac": fl_ach / peak, "avg_launch_ms": fl_ms,
                 "alg_bytes_per_launch": STENCIL_BYTES_RHS_POINT * npts * nrhs_int + 4.0 * npts,
-                "traffic": STENCIL_DRAM_BYTES_PER_RHS_POINT * npts * nrhs_int
-                           if STENCIL_DRAM_BYTES_PER_RHS_POINT else None,
+                "traffic": dram * npts * nrhs_int if dram else None,
                 "sample": f"full load: {nrhs_int} RHS of the bench wire all active, 20 timed "
                           f"launches (iobm_time_operator), autotuned tiling z-chunk {zc}, "
                           f"variant {var}",
@@ -785,7 +792,7 @@ def ablation_arm(args, rank, world, local_rank):
 def stencil_arm(args, rank, world, local_rank):
     """The explicit-form FD stencil kernel alone at full load: --stencil-rhs RHS of the
     48x48x160 wire, every RHS active, --steps timed launches after --warmup (iobm_time_operator),
-    the handle's default tiling (z-chunk 32, the fastest kernel for the shape)."""
+    tiling --stencil-variant / --stencil-zchunk (variant -1: the autotuner's choice)."""
     import torch
     import iobm_synth as S
     from paper_1009_5300_gb300 import IOBMSolver, build_library
@@ -796,6 +803,11 @@ def stencil_arm(args, rank, world, local_rank):
     jn = S.wire48()
     sol = IOBMSolver.from_junction(jn, precision="mixed", device=dev, op_form="explicit")
     nrhs = args.stencil_rhs
+    if args.stencil_variant < 0:
+        zc, var = sol.autotune(nrhs)
+    else:
+        zc, var = args.stencil_zchunk, args.stencil_variant
+        sol.set_tiling(zc, var)
     sol.time_operator(nrhs, reps=max(1, args.warmup))
     ms = sol.time_operator(nrhs, reps=max(1, args.steps))
     sol.close()
@@ -803,7 +815,8 @@ def stencil_arm(args, rank, world, local_rank):
     alg = STENCIL_BYTES_RHS_POINT * npts * nrhs + 4.0 * npts
     peak, kind = load_peaks()
     if rank == 0:
-        print(json.dumps({"workload": "stencil", "kernel": STENCIL_KERNEL, "nrhs": nrhs,
+        print(json.dumps({"workload": "stencil", "kernel": STENCIL_KERNELS.get(var, str(var)),
+                          "zchunk": zc, "variant": var, "nrhs": nrhs,
                           "avg_launch_ms": ms, "achieved_gbs": alg / (ms / 1e3) / 1e9,
                           "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": kind}), flush=True)
     return 0
@@ -827,6 +840,10 @@ def main():
                     help="COCG iterations per captured graph (library default)")
     ap.add_argument("--stencil-rhs", type=int, default=228,
                     help="RHS of the stencil-only measurement (--workload stencil)")
+    ap.add_argument("--stencil-variant", type=int, default=-1,
+                    help="stencil variant of --workload stencil (-1: autotuned)")
+    ap.add_argument("--stencil-zchunk", type=int, default=32,
+                    help="z-planes per CTA of --workload stencil with an explicit variant")
     ap.add_argument("--workload", choices=["wire48", "batch", "wire128", "stencil", "ablation"],
                     default="wire48",
                     help="wire48: the 48x48x160 wire (default line); batch: the uneven "

@@ -272,8 +272,8 @@ int iobm_solve_batch(int n, iobm_handle* const* handles, const double* const* E,
 
 /* Stencil tiling autotuner: times the fused COCG stencil (p = z + beta p_old,
  * A p, p^T A p) on nrhs RHS of this handle's grid for z-chunks of 16, 32 and 64
- * planes per CTA and, in the mixed solver, for both FP32 row kernels (bulk-copy
- * staged or register-pipelined), keeps the fastest for the handle's later solves
+ * planes per CTA and, in the mixed solver, for the FP32 row kernels (variants 0, 1,
+ * 3, 4 of iobm_set_tiling), keeps the fastest for the handle's later solves
  * and returns it in *zchunk / *variant (either may be NULL).  Binds the workspace
  * for nrhs RHS (the attached one must be large enough).  The choice changes only
  * the order of the partial sums of the dot products. */
@@ -281,7 +281,9 @@ int iobm_autotune(iobm_handle* h, int nrhs, int* zchunk, int* variant);
 
 /* Set the stencil tiling explicitly: zchunk >= 16 z-planes per CTA; variant 0 =
  * the fastest kernel for the shape, 1 = the register-pipelined row kernel, 3 = the
- * bulk-copy row kernel with one row per thread (FP32 rows of 12 .. 64 points; 0 takes
+ * bulk-copy row kernel with one row per thread, 4 = the bulk-copy kernel whose operand
+ * planes k - N_f .. k + N_f sit in a shared-memory ring (one thread per point of a
+ * 16-row tile; N_f 1 or 4, ny a multiple of 16) (FP32 rows of 12 .. 64 points; 0 takes
  * the bulk-copy kernel with several rows per thread where the shape allows). */
 int iobm_set_tiling(iobm_handle* h, int zchunk, int variant);
 

@@ -1685,9 +1685,9 @@ int autotune_stencil(iobm_handle* h, int nrhs, int* zchunk_out, int* variant_out
     a.slot_stride = h->slot_stride;
     const int zcands[3] = {kZChunkMin, 32, 64};
     // FP32: the fastest kernel for the shape, the register-pipelined rows, the one-row
-    // bulk-copy rows; FP64: one kernel
-    const int vcands[3] = {0, 1, 3};
-    const int nvar = std::is_same<T, float>::value ? 3 : 1;
+    // bulk-copy rows, the shared-memory plane ring; FP64: one kernel
+    const int vcands[4] = {0, 1, 3, 4};
+    const int nvar = std::is_same<T, float>::value ? 4 : 1;
     float best = -1.f;
     int best_z = h->zchunk, best_v = h->stencil_variant;
     for (int zi = 0; zi < 3; ++zi) {
@@ -2029,7 +2029,7 @@ int iobm_autotune(iobm_handle* h, int nrhs, int* zchunk, int* variant) {
 
 int iobm_set_tiling(iobm_handle* h, int zchunk, int variant) {
     if (!h) return IOBM_E_ARG;
-    if (zchunk < kZChunkMin || (variant != 0 && variant != 1 && variant != 3))
+    if (zchunk < kZChunkMin || (variant != 0 && variant != 1 && variant != 3 && variant != 4))
         return fail(h, IOBM_E_ARG, "z-chunk below the minimum or unknown stencil variant");
     h->zchunk = zchunk;
     h->stencil_variant = variant;

@@ -121,7 +121,8 @@ struct StencilArgs {
     int* err;              // set to a nonzero code when a bounded wait gives up (or nullptr)
     int variant;           // 0: the fastest kernel for the shape, 1: the register-pipelined row
                            // kernel, 2 (FP64 data): double-float arithmetic, 3: the bulk-copy
-                           // row kernel with one row per thread (FP32)
+                           // row kernel with one row per thread (FP32), 4: the bulk-copy
+                           // kernel with a shared-memory ring of operand planes (FP32)
     float2 dfx[kMaxNf + 1];  // variant 2: cx[n], cy[n], cz[n] as FP32 pairs (hi, lo)
     float2 dfy[kMaxNf + 1];
     float2 dfz[kMaxNf + 1];

@@ -965,6 +965,230 @@ __global__ void __launch_bounds__(NX * TY, MINB) k_stencil_blk(const StencilArgs
     }
 }
 
+// Ring kernel (variant 4): the operand planes k - N_f .. k + N_f of a 16-row tile live
+// in a ring of 2 N_f + 2 shared-memory slots (combined p = z + beta p_old, N_f halo rows,
+// periodic pad columns), so the z taps come from shared memory like the x and y taps and
+// no register z-queue is needed: one thread per tile point (NX x 16 threads), a few
+// dozen registers.  Fill step f: wait for the bulk copies of plane f (all tile rows of
+// z and p_old, periodic in y), fill its ring slot and write p for the own rows, one CTA
+// barrier, issue the copies of plane f + 2, and compute output plane f - N_f from the
+// ring.  A slot written at step f + 1 held plane f + 1 - (2 N_f + 2), which only step
+// f - 1's outputs read; every thread finished those before the barrier of step f.
+template <int NX, int NF>
+struct RingTma {
+    static constexpr int RY = 16;                // own rows of a CTA
+    static constexpr int SR = RY + 2 * NF;       // rows of a slot / stage
+    static constexpr int TP = NX + 2 * NF;       // slot pitch (pad columns)
+    static constexpr int TILE = SR * TP;
+    static constexpr int NR = 2 * NF + 2;        // ring slots
+    static constexpr int SLAB = SR * NX;
+    static constexpr int D = 2;                  // stages (copies issued D planes ahead)
+    static constexpr int STAGE = 2 * SLAB;
+    static constexpr int NT = NX * RY;
+    static constexpr size_t smem = 128 + sizeof(float2) * ((size_t)NR * TILE + (size_t)D * STAGE);
+};
+
+template <int NX, int NF>
+__global__ void __launch_bounds__(NX * 16) k_stencil_ring(const StencilArgs<float> a) {
+    using T = float;
+    using C = float2;
+    using L = RingTma<NX, NF>;
+    constexpr int RY = L::RY, SR = L::SR, TP = L::TP, TILE = L::TILE, NR = L::NR;
+    constexpr int SLAB = L::SLAB, D = L::D, STAGE = L::STAGE, NT = L::NT;
+    extern __shared__ __align__(128) unsigned char smem_ring[];
+    __shared__ double red[3 * 32];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_ring);   // [D + 1]
+
+    const int rhs = blockIdx.z;
+    int st = ST_ACTIVE;
+    C beta = czero<C>();
+    bool first_dir = false;
+    if (a.state) {
+        st = a.state[rhs].status;
+        if (a.fused_p && !a.state[rhs].first) beta = from_d2<C>(a.state[rhs].beta);
+        else if (a.fused_p) first_dir = true;
+    }
+    if (!((1 << st) & a.mask)) return;
+
+    const int ny = a.ny, nz = a.nz;
+    const int tid = threadIdx.x;
+    const int x = tid % NX, r = tid / NX;    // own point: row r of the tile's RY rows
+    const int ty0 = blockIdx.x * RY;
+    const int k0 = blockIdx.y * a.zchunk;
+    const int k1 = min(k0 + a.zchunk, nz);
+    const long long plane = (long long)NX * ny;
+    const long long base = (long long)rhs * a.npts;
+    const C* __restrict__ X = a.x + base;
+    const int pb = (a.fused_p && a.state) ? (a.state[rhs].pbuf & 1) : 0;
+    const C* __restrict__ PO = (a.fused_p && !first_dir) ? a.pbufs[pb] + base : nullptr;
+    C* __restrict__ PN = a.fused_p ? a.pbufs[1 - pb] + base : nullptr;
+    const T* __restrict__ Vg = a.V;
+    const T ed = a.ediag ? (T)a.ediag[a.rhs_energy ? a.rhs_energy[rhs] : 0] : (T)0;
+    const T cen = a.c0 + ed;
+
+    C* ring = reinterpret_cast<C*>(smem_ring + 128);   // [NR][SR][TP]
+    C* stages = ring + NR * TILE;                        // [D]: z [SLAB], p_old [SLAB]
+    if (tid == 0) {
+        for (int q = 0; q <= D; ++q) mbar_init(&bar[q], 1);   // bar[D]: no copy completes it
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const long long wlim = a.wait_cycles > 0 ? a.wait_cycles : kWaitCycles;
+
+    // copies of plane f into stage q (thread 0): tile rows ty0 - NF .. ty0 + RY + NF - 1,
+    // periodic in y, one copy per contiguous run of rows; planes outside the grid
+    // complete the stage's phase without a copy
+    constexpr uint32_t row_bytes = NX * sizeof(C);
+    auto issue = [&](int f, int q) {
+        if (f < 0 || f >= nz) {
+            mbar_arrive_expect_tx(&bar[q], 0u);
+            return;
+        }
+        mbar_arrive_expect_tx(&bar[q], (PO ? 2u : 1u) * SR * row_bytes);
+        C* sz = stages + q * STAGE;
+        C* sp = sz + SLAB;
+        fence_proxy_async_smem();
+        int srow = 0;
+        while (srow < SR) {
+            int gy = (ty0 - NF + srow) % ny;
+            if (gy < 0) gy += ny;
+            const int n = min(SR - srow, ny - gy);
+            const long long src = (long long)f * plane + (long long)gy * NX;
+            bulk_g2s(sz + srow * NX, X + src, (uint32_t)n * row_bytes, &bar[q]);
+            if (PO) bulk_g2s(sp + srow * NX, PO + src, (uint32_t)n * row_bytes, &bar[q]);
+            srow += n;
+        }
+    };
+    // ring slot of fill step j = f - f0 is j mod NR: the plane loop below is unrolled by
+    // NR, so every slot index is a compile-time constant
+    const int f0 = k0 - NF, f1 = k1 + NF;
+    // ring slot u from stage q (zeros outside the grid), p of the own rows
+    auto fill = [&](int f, int u, int q) {
+        C* slot = ring + u * TILE;
+        const bool in = f >= 0 && f < nz;
+        const bool own_p = PN && f >= k0 && f < k1;
+        const C* sz = stages + q * STAGE;
+        const C* sp = sz + SLAB;
+        C* pn = own_p ? PN + (long long)f * plane + (long long)ty0 * NX : nullptr;
+#pragma unroll
+        for (int it = 0; it < (SR * NX + NT - 1) / NT; ++it) {
+            const int i = tid + it * NT;
+            if ((SR * NX) % NT == 0 || i < SR * NX) {
+                const int row = i / NX, col = i - row * NX;
+                C v = czero<C>();
+                if (in) {
+                    v = sz[i];
+                    if (PO) v = cfma(beta, sp[i], v);
+                }
+                C* trow = slot + row * TP;
+                trow[NF + col] = v;
+                if (col < NF) trow[NF + NX + col] = v;
+                if (col >= NX - NF) trow[col - (NX - NF)] = v;
+                if (own_p && row >= NF && row < NF + RY) pn[i - NF * NX] = v;
+            }
+        }
+    };
+    // a CTA barrier that also agrees on a failed wait; on failure the CTA drains the
+    // copies it still has in flight (fill steps fw .. fw + D - 1) and the kernel returns
+    auto barrier_ok = [&](bool ok, int fw) -> bool {
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                if (a.err) atomicExch(a.err, ERR_STAGE_TIMEOUT);
+                for (int j = fw; j < fw + D && j < f1; ++j)
+                    mbar_wait_bounded(&bar[(j - f0) % D], ((j - f0) / D) & 1);
+            }
+            __syncthreads();
+            return false;
+        }
+        return true;
+    };
+
+    if (tid == 0)
+        for (int j = 0; j < D && f0 + j < f1; ++j) issue(f0 + j, j);
+    float dre = 0.f, dim = 0.f, nrm = 0.f;
+    const int own = (NF + r) * TP + NF + x;
+    const long long own_g = (long long)(ty0 + r) * NX + x;
+    C* __restrict__ Yk = a.y + base + (long long)k0 * plane + own_g;
+    const T* __restrict__ Vk = Vg ? Vg + (long long)k0 * plane + own_g : nullptr;
+    bool failed = false;
+    for (int f = f0; f < f1 && !failed; f += NR) {
+#pragma unroll
+        for (int u = 0; u < NR; ++u) {
+            const int fu = f + u;
+            if (fu >= f1) break;
+            const int j = fu - f0;   // = (f - f0) + u with (f - f0) a multiple of NR
+            constexpr int Dq = D;
+            const int q = (NR % Dq == 0) ? (u % Dq) : (j % Dq);
+            bool ok = mbar_wait_bounded(&bar[q], (j / Dq) & 1, wlim);
+            if (j == 0 && a.wait_inject && tid == 0) ok = ok && mbar_wait_bounded(&bar[D], 0, wlim);
+            fill(fu, u, q);
+            if (!barrier_ok(ok, fu)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0 && fu + D < f1) issue(fu + D, q);
+            if (fu - NF < k0) continue;
+            // output plane k = fu - N_f in slot (u - N_f) mod NR; every tap from the ring
+            const C* c = ring + ((u - NF + NR) % NR) * TILE + own;
+            const C x0 = *c;
+            const T d = cen + a.vsign * (Vk ? *Vk : (T)0);
+            C acc;
+            if (a.iso) {
+                const C x2 = p2add(x0, x0);
+                C az = p2mul(x0, make_float2(d, d));
+                C ax = make_float2(0.f, 0.f), ay = ax;
+#pragma unroll
+                for (int n = 1; n <= NF; ++n) {
+                    const C cc = make_float2(a.cz[n], a.cz[n]);
+                    const C zm = ring[((u - NF - n + 2 * NR) % NR) * TILE + own];
+                    const C zp = ring[((u - NF + n + NR) % NR) * TILE + own];
+                    az = p2fma(cc, p2sub(p2add(zm, zp), x2), az);
+                    ax = p2fma(cc, p2sub(p2add(c[-n], c[n]), x2), ax);
+                    ay = p2fma(cc, p2sub(p2add(c[-n * TP], c[n * TP]), x2), ay);
+                }
+                acc = p2add(az, p2add(ax, ay));
+            } else {
+                const C x2 = cadd(x0, x0);
+                C az = cscale(x0, d);
+                C ax = make_float2(0.f, 0.f), ay = ax;
+#pragma unroll
+                for (int n = 1; n <= NF; ++n) {
+                    const C zm = ring[((u - NF - n + 2 * NR) % NR) * TILE + own];
+                    const C zp = ring[((u - NF + n + NR) % NR) * TILE + own];
+                    az = caxpy(a.cz[n], csub(cadd(zm, zp), x2), az);
+                    ax = caxpy(a.cx[n], csub(cadd(c[-n], c[n]), x2), ax);
+                    ay = caxpy(a.cy[n], csub(cadd(c[-n * TP], c[n * TP]), x2), ay);
+                }
+                acc = cadd(az, cadd(ax, ay));
+            }
+            *Yk = acc;
+            Yk += plane;
+            if (Vk) Vk += plane;
+            if (a.dot_mode) {
+                dre = fmaf(x0.x, acc.x, fmaf(-x0.y, acc.y, dre));
+                dim = fmaf(x0.x, acc.y, fmaf(x0.y, acc.x, dim));
+                nrm = fmaf(x0.x, x0.x, fmaf(x0.y, x0.y, nrm));
+            }
+        }
+    }
+    if (failed) return;
+
+    if (a.dot_mode) {
+        // partial slots are numbered per kRowTY-row tile (stencil_slots): the CTA's sum
+        // goes to the first of its RY / kRowTY slots, zeros to the others
+        static_assert(RY % kRowTY == 0, "RY spans whole row tiles");
+        double r0d = dre, r1 = dim, r2 = nrm;
+        block_reduce_3(r0d, r1, r2, red);
+        if (tid < RY / kRowTY) {
+            const int tiles_y = ny / kRowTY;
+            const int slot = a.slot_base + blockIdx.x * (RY / kRowTY) + tid + blockIdx.y * tiles_y;
+            a.dot_part[(long long)rhs * a.slot_stride + slot] =
+                tid == 0 ? make_double2(r0d, r1) : make_double2(0.0, 0.0);
+            if (a.nrm_part) a.nrm_part[(long long)rhs * a.slot_stride + slot] = tid == 0 ? r2 : 0.0;
+        }
+    }
+}
+
 static bool use_rows(int nx, int nf) { return nx >= nf && nx >= 4 && nx <= 64; }
 
 // bulk-copy variant: FP32, rows of a multiple of 16 bytes, 16-byte aligned operands
@@ -974,7 +1198,7 @@ static bool tma_width(int nx) {
 
 template <typename T>
 static bool use_rows_tma(const StencilArgs<T>& a) {
-    if (sizeof(T) != 4 || (a.variant != 0 && a.variant != 3) || !use_rows(a.nx, a.nf) ||
+    if (sizeof(T) != 4 || (a.variant != 0 && a.variant != 3 && a.variant != 4) || !use_rows(a.nx, a.nf) ||
         !tma_width(a.nx))
         return false;
     uintptr_t al = reinterpret_cast<uintptr_t>(a.x);
@@ -1042,6 +1266,30 @@ static cudaError_t launch_blk_nf(const StencilArgs<float>& a, int nrhs, cudaStre
     return cudaGetLastError();
 }
 
+template <int NX, int NF>
+static cudaError_t prepare_ring() {
+    return cudaFuncSetAttribute(k_stencil_ring<NX, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RingTma<NX, NF>::smem);
+}
+
+// the ring kernel: FP32 bulk-copy rows, N_f 1 or 4, whole 16-row tiles in y
+template <typename T>
+static bool use_ring(const StencilArgs<T>& a) {
+    return a.variant == 4 && (a.nf == 1 || a.nf == 4) && a.ny % 16 == 0 && a.nx >= 2 * a.nf;
+}
+
+template <int NX>
+static cudaError_t launch_ring_nf(const StencilArgs<float>& a, int nrhs, cudaStream_t s) {
+    const int nzc = (a.nz + a.zchunk - 1) / a.zchunk;
+    dim3 grid(a.ny / 16, nzc, nrhs);
+    switch (a.nf) {
+        case 1: k_stencil_ring<NX, 1><<<grid, NX * 16, RingTma<NX, 1>::smem, s>>>(a); break;
+        case 4: k_stencil_ring<NX, 4><<<grid, NX * 16, RingTma<NX, 4>::smem, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int NX>
 static cudaError_t prepare_tma_nf() {
     cudaError_t e = prepare_tma<NX, 1>();
@@ -1050,6 +1298,8 @@ static cudaError_t prepare_tma_nf() {
     if (e == cudaSuccess) e = prepare_tma<NX, 4>();
     if (e == cudaSuccess && NX >= 2) e = prepare_blk<NX, 1>();
     if (e == cudaSuccess && NX >= 8) e = prepare_blk<NX, 4>();
+    if (e == cudaSuccess && NX >= 2) e = prepare_ring<NX, 1>();
+    if (e == cudaSuccess && NX >= 8) e = prepare_ring<NX, 4>();
     return e;
 }
 
@@ -1098,6 +1348,17 @@ cudaError_t launch_stencil(const StencilArgs<T>& a0, int nrhs, cudaStream_t s) {
         const int threads = a.nx * kRowTY;
         using C = typename Cplx<T>::type;
         if constexpr (sizeof(T) == 4) {
+            if (use_rows_tma(a) && use_ring(a)) {
+                switch (a.nx) {
+                    case 12: return launch_ring_nf<12>(a, nrhs, s);
+                    case 16: return launch_ring_nf<16>(a, nrhs, s);
+                    case 24: return launch_ring_nf<24>(a, nrhs, s);
+                    case 32: return launch_ring_nf<32>(a, nrhs, s);
+                    case 48: return launch_ring_nf<48>(a, nrhs, s);
+                    case 64: return launch_ring_nf<64>(a, nrhs, s);
+                    default: return cudaErrorInvalidValue;
+                }
+            }
             if (use_rows_tma(a) && use_blk(a)) {
                 switch (a.nx) {
                     case 12: return launch_blk_nf<12>(a, nrhs, s);

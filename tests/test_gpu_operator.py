@@ -145,6 +145,31 @@ def test_fourier_precond_matches_oracle(nx, ny, nz, nf, kb):
     sol.close()
 
 
+@pytest.mark.parametrize("nx,ny,nz,nf,kb", [(24, 32, 37, 4, True), (64, 16, 29, 1, False),
+                                             (12, 48, 21, 4, False), (48, 48, 40, 4, True),
+                                             (16, 16, 12, 4, False)])
+def test_ring_stencil_matches_oracle(nx, ny, nz, nf, kb):
+    # variant 4: operand planes in a shared-memory ring (z-chunks of 16 and 32: ragged
+    # last chunks, several tiles in y, the y-wrap split into up to three copies when the
+    # tile with its halo is taller than the plane)
+    from paper_1009_5300_gb300 import IOBMSolver
+    jn = make(nx, ny, nz, nf, kb)
+    E = jn.e_fermi + 0.013
+    md = modes.mode_data(nx, ny, jn.hx, jn.hy, jn.hz, nf, E)
+    x = np.stack([S.random_field((nz, ny, nx), 500 + i) for i in range(3)])
+    ref = np.stack([operator.apply_A(jn, E, md, xi) for xi in x])
+    scale = np.max(np.abs(ref))
+    xd = torch.from_numpy(x).cuda().to(torch.complex64)
+    sol = IOBMSolver.from_junction(jn, precision="mixed")
+    y0 = sol.apply(E, xd).cpu().numpy()
+    for zc in (16, 32):
+        sol.set_tiling(zc, 4)
+        y4 = sol.apply(E, xd).cpu().numpy()
+        assert np.max(np.abs(y4 - ref)) < 2e-5 * scale
+        assert np.max(np.abs(y4 - y0)) < 2e-6 * scale
+    sol.close()
+
+
 @pytest.mark.parametrize("n,nz,nf", [(32, 14, 2), (48, 12, 4), (64, 10, 3)])
 def test_two_factor_inverse_transform_matches_oracle(n, nz, nf):
     # square planes of 32, 48, 64 points take the two-factor inverse transform

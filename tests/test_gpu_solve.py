@@ -79,16 +79,17 @@ def test_multichannel_kb(nf, precision, precond):
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_explicit_form_on_row_blocked_stencil(precision):
-    # a 12 x 16 plane takes the row-blocked FP32 stencil (fused p update, operator and
-    # p^T A p over 16-row tiles) in every explicit-form iteration: oracle T, R, G
+    # a 12 x 16 plane takes the row-blocked FP32 stencil (variant 0: fused p update,
+    # operator and p^T A p over 16-row tiles) or the plane-ring kernel (variant 4) in
+    # every explicit-form iteration: oracle T, R, G
     from paper_1009_5300_gb300 import IOBMSolver
     jn = S.small_wire(nx=12, ny=16, nz=30, h=0.5, natom=2, spacing=3.4, depth=0.7, width=0.9,
                       rs=1.6, kb_kinds=S.SP, nf=4, seed=78)
     E = jn.e_fermi
     ref = transport.solve(jn, E)
-    for z in (16, 32, 64):
+    for z, var in ((16, 0), (32, 0), (64, 0), (16, 4), (32, 4)):
         sol = IOBMSolver.from_junction(jn, precision=precision, op_form="explicit")
-        sol.set_tiling(z, 0)
+        sol.set_tiling(z, var)
         res = sol.solve([E])
         assert ref.n_open >= 3
         compare(res, ref)
