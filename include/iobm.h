@@ -150,9 +150,11 @@ typedef struct {
  * op_form: IOBM_OP_AUTO or IOBM_OP_EXPLICIT (above).
  * fp64_modes: in IOBM_MIXED with IOBM_PRECOND_FOURIER, the number of lateral modes
  * per energy nearest their channel threshold (smallest |E - eps_perp|) whose
- * preconditioner z-sweeps run in FP64 with FP64 factors inside the FP32 iterations:
- * their banded z-systems are the worst conditioned, and FP32 sweeps there cost
- * iterations; 0 sweeps every mode in FP32.
+ * preconditioner z-sweeps run in double-float arithmetic with FP64 factors inside the
+ * FP32 iterations: their banded z-systems are the worst conditioned, and FP32 sweeps
+ * there cost iterations; 0 sweeps every mode in FP32; -1 (default) takes
+ * max(16, N_xy / 128) (16 up to 48 x 48 planes, 128 at 128 x 128, where the larger
+ * plane has more modes near threshold).
  * sigma_form: IOBM_SIGMA_FFT or IOBM_SIGMA_DENSE (above). */
 typedef struct {
     double alpha;
@@ -182,7 +184,8 @@ typedef struct {
 
 /* Fill opts with the defaults: alpha 1.8, use_precond IOBM_PRECOND_FOURIER, tol 1e-8,
  * max_iter 20000, precision IOBM_MIXED, refine_delta 0.01, chunk 32,
- * max_iter_mixed 1000, op_form IOBM_OP_AUTO, fp64_modes 16, sigma_form IOBM_SIGMA_FFT. */
+ * max_iter_mixed 1000, op_form IOBM_OP_AUTO, fp64_modes -1 (automatic), sigma_form
+ * IOBM_SIGMA_FFT. */
 void iobm_default_options(iobm_options* opts);
 
 /* Create a solver for one junction: the truncated Hamiltonian H_T of the

@@ -1198,9 +1198,10 @@ int upload_solve_tables(iobm_handle* h) {
     }
     // per energy slot the fp64_modes lateral modes nearest their threshold (smallest
     // |E - eps_perp|, ties by bin): FP64 z-sweeps in the FP32 iterations
+    const int want = h->opt.fp64_modes >= 0 ? h->opt.fp64_modes : std::max(16, h->nxy / 128);
     h->zf_k = (h->opt.precision == IOBM_MIXED && fourier_precond(h) &&
                h->opt.use_precond == IOBM_PRECOND_FOURIER)
-                  ? std::min(h->opt.fp64_modes, h->nxy) : 0;
+                  ? std::min(want, h->nxy) : 0;
     if (h->zf_k > 0) {
         const int K = h->zf_k, nxy = h->nxy;
         std::vector<unsigned char> flag((size_t)nE * nxy, 0);
@@ -1779,7 +1780,7 @@ void iobm_default_options(iobm_options* o) {
     o->chunk = 32;
     o->max_iter_mixed = 1000;
     o->op_form = IOBM_OP_AUTO;
-    o->fp64_modes = 16;
+    o->fp64_modes = -1;
     o->sigma_form = IOBM_SIGMA_FFT;
 }
 
@@ -1832,7 +1833,7 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
         (h->opt.precision != IOBM_FP64 && h->opt.precision != IOBM_MIXED) || !(h->opt.alpha > 0) ||
         h->opt.use_precond < IOBM_PRECOND_NONE || h->opt.use_precond > IOBM_PRECOND_EQ10_FOURIER ||
         (h->opt.op_form != IOBM_OP_AUTO && h->opt.op_form != IOBM_OP_EXPLICIT) ||
-        h->opt.fp64_modes < 0 ||
+        h->opt.fp64_modes < -1 ||
         (h->opt.sigma_form != IOBM_SIGMA_FFT && h->opt.sigma_form != IOBM_SIGMA_DENSE))
         return bad(IOBM_E_ARG, "invalid solver options");
     h->nxy = g.nx * g.ny;

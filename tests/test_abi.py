@@ -52,5 +52,5 @@ def test_default_options_and_binding_layout(lib):
     lib.iobm_default_options(C.byref(o))
     assert (o.alpha, o.use_precond, o.tol, o.max_iter) == (1.8, _lib.IOBM_PRECOND_FOURIER, 1e-8, 20000)
     assert (o.precision, o.refine_delta, o.chunk) == (_lib.IOBM_MIXED, 0.01, 32)
-    assert (o.max_iter_mixed, o.op_form, o.fp64_modes) == (1000, _lib.IOBM_OP_AUTO, 16)
+    assert (o.max_iter_mixed, o.op_form, o.fp64_modes) == (1000, _lib.IOBM_OP_AUTO, -1)
     assert o.sigma_form == _lib.IOBM_SIGMA_FFT
