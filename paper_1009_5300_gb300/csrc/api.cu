@@ -57,6 +57,8 @@ constexpr int kZChunkMin = 16;       // smallest candidate: sizes the per-CTA pa
 // FP64 residual replacements run after every kReplaceEvery-th captured iteration
 // (RHS that became PENDING wait at most kReplaceEvery - 1 iterations)
 constexpr int kReplaceEvery = 2;
+// z-segments (lanes) per mode of the double-float sweeps
+constexpr int kZfSegments = 8;
 
 }  // namespace
 
@@ -112,6 +114,8 @@ struct iobm_handle {
     DevBuf esc_rhs_sign;                 // the FP64 continuation's signs
     DevBuf zflag, zf_bins, zf_pc;        // FP64 z-sweep modes of the solve's energy slots
     int zf_k = 0;
+    DevBuf zf_tab, zf_scr;               // their segment responses and scratch
+    int zf_S = 1, zf_L = 0, zf_Lt = 0;
     long long wait_cycles = 0;           // bounded-wait limit of the bulk-copy kernels (0: default)
     int wait_inject = 0;                 // 1: their CTAs also wait on a barrier no copy completes
     int zchunk = kZChunkDefault;         // stencil z-planes per CTA (autotuned)
@@ -456,6 +460,11 @@ void set_fp64_modes(const iobm_handle* h, PrecondArgs<T>& f) {
     f.zf_bins = h->zf_bins.as<int>();
     f.zf_pc = h->zf_pc.as<double2>();
     f.zf_k = h->zf_k;
+    f.zf_tab = h->zf_tab.as<float4>();
+    f.zf_scr = h->zf_scr.as<float4>();
+    f.zf_S = h->zf_S;
+    f.zf_L = h->zf_L;
+    f.zf_Lt = h->zf_Lt;
     // the side stream joins the capture of the main graph when it forks there, so the
     // body of a conditional node (a capture of its own) takes the single-launch sweeps
     if (!h->in_cond_body) {
@@ -1228,6 +1237,49 @@ int upload_solve_tables(iobm_handle* h) {
         CK(upload(h->zflag, flag, h->stream));
         CK(upload(h->zf_bins, bins, h->stream));
         CK(upload(h->zf_pc, zpc, h->stream));
+        // z-segments of the double-float sweeps: at most kZfSegments, each >= nf planes,
+        // the last one absorbing the remainder (< L + nf planes)
+        const int NF = h->nf, m = h->g.nz - NF;
+        int S = std::max(1, std::min(kZfSegments, m / NF));
+        int L = (m + S - 1) / S;
+        while (S > 1 && m - (S - 1) * L < NF) --S;
+        if (S > 1) L = std::max(L, NF);
+        h->zf_S = S;
+        h->zf_L = S > 1 ? L : m;
+        h->zf_Lt = S > 1 ? L + NF : m;
+        const int Lt = h->zf_Lt;
+        // responses h_j (j < Lt) of h_j = sum_t c_t h_{j-t} to the history h_{-1-i} = 1:
+        // forward c_t = -l_t, backward c_t = -u_t / u_0 (the factors of the sweeps)
+        std::vector<float4> tab((size_t)nE * K * 2 * NF * Lt);
+        auto split = [](std::complex<double> v) {
+            const float hr = (float)v.real(), hi = (float)v.imag();
+            return make_float4(hr, hi, (float)(v.real() - (double)hr), (float)(v.imag() - (double)hi));
+        };
+        std::vector<std::complex<double>> hv(Lt + NF);
+        for (int e = 0; e < nE; ++e)
+            for (int f = 0; f < K; ++f) {
+                const double2* pc = &zpc[((size_t)e * K + f) * kPcStrideDev];
+                std::complex<double> c[2][5];
+                const std::complex<double> u0(pc[NF].x, pc[NF].y);
+                for (int t = 1; t <= NF; ++t) {
+                    c[0][t] = -std::complex<double>(pc[t - 1].x, pc[t - 1].y);
+                    c[1][t] = -std::complex<double>(pc[NF + t].x, pc[NF + t].y) / u0;
+                }
+                for (int d = 0; d < 2; ++d)
+                    for (int i = 0; i < NF; ++i) {
+                        // hv[NF + j] = h_j; hv[NF - 1 - i'] = history h_{-1-i'}
+                        std::fill(hv.begin(), hv.end(), std::complex<double>(0.0, 0.0));
+                        hv[NF - 1 - i] = 1.0;
+                        for (int j = 0; j < Lt; ++j) {
+                            std::complex<double> acc(0.0, 0.0);
+                            for (int t = 1; t <= NF; ++t) acc += c[d][t] * hv[NF + j - t];
+                            hv[NF + j] = acc;
+                            tab[((((size_t)e * K + f) * 2 + d) * NF + i) * Lt + j] = split(acc);
+                        }
+                    }
+            }
+        CK(upload(h->zf_tab, tab, h->stream));
+        CK(h->zf_scr.ensure(sizeof(float4) * (size_t)std::max(h->nrhs, 1) * K * m));
     }
     return IOBM_OK;
 }
@@ -1957,7 +2009,8 @@ void iobm_destroy(iobm_handle* h) {
                       &h->batch_ctr, &h->sig_scratch, &h->kb_scratch, &h->uplane, &h->esc_ws,
                       &h->esc_descs, &h->esc_rhs_energy, &h->rhs_sign, &h->apply_sign,
                       &h->gph32, &h->gph64, &h->gpx, &h->gpy, &h->esc_rhs_sign,
-                      &h->zflag, &h->zf_bins, &h->zf_pc, &h->dense32, &h->dense64,
+                      &h->zflag, &h->zf_bins, &h->zf_pc, &h->zf_tab, &h->zf_scr,
+                      &h->dense32, &h->dense64,
                       &h->apply_dense32, &h->apply_dense64, &h->dense_k, &h->dense_part};
     for (DevBuf* b : bufs) b->release();
     if (h->ev_sync) cudaEventDestroy(h->ev_sync);

@@ -230,6 +230,13 @@ struct PrecondArgs {
     const int* zf_bins;
     const double2* zf_pc;
     int zf_k;
+    // the double-float sweeps split z into zf_S segments of zf_L planes (the last one
+    // longer, < zf_L + nf), one lane each: zf_tab[e][f][2][nf][zf_Lt] the responses of the
+    // forward and backward recurrences to each unit history value (hi.re, hi.im, lo.re,
+    // lo.im), zf_scr[rhs][f][nz - nf] the segments' particular solutions
+    const float4* zf_tab;
+    float4* zf_scr;
+    int zf_S, zf_L, zf_Lt;
     // host side: with zf_side set, the double-float sweeps run on stream zf_side
     // (forked from and joined back to the launching stream by the two events)
     // concurrently with the FP32 sweeps of the other modes

@@ -297,6 +297,174 @@ __device__ __forceinline__ void zsweep_df(float2* __restrict__ s, const double2*
     }
 }
 
+// The same sweeps split along z into S segments, one lane each (a group of kZfLanes
+// lanes per (RHS, mode)).  The interior recurrences have constant coefficients, so a
+// segment's true values are its particular solution from a zero history plus the
+// responses to the true history at its start: y_{k0+j} = y^_{k0+j} + sum_i T_i(j) y_{k0-1-i},
+// T_i the response to a unit history value (tabulated per mode in FP64, stored as
+// float pairs).  Phase 1: every lane solves its segment from a zero history; phase 2:
+// the S - 1 segment starts are chained lane to lane by shuffles (each a N_f x N_f
+// multiply-add); phase 3: every lane adds its correction.  The backward sweep likewise
+// from the top, its first history being the end block's values.  The serial chain per
+// sweep falls from m planes to about 2 m / S planes plus S carry steps.
+constexpr int kZfLanes = 8;
+
+__device__ __forceinline__ Dfc df_from4(float4 v) {
+    Dfc r;
+    r.hi = make_float2(v.x, v.y);
+    r.lo = make_float2(v.z, v.w);
+    return r;
+}
+__device__ __forceinline__ float4 df_to4(const Dfc& a) { return make_float4(a.hi.x, a.hi.y, a.lo.x, a.lo.y); }
+// the previous lane's value within the group of kZfLanes lanes
+__device__ __forceinline__ Dfc df_shfl_up(const Dfc& v, unsigned gm) {
+    Dfc r;
+    r.hi.x = __shfl_up_sync(gm, v.hi.x, 1, kZfLanes);
+    r.hi.y = __shfl_up_sync(gm, v.hi.y, 1, kZfLanes);
+    r.lo.x = __shfl_up_sync(gm, v.lo.x, 1, kZfLanes);
+    r.lo.y = __shfl_up_sync(gm, v.lo.y, 1, kZfLanes);
+    return r;
+}
+__device__ __forceinline__ Dfc df_shfl(const Dfc& v, int src, unsigned gm) {
+    Dfc r;
+    r.hi.x = __shfl_sync(gm, v.hi.x, src, kZfLanes);
+    r.hi.y = __shfl_sync(gm, v.hi.y, src, kZfLanes);
+    r.lo.x = __shfl_sync(gm, v.lo.x, src, kZfLanes);
+    r.lo.y = __shfl_sync(gm, v.lo.y, src, kZfLanes);
+    return r;
+}
+
+template <int NF>
+__device__ __forceinline__ void zsweep_df_seg(float2* __restrict__ s, const double2* __restrict__ pc,
+                                              const float4* __restrict__ tab, float4* __restrict__ scr,
+                                              int nz, int nxy, int S, int L, int Lt, int sig, unsigned gm) {
+    Dfc nl[NF + 1], nw[NF + 1];
+#pragma unroll
+    for (int j = 1; j <= NF; ++j) nl[j] = df_neg(df_load(pc[j - 1]));
+    const double2 u0 = pc[NF];
+    const double den = u0.x * u0.x + u0.y * u0.y;
+    const double2 ui = make_double2(u0.x / den, -u0.y / den);
+    const Dfc uinv = df_load(ui);
+#pragma unroll
+    for (int j = 1; j <= NF; ++j) {
+        const double2 uj = pc[NF + j];
+        nw[j] = df_load(make_double2(-(uj.x * ui.x - uj.y * ui.y), -(uj.x * ui.y + uj.y * ui.x)));
+    }
+    float sch, scl;
+    df_split(1.0 / (double)nxy, sch, scl);   // the forward FFT carries no 1/N_xy
+    const Dfc zero = df_from(make_float2(0.f, 0.f));
+    const int m = nz - NF;
+    const float4* __restrict__ tf = tab;             // [NF][Lt] forward responses
+    const float4* __restrict__ tb = tab + NF * Lt;   // backward
+    const bool act = sig < S;
+    // the next segment's history from this one's tail and its own history C
+    auto chain = [&](const float4* t, const Dfc (&tail)[NF], Dfc (&C)[NF]) {
+        for (int step = 1; step < S; ++step) {
+            Dfc cand[NF];
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+                cand[i] = tail[i];
+#pragma unroll
+                for (int i2 = 0; i2 < NF; ++i2) df_cacc(cand[i], df_from4(t[i2 * Lt + (L - 1 - i)]), C[i2]);
+                df_norm(cand[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+                const Dfc up = df_shfl_up(cand[i], gm);
+                if (sig == step) C[i] = up;
+            }
+        }
+    };
+
+    // ---- forward: y_k = r_k / N_xy - sum_t l_t y_{k-t}, segment [lo, hi)
+    const int lo = sig * L, hi = (sig == S - 1) ? m : lo + L;
+    Dfc hist[NF];   // hist[i] = y^_{k-1-i}
+#pragma unroll
+    for (int i = 0; i < NF; ++i) hist[i] = zero;
+    if (act)
+        for (int k = lo; k < hi; ++k) {
+            Dfc y = df_scale(sch, scl, df_from(s[(long long)k * nxy]));
+#pragma unroll
+            for (int t = NF; t >= 1; --t) df_cacc(y, nl[t], hist[t - 1]);
+            df_norm(y);
+            scr[k] = df_to4(y);
+#pragma unroll
+            for (int t = NF - 1; t > 0; --t) hist[t] = hist[t - 1];
+            hist[0] = y;
+        }
+    Dfc C[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) C[i] = zero;
+    chain(tf, hist, C);
+    if (act)
+        for (int k = lo; k < hi; ++k) {
+            Dfc y = df_from4(scr[k]);
+#pragma unroll
+            for (int i = 0; i < NF; ++i) df_cacc(y, df_from4(tf[i * Lt + (k - lo)]), C[i]);
+            df_norm(y);
+            s[(long long)k * nxy] = df_round(y);
+#pragma unroll
+            for (int t = NF - 1; t > 0; --t) hist[t] = hist[t - 1];
+            hist[0] = y;   // the last segment ends with the true y_{m-1-i}
+        }
+    // ---- the last nf planes (every lane, from the last segment's values)
+    Dfc yl[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) yl[i] = df_shfl(hist[i], S - 1, gm);
+    Dfc g[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        Dfc v = df_scale(sch, scl, df_from(s[(long long)(m + i) * nxy]));
+#pragma unroll
+        for (int j = 1; j <= NF; ++j)
+            if (j > i) df_cacc(v, nl[j], yl[j - 1 - i]);
+        df_norm(v);
+        g[i] = v;
+    }
+    Dfc xe[NF];   // x_{m+i}
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        Dfc v = zero;
+#pragma unroll
+        for (int j = 0; j < NF; ++j) df_cacc(v, df_load(pc[2 * NF + 1 + i * NF + j]), g[j]);
+        df_norm(v);
+        xe[i] = v;
+    }
+    __syncwarp(gm);   // every lane read the last planes' r and every segment stored its y
+    if (sig == 0)
+#pragma unroll
+        for (int i = 0; i < NF; ++i) s[(long long)(m + i) * nxy] = df_round(xe[i]);
+
+    // ---- backward: x_k = y_k / u_0 - sum_t (u_t / u_0) x_{k+t}, segment [bot, top)
+    const int top = m - sig * L, bot = (sig == S - 1) ? 0 : top - L;
+    Dfc nxt[NF];   // nxt[i] = x^_{k+1+i}
+#pragma unroll
+    for (int i = 0; i < NF; ++i) nxt[i] = zero;
+    if (act)
+        for (int k = top - 1; k >= bot; --k) {
+            Dfc x = zero;
+            df_cacc(x, uinv, df_from(s[(long long)k * nxy]));
+#pragma unroll
+            for (int t = NF; t >= 1; --t) df_cacc(x, nw[t], nxt[t - 1]);
+            df_norm(x);
+            scr[k] = df_to4(x);
+#pragma unroll
+            for (int t = NF - 1; t > 0; --t) nxt[t] = nxt[t - 1];
+            nxt[0] = x;   // at the end nxt[i] = x^_{bot+i}
+        }
+#pragma unroll
+    for (int i = 0; i < NF; ++i) C[i] = (sig == 0) ? xe[i] : zero;   // x_{top+i} of segment 0
+    chain(tb, nxt, C);
+    if (act)
+        for (int k = top - 1; k >= bot; --k) {
+            Dfc x = df_from4(scr[k]);
+#pragma unroll
+            for (int i = 0; i < NF; ++i) df_cacc(x, df_from4(tb[i * Lt + (top - 1 - k)]), C[i]);
+            df_norm(x);
+            s[(long long)k * nxy] = df_round(x);
+        }
+}
+
 // every mode but the double-float ones (flagged in zflag), in the working precision
 template <typename T, int NF>
 __global__ void __launch_bounds__(kZThreads) k_zsolve(const PrecondArgs<T> a) {
@@ -312,14 +480,30 @@ __global__ void __launch_bounds__(kZThreads) k_zsolve(const PrecondArgs<T> a) {
                      a.pc + ((size_t)e * nxy + mode) * kPcStrideDev, a.nz, nxy);
 }
 
-// the double-float sweeps of the flagged modes (FP32 solves; beside or before k_zsolve)
+// the double-float sweeps of the flagged modes (FP32 solves; beside or before k_zsolve):
+// with segments a group of kZfLanes lanes per (RHS, mode), else one thread
 template <int NF>
 __global__ void __launch_bounds__(kZThreads) k_zsolve_df(const PrecondArgs<float> a) {
     const int rhs = blockIdx.y;
     if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= a.zf_k) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int e = a.rhs_energy ? a.rhs_energy[rhs] : 0;
+    if (a.zf_S > 1) {
+        const int f = t / kZfLanes;
+        if (f >= a.zf_k) return;   // the lanes of a group leave together
+        const int sig = t % kZfLanes;
+        const unsigned gm = 0xFFu << (threadIdx.x & 31 & ~(kZfLanes - 1));
+        const int mode = a.zf_bins[(size_t)e * a.zf_k + f];
+        const int m = a.nz - NF;
+        zsweep_df_seg<NF>(a.spec + (long long)rhs * a.npts + mode,
+                          a.zf_pc + ((size_t)e * a.zf_k + f) * kPcStrideDev,
+                          a.zf_tab + ((size_t)e * a.zf_k + f) * 2 * NF * a.zf_Lt,
+                          a.zf_scr + ((size_t)rhs * a.zf_k + f) * m, a.nz, a.nx * a.ny, a.zf_S,
+                          a.zf_L, a.zf_Lt, sig, gm);
+        return;
+    }
+    const int f = t;
+    if (f >= a.zf_k) return;
     const int mode = a.zf_bins[(size_t)e * a.zf_k + f];
     zsweep_df<NF>(a.spec + (long long)rhs * a.npts + mode,
                   a.zf_pc + ((size_t)e * a.zf_k + f) * kPcStrideDev, a.nz, a.nx * a.ny);
@@ -639,7 +823,8 @@ static cudaError_t launch_zsolve(const PrecondArgs<T>& a, int nrhs, cudaStream_t
             sd = a.zf_side;
         }
         if constexpr (sizeof(T) == 4) {
-            dim3 gd((a.zf_k + kZThreads - 1) / kZThreads, nrhs);
+            const int per = a.zf_S > 1 ? kZfLanes * a.zf_k : a.zf_k;
+            dim3 gd((per + kZThreads - 1) / kZThreads, nrhs);
             switch (a.nf) {
                 case 1: k_zsolve_df<1><<<gd, kZThreads, 0, sd>>>(a); break;
                 case 2: k_zsolve_df<2><<<gd, kZThreads, 0, sd>>>(a); break;
