@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(kZThreads) k_zsolve_df(const PrecondArgs<float
         const int f = t / kZfLanes;
         if (f >= a.zf_k) return;   // the lanes of a group leave together
         const int sig = t % kZfLanes;
-        const unsigned gm = 0xFFu << (threadIdx.x & 31 & ~(kZfLanes - 1));
+        const unsigned gm = ((1u << kZfLanes) - 1u) << (threadIdx.x & 31 & ~(kZfLanes - 1));
         const int mode = a.zf_bins[(size_t)e * a.zf_k + f];
         const int m = a.nz - NF;
         zsweep_df_seg<NF>(a.spec + (long long)rhs * a.npts + mode,
