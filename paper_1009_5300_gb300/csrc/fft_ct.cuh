@@ -208,20 +208,21 @@ struct Ct2Shape {
     __device__ static int out_col(int tid) { return tid % N; }
 };
 
-// 2D transform of one N x N plane by NT threads.  v holds the thread's inputs of the
-// first row pass (Ct2Shape::in_row / in_col: the caller reads them from global
-// memory), store(row, col, value, slot) takes the output from the last column pass.
-// A and B are two
-// shared-memory planes of pitch N + 1; tw holds exp(-2 pi i t / N), t < N, and must
-// be visible to every thread before the first barrier inside.
+// 2D transform of one N x N plane by NT threads in one shared-memory plane A (pitch
+// N + 1).  v holds the thread's inputs of the first row pass (Ct2Shape::in_row /
+// in_col: the caller reads them from global memory), store(row, col, value, slot) takes
+// the output from the last column pass.  tw holds exp(-2 pi i t / N), t < N, and must be
+// visible to every thread before the first barrier inside.
 //
-// Pass 1 (rows): thread (row y, j = tid % R2) forms the R1-point DFT of
-// x[y][j + m R2] into A[y][j R1 + a]; pass 2 (rows): butterfly (y, j < R1), y fastest,
-// reads A[y][j + r R1] exp(-+2 pi i r j / N) and writes its R2-point DFT to
-// B[y][j + a R1]; passes 3 and 4 do the same along the columns, B -> A -> store.
-// Every shared-memory access of a warp touches each 8-byte bank pair at most twice.
+// Pass 1 (rows): thread (row y, j = tid % R2) forms the R1-point DFT of x[y][j + m R2]
+// into A[y][j R1 + a]; pass 2 (rows): butterfly (y, j < R1), y fastest, reads
+// A[y][j + r R1] exp(-+2 pi i r j / N) and writes its R2-point DFT to the same
+// positions (in place: the butterflies touch disjoint sets); pass 3 (columns) reads
+// A[j + m R2][x], holds its outputs across a barrier and writes them to rows
+// j R1 + a; pass 4 (columns, in place) hands its outputs to the store.  Every
+// shared-memory access of a warp touches each 8-byte bank pair at most twice.
 template <typename C, int N, bool INV, typename Store>
-__device__ __forceinline__ void ct2_fft2(const C (&v1)[Ct2Plan<N>::R1], C* A, C* B, const C* tw,
+__device__ __forceinline__ void ct2_fft2(const C (&v1)[Ct2Plan<N>::R1], C* A, const C* tw,
                                          Store store) {
     using S = Ct2Shape<N>;
     constexpr int R1 = S::R1, R2 = S::R2, NT = S::NT, K2 = S::K2, PT = S::PT;
@@ -240,7 +241,7 @@ __device__ __forceinline__ void ct2_fft2(const C (&v1)[Ct2Plan<N>::R1], C* A, C*
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K2; ++k) {   // pass 2: rows, R2 points
+    for (int k = 0; k < K2; ++k) {   // pass 2: rows, R2 points, in place
         const int t = tid + k * NT;
         const int y = t % N, j = t / N;
         C v[R2], o[R2];
@@ -249,15 +250,16 @@ __device__ __forceinline__ void ct2_fft2(const C (&v1)[Ct2Plan<N>::R1], C* A, C*
         for (int r = 1; r < R2; ++r) v[r] = twiddled(A[y * PT + j + r * R1], r * j);
         dft_reg<C, R2, INV>(v, o);
 #pragma unroll
-        for (int a = 0; a < R2; ++a) B[y * PT + j + a * R1] = o[a];
+        for (int a = 0; a < R2; ++a) A[y * PT + j + a * R1] = o[a];
     }
     __syncthreads();
-    {   // pass 3: columns, R1 points
+    {   // pass 3: columns, R1 points; every input read before any output is written
         const int x = tid % N, j = tid / N;
         C v[R1], o[R1];
 #pragma unroll
-        for (int m = 0; m < R1; ++m) v[m] = B[(j + m * R2) * PT + x];
+        for (int m = 0; m < R1; ++m) v[m] = A[(j + m * R2) * PT + x];
         dft_reg<C, R1, INV>(v, o);
+        __syncthreads();
 #pragma unroll
         for (int a = 0; a < R1; ++a) A[(j * R1 + a) * PT + x] = o[a];
     }

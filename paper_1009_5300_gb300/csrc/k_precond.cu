@@ -704,13 +704,15 @@ __global__ void __launch_bounds__(256, (CtOccupancy<T, N>::value)) k_ifft_dots_c
 // 64): the first row pass reads the spectrum from global memory, the last column
 // pass writes z, so a point crosses shared memory twice per axis; r at the outputs
 // of the thread's last pass is loaded with the spectrum, so its latency overlaps
-// the transform.  CTAs of N R2 threads (192 at N = 48), at most five per SM (FP32)
-// or two (FP64), which the registers of the prefetched operands allow without spills.
+// the transform.  One shared-memory plane per CTA (the passes work in place); CTAs of
+// N R2 threads (192 at N = 48), at most five per SM (three at N = 64; FP64: two), which
+// the registers of the prefetched operands allow without spills.
 template <typename T, int N>
 struct Ct2Occupancy {
-    static constexpr int kSmem = (int)sizeof(typename Cplx<T>::type) * (2 * N * (N + 1) + N) + 1024 + 192;
+    static constexpr size_t kDyn = sizeof(typename Cplx<T>::type) * ((size_t)N * (N + 1) + N);
+    static constexpr int kSmem = (int)kDyn + 1024 + 192;
     static constexpr int kFit = (228 * 1024) / kSmem;
-    static constexpr int kCap = sizeof(typename Cplx<T>::type) == 8 ? 5 : 2;
+    static constexpr int kCap = sizeof(typename Cplx<T>::type) == 8 ? (N >= 64 ? 3 : 5) : 2;
     static constexpr int value = kFit < 1 ? 1 : (kFit > kCap ? kCap : kFit);
 };
 
@@ -725,8 +727,7 @@ __global__ void __launch_bounds__(Ct2Shape<N>::NT, (Ct2Occupancy<T, N>::value))
     if (a.state && !((1 << a.state[rhs].status) & a.mask)) return;
     constexpr int PT = S::PT;
     C* A = reinterpret_cast<C*>(smem_raw);
-    C* B = A + N * PT;
-    C* tw = B + N * PT;
+    C* tw = A + N * PT;
     for (int i = threadIdx.x; i < N; i += S::NT) tw[i] = a.twx[i];
     const long long off = (long long)rhs * a.npts + (long long)plane * (N * N);
     const C* __restrict__ spec = a.spec + off;
@@ -743,7 +744,7 @@ __global__ void __launch_bounds__(Ct2Shape<N>::NT, (Ct2Occupancy<T, N>::value))
         for (int aa = 0; aa < S::R2; ++aa)
             rv[k * S::R2 + aa] = dots ? rin[S::out_row(threadIdx.x, k, aa) * N + S::out_col(threadIdx.x)] : czero<C>();
     T dre = 0, dim = 0, nrm = 0;
-    ct2_fft2<C, N, true>(v, A, B, tw, [&](int row, int col, C z, int slot) {
+    ct2_fft2<C, N, true>(v, A, tw, [&](int row, int col, C z, int slot) {
         zo[row * N + col] = z;
         if (dots) {
             const C r = rv[slot];
@@ -876,7 +877,8 @@ static cudaError_t launch_inv_ct(const PrecondArgs<T>& a, int nrhs, cudaStream_t
     dim3 gp(a.nz, nrhs);
     switch (N) {
 #define IOBM_CT(NN) case NN: k_ifft_dots_ct<T, NN><<<gp, 256, smem, s>>>(a); break;
-#define IOBM_CT2(NN) case NN: k_ifft2_dots<T, NN><<<gp, Ct2Shape<NN>::NT, smem, s>>>(a); break;
+#define IOBM_CT2(NN) \
+        case NN: k_ifft2_dots<T, NN><<<gp, Ct2Shape<NN>::NT, Ct2Occupancy<T, NN>::kDyn, s>>>(a); break;
         IOBM_CT(12) IOBM_CT(16) IOBM_CT(24) IOBM_CT2(32) IOBM_CT2(48) IOBM_CT2(64)
 #undef IOBM_CT
 #undef IOBM_CT2
