@@ -71,7 +71,9 @@ struct iobm_handle {
     cudaStream_t stream = nullptr;      // private stream (capturable)
     cudaStream_t cond_stream = nullptr; // captures the bodies of conditional graph nodes
     cudaStream_t side_stream = nullptr; // the double-float z-sweeps beside the FP32 ones
+    cudaStream_t cond_side = nullptr;   // the same inside conditional bodies (a capture of their own)
     cudaEvent_t ev_zfork = nullptr, ev_zjoin = nullptr;
+    cudaEvent_t ev_sfork = nullptr, ev_sjoin = nullptr;   // FP64 self-energy beside the stencil
     bool in_cond_body = false;          // launches go into a conditional node's body graph
     bool graph_conditionals = true;     // IF nodes around the residual replacements
     cudaEvent_t ev_sync = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
@@ -122,6 +124,7 @@ struct iobm_handle {
     int stencil_variant = 0;             // StencilArgs::variant (autotuned)
     DevBuf batch_ctr;                    // chunk counter of this junction in a batched solve
     DevBuf sig_scratch;                  // large-plane self-energy spectra
+    DevBuf sig_end;                      // FP64 end-plane self-energy terms of the residual
     DevBuf kb_scratch;                  // KB projections [rhs][projector]
     DevBuf uplane;                      // [nz+1] first union-of-supports entry of each plane
     DevBuf esc_ws, esc_descs, esc_rhs_energy;   // FP64 continuation of stalled mixed RHS
@@ -292,7 +295,11 @@ cudaError_t ensure_sigma_scratch(iobm_handle* h, int nrhs) {
                                                    dense_row_tiles(h->nf, h->nxy));
         if (e != cudaSuccess) return e;
     }
-    if (!large_plane(h)) return cudaSuccess;
+    if (!large_plane(h)) {
+        if (dense_sigma(h)) return cudaSuccess;
+        // -(Sigma x) of the FP64 residual per (RHS, end, depth), formed beside the stencil
+        return h->sig_end.ensure((size_t)std::max(nrhs, 1) * 2 * h->nf * h->nxy * sizeof(double2));
+    }
     return h->sig_scratch.ensure(2 * (size_t)std::max(nrhs, 1) * 2 * h->nf * h->nxy * sizeof(double2));
 }
 
@@ -466,12 +473,10 @@ void set_fp64_modes(const iobm_handle* h, PrecondArgs<T>& f) {
     f.zf_L = h->zf_L;
     f.zf_Lt = h->zf_Lt;
     // the side stream joins the capture of the main graph when it forks there, so the
-    // body of a conditional node (a capture of its own) takes the single-launch sweeps
-    if (!h->in_cond_body) {
-        f.zf_side = h->side_stream;
-        f.zf_fork = h->ev_zfork;
-        f.zf_join = h->ev_zjoin;
-    }
+    // body of a conditional node (a capture of its own) forks to a side stream of its own
+    f.zf_side = h->in_cond_body ? h->cond_side : h->side_stream;
+    f.zf_fork = h->ev_zfork;
+    f.zf_join = h->ev_zjoin;
 }
 
 template <typename T>
@@ -525,10 +530,12 @@ KbArgs<T> kb_args(const iobm_handle* h) {
 }
 
 // y = A x (FP64 or FP32) for the RHS selected by (state, mask); energies per RHS.
+// no_sigma: leave out the end-plane self-energy (the caller forms it apart).
 template <typename T>
 int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void* sig,
                    const double* ediag, const int* rhs_energy, const RhsState* st, int mask,
-                   long long& launches, bool df = false, const int* signs = nullptr) {
+                   long long& launches, bool df = false, const int* signs = nullptr,
+                   bool no_sigma = false) {
     using C = typename Cplx<T>::type;
     StencilArgs<T> a = op_args<T>(h);
     // FP64 data, double-float stencil arithmetic (the double-float kernel has no
@@ -542,17 +549,18 @@ int apply_operator(iobm_handle* h, const void* x, void* y, int nrhs, const void*
     a.state = st;
     a.mask = mask;
     CK(launch_stencil<T>(a, nrhs, h->stream));
-    SigmaArgs<T> s = sigma_args<T>(h, sig);
-    s.x = (const C*)x;
-    s.y = (C*)y;
-    s.rhs_energy = rhs_energy;
-    s.state = st;
-    s.mask = mask;
-    {
+    launches += 1;
+    if (!no_sigma) {
+        SigmaArgs<T> s = sigma_args<T>(h, sig);
+        s.x = (const C*)x;
+        s.y = (C*)y;
+        s.rhs_energy = rhs_energy;
+        s.state = st;
+        s.mask = mask;
         const int rc = apply_sigma<T>(h, s, sig, nrhs);
         if (rc) return rc;
+        launches += 1;
     }
-    launches += 2;
     if (h->pt.nproj > 0) {
         KbArgs<T> k = kb_args<T>(h);
         k.x = (const C*)x;
@@ -614,24 +622,56 @@ int apply_precond_dots(iobm_handle* h, int nrhs, int mask, long long& launches) 
     return pair_rho<T>(h, nrhs, mask, launches);
 }
 
+// FP64 residual r = b - A x64 of the RHS in `mask` into r (working precision) and
+// its |r|^2 partials (*nslots per RHS).  The stencil (double-float when mixed) and
+// the KB term run on h->stream; the end-plane self-energy, which reads only x64,
+// runs beside them on a side stream into its own buffer, and the residual kernel
+// adds it to y on the end planes: the same FP64 sums as when it updates y in place.
+template <typename T>
+int fp64_residual(iobm_handle* h, int nrhs, int mask, bool mixed, long long& launches, int* nslots) {
+    using C = typename Cplx<T>::type;
+    const bool apart = h->sig_end.p && !large_plane(h) && !dense_sigma(h) && !bloch(h);
+    cudaStream_t side = h->in_cond_body ? h->cond_side : h->side_stream;
+    if (apart) {
+        CK(cudaEventRecord(h->ev_sfork, h->stream));
+        CK(cudaStreamWaitEvent(side, h->ev_sfork, 0));
+        SigmaArgs<double> s = sigma_args<double>(h, h->sig64.p);
+        s.x = h->x64;
+        s.y = h->y64;
+        s.yend = h->sig_end.as<double2>();
+        s.rhs_energy = h->rhs_energy.as<int>();
+        s.state = h->st;
+        s.mask = mask;
+        CK(launch_sigma<double>(s, nrhs, side));
+        CK(cudaEventRecord(h->ev_sjoin, side));
+        launches += 1;
+    }
+    const int rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
+                                          h->rhs_energy.as<int>(), h->st, mask, launches, mixed,
+                                          nullptr, apart);
+    if (apart) CK(cudaStreamWaitEvent(h->stream, h->ev_sjoin, 0));   // joined even after a failure
+    if (rc) return rc;
+    CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
+                          h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, h->st, mask,
+                          h->rr_part, h->slot_stride, nrhs, h->stream, nslots,
+                          apart ? h->sig_end.as<double2>() : nullptr));
+    launches += 1;
+    return IOBM_OK;
+}
+
 // FP64 residual replacement for RHS in `mask` (PENDING): x64 (+)= x, r = b - A x64.
 template <typename T>
 int residual_replacement(iobm_handle* h, int nrhs, int mask, bool mixed, long long& launches) {
-    using C = typename Cplx<T>::type;
     if (mixed) {
         CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
         launches += 1;
     }
-    int rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
-                                    h->rhs_energy.as<int>(), h->st, mask, launches, mixed);
-    if (rc) return rc;
     int nslots = 0;
-    CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
-                          h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, h->st, mask,
-                          h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
+    const int rc = fp64_residual<T>(h, nrhs, mask, mixed, launches, &nslots);
+    if (rc) return rc;
     CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, internal_tol2(h), 0, h->stream,
                     h->pairs));
-    launches += 2;
+    launches += 1;
     // RESTART RHS get z = P r and the rho / |r|^2 partials of the replaced residual;
     // the next iteration returns them to ACTIVE and forms beta from these partials
     return apply_precond_dots<T>(h, nrhs, M_RESTART, launches);
@@ -912,13 +952,9 @@ int solver_epilogue(iobm_handle* h, int nrhs, long long& launches) {
     if (mixed) {
         CK(launch_fold(h->x64, (float2*)h->vx, h->st, mask, h->npts, nrhs, h->stream));
     }
-    int rc = apply_operator<double>(h, h->x64, h->y64, nrhs, h->sig64.p, h->ediag.as<double>(),
-                                    h->rhs_energy.as<int>(), h->st, mask, launches, mixed);
-    if (rc) return rc;
     int nslots = 0;
-    CK(launch_residual<T>(h->y64, nullptr, (C*)h->vr, h->descs.as<RhsDesc>(), h->phx.as<double2>(),
-                          h->phy.as<double2>(), h->g.nx, h->g.ny, h->g.nz, h->nf, h->st, mask,
-                          h->rr_part, h->slot_stride, nrhs, h->stream, &nslots));
+    const int rc = fp64_residual<T>(h, nrhs, mask, mixed, launches, &nslots);
+    if (rc) return rc;
     CK(launch_check(h->st, h->rr_part, nslots, h->slot_stride, nrhs, 0.0, 2, h->stream));
     CK(cudaEventRecord(h->ev_t1, h->stream));
     h->hstate.resize(nrhs);
@@ -1921,8 +1957,11 @@ int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projector
     cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cond_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cond_side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_zfork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_zjoin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sjoin, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sync, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_t1);
@@ -2006,7 +2045,7 @@ void iobm_destroy(iobm_handle* h) {
                       &h->pc64, &h->ediag, &h->rhs_energy, &h->descs, &h->open_ptr, &h->open_bins,
                       &h->proj_out, &h->apply_sig32, &h->apply_sig64, &h->apply_pc32,
                       &h->apply_pc64, &h->apply_ediag, &h->ws_owned, &h->errflag,
-                      &h->batch_ctr, &h->sig_scratch, &h->kb_scratch, &h->uplane, &h->esc_ws,
+                      &h->batch_ctr, &h->sig_scratch, &h->sig_end, &h->kb_scratch, &h->uplane, &h->esc_ws,
                       &h->esc_descs, &h->esc_rhs_energy, &h->rhs_sign, &h->apply_sign,
                       &h->gph32, &h->gph64, &h->gpx, &h->gpy, &h->esc_rhs_sign,
                       &h->zflag, &h->zf_bins, &h->zf_pc, &h->zf_tab, &h->zf_scr,
@@ -2020,8 +2059,11 @@ void iobm_destroy(iobm_handle* h) {
     if (h->stream) cudaStreamDestroy(h->stream);
     if (h->cond_stream) cudaStreamDestroy(h->cond_stream);
     if (h->side_stream) cudaStreamDestroy(h->side_stream);
+    if (h->cond_side) cudaStreamDestroy(h->cond_side);
     if (h->ev_zfork) cudaEventDestroy(h->ev_zfork);
     if (h->ev_zjoin) cudaEventDestroy(h->ev_zjoin);
+    if (h->ev_sfork) cudaEventDestroy(h->ev_sfork);
+    if (h->ev_sjoin) cudaEventDestroy(h->ev_sjoin);
     delete h;
 }
 

@@ -152,6 +152,8 @@ struct SigmaArgs {
     const C* x;             // operand planes are read from here
     const C* pnew[2];       // if set: operand = pnew[1 - pbuf] of the RHS (COCG direction)
     C* y;                   // y[end planes] -= Sigma x
+    C* yend;                // if set (planes <= 4096 points): yend[((rhs 2 + end) nf + d) nxy + i]
+                            // = -(Sigma x) of that plane instead, y untouched
     const C* sigma;         // [energy][ky][kx][nf][nf]
     const int* rhs_energy;
     const RhsState* state;
@@ -336,13 +338,14 @@ template <typename T> cudaError_t launch_kb_proj(const KbArgs<T>& a, int nrhs, c
 cudaError_t launch_fold(double2* x64, float2* x32, const RhsState* st, int mask, long long npts,
                         int nrhs, cudaStream_t s);
 // r = b - y (y may be null) in FP64; writes r64 (may be null) and rT (element type T);
-// rr partials per block.
+// rr partials per block.  yend (may be null): the end-plane terms -(Sigma x) kept apart
+// by the self-energy (SigmaArgs::yend layout), added to y on those planes first.
 template <typename T>
 cudaError_t launch_residual(const double2* y, double2* r64, typename Cplx<T>::type* rT,
                             const RhsDesc* desc, const double2* phx, const double2* phy,
                             int nx, int ny, int nz, int nf, const RhsState* st, int mask,
                             double* rr_part, int slot_stride, int nrhs, cudaStream_t s,
-                            int* nslots_out);
+                            int* nslots_out, const double2* yend = nullptr);
 cudaError_t launch_set_status(RhsState* st, int nrhs, int from, int to, cudaStream_t s);
 cudaError_t launch_status_cond(cudaGraphConditionalHandle cond, const RhsState* st, int nrhs,
                                int mask, cudaStream_t s);

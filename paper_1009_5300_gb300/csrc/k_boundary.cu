@@ -113,11 +113,13 @@ __global__ void __launch_bounds__(kSigmaMaxThreads) k_sigma(const SigmaArgs<T> a
     fft2(buf, scratch, a.ax, a.ay, a.twx, a.twy, true);
 
     C* __restrict__ Y = a.y + off;
+    C* __restrict__ YE = a.yend ? a.yend + ((long long)(rhs * 2 + end) * nf + d) * nxy : nullptr;
     T tre = 0, tim = 0;   // per-thread partials in the working precision
     for (int i = threadIdx.x; i < nxy; i += blockDim.x) {
         const C s = buf[(i / nx) * pitch + (i % nx)];
         const C xv = X[i];
-        Y[i] = csub(Y[i], s);
+        if (YE) YE[i] = cneg(s);
+        else Y[i] = csub(Y[i], s);
         tre -= xv.x * s.x - xv.y * s.y;
         tim -= xv.x * s.y + xv.y * s.x;
     }
@@ -203,13 +205,15 @@ __global__ void __launch_bounds__(kSigmaCtThreads) k_sigma_ct(const SigmaArgs<T>
     __syncthreads();
     ct_fft2<C, N, kSigmaCtThreads>(A, B, tw, true);
 
+    C* __restrict__ YE = a.yend ? a.yend + ((long long)(rhs * 2 + end) * nf + d) * NXY : nullptr;
     T tre = 0, tim = 0;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const int i = threadIdx.x + j * kSigmaCtThreads;
         if (i < NXY) {
             const C sv = A[(i / N) * PT + (i % N)];
-            Y[i] = csub(Y[i], sv);
+            if (YE) YE[i] = cneg(sv);
+            else Y[i] = csub(Y[i], sv);
             tre -= xv[j].x * sv.x - xv[j].y * sv.y;
             tim -= xv[j].x * sv.y + xv[j].y * sv.x;
         }

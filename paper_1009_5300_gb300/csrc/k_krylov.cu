@@ -466,73 +466,103 @@ __device__ __forceinline__ double2 source_value(const RhsDesc& D, const double2*
     return cmul(D.coef[d], ph);
 }
 
-// r = b - y (or r = b when y is null) and per-CTA partials of ||r||^2.  CTAs
-// take whole planes; the source b is nonzero only on the N_f end planes of the
-// incident side, so interior planes give r = -y without FP64 arithmetic.  The
-// squares are summed per thread in FP32 (an estimate of the norm needs no more)
-// and across the CTA in FP64.
+// r = b - y (or r = b when y is null) and per-CTA partials of ||r||^2.  The points
+// of each RHS are dealt to its CTAs in chunks of 256, round robin, so every CTA
+// gets the same share of interior and end-plane points.  Interior points take
+// r = -y by sign flips alone (no FP64 arithmetic, which GB300 runs at a small
+// fraction of its FP32 rate); the N_f end planes at either end add the source b
+// (nonzero on the incident side's planes only) and, with yend, the self-energy
+// terms computed apart (y + yend: the same sum the self-energy forms in place).
+// The squares are summed per thread in FP32 (an estimate of the norm needs no
+// more) and across the CTA in FP64.
+__device__ __forceinline__ double2 dneg2(double2 v) {
+    return make_double2(__hiloint2double(__double2hiint(v.x) ^ (int)0x80000000, __double2loint(v.x)),
+                        __hiloint2double(__double2hiint(v.y) ^ (int)0x80000000, __double2loint(v.y)));
+}
+
+__device__ __noinline__ double2 end_residual(const double2* __restrict__ y, const double2* __restrict__ yend,
+                                             const RhsDesc* __restrict__ Dp, const double2* phx,
+                                             const double2* phy,
+                                             int nx, int ny, int nz, int nf, int rhs, long long base,
+                                             long long i) {
+    const int plane = nx * ny;
+    const int k = (int)(i / plane);
+    const int lat = (int)(i - (long long)k * plane);
+    double2 yv = make_double2(0.0, 0.0);
+    if (y) {
+        yv = y[base + i];
+        if (yend) {
+            const int end = k < nf ? 0 : 1;
+            const int d = end == 0 ? k : nz - 1 - k;
+            yv = cadd(yv, yend[((long long)(rhs * 2 + end) * nf + d) * plane + lat]);
+        }
+    }
+    const RhsDesc& D = *Dp;
+    const bool src = (D.side == 0) ? (k < nf) : (k >= nz - nf);
+    if (src) {
+        const int iy = lat / nx, ix = lat - iy * nx;
+        const double2 b = source_value(D, phx, phy, nx, ny, nz, nf, k, ix, iy);
+        return y ? csub(b, yv) : b;
+    }
+    return y ? dneg2(yv) : make_double2(0.0, 0.0);
+}
+
 template <typename T>
-__global__ void k_residual(const double2* __restrict__ y, double2* __restrict__ r64,
-                           typename Cplx<T>::type* __restrict__ rT, const RhsDesc* desc,
-                           const double2* phx, const double2* phy, int nx, int ny, int nz, int nf,
-                           const RhsState* st, int mask, double* rr_part, int stride) {
+__global__ void __launch_bounds__(256) k_residual(const double2* __restrict__ y, double2* __restrict__ r64,
+                                                  typename Cplx<T>::type* __restrict__ rT,
+                                                  const RhsDesc* desc, const double2* phx,
+                                                  const double2* phy, int nx, int ny, int nz, int nf,
+                                                  const RhsState* st, int mask, double* rr_part,
+                                                  int stride, const double2* __restrict__ yend) {
     using C = typename Cplx<T>::type;
     __shared__ double red[3 * 8];
     const int rhs = blockIdx.y;
     if (st && !((1 << st[rhs].status) & mask)) return;
-    const int plane = nx * ny;
-    const long long base = (long long)rhs * plane * nz;
-    const RhsDesc D = desc[rhs];
+    const long long plane = (long long)nx * ny;
+    const long long n = plane * nz;
+    const long long base = (long long)rhs * n;
+    const long long e0 = (long long)nf * plane, e1 = n - e0;   // interior points [e0, e1)
+    const long long step = (long long)gridDim.x * blockDim.x;
     float acc = 0.f;
-    for (int k = blockIdx.x; k < nz; k += gridDim.x) {
-        const bool src = (D.side == 0) ? (k < nf) : (k >= nz - nf);
-        const long long off = base + (long long)k * plane;
-        for (int lat = threadIdx.x; lat < plane; lat += blockDim.x) {
-            double2 v;
-            if (src) {
-                const int iy = lat / nx, ix = lat - iy * nx;
-                v = source_value(D, phx, phy, nx, ny, nz, nf, k, ix, iy);
-                if (y) v = csub(v, y[off + lat]);
-            } else if (y) {
-                const double2 w = y[off + lat];
-                v = make_double2(-w.x, -w.y);
-            } else {
-                v = make_double2(0.0, 0.0);
-            }
-            if (r64) r64[off + lat] = v;
-            const C c = from_d2<C>(v);
-            if (rT) rT[off + lat] = c;
-            const float fx = (float)c.x, fy = (float)c.y;
-            acc = fmaf(fx, fx, fmaf(fy, fy, acc));
-        }
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+        double2 v;
+        if (i >= e0 && i < e1) v = y ? dneg2(y[base + i]) : make_double2(0.0, 0.0);
+        else v = end_residual(y, yend, desc + rhs, phx, phy, nx, ny, nz, nf, rhs, base, i);
+        if (r64) r64[base + i] = v;
+        const C c = from_d2<C>(v);
+        if (rT) rT[base + i] = c;
+        const float fx = (float)c.x, fy = (float)c.y;
+        acc = fmaf(fx, fx, fmaf(fy, fy, acc));
     }
     double a0 = acc, z1 = 0.0, z2 = 0.0;
     block_reduce_3(a0, z1, z2, red);
     if (threadIdx.x == 0) rr_part[(long long)rhs * stride + blockIdx.x] = a0;
 }
 
-constexpr int kResidualBlocks = 64;
+constexpr int kResidualBlocks = 128;   // CTAs per RHS (fewer when the RHS has fewer slots)
 
 template <typename T>
 cudaError_t launch_residual(const double2* y, double2* r64, typename Cplx<T>::type* rT,
                             const RhsDesc* desc, const double2* phx, const double2* phy,
                             int nx, int ny, int nz, int nf, const RhsState* st, int mask,
                             double* rr_part, int slot_stride, int nrhs, cudaStream_t s,
-                            int* nslots_out) {
-    dim3 grid(kResidualBlocks, nrhs);
+                            int* nslots_out, const double2* yend) {
+    const int blocks = slot_stride < kResidualBlocks ? slot_stride : kResidualBlocks;
+    if (blocks < 1) return cudaErrorInvalidValue;
+    dim3 grid(blocks, nrhs);
     k_residual<T><<<grid, 256, 0, s>>>(y, r64, rT, desc, phx, phy, nx, ny, nz, nf, st, mask,
-                                       rr_part, slot_stride);
-    if (nslots_out) *nslots_out = kResidualBlocks;
+                                       rr_part, slot_stride, yend);
+    if (nslots_out) *nslots_out = blocks;
     return cudaGetLastError();
 }
 template cudaError_t launch_residual<float>(const double2*, double2*, float2*, const RhsDesc*,
                                             const double2*, const double2*, int, int, int, int,
                                             const RhsState*, int, double*, int, int, cudaStream_t,
-                                            int*);
+                                            int*, const double2*);
 template cudaError_t launch_residual<double>(const double2*, double2*, double2*, const RhsDesc*,
                                              const double2*, const double2*, int, int, int, int,
                                              const RhsState*, int, double*, int, int, cudaStream_t,
-                                             int*);
+                                             int*, const double2*);
 
 // init = 1: record ||b||^2 and start every RHS; init = 0: judge the FP64
 // residual of the PENDING RHS; init = 2: record the residual of RHS that stopped.
