@@ -945,7 +945,6 @@ int launch_chunk(iobm_handle* h, int nrhs, bool timed, long long& per_chunk) {
 // record their FP64 residual, read the per-RHS state back.
 template <typename T>
 int solver_epilogue(iobm_handle* h, int nrhs, long long& launches) {
-    using C = typename Cplx<T>::type;
     const bool mixed = std::is_same<T, float>::value;
     const int mask = (1 << ST_NOCONV) | (1 << ST_BREAKDOWN) | (1 << ST_ACTIVE) | (1 << ST_PENDING) |
                      (1 << ST_RESTART);
