@@ -189,6 +189,19 @@ def cpu_baseline_entry(budget_s=12.0):
 
 # ---------------------------------------------------------------------------
 
+def reduce_over_ranks(dist, device, elapsed, units):
+    """Whole-job (elapsed, units) of a replicated run, one process per GPU: the slowest
+    rank's elapsed time and the units every rank processed (dist None: one process)."""
+    if dist is None:
+        return float(elapsed), float(units)
+    import torch
+    t = torch.tensor([float(elapsed), float(units)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+    dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
@@ -336,14 +349,7 @@ def native_arm(args, rank, world, local_rank):
     iters_total = sum(r.iterations_total for r in results)
     launches = sum(r.launches for r in results)
     max_res = max(float(r.residual.max()) for r in results)
-    t = torch.tensor([ms, float(solves)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_max, solves_all = float(tmax[0]), float(t[1])
-    else:
-        ms_max, solves_all = ms, float(solves)
+    ms_max, solves_all = reduce_over_ranks(dist, dev, ms, solves)
     value = solves_all / (ms_max / 1000.0)
 
     # roofline of the dominant kernel: algorithmic bytes of its launches (per
@@ -460,13 +466,7 @@ def native_arm(args, rank, world, local_rank):
             s._ws = None
             s.close()
         barrier()
-        dt = time.perf_counter() - t0
-        e2e_solves = r.nrhs * e2e_steps
-        if dist is not None:
-            tt = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt[0])
-            e2e_solves *= world
+        dt, e2e_solves = reduce_over_ranks(dist, dev, time.perf_counter() - t0, r.nrhs * e2e_steps)
         e2e = {"value": e2e_solves / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
@@ -627,15 +627,7 @@ def batch_arm(args, rank, world, local_rank):
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms, float(solves)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms, solves_all = float(tmax[0]), float(t[1])
-    else:
-        solves_all = float(solves)
+    ms, solves_all = reduce_over_ranks(dist, dev, ev0.elapsed_time(ev1), solves)
     if rank == 0:
         line = {"metric": METRIC, "value": solves_all / (ms / 1000.0), "unit": UNIT,
                 "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": ms,
