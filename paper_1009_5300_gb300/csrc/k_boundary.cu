@@ -8,8 +8,10 @@
 // barrier every CTA reads the N_f spectra of its cluster through distributed
 // shared memory and forms, per lateral mode nu, sum_d' Sigma~_nu[d][d'] psi~_nu(d')
 // (for N_f = 1 this is the diagonal product of Eq. 18-2), transforms back and
-// subtracts the result from the operator output on its plane.  The
-// unconjugated product x^T (-Sigma x) over the plane goes to a dot slot.
+// subtracts the result from the operator output on its plane (or, for the FP64
+// residual, stores -Sigma x in an end-plane buffer of its own, so that it can run
+// beside the stencil that writes the operator output).  The unconjugated product
+// x^T (-Sigma x) over the plane goes to a dot slot.
 //
 // KB term: one CTA per RHS.  Warps first form s_p = dvol * sum_r p(r) x(r) for
 // every projector (fixed per-lane order plus a fixed shuffle tree), then the
