@@ -3,7 +3,7 @@
 Paper passages followed:
 
 * Eq. 1: the kinetic operator -1/2 d^2/dr^2 with FD weights on each axis;
-  x and y periodic (Sec. II: "periodic in the x and y directions"), or Bloch
+  x and y periodic (Sec. II takes both lateral directions periodic), or Bloch
   periodic psi(r + L) = exp(i kappa L) psi(r) for a lateral Bloch vector kappa
   (Eq. 8): a coupling that wraps across the lateral period carries that phase.
 * Eqs. 2-4: H_T is the Hamiltonian of planes z_0 .. z_{N_z+1}; couplings that
