@@ -564,7 +564,7 @@ template cudaError_t launch_residual<double>(const double2*, double2*, double2*,
                                              const RhsState*, int, double*, int, int, cudaStream_t,
                                              int*, const double2*);
 
-// init = 1: record ||b||^2 and start every RHS; init = 0: judge the FP64
+// init = 1: record ||b||^2 and start every RHS; init = 0: assess the FP64
 // residual of the PENDING RHS; init = 2: record the residual of RHS that stopped.
 // pairs > 0, init = 0: the FP64 check of a Bi-CG pair, both members together
 __device__ void check_pair(RhsState* st, const double* rr_part, int nslots, int stride, int i,

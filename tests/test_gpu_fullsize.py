@@ -10,7 +10,8 @@ preconditioned GMRES on the matrix-free Eq. 7 operator to a relative residual of
 energies are the three just below the opening of four new channels (the slowest
 for the mixed solver) and the top of the window.
 
-Bars (spec accuracy): conductance within 1e-6 G_0 of the oracle per energy,
+Bars (the accuracy the method is held to): conductance within 1e-6 G_0 of the oracle
+per energy,
 every T and R entry within 1e-6, and for EVERY returned wave the oracle's own
 matrix-free FP64 operator gives ||b - A psi|| / ||b|| <= 1e-8."""
 import json
