@@ -11,9 +11,8 @@ energies are the three just below the opening of four new channels (the slowest
 for the mixed solver) and the top of the window.
 
 Bars (the accuracy the method is held to): conductance within 1e-6 G_0 of the oracle
-per energy,
-every T and R entry within 1e-6, and for EVERY returned wave the oracle's own
-matrix-free FP64 operator gives ||b - A psi|| / ||b|| <= 1e-8."""
+per energy, every T and R entry within 1e-6, and for EVERY returned wave the oracle's
+own matrix-free FP64 operator gives ||b - A psi|| / ||b|| <= 1e-8."""
 import json
 import os
 
