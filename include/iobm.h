@@ -60,7 +60,7 @@ extern "C" {
                                     call's results are invalid, the context stays usable   */
 #define IOBM_E_CUDA           7  /* CUDA runtime error                                    */
 #define IOBM_E_STATE          8  /* call out of order (e.g. transmission before solve)    */
-#define IOBM_E_UNSUPPORTED    9  /* size outside what this build supports (see message)   */
+#define IOBM_E_UNSUPPORTED    9  /* size outside what the library supports (see message)*/
 
 /* precision of the solver */
 #define IOBM_FP64   0  /* plain FP64: vectors, stencil, Krylov recurrences in FP64     */
@@ -198,7 +198,7 @@ void iobm_default_options(iobm_options* opts);
  * cudaStream_t (NULL = legacy default stream).  Errors: IOBM_E_ARG for bad
  * sizes / non-finite V, IOBM_E_PROJ_BOUNDARY if a projector reaches the nf
  * outermost planes, IOBM_E_UNSUPPORTED for lateral sizes whose FFT does not
- * fit this build, IOBM_E_CUDA.  On an error *out may still receive a handle
+ * fit the library's kernels, IOBM_E_CUDA.  On an error *out may still receive a handle
  * (so that iobm_last_error can explain it); pass it to iobm_destroy. */
 int iobm_create(const iobm_grid* grid, const double* V_loc, const iobm_projectors* proj,
                 double rs, const iobm_options* opts, void* cuda_stream, iobm_handle** out);
