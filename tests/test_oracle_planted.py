@@ -1,0 +1,94 @@
+"""The symmetry pins catch plausible mistakes: each test plants one slip in the oracle
+(a patched copy of one of its functions, on the CPU) and checks that at least one pin
+of test_oracle_symmetries then fails.  The slips are the kind an implementation of
+Eqs. 8, 19 and the N_f end planes of Eq. 7 can make: a transposed lateral operand, a
+dropped Bloch vector in the modes, the phases or the wrapped couplings, an end plane
+taken in the wrong order or one plane in."""
+import numpy as np
+import pytest
+
+import oracle.modes as M
+import oracle.operator as O
+import oracle.transport as T
+import test_oracle_symmetries as TS
+
+PINS = [("supercell", TS.test_supercell_folds_two_bloch_vectors, ()),
+        ("transpose", TS.test_transposed_cell_same_conductance, ()),
+        ("translate", TS.test_lateral_translation_same_t_and_r, (1, 3)),
+        ("mirror", TS.test_mirror_image_swaps_the_electrodes, (4,))]
+
+_mode_data = M.mode_data
+
+
+def _phase(nx, ny, hx, hy, md, Gx, Gy):
+    x = np.arange(nx) * hx
+    y = np.arange(ny) * hy
+    ph = np.exp(-1j * (Gy[:, None, None] * y[None, :, None] + Gx[:, None, None] * x[None, None, :]))
+    return ph.reshape(len(md.nu), nx * ny)
+
+
+def phase_gy_from_x(nx, ny, hx, hy, md):
+    Gx = 2 * np.pi * md.nu[:, 0] / (nx * hx) + md.kappa[0]
+    Gy = 2 * np.pi * md.nu[:, 1] / (nx * hx) + md.kappa[1]     # slip: n_x h_x for y
+    return _phase(nx, ny, hx, hy, md, Gx, Gy)
+
+
+def phase_without_kappa(nx, ny, hx, hy, md):
+    Gx = 2 * np.pi * md.nu[:, 0] / (nx * hx)                    # slip: kappa dropped
+    Gy = 2 * np.pi * md.nu[:, 1] / (ny * hy)
+    return _phase(nx, ny, hx, hy, md, Gx, Gy)
+
+
+def modes_hy_from_hx(nx, ny, hx, hy, hz, nf, E, check_threshold=True, kappa=(0.0, 0.0)):
+    return _mode_data(nx, ny, hx, hx, hz, nf, E, check_threshold, kappa)   # slip: h_y <- h_x
+
+
+def modes_without_kappa(nx, ny, hx, hy, hz, nf, E, check_threshold=True, kappa=(0.0, 0.0)):
+    md = _mode_data(nx, ny, hx, hy, hz, nf, E, check_threshold, (0.0, 0.0))  # slip: eps(G)
+    md.kappa = (float(kappa[0]), float(kappa[1]))
+    return md
+
+
+def wrap_without_phase(jn, kappa):
+    return None, None                                            # slip: plain periodic wrap
+
+
+def right_planes_in_depth_order(jn, side):
+    # slip: the right electrode's planes taken from the interior outwards
+    return np.arange(jn.nf) + (jn.nz - jn.nf) if side == "R" else np.arange(jn.nf)
+
+
+def right_planes_one_in(jn, side):
+    return jn.nz - 2 - np.arange(jn.nf) if side == "R" else np.arange(jn.nf)   # slip: shifted
+
+
+PLANTS = {
+    "lateral phase G_y from n_x h_x": [(M, "lateral_phase", phase_gy_from_x),
+                                       (O, "lateral_phase", phase_gy_from_x),
+                                       (T, "lateral_phase", phase_gy_from_x)],
+    "lateral phase without kappa": [(M, "lateral_phase", phase_without_kappa),
+                                    (O, "lateral_phase", phase_without_kappa),
+                                    (T, "lateral_phase", phase_without_kappa)],
+    "mode tables with h_y = h_x": [(M, "mode_data", modes_hy_from_hx),
+                                   (T, "mode_data", modes_hy_from_hx)],
+    "mode energies without kappa": [(M, "mode_data", modes_without_kappa),
+                                    (T, "mode_data", modes_without_kappa)],
+    "wrapped couplings without phase": [(O, "_bloch_phases", wrap_without_phase)],
+    "right end planes in depth order": [(O, "end_planes", right_planes_in_depth_order),
+                                        (T, "end_planes", right_planes_in_depth_order)],
+    "right end planes one plane in": [(O, "end_planes", right_planes_one_in),
+                                      (T, "end_planes", right_planes_one_in)],
+}
+
+
+@pytest.mark.parametrize("plant", list(PLANTS))
+def test_planted_slip_fails_a_symmetry_pin(plant, monkeypatch):
+    for mod, attr, fn in PLANTS[plant]:
+        monkeypatch.setattr(mod, attr, fn)
+    failed = []
+    for name, pin, args in PINS:
+        try:
+            pin(*args)
+        except AssertionError:
+            failed.append(name)
+    assert failed, f"'{plant}' passes every symmetry pin"

@@ -1,0 +1,106 @@
+"""Symmetry pins of the oracle: exact identities of the discrete transport problem
+(Eqs. 1-8, 19, Landauer G of Sec. III) that a slip anywhere in the oracle's lateral
+indexing, Bloch phases, end-plane handling or flux normalisation would break.
+
+* lateral supercell: doubling the periodic cell along x at kappa = 0 folds the
+  Bloch vectors 0 and pi / L_x of the original cell (the supercell's lateral modes
+  2 pi m / (2 L_x) are the original G_nu for even m and G_nu + pi / L_x for odd m), so
+  G_super(0) = G(0) + G(pi / L_x);
+* x <-> y transposition of a non-square cell (nx != ny, h_x != h_y) leaves G unchanged;
+* a lateral translation by whole grid steps multiplies each mode by a phase: T and R
+  unchanged entry by entry;
+* the mirror image z -> -z swaps the electrodes: T^{L->R} of the mirrored junction is
+  T^{R->L} of the original, entry by entry.
+
+The potential is a wire of wells with a seeded random perturbation (no symmetry of
+its own), with s/p Kleinman-Bylander projectors.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import iobm_synth as S
+from oracle import transport
+
+
+def junction(nx=8, ny=6, nz=18, h=0.6, nf=4, seed=5):
+    jn = S.small_wire(nx=nx, ny=ny, nz=nz, h=h, natom=2, spacing=3.0, depth=0.6, width=0.9,
+                      rs=1.4, kb_kinds=S.SP, nf=nf, seed=seed, kb_radius=1.4, kb_width=0.6)
+    rng = np.random.default_rng(seed + 1)
+    bump = 0.08 * rng.standard_normal(jn.V.shape)
+    bump[:nf] = 0.0          # keep the end planes' potential as generated
+    bump[-nf:] = 0.0
+    return jn.copy_with(V=jn.V + bump)
+
+
+def remap(jn, V, f, **grid):
+    """Junction with potential V and every projector point (z, y, x) moved to the
+    linear index f(z, y, x) of the new grid."""
+    projs = []
+    for p in jn.projectors:
+        z, rem = np.divmod(p.idx.astype(np.int64), jn.nx * jn.ny)
+        y, x = np.divmod(rem, jn.nx)
+        idx = f(z, y, x)
+        order = np.argsort(idx, kind="stable")
+        projs.append(S.Projector(idx=idx[order].astype(np.int32), val=p.val[order],
+                                 coupling=p.coupling, atom=p.atom))
+    return jn.copy_with(V=np.ascontiguousarray(V), projectors=projs, **grid)
+
+
+def test_supercell_folds_two_bloch_vectors():
+    jn = junction(nx=6, ny=6, nz=16, h=0.65)
+    nx, ny = jn.nx, jn.ny
+    projs = []
+    for shift in (0, nx):   # two copies of every projector, one per original cell
+        for p in jn.projectors:
+            z, rem = np.divmod(p.idx.astype(np.int64), nx * ny)
+            y, x = np.divmod(rem, nx)
+            projs.append(S.Projector(idx=((z * ny + y) * 2 * nx + x + shift).astype(np.int32),
+                                     val=p.val, coupling=p.coupling, atom=p.atom))
+    sup = jn.copy_with(nx=2 * nx, V=np.concatenate([jn.V, jn.V], axis=2), projectors=projs)
+    for E in (jn.e_fermi - 0.05, jn.e_fermi + 0.03):
+        g0 = transport.solve(jn, E)
+        gpi = transport.solve(jn, E, kappa=(math.pi / (nx * jn.hx), 0.0))
+        gs = transport.solve(sup, E)
+        assert gs.n_open == g0.n_open + gpi.n_open
+        assert g0.n_open > 0 and gpi.n_open > 0
+        assert abs(gs.G - (g0.G + gpi.G)) < 1e-9, (gs.G, g0.G, gpi.G)
+
+
+def test_transposed_cell_same_conductance():
+    jn = junction(nx=8, ny=6, nz=18)
+    jn = jn.copy_with(hy=0.55)   # h_x != h_y as well as nx != ny
+    tr = remap(jn, jn.V.transpose(0, 2, 1), lambda z, y, x: (z * jn.nx + x) * jn.ny + y,
+               nx=jn.ny, ny=jn.nx, hx=jn.hy, hy=jn.hx)
+    for E in (jn.e_fermi - 0.04, jn.e_fermi + 0.02):
+        a, b = transport.solve(jn, E), transport.solve(tr, E)
+        assert a.n_open == b.n_open and a.n_open > 1
+        assert abs(a.G - b.G) < 1e-9
+        # the channels pair up: the same set of per-channel transmissions
+        assert np.allclose(np.sort(a.T.sum(axis=0)), np.sort(b.T.sum(axis=0)), atol=1e-9)
+
+
+@pytest.mark.parametrize("sy,sx", [(1, 3), (5, 2)])
+def test_lateral_translation_same_t_and_r(sy, sx):
+    jn = junction(nx=8, ny=6, nz=18)
+    sh = remap(jn, np.roll(jn.V, (sy, sx), axis=(1, 2)),
+               lambda z, y, x: (z * jn.ny + (y + sy) % jn.ny) * jn.nx + (x + sx) % jn.nx)
+    E = jn.e_fermi - 0.01
+    a, b = transport.solve(jn, E), transport.solve(sh, E)
+    assert np.array_equal(a.open_modes, b.open_modes)
+    assert np.max(np.abs(a.T - b.T)) < 1e-9 and np.max(np.abs(a.R - b.R)) < 1e-9
+
+
+@pytest.mark.parametrize("nf", [1, 4])
+def test_mirror_image_swaps_the_electrodes(nf):
+    jn = junction(nx=8, ny=6, nz=18, nf=nf)
+    mi = remap(jn, jn.V[::-1], lambda z, y, x: ((jn.nz - 1 - z) * jn.ny + y) * jn.nx + x)
+    E = jn.e_fermi + 0.01
+    right = transport.solve(jn, E, side="R")
+    left_of_mirror = transport.solve(mi, E, side="L")
+    assert np.array_equal(right.open_modes, left_of_mirror.open_modes) and right.n_open > 1
+    assert np.max(np.abs(right.T - left_of_mirror.T)) < 1e-9
+    assert np.max(np.abs(right.R - left_of_mirror.R)) < 1e-9
+    # the junction has no mirror symmetry of its own: the two sides reflect differently
+    assert np.max(np.abs(transport.solve(jn, E, side="L").R - right.R)) > 1e-6
