@@ -7,7 +7,10 @@ side agrees with the FP64 oracle to the 1e-6 G_0 bar.
 * the mirror image z -> -z: incidence from the left of the mirror = from the right of
   the original;
 * the lateral supercell: G_super(kappa = 0) = G(0) + G(pi / L_x) of the original cell,
-  the latter through the library's Bloch-vector solve.
+  the latter through the library's Bloch-vector solve;
+* on large planes, GPU against GPU (no oracle at these sizes): a translation of a
+  128 x 128 cell (on-chip CTA-pair transforms) and the transposition of a 128 x 64 cell
+  (two-pass global-memory transforms).
 """
 import math
 
@@ -100,3 +103,34 @@ def test_supercell_folds_two_bloch_vectors_on_gpu():
     assert abs(gpi.G[0] - gpi.G[1]) < TOL        # pi / L_x and -pi / L_x: the same waves
     assert abs(gs.G[0] - (g0.G[0] + gpi.G[0])) < 2 * TOL
     assert abs(gs.G[0] - transport.solve(sup, E[0]).G) < TOL
+
+
+def large_junction(nx, ny):
+    import iobm_synth as S
+    return S.small_wire(nx=nx, ny=ny, nz=20, h=0.3, natom=1, depth=0.4, width=1.0, rs=6.0,
+                        kb_kinds=S.SP, nf=4, seed=9, kb_radius=1.4, kb_width=0.6)
+
+
+def test_large_plane_translation_on_gpu():
+    # 128 x 128 planes: the self-energy and the free propagator transform on chip in CTA
+    # pairs; a lateral translation must leave T and R unchanged entry by entry
+    jn = large_junction(128, 128)
+    sy, sx = 37, 91
+    sh = TS.remap(jn, np.roll(jn.V, (sy, sx), axis=(1, 2)),
+                  lambda z, y, x: (z * jn.ny + (y + sy) % jn.ny) * jn.nx + (x + sx) % jn.nx)
+    E = [jn.e_fermi]
+    a, b = gpu_solve(jn, E), gpu_solve(sh, E)
+    assert a.nrhs > 1 and np.array_equal(a.channel, b.channel)
+    assert np.max(np.abs(a.T - b.T)) < TOL and np.max(np.abs(a.R - b.R)) < TOL
+
+
+def test_large_plane_transposition_on_gpu():
+    # 128 x 64 planes (above 4096 points: the two-pass global-memory transforms) and
+    # their 64 x 128 transpose: the same conductance
+    jn = large_junction(128, 64)
+    tr = TS.remap(jn, jn.V.transpose(0, 2, 1), lambda z, y, x: (z * jn.nx + x) * jn.ny + y,
+                  nx=jn.ny, ny=jn.nx, hx=jn.hy, hy=jn.hx)
+    E = [jn.e_fermi]
+    a, b = gpu_solve(jn, E), gpu_solve(tr, E)
+    assert a.n_open[0] == b.n_open[0] > 1
+    assert abs(a.G[0] - b.G[0]) < TOL
