@@ -3,7 +3,8 @@
 of test_oracle_symmetries then fails.  The slips are the kind an implementation of
 Eqs. 8, 19 and the N_f end planes of Eq. 7 can make: a transposed lateral operand, a
 dropped Bloch vector in the modes, the phases or the wrapped couplings, an end plane
-taken in the wrong order or one plane in."""
+taken in the wrong order or one plane in, a projected amplitude with the right modulus
+and the wrong phase (which current conservation cannot see)."""
 import numpy as np
 import pytest
 
@@ -15,7 +16,8 @@ import test_oracle_symmetries as TS
 PINS = [("supercell", TS.test_supercell_folds_two_bloch_vectors, ()),
         ("transpose", TS.test_transposed_cell_same_conductance, ()),
         ("translate", TS.test_lateral_translation_same_t_and_r, (1, 3)),
-        ("mirror", TS.test_mirror_image_swaps_the_electrodes, (4,))]
+        ("mirror", TS.test_mirror_image_swaps_the_electrodes, (4,)),
+        ("unitarity", TS.test_scattering_matrix_unitary, (4, (0.0, 0.0)))]
 
 _mode_data = M.mode_data
 
@@ -62,6 +64,19 @@ def right_planes_one_in(jn, side):
     return jn.nz - 2 - np.arange(jn.nf) if side == "R" else np.arange(jn.nf)   # slip: shifted
 
 
+_project = T.project
+
+
+def project_conj_r(jn, md, psi, m_in, side):
+    t, r = _project(jn, md, psi, m_in, side)
+    return t, np.conj(r)                                         # slip: |r| right, phase wrong
+
+
+def project_conj_t(jn, md, psi, m_in, side):
+    t, r = _project(jn, md, psi, m_in, side)
+    return np.conj(t), r                                         # slip: |t| right, phase wrong
+
+
 PLANTS = {
     "lateral phase G_y from n_x h_x": [(M, "lateral_phase", phase_gy_from_x),
                                        (O, "lateral_phase", phase_gy_from_x),
@@ -78,6 +93,8 @@ PLANTS = {
                                         (T, "end_planes", right_planes_in_depth_order)],
     "right end planes one plane in": [(O, "end_planes", right_planes_one_in),
                                       (T, "end_planes", right_planes_one_in)],
+    "reflection amplitudes conjugated": [(T, "project", project_conj_r)],
+    "transmission amplitudes conjugated": [(T, "project", project_conj_t)],
 }
 
 

@@ -10,7 +10,13 @@ indexing, Bloch phases, end-plane handling or flux normalisation would break.
 * a lateral translation by whole grid steps multiplies each mode by a phase: T and R
   unchanged entry by entry;
 * the mirror image z -> -z swaps the electrodes: T^{L->R} of the mirrored junction is
-  T^{R->L} of the original, entry by entry.
+  T^{R->L} of the original, entry by entry;
+* unitarity of the flux-normalised scattering matrix S = [[r, t'], [t, r']] (left- and
+  right-incident amplitudes scaled by sqrt(v_out / v_in)): S^H S = I, off-diagonal
+  entries included, at kappa = 0 and at a Bloch vector kappa (both sides at the same
+  kappa).  Current conservation T + R = 1 is its diagonal; the rest fixes the phases
+  of the projected amplitudes (Eq. 6, Eq. 19) up to the diagonal phase conventions,
+  which leave S unitary.
 
 The potential is a wire of wells with a seeded random perturbation (no symmetry of
 its own), with s/p Kleinman-Bylander projectors.
@@ -104,3 +110,22 @@ def test_mirror_image_swaps_the_electrodes(nf):
     assert np.max(np.abs(right.R - left_of_mirror.R)) < 1e-9
     # the junction has no mirror symmetry of its own: the two sides reflect differently
     assert np.max(np.abs(transport.solve(jn, E, side="L").R - right.R)) > 1e-6
+
+
+def scattering_matrix(jn, E, kappa=(0.0, 0.0)):
+    L = transport.solve(jn, E, side="L", kappa=kappa)
+    R = transport.solve(jn, E, side="R", kappa=kappa)
+    f = np.sqrt(L.vel[:, None] / L.vel[None, :])
+    return np.block([[L.r * f, R.t * f], [L.t * f, R.r * f]])
+
+
+@pytest.mark.parametrize("nf", [1, 4])
+@pytest.mark.parametrize("fk", [(0.0, 0.0), (0.37, -0.52)])
+def test_scattering_matrix_unitary(nf, fk):
+    jn = junction(nx=8, ny=6, nz=18, nf=nf)
+    k = (fk[0] * math.pi / (jn.nx * jn.hx), fk[1] * math.pi / (jn.ny * jn.hy))
+    for E in (jn.e_fermi - 0.03, jn.e_fermi + 0.01):
+        S_ = scattering_matrix(jn, E, k)
+        n2 = S_.shape[0]
+        assert n2 >= 4
+        assert np.max(np.abs(S_.conj().T @ S_ - np.eye(n2))) < 1e-10
