@@ -57,8 +57,20 @@ std::vector<double> fd_weights(int nf) {
     return w;
 }
 
-// roots of sum_k a[k] u^k (real coefficients, a.back() != 0)
-static std::vector<cd> poly_roots(const std::vector<double>& a) {
+// a / b by the textbook formula: the library operator guards against overflow by
+// scaling, which the moderate operands of the root finder never need
+static inline cd cdiv(cd a, cd b) {
+    const double d = b.real() * b.real() + b.imag() * b.imag();
+    return cd((a.real() * b.real() + a.imag() * b.imag()) / d,
+              (a.imag() * b.real() - a.real() * b.imag()) / d);
+}
+
+// Roots of sum_k a[k] u^k (real coefficients, a.back() != 0) by the Aberth-Ehrlich
+// simultaneous iteration, then a Newton polish on the same polynomial.  guess
+// (may be null): starting points, e.g. the roots of a nearby polynomial; if they
+// do not converge within a few dozen steps the iteration restarts from points on
+// a circle inside the Cauchy bound.
+static std::vector<cd> poly_roots(const std::vector<double>& a, const std::vector<cd>* guess) {
     const int n = (int)a.size() - 1;
     std::vector<cd> z(n);
     if (n == 1) {
@@ -67,10 +79,6 @@ static std::vector<cd> poly_roots(const std::vector<double>& a) {
     }
     std::vector<double> c(a.size());
     for (int k = 0; k <= n; ++k) c[k] = a[k] / a[n];
-    double R = 0.0;
-    for (int k = 0; k < n; ++k) R = std::max(R, std::fabs(c[k]));
-    R = 1.0 + R;   // Cauchy bound
-    for (int k = 0; k < n; ++k) z[k] = std::polar(0.7 * R, 2.0 * M_PI * k / n + 0.4);
     auto eval = [&](cd x, cd& p, cd& dp) {
         p = cd(1.0, 0.0);
         dp = cd(0.0, 0.0);
@@ -79,30 +87,55 @@ static std::vector<cd> poly_roots(const std::vector<double>& a) {
             p = p * x + c[k];
         }
     };
-    for (int it = 0; it < 80; ++it) {
-        double maxstep = 0.0;
+    auto aberth = [&](int max_it) {
+        for (int it = 0; it < max_it; ++it) {
+            double maxstep = 0.0;
+            for (int k = 0; k < n; ++k) {
+                cd p, dp;
+                eval(z[k], p, dp);
+                if (p == cd(0.0, 0.0)) continue;
+                const cd ratio = cdiv(p, dp);
+                cd s(0.0, 0.0);
+                for (int j = 0; j < n; ++j)
+                    if (j != k) s += cdiv(1.0, z[k] - z[j]);
+                const cd w = cdiv(ratio, 1.0 - ratio * s);
+                z[k] -= w;
+                maxstep = std::max(maxstep, std::abs(w) / std::max(1.0, std::abs(z[k])));
+            }
+            if (!(maxstep >= 1e-13)) return maxstep == maxstep;   // converged (not NaN)
+        }
+        return false;
+    };
+    auto polish = [&]() {   // Newton steps on the same polynomial
         for (int k = 0; k < n; ++k) {
-            cd p, dp;
-            eval(z[k], p, dp);
-            if (p == cd(0.0, 0.0)) continue;
-            const cd ratio = p / dp;
-            cd s(0.0, 0.0);
-            for (int j = 0; j < n; ++j)
-                if (j != k) s += 1.0 / (z[k] - z[j]);
-            const cd w = ratio / (1.0 - ratio * s);
-            z[k] -= w;
-            maxstep = std::max(maxstep, std::abs(w) / std::max(1.0, std::abs(z[k])));
+            for (int it = 0; it < 3; ++it) {
+                cd p, dp;
+                eval(z[k], p, dp);
+                if (dp == cd(0.0, 0.0)) break;
+                z[k] -= p / dp;
+            }
         }
-        if (maxstep < 1e-13) break;   // the Newton polish below finishes the digits
-    }
-    for (int k = 0; k < n; ++k) {   // Newton polish on the same polynomial
-        for (int it = 0; it < 3; ++it) {
-            cd p, dp;
-            eval(z[k], p, dp);
-            if (dp == cd(0.0, 0.0)) break;
-            z[k] -= p / dp;
+    };
+    auto distinct = [&](double tol) {
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < k; ++j)
+                if (!(std::abs(z[k] - z[j]) > tol * std::max(1.0, std::abs(z[k])))) return false;
+        return true;
+    };
+    if (guess && (int)guess->size() == n) {
+        z = *guess;
+        if (distinct(1e-12) && aberth(40)) {
+            polish();
+            // two starting points drawn to one root would leave another root unfound
+            if (distinct(1e-10)) return z;
         }
     }
+    double R = 0.0;
+    for (int k = 0; k < n; ++k) R = std::max(R, std::fabs(c[k]));
+    R = 1.0 + R;   // Cauchy bound
+    for (int k = 0; k < n; ++k) z[k] = std::polar(0.7 * R, 2.0 * M_PI * k / n + 0.4);
+    aberth(80);
+    polish();
     return z;
 }
 
@@ -143,7 +176,7 @@ bool cinv_small(cd* A, int n) {
             std::swap(A[c * n + j], A[piv * n + j]);
             std::swap(I[c * n + j], I[piv * n + j]);
         }
-        const cd inv = 1.0 / A[c * n + c];
+        const cd inv = cdiv(1.0, A[c * n + c]);
         for (int j = 0; j < n; ++j) {
             A[c * n + j] *= inv;
             I[c * n + j] *= inv;
@@ -165,7 +198,7 @@ bool cinv_small(cd* A, int n) {
 cd ipow(cd x, int n) {
     cd r(1.0, 0.0);
     if (n < 0) {
-        x = 1.0 / x;
+        x = cdiv(1.0, x);
         n = -n;
     }
     for (int i = 0; i < n; ++i) r *= x;
@@ -175,14 +208,17 @@ cd ipow(cd x, int n) {
 // Roots, self-energy, preconditioner factors, projection row and source of
 // one lateral mode with E - eps_perp = dE.  Returns 0 or 9 (more than one
 // propagating root / singular block).
+// roots: in, the u-roots of a nearby mode as starting points (may be empty); out,
+// this mode's u-roots.
 int solve_mode(double dE, int nf, double hz, const std::vector<double>& w,
                const std::vector<std::vector<double>>& tc, const double* K, bool want_sigma,
-               ModeSolution& m, std::string& msg) {
+               ModeSolution& m, std::string& msg, std::vector<cd>& roots) {
     std::vector<double> a(nf + 1, 0.0);
     a[0] = 2.0 * hz * hz * dE + w[0];
     for (int n = 1; n <= nf; ++n)
         for (int k = 0; k <= n; ++k) a[k] += 2.0 * w[n] * tc[n][k];
-    const std::vector<cd> us = poly_roots(a);
+    const std::vector<cd> us = poly_roots(a, roots.empty() ? nullptr : &roots);
+    roots = us;
     cd lam[kMaxNfHost];
     int prop = -1;
     for (int j = 0; j < nf; ++j) {
@@ -330,6 +366,7 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
     std::sort(uniq.begin(), uniq.end());
     uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
     std::vector<ModeSolution> sol(uniq.size());
+    std::vector<cd> roots;   // the previous (nearest smaller) eps_perp's roots start the next
     for (size_t u = 0; u < uniq.size(); ++u) {
         if (std::fabs(E - uniq[u]) < 1e-9 || std::fabs(E - uniq[u] - band_top) < 1e-9) {
             std::ostringstream os;
@@ -338,7 +375,7 @@ int build_mode_tables(int nx, int ny, double hx, double hy, double hz, int nf, d
             msg = os.str();
             return 2;
         }
-        const int rc = solve_mode(E - uniq[u], nf, hz, w, tc, K, want_sigma, sol[u], msg);
+        const int rc = solve_mode(E - uniq[u], nf, hz, w, tc, K, want_sigma, sol[u], msg, roots);
         if (rc) return rc;
     }
     for (int iy = 0; iy < ny; ++iy) {
