@@ -1,23 +1,30 @@
-"""The symmetry pins catch plausible mistakes: each test plants one slip in the oracle
+"""The oracle's pins catch plausible mistakes: each test plants one slip in the oracle
 (a patched copy of one of its functions, on the CPU) and checks that at least one pin
-of test_oracle_symmetries then fails.  The slips are the kind an implementation of
+then fails — the symmetry pins of test_oracle_symmetries, or the central-difference
+gradient at a generic Bloch vector of test_oracle_bloch (at kappa = pi / L_x, the
+supercell's second fold, A(kappa) is complex symmetric, so a missing transposition of
+the adjoint solve shows only at a generic kappa).  The slips are the kind an implementation of
 Eqs. 8, 19 and the N_f end planes of Eq. 7 can make: a transposed lateral operand, a
 dropped Bloch vector in the modes, the phases or the wrapped couplings, an end plane
 taken in the wrong order or one plane in, a projected amplitude with the right modulus
-and the wrong phase (which current conservation cannot see)."""
+and the wrong phase (which current conservation cannot see), an adjoint solve that
+treats A(kappa) as complex symmetric."""
 import numpy as np
 import pytest
 
 import oracle.modes as M
 import oracle.operator as O
 import oracle.transport as T
+import test_oracle_bloch as TB
 import test_oracle_symmetries as TS
 
 PINS = [("supercell", TS.test_supercell_folds_two_bloch_vectors, ()),
         ("transpose", TS.test_transposed_cell_same_conductance, ()),
         ("translate", TS.test_lateral_translation_same_t_and_r, (1, 3)),
         ("mirror", TS.test_mirror_image_swaps_the_electrodes, (4,)),
-        ("unitarity", TS.test_scattering_matrix_unitary, (4, (0.0, 0.0)))]
+        ("unitarity", TS.test_scattering_matrix_unitary, (4, (0.0, 0.0))),
+        ("supercell gradient", TS.test_supercell_gradient_folds_two_bloch_vectors, ()),
+        ("gradient at kappa", TB.test_gradient_at_kappa_matches_finite_differences, ())]
 
 _mode_data = M.mode_data
 
@@ -77,6 +84,25 @@ def project_conj_t(jn, md, psi, m_in, side):
     return np.conj(t), r                                         # slip: |t| right, phase wrong
 
 
+def grad_adjoint_untransposed(jn, E, sol=None, kappa=(0.0, 0.0)):
+    # slip: the adjoint waves solved with A instead of A^T, although A(kappa) is not
+    # complex symmetric at kappa != 0
+    import scipy.sparse.linalg as spla
+    if sol is None:
+        sol = T.solve(jn, E, kappa=kappa)
+    md = sol.md
+    lu = spla.splu(T.assemble_augmented(jn, E, md))
+    nproj = len(jn.projectors)
+    g = np.zeros((jn.nz, jn.ny, jn.nx))
+    for o, m_out in enumerate(sol.open_modes):
+        wv = T.exit_functional(jn, md, m_out, sol.side).reshape(-1)
+        lam = lu.solve(np.concatenate([wv, np.zeros(nproj, np.complex128)]))[: jn.npts]
+        lam = lam.reshape(jn.nz, jn.ny, jn.nx)
+        for i in range(sol.psi.shape[0]):
+            g += np.real(2.0 * sol.vel[o] / sol.vel[i] * np.conj(sol.t[o, i]) * lam * sol.psi[i])
+    return g
+
+
 PLANTS = {
     "lateral phase G_y from n_x h_x": [(M, "lateral_phase", phase_gy_from_x),
                                        (O, "lateral_phase", phase_gy_from_x),
@@ -95,6 +121,7 @@ PLANTS = {
                                       (T, "end_planes", right_planes_one_in)],
     "reflection amplitudes conjugated": [(T, "project", project_conj_r)],
     "transmission amplitudes conjugated": [(T, "project", project_conj_t)],
+    "adjoint solve untransposed at kappa": [(T, "grad_V", grad_adjoint_untransposed)],
 }
 
 
@@ -108,4 +135,5 @@ def test_planted_slip_fails_a_symmetry_pin(plant, monkeypatch):
             pin(*args)
         except AssertionError:
             failed.append(name)
-    assert failed, f"'{plant}' passes every symmetry pin"
+            break   # one failing pin shows the slip
+    assert failed, f"'{plant}' passes every pin"

@@ -11,6 +11,10 @@ indexing, Bloch phases, end-plane handling or flux normalisation would break.
   unchanged entry by entry;
 * the mirror image z -> -z swaps the electrodes: T^{L->R} of the mirrored junction is
   T^{R->L} of the original, entry by entry;
+* the supercell fold of the gradient: a perturbation with the original cell's period
+  changes both folded problems, and the supercell's gradient is the same on both copies
+  of the cell, so 2 dG_super/dV(r) = dG(0)/dV(r) + dG(pi / L_x)/dV(r) on each copy —
+  the adjoint gradient at kappa != 0 (transposed solve) against the periodic one;
 * unitarity of the flux-normalised scattering matrix S = [[r, t'], [t, r']] (left- and
   right-incident amplitudes scaled by sqrt(v_out / v_in)): S^H S = I, off-diagonal
   entries included, at kappa = 0 and at a Bloch vector kappa (both sides at the same
@@ -54,8 +58,8 @@ def remap(jn, V, f, **grid):
     return jn.copy_with(V=np.ascontiguousarray(V), projectors=projs, **grid)
 
 
-def test_supercell_folds_two_bloch_vectors():
-    jn = junction(nx=6, ny=6, nz=16, h=0.65)
+def supercell_x2(jn):
+    """The cell doubled along x: V and every projector repeated in the second copy."""
     nx, ny = jn.nx, jn.ny
     projs = []
     for shift in (0, nx):   # two copies of every projector, one per original cell
@@ -64,7 +68,13 @@ def test_supercell_folds_two_bloch_vectors():
             y, x = np.divmod(rem, nx)
             projs.append(S.Projector(idx=((z * ny + y) * 2 * nx + x + shift).astype(np.int32),
                                      val=p.val, coupling=p.coupling, atom=p.atom))
-    sup = jn.copy_with(nx=2 * nx, V=np.concatenate([jn.V, jn.V], axis=2), projectors=projs)
+    return jn.copy_with(nx=2 * nx, V=np.concatenate([jn.V, jn.V], axis=2), projectors=projs)
+
+
+def test_supercell_folds_two_bloch_vectors():
+    jn = junction(nx=6, ny=6, nz=16, h=0.65)
+    nx = jn.nx
+    sup = supercell_x2(jn)
     for E in (jn.e_fermi - 0.05, jn.e_fermi + 0.03):
         g0 = transport.solve(jn, E)
         gpi = transport.solve(jn, E, kappa=(math.pi / (nx * jn.hx), 0.0))
@@ -72,6 +82,19 @@ def test_supercell_folds_two_bloch_vectors():
         assert gs.n_open == g0.n_open + gpi.n_open
         assert g0.n_open > 0 and gpi.n_open > 0
         assert abs(gs.G - (g0.G + gpi.G)) < 1e-9, (gs.G, g0.G, gpi.G)
+
+
+def test_supercell_gradient_folds_two_bloch_vectors():
+    jn = junction(nx=6, ny=6, nz=16, h=0.65)
+    nx = jn.nx
+    E = jn.e_fermi - 0.05
+    g0 = transport.grad_V(jn, E)
+    gpi = transport.grad_V(jn, E, kappa=(math.pi / (nx * jn.hx), 0.0))
+    gs = transport.grad_V(supercell_x2(jn), E)
+    scale = np.max(np.abs(g0 + gpi))
+    assert scale > 0
+    assert np.max(np.abs(gs[:, :, :nx] - gs[:, :, nx:])) < 1e-10 * scale
+    assert np.max(np.abs(2.0 * gs[:, :, :nx] - (g0 + gpi))) < 1e-10 * scale
 
 
 def test_transposed_cell_same_conductance():
