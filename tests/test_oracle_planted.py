@@ -8,7 +8,7 @@ Eqs. 8, 19 and the N_f end planes of Eq. 7 can make: a transposed lateral operan
 dropped Bloch vector in the modes, the phases or the wrapped couplings, an end plane
 taken in the wrong order or one plane in, a projected amplitude with the right modulus
 and the wrong phase (which current conservation cannot see), an adjoint solve that
-treats A(kappa) as complex symmetric."""
+treats A(kappa) as complex symmetric, a wrong power or axis of the grid spacing."""
 import numpy as np
 import pytest
 
@@ -24,7 +24,9 @@ PINS = [("supercell", TS.test_supercell_folds_two_bloch_vectors, ()),
         ("mirror", TS.test_mirror_image_swaps_the_electrodes, (4,)),
         ("unitarity", TS.test_scattering_matrix_unitary, (4, (0.0, 0.0))),
         ("supercell gradient", TS.test_supercell_gradient_folds_two_bloch_vectors, ()),
-        ("gradient at kappa", TB.test_gradient_at_kappa_matches_finite_differences, ())]
+        ("gradient at kappa", TB.test_gradient_at_kappa_matches_finite_differences, ()),
+        ("scaling", TS.test_dimensional_scaling, (4,)),
+        ("flat anisotropic", TS.test_flat_potential_anisotropic_grid, (4,))]
 
 _mode_data = M.mode_data
 
@@ -103,6 +105,23 @@ def grad_adjoint_untransposed(jn, E, sol=None, kappa=(0.0, 0.0)):
     return g
 
 
+_kb_factors = O.kb_factors
+_coupling_matrix = M.coupling_matrix
+
+
+def kb_volume_without_hz(jn):
+    P, coupling, dvol = _kb_factors(jn)
+    return P, coupling, jn.hx * jn.hy                            # slip: h_z dropped
+
+
+def coupling_one_power_of_hz(w, hz):
+    return _coupling_matrix(w, hz) * hz                          # slip: w / (2 h_z)
+
+
+def modes_hz_from_hx(nx, ny, hx, hy, hz, nf, E, check_threshold=True, kappa=(0.0, 0.0)):
+    return _mode_data(nx, ny, hx, hy, hx, nf, E, check_threshold, kappa)   # slip: h_z <- h_x
+
+
 PLANTS = {
     "lateral phase G_y from n_x h_x": [(M, "lateral_phase", phase_gy_from_x),
                                        (O, "lateral_phase", phase_gy_from_x),
@@ -122,6 +141,11 @@ PLANTS = {
     "reflection amplitudes conjugated": [(T, "project", project_conj_r)],
     "transmission amplitudes conjugated": [(T, "project", project_conj_t)],
     "adjoint solve untransposed at kappa": [(T, "grad_V", grad_adjoint_untransposed)],
+    "KB volume element without h_z": [(O, "kb_factors", kb_volume_without_hz),
+                                      (T, "kb_factors", kb_volume_without_hz)],
+    "self-energy coupling over h_z": [(M, "coupling_matrix", coupling_one_power_of_hz)],
+    "electrode modes with h_x for h_z": [(M, "mode_data", modes_hz_from_hx),
+                                         (T, "mode_data", modes_hz_from_hx)],
 }
 
 

@@ -15,6 +15,12 @@ indexing, Bloch phases, end-plane handling or flux normalisation would break.
   changes both folded problems, and the supercell's gradient is the same on both copies
   of the cell, so 2 dG_super/dV(r) = dG(0)/dV(r) + dG(pi / L_x)/dV(r) on each copy —
   the adjoint gradient at kappa != 0 (transposed solve) against the periodic one;
+* dimensional scaling: every spacing times lambda, E and V over lambda^2, the projector
+  couplings over lambda^5 (the h^3 of <p|psi> gives lambda^3) scale the whole discrete
+  equation by 1 / lambda^2: T and R unchanged — every power of h in the FD weights, the
+  self-energy coupling, the KB term and the velocities;
+* a flat potential on an anisotropic grid (h_x, h_y, h_z all different, nx != ny):
+  T = I, R = 0 — the electrodes' z-modes and the interior's z-couplings use the same h_z;
 * unitarity of the flux-normalised scattering matrix S = [[r, t'], [t, r']] (left- and
   right-incident amplitudes scaled by sqrt(v_out / v_in)): S^H S = I, off-diagonal
   entries included, at kappa = 0 and at a Bloch vector kappa (both sides at the same
@@ -152,3 +158,27 @@ def test_scattering_matrix_unitary(nf, fk):
         n2 = S_.shape[0]
         assert n2 >= 4
         assert np.max(np.abs(S_.conj().T @ S_ - np.eye(n2))) < 1e-10
+
+
+@pytest.mark.parametrize("nf", [1, 4])
+def test_dimensional_scaling(nf):
+    jn = junction(nx=8, ny=6, nz=18, nf=nf).copy_with(hy=0.55, hz=0.5)
+    lam = 1.37
+    projs = [S.Projector(idx=p.idx, val=p.val, coupling=p.coupling / lam ** 5, atom=p.atom)
+             for p in jn.projectors]
+    sc = jn.copy_with(hx=jn.hx * lam, hy=jn.hy * lam, hz=jn.hz * lam, V=jn.V / lam ** 2,
+                      projectors=projs)
+    E = jn.e_fermi - 0.02
+    a, b = transport.solve(jn, E), transport.solve(sc, E / lam ** 2)
+    assert a.n_open == b.n_open and a.n_open > 1
+    assert np.max(np.abs(a.T - b.T)) < 1e-10 and np.max(np.abs(a.R - b.R)) < 1e-10
+
+
+@pytest.mark.parametrize("nf", [1, 4])
+def test_flat_potential_anisotropic_grid(nf):
+    jn = S.small_wire(nx=10, ny=9, nz=16, h=0.55, natom=1, depth=0.0, rs=1.4, nf=nf)
+    jn = jn.copy_with(hy=0.62, hz=0.47, V=np.zeros_like(jn.V))
+    sol = transport.solve(jn, jn.e_fermi)
+    assert sol.n_open >= 3
+    assert np.max(np.abs(sol.T - np.eye(sol.n_open))) < 1e-10
+    assert np.max(np.abs(sol.R)) < 1e-10
